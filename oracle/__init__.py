@@ -1,0 +1,19 @@
+"""Plain CPU FP64 oracle for the MERA energy/gradient and the Riemannian step.
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct
+restatement of the method (Hauru, Van Damme, Haegeman, "Riemannian
+optimization of isometric tensor networks", arXiv:2007.03638) that the CUDA
+library is checked against.  Only the test-suite, ``__graft_entry__.smoke()``
+and ``bench.py``'s CPU-baseline / reference leg may import it; the product
+path (``paper_2007_03638_gb300``) never does, and the two share no code.
+
+Modules
+-------
+``mera``      binary MERA networks (ascending/descending superoperators, Sec. 4),
+              the scale-invariant fixed point and environment series (App. B),
+              partial derivatives D_v (Sec. 4).
+``geometry``  tangent projection, exponential retraction, vector transport,
+              metric, Hilbert-space preconditioner (Sec. 2, Sec. 3).
+``optim``     Hager-Zhang line search, L-BFGS two-loop and nonlinear CG on the
+              product manifold (Sec. 3).
+"""

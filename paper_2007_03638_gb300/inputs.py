@@ -1,0 +1,134 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the tests.
+
+This module holds no arithmetic of the optimisation method itself: it only
+builds the problem data (local Hamiltonian terms on Pauli matrices, blocked
+into three-site terms) and seeded random starting tensors (QR of Gaussian
+matrices).  Both implementations receive the same bytes from here.
+
+Conventions
+-----------
+* A 3-site operator ``o`` on sites of dimension ``d`` is a ``(d**3, d**3)``
+  matrix ``o[f0 f1 f2, g0 g1 g2] = <f0 f1 f2| o |g0 g1 g2>`` (row-major, left
+  site most significant).
+* A disentangler ``u`` of a layer with fine dimension ``c`` is a ``(c*c, c*c)``
+  unitary ``u[f_a f_b, x_a x_b]`` (rows: fine/output legs, columns: legs that
+  connect to the isometries above).
+* An isometry ``w`` maps one coarse site (dimension ``c'``) to a pair of fine
+  sites: a ``(c*c, c')`` matrix ``w[x_a x_b, k]`` with ``w^dag w = 1``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PAULI_X = np.array([[0.0, 1.0], [1.0, 0.0]])
+PAULI_Y = np.array([[0.0, -1.0j], [1.0j, 0.0]])
+PAULI_Z = np.array([[1.0, 0.0], [0.0, -1.0]])
+ID2 = np.eye(2)
+
+
+def ising_bond(h: float = 1.0, hx: float = 0.0) -> np.ndarray:
+    """Two-spin term of H = -sum(X X + h Z + hx X) with the one-site fields
+    split evenly over the two bonds that touch a spin (4x4, real)."""
+    t = -np.kron(PAULI_X, PAULI_X)
+    t = t - 0.5 * h * (np.kron(PAULI_Z, ID2) + np.kron(ID2, PAULI_Z))
+    t = t - 0.5 * hx * (np.kron(PAULI_X, ID2) + np.kron(ID2, PAULI_X))
+    return t
+
+
+def xxz_bond(delta: float = 1.0) -> np.ndarray:
+    """Two-spin term X X + Y Y + delta Z Z on Pauli matrices (4x4, real)."""
+    t = np.kron(PAULI_X, PAULI_X) + np.kron(PAULI_Y, PAULI_Y) + delta * np.kron(PAULI_Z, PAULI_Z)
+    return np.real_if_close(t).astype(np.float64)
+
+
+def three_site_unblocked(bond: np.ndarray) -> np.ndarray:
+    """3-site term on spin sites (d=2) whose translates sum to sum_i bond(i,i+1)."""
+    return 0.5 * (np.kron(bond, ID2) + np.kron(ID2, bond))
+
+
+def three_site_blocked(bond: np.ndarray) -> np.ndarray:
+    """3-site term on blocked sites of dimension 4 (spins 2i, 2i+1 form site i).
+
+    The blocked two-site term keeps half of each block's internal bond plus the
+    bond between the blocks; the 3-site term is the average of the two-site
+    term on its left and right pairs.  Translates of the result sum to the spin
+    Hamiltonian, so the energy per blocked site is twice the energy per spin.
+    """
+    id4 = np.eye(4)
+    intra = 0.5 * (np.kron(bond, id4) + np.kron(id4, bond))
+    inter = np.kron(np.kron(ID2, bond), ID2)
+    hb = intra + inter
+    return 0.5 * (np.kron(hb, id4) + np.kron(id4, hb))
+
+
+def layer_dims(d_b: int, chi: int, n_trans: int) -> list[int]:
+    """Bond dimensions chi_0 = d_b, chi_{l+1} = min(chi, chi_l**2); the last
+    entry (index n_trans) is the scale-invariant layer's dimension, forced to chi."""
+    dims = [d_b]
+    for _ in range(n_trans):
+        dims.append(min(chi, dims[-1] ** 2))
+    if dims[-1] != chi:
+        raise ValueError(f"transition layers cannot reach chi={chi} from d_b={d_b}")
+    return dims
+
+
+def _haar_like(rng: np.random.Generator, n: int, p: int, dtype) -> np.ndarray:
+    g = rng.standard_normal((n, p))
+    if np.dtype(dtype).kind == "c":
+        g = g + 1j * rng.standard_normal((n, p))
+    q, r = np.linalg.qr(g)
+    s = np.sign(np.diag(r).real)
+    s[s == 0] = 1.0
+    return (q * s[None, :]).astype(dtype)
+
+
+def random_mera(d_b: int, chi: int, n_trans: int, seed: int, dtype=np.float64):
+    """Seeded starting point: per layer (transition layers, then the
+    scale-invariant one) a unitary u (QR of a square Gaussian) and an isometry w
+    (thin QR of a Gaussian), columns sign-fixed by diag(R)."""
+    rng = np.random.default_rng(seed)
+    dims = layer_dims(d_b, chi, n_trans)
+    us, ws = [], []
+    for l in range(n_trans + 1):
+        c = dims[l]
+        cp = dims[l + 1] if l < n_trans else dims[n_trans]
+        us.append(_haar_like(rng, c * c, c * c, dtype))
+        ws.append(_haar_like(rng, c * c, cp, dtype))
+    return us, ws
+
+
+def product_state_mera(d_b: int, n_trans: int, chi: int | None = None):
+    """u = 1 and w|k> = |k>|0>: a MERA for the product state |0 0 ...>."""
+    chi = d_b if chi is None else chi
+    dims = layer_dims(d_b, chi, n_trans)
+    us, ws = [], []
+    for l in range(n_trans + 1):
+        c = dims[l]
+        cp = dims[l + 1] if l < n_trans else dims[n_trans]
+        us.append(np.eye(c * c))
+        w = np.zeros((c * c, cp))
+        for k in range(min(cp, c)):
+            w[k * c + 0, k] = 1.0
+        ws.append(w)
+    return us, ws
+
+
+def random_tangent_like(rng: np.random.Generator, tensors, dtype=np.float64):
+    out = []
+    for t in tensors:
+        g = rng.standard_normal(t.shape)
+        if np.dtype(dtype).kind == "c":
+            g = g + 1j * rng.standard_normal(t.shape)
+        out.append(g.astype(dtype))
+    return out
+
+
+def exact_ising_energy_per_spin(h: float = 1.0, n: int = 200000) -> float:
+    """Ground-state energy per spin of -sum(X X + h Z) (free fermions):
+    -(1/pi) int_0^pi sqrt(1 + h^2 + 2 h cos k) dk, by the midpoint rule."""
+    k = (np.arange(n) + 0.5) * np.pi / n
+    return float(-np.mean(np.sqrt(1.0 + h * h + 2.0 * h * np.cos(k))))
+
+
+EXACT_ISING_CRITICAL = -4.0 / np.pi
+EXACT_XXZ_DELTA1 = 1.0 - 4.0 * np.log(2.0)
