@@ -1,0 +1,196 @@
+/*
+ * mera.h -- C ABI of libmera: energy/gradient and Riemannian optimisation of
+ * a scale-invariant binary MERA on one GB300 (sm_103a).
+ *
+ * Method: Hauru, Van Damme, Haegeman, "Riemannian optimization of isometric
+ * tensor networks" (arXiv:2007.03638).  Section numbers and equation labels
+ * below refer to that paper.
+ *
+ * Object model
+ * ------------
+ * A mera_t owns every piece of device state of one optimisation problem: the
+ * tensors (the current point), the Hamiltonian, the ascended operators and
+ * density matrices, the Krylov warm starts of the scale-invariant layer, the
+ * last gradient, the preconditioner's density matrices and the L-BFGS/CG
+ * history.  All work is issued on the CUDA stream given to mera_create.
+ *
+ * Tensor list
+ * -----------
+ * The point is the list [u_0, w_0, u_1, w_1, ..., u_L, w_L] (2*(n_trans+1)
+ * matrices): n_trans transition layers followed by the scale-invariant
+ * layer L.  With layer dimensions chi_0 = d_b, chi_{l+1} = min(chi, chi_l^2)
+ * (and chi_L = chi):
+ *   u_l : (chi_l^2) x (chi_l^2) unitary, row-major, u[f_a f_b, x_a x_b]
+ *         (rows: the fine pair it outputs; columns: the pair of isometry
+ *         outputs it acts on; left leg most significant);
+ *   w_l : (chi_l^2) x (chi_{l+1}) isometry, row-major, w[x_a x_b, k],
+ *         w^dag w = 1 (w_L is chi^2 x chi).
+ * Tangent vectors, partial derivatives and gradients use the same shapes.
+ * mera_tensor_shape() reports them.  Element type: double (MERA_F64) or
+ * interleaved complex double (MERA_C128).
+ *
+ * Pointers
+ * --------
+ * Every data pointer argument may be host or device memory (unified virtual
+ * addressing decides); the library copies in or out on its stream and the
+ * caller keeps ownership.  Calls return after the stream work they need for
+ * their scalar outputs has completed; array outputs are complete when the
+ * call returns.
+ *
+ * Errors
+ * ------
+ * Every int-returning call returns MERA_OK (0) or a negative MERA_ERR_* code;
+ * mera_strerror() names it and mera_last_error() gives the detail of the last
+ * failure on that object.  No call aborts or exits; after an error the object
+ * stays valid (the point is unchanged unless stated otherwise).
+ */
+#ifndef MERA_H
+#define MERA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mera_ctx* mera_t;
+
+enum {
+    MERA_OK = 0,
+    MERA_ERR_ARG = -1,            /* invalid argument / shape / config        */
+    MERA_ERR_OOM = -2,            /* device allocation failed                 */
+    MERA_ERR_NONFINITE = -3,      /* NaN/Inf in energy or gradient            */
+    MERA_ERR_NOCONV = -4,         /* Krylov solve or line search not converged*/
+    MERA_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired       */
+    MERA_ERR_NOT_ISOMETRIC = -6,  /* input tensor violates W^dag W = 1        */
+    MERA_ERR_CUDA = -7,           /* CUDA runtime error                       */
+    MERA_ERR_UNSUPPORTED = -8     /* valid request this build cannot serve    */
+};
+
+typedef enum { MERA_F64 = 0, MERA_C128 = 1 } mera_dtype;
+
+/* Arithmetic of the bulk contractions (ascending/descending maps and
+ * environments).  FP64 keeps everything in double; the mixed modes run the
+ * contractions on tensor cores with FP32 accumulation and keep the Krylov
+ * solves, reductions, geometry and line search in FP64. */
+typedef enum { MERA_PREC_FP64 = 0, MERA_PREC_3XTF32 = 1, MERA_PREC_SPLIT_BF16 = 2 } mera_prec;
+
+typedef struct {
+    int d_b;           /* bottom site dimension (4: two spins blocked)        */
+    int chi;           /* bond dimension of the scale-invariant layer          */
+    int n_trans;       /* number of transition layers (>= 1)                   */
+    int dtype;         /* mera_dtype                                           */
+    int prec;          /* mera_prec                                            */
+    int w_stiefel;     /* 0: isometries on the Grassmann manifold (Sec. 4),
+                          1: treat them as Stiefel points                      */
+    int precond;       /* 1: Hilbert-space preconditioner (Sec. 3, Sec. 4)     */
+    int krylov_dim;    /* restart length of the scale-invariant Krylov solves  */
+    int krylov_maxiter;/* max matrix-vector products per Krylov solve          */
+    double krylov_tol; /* relative residual target of the Krylov solves        */
+    int recompute_env; /* 1: recompute the ascending intermediates in the
+                          gradient pass instead of keeping them (less memory)  */
+    int lbfgs_m;       /* L-BFGS memory length                                 */
+} mera_config;
+
+/* Fill *cfg with defaults for (d_b, chi, n_trans): F64, FP64 contractions,
+ * Grassmann isometries, preconditioner on, Krylov dim 20, 2000 products,
+ * tol 1e-14, no recomputation, m = 8. */
+void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
+
+/* Create a problem.  h3 is the 3-site Hamiltonian term on bottom sites,
+ * a (d_b^3) x (d_b^3) row-major matrix h[f0 f1 f2, g0 g1 g2] of the config's
+ * element type whose translates sum to H (the cost is the energy per bottom
+ * site, C = Tr(h rho), Sec. 4).  stream: a cudaStream_t (NULL = default
+ * stream).  The tensors start as the identity-disentangler / first-columns
+ * isometry point until mera_set_tensors is called. */
+int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
+int mera_destroy(mera_t m);
+
+/* Number of tensors (2*(n_trans+1)) and the shape of tensor i. */
+int mera_num_tensors(mera_t m);
+int mera_tensor_shape(mera_t m, int i, int64_t* rows, int64_t* cols);
+
+/* Copy the point in / out (arrays in the tensor-list order above).
+ * mera_set_tensors checks W^dag W = 1 to 1e-10 (MERA_ERR_NOT_ISOMETRIC) and
+ * clears the optimiser history. */
+int mera_set_tensors(mera_t m, const void* const* tensors);
+int mera_get_tensors(mera_t m, void* const* tensors);
+
+/* Energy per bottom site C = Tr(h rho) and the Riemannian gradient G at the
+ * current point (Sec. 4 with App. B; G_v is the tangent projection of the
+ * partial derivative D_v = 2 dC/d conj(v), Eqs. stiefel_gradient /
+ * grassmann_gradient).  grad may be NULL; otherwise grad[i] receives G_i.
+ * D (unprojected) is written to deriv[i] if deriv is not NULL.  Also
+ * refreshes the density matrices used by mera_precondition. */
+int mera_energy_grad(mera_t m, double* energy, void* const* grad, void* const* deriv);
+
+/* G = projection of arbitrary D onto the tangent space at the current point. */
+int mera_project(mera_t m, const void* const* D, void* const* G);
+
+/* g(X, Y) = sum_v Re Tr(X_v^dag Y_v)  (Euclidean metric, Sec. 2.2). */
+int mera_inner(mera_t m, const void* const* X, const void* const* Y, double* out);
+
+/* Vector transport along the retraction from the current point (Eq. transport):
+ * Y_i <- exp(alpha Q_{X_i}) Y_i, in place.  Call before mera_retract moves the
+ * point. */
+int mera_transport(mera_t m, const void* const* X, double alpha, void* const* Y);
+
+/* Move the current point along the exponential retraction (Eq. retraction):
+ * W_i <- exp(alpha Q_{X_i}) W_i, followed by re-isometrisation (polar factor).
+ * If Xprime is not NULL it receives dR/dalpha = exp(alpha Q_X) X. */
+int mera_retract(mera_t m, const void* const* X, double alpha, void* const* Xprime);
+
+/* Hilbert-space preconditioner (Eq. preconditioner_solution) with the
+ * density matrices of the last mera_energy_grad and delta_v = |G_v|. */
+int mera_precondition(mera_t m, const void* const* X, void* const* Xt);
+
+typedef struct {
+    int iter;           /* iterations done so far                       */
+    double energy;      /* energy per bottom site after the step         */
+    double gnorm;       /* |G| after the step                            */
+    double alpha;       /* accepted step                                 */
+    int n_evals;        /* energy_grad evaluations in this step          */
+    int ls_ok;          /* 1: Wolfe / approximate Wolfe met              */
+    int krylov_matvecs; /* superoperator applications in this step       */
+} mera_iter_info;
+
+/* One full Riemannian L-BFGS iteration (Sec. 3): two-loop direction with the
+ * preconditioned initial Hessian, Hager-Zhang line search along the
+ * retraction, transport of the history.  The first call evaluates the
+ * gradient at the current point. */
+int mera_lbfgs_step(mera_t m, mera_iter_info* info);
+
+/* One nonlinear conjugate-gradient iteration (Hager-Zhang beta, Sec. 3). */
+int mera_cg_step(mera_t m, mera_iter_info* info);
+
+typedef struct {
+    int method;       /* 0 = L-BFGS, 1 = CG                  */
+    int maxiter;
+    double gtol;      /* stop when |G| < gtol                 */
+} mera_solve_opts;
+
+typedef struct {
+    int iters;
+    int n_evals;
+    double energy;
+    double gnorm;
+    int converged;
+} mera_solve_result;
+
+/* Run iterations until |G| < gtol or maxiter. */
+int mera_solve(mera_t m, const mera_solve_opts* opts, mera_solve_result* res);
+
+/* Device bytes a problem with this config holds (for admission control). */
+size_t mera_footprint_bytes(const mera_config* cfg);
+
+/* Number of kernel launches issued by this object so far. */
+int64_t mera_launch_count(mera_t m);
+
+const char* mera_strerror(int code);
+const char* mera_last_error(mera_t m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MERA_H */

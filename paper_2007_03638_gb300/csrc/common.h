@@ -1,0 +1,127 @@
+// Internal declarations shared by the translation units of libmera.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <stdexcept>
+
+#include "../../include/mera.h"
+
+namespace mera {
+
+// Error carrying a MERA_ERR_* code; thrown inside the library, converted to a
+// return code at the C ABI.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& msg) : std::runtime_error(msg), code(c) {}
+};
+
+#define MERA_CUDA(call)                                                             \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      throw ::mera::Error(_e == cudaErrorMemoryAllocation ? MERA_ERR_OOM : MERA_ERR_CUDA, \
+                          std::string(#call) + ": " + cudaGetErrorString(_e));      \
+    }                                                                               \
+  } while (0)
+
+#define MERA_CHECK_LAUNCH() MERA_CUDA(cudaGetLastError())
+
+// Counts kernel launches issued by the library (reported to callers).
+extern thread_local int64_t* g_launch_counter;
+inline void count_launch(int n = 1) {
+  if (g_launch_counter) *g_launch_counter += n;
+}
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t n) { alloc(n); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t n) {
+    release();
+    if (n == 0) return;
+    MERA_CUDA(cudaMalloc(&p, n));
+    bytes = n;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------- GETT ----
+// C[cm[m] + cn[n]] = alpha * sum_k A[am[m] + ak[k]] * B[bk[k] + bn[n]] + beta * C[..]
+// Each index group is addressed through an int64 offset table, or, when the
+// table pointer is null, through idx * stride.
+struct GettOperand {
+  const int64_t* t0 = nullptr;  // row-group table (M for A/C, K for B)
+  const int64_t* t1 = nullptr;  // column-group table (K for A, N for B/C)
+  int64_t s0 = 0, s1 = 0;       // strides used when a table is null
+};
+struct GettCall {
+  const double* A = nullptr;
+  GettOperand a;
+  const double* B = nullptr;
+  GettOperand b;
+  double* C = nullptr;
+  GettOperand c;
+  int64_t M = 0, N = 0, K = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+void gett_f64(const GettCall& g, cudaStream_t s);
+
+// Plain row-major matrix product C = alpha op(A) op(B) + beta C with
+// op = identity or transpose ('N'/'T'); leading dimensions are row strides.
+void gemm_f64(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha,
+              const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+              double* C, int64_t ldc, cudaStream_t s);
+
+// ---------------------------------------------------------- BLAS-1 etc ----
+// Deterministic reductions: fixed grid, fixed per-thread ranges, two passes.
+struct Reducer {
+  DevBuf partial;    // per-block partial sums
+  DevBuf result;     // device results
+  std::vector<double> host;
+  int nblocks = 0;
+  void init(int max_vectors);
+  // out[i] = sum_j X_i[j] * y[j] for i < k, where X_i = X + i*ldx
+  void dots(const double* X, int64_t ldx, int k, const double* y, int64_t n, cudaStream_t s,
+            double* out_host);
+  double dot(const double* x, const double* y, int64_t n, cudaStream_t s);
+  double trace(const double* a, int64_t n, cudaStream_t s);  // n x n matrix
+};
+void axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s);          // y += a x
+void axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s); // y = a x + b y
+void scal(double a, double* x, int64_t n, cudaStream_t s);
+void fill(double v, double* x, int64_t n, cudaStream_t s);
+void add_identity(double a, double* x, int64_t n, cudaStream_t s);   // x += a * 1 (n x n)
+void symmetrize(double* x, int64_t n, cudaStream_t s);               // x = (x + x^T)/2
+// y = sum_i c_i X_i   (c on device, length k), accumulate if beta==1
+void combine(const double* X, int64_t ldx, int k, const double* c_dev, double* y, int64_t n,
+             double beta, cudaStream_t s);
+void copy(double* dst, const double* src, int64_t n, cudaStream_t s);
+// partial traces of a 3-site operator (dim c per site, row-major)
+void marginal_1site_mid(const double* r, int64_t c, double* out, cudaStream_t s);  // c x c
+void marginal_2site_left(const double* r, int64_t c, double* out, cudaStream_t s); // c^2 x c^2
+int check_finite(const double* x, int64_t n, cudaStream_t s);   // 1 if all finite
+
+// --------------------------------------------------------- small linalg ----
+// Symmetric eigendecomposition of an n x n matrix (in place -> eigenvalues in
+// evals_dev, eigenvectors as columns of V), cyclic parallel Jacobi in one CTA.
+void sym_eig(double* A, double* V, double* evals, int n, cudaStream_t s);
+
+}  // namespace mera

@@ -1,0 +1,123 @@
+// FP64 tensor contraction kernel (GEMM-like tensor-tensor, "GETT").
+//
+// Every pairwise contraction of the MERA networks is a matrix product over
+// three index groups (free legs of A, contracted legs, free legs of B).  The
+// legs of a group need not be adjacent or ordered in memory: each group is
+// addressed through an offset table, so input and output permutations are
+// folded into the loads and stores and no permuted copy of any tensor is
+// ever made.  GB300's FP64 units are the bound of this path (a few DFMA per
+// clock per SM), so the kernel is a plain register-blocked tile: 64x64 C
+// tile, 16-deep K slices staged in shared memory, 4x4 outputs per thread.
+#include "common.h"
+
+namespace mera {
+
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ int64_t off(const int64_t* t, int64_t s, int64_t i) {
+  return t ? t[i] : i * s;
+}
+
+__global__ __launch_bounds__(NT) void gett_f64_kernel(GettCall g) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ int64_t am[BM], bn[BN], cm[BM], cn[BN], ak[BK], bk[BK];
+  const int tid = threadIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int64_t n0 = (int64_t)blockIdx.y * BN;
+  if (tid < BM) {
+    const int64_t m = m0 + tid;
+    am[tid] = m < g.M ? off(g.a.t0, g.a.s0, m) : 0;
+    cm[tid] = m < g.M ? off(g.c.t0, g.c.s0, m) : 0;
+  } else if (tid < BM + BN) {
+    const int j = tid - BM;
+    const int64_t n = n0 + j;
+    bn[j] = n < g.N ? off(g.b.t1, g.b.s1, n) : 0;
+    cn[j] = n < g.N ? off(g.c.t1, g.c.s1, n) : 0;
+  }
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+    __syncthreads();
+    if (tid < BK) {
+      const int64_t k = k0 + tid;
+      ak[tid] = k < g.K ? off(g.a.t1, g.a.s1, k) : 0;
+      bk[tid] = k < g.K ? off(g.b.t0, g.b.s0, k) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = tid; i < BM * BK; i += NT) {
+      const int mm = i % BM, kk = i / BM;
+      const bool ok = (m0 + mm < g.M) && (k0 + kk < g.K);
+      As[kk][mm] = ok ? g.A[am[mm] + ak[kk]] : 0.0;
+    }
+#pragma unroll
+    for (int i = tid; i < BN * BK; i += NT) {
+      const int nn = i % BN, kk = i / BN;
+      const bool ok = (n0 + nn < g.N) && (k0 + kk < g.K);
+      Bs[kk][nn] = ok ? g.B[bk[kk] + bn[nn]] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int mm = ty + 16 * i;
+    if (m0 + mm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nn = tx + 16 * j;
+      if (n0 + nn >= g.N) continue;
+      const int64_t idx = cm[mm] + cn[nn];
+      double v = g.alpha * acc[i][j];
+      if (g.beta != 0.0) v = fma(g.beta, g.C[idx], v);
+      g.C[idx] = v;
+    }
+  }
+}
+}  // namespace
+
+void gett_f64(const GettCall& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return;
+  if (g.K <= 0) {
+    throw Error(MERA_ERR_ARG, "gett_f64: empty contraction");
+  }
+  const int64_t gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
+  if (gy > 65535) throw Error(MERA_ERR_UNSUPPORTED, "gett_f64: N too large for grid");
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  gett_f64_kernel<<<grid, NT, 0, s>>>(g);
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+
+void gemm_f64(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+              int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+              cudaStream_t s) {
+  GettCall g;
+  g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.B = B; g.C = C;
+  // A: op(A)[m,k];  'N': A[m*lda + k], 'T': A[k*lda + m]
+  if (ta == 'N') { g.a.s0 = lda; g.a.s1 = 1; } else { g.a.s0 = 1; g.a.s1 = lda; }
+  if (tb == 'N') { g.b.s0 = ldb; g.b.s1 = 1; } else { g.b.s0 = 1; g.b.s1 = ldb; }
+  g.c.s0 = ldc; g.c.s1 = 1;
+  gett_f64(g, s);
+}
+
+}  // namespace mera

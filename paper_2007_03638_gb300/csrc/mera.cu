@@ -1,0 +1,1320 @@
+// libmera: scale-invariant binary MERA energy/gradient and the Riemannian
+// optimisation step on one GPU (FP64 path).
+//
+//   energy_grad   (Sec. 4, App. B)
+//     up-sweep    h_{l+1} = (A_L + A_R)(h_l)/2 through the transition layers
+//     fixed point rho_S:  (1 - Dbar_S + |b><1|) rho = b, b = 1/chi^3, GMRES
+//     series      x (1 - A') = <h_L|:  x - Abar_S(x) + Tr(x rho_S) 1 = h_L, GMRES
+//     down-sweep  reverse pass of Tr(Abar_l(h_l) rho_{l+1}) per layer gives
+//                 rho_l and the environments; the scale-invariant layer uses
+//                 Tr(Abar_S(x) rho_S)
+//     projection  Eqs. (stiefel_gradient), (grassmann_gradient)
+//   geometry      retraction / transport (Eqs. retraction, transport) with the
+//                 low-rank forms: W exp(alpha W^dag X) for unitaries, sines and
+//                 cosines of the singular values of X for Grassmann tangents;
+//                 polar re-isometrisation by Newton-Schulz
+//   preconditioner Eq. (preconditioner_solution) in the eigenbasis of rho_v
+//   optimiser     L-BFGS two-loop / Hager-Zhang CG, Hager-Zhang line search
+#include "common.h"
+#include "tn.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+
+namespace mera {
+thread_local int64_t* g_launch_counter = nullptr;
+
+namespace {
+
+// ------------------------------------------------------------ kernels -----
+__global__ void vfvt_k(const double* __restrict__ V, const double* __restrict__ f, int n,
+                       double* __restrict__ out) {
+  // out = V diag(f) V^T  (n x n)
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s = fma(V[(int64_t)i * n + k] * f[k], V[(int64_t)j * n + k], s);
+  out[idx] = s;
+}
+
+// out_ij = 2 a_ij / (lt_i + lt_j)
+__global__ void sylvester_scale_k(double* a, const double* __restrict__ lt, int n) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  a[idx] = 2.0 * a[idx] / (lt[i] + lt[j]);
+}
+
+// evals -> function values used by the Grassmann retraction/transport and
+// the preconditioner (kind: 0 cos(a s), 1 sin(a s)/s, 2 (1-cos(a s))/s^2,
+// 3 1/sqrt(l^2+d^2), 4 sqrt(l^2+d^2)); for kinds 0-2 the input is s^2.
+__global__ void spectral_k(const double* __restrict__ ev, int n, int kind, double a, double d,
+                           double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l = ev[i];
+  double r;
+  if (kind <= 2) {
+    const double s = sqrt(fmax(l, 0.0));
+    const double x = a * s;
+    if (kind == 0) {
+      r = cos(x);
+    } else if (kind == 1) {
+      r = (fabs(x) < 1e-4) ? a * (1.0 - x * x / 6.0 + x * x * x * x / 120.0) : sin(x) / s;
+    } else {
+      r = (fabs(x) < 1e-4) ? a * a * (0.5 - x * x / 24.0 + x * x * x * x / 720.0)
+                           : (1.0 - cos(x)) / (s * s);
+    }
+  } else if (kind == 3) {
+    r = 1.0 / sqrt(l * l + d * d);
+  } else {
+    r = sqrt(l * l + d * d);
+  }
+  out[i] = r;
+}
+
+__global__ void add_scaled_identity_dev_k(double* x, int64_t n, const double* scale, double f) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i * n + i] += f * (*scale);
+}
+
+inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+// ===================================================================== ctx ==
+struct Layer {
+  int64_t cf = 0, cc = 0;
+  std::unique_ptr<SideNet> net[2];
+  SideBufs buf[2];
+  std::vector<DevBuf> own[2];
+};
+
+// Per-evaluation results at one point.
+struct Eval {
+  double e = 0.0;
+  DevBuf G;                       // projected gradient, all tensors concatenated
+  DevBuf D;                       // partial derivatives
+  std::vector<DevBuf> rho_v;      // per-tensor density matrices (preconditioner)
+  std::vector<double> delta;      // |G_v|
+  bool eig_ready = false;
+  std::vector<DevBuf> evec, eval; // eigendecomposition of rho_v
+  bool valid = false;
+};
+
+// Quantities of the low-rank exponential for one (point, direction, alpha).
+struct StepGeom {
+  bool valid = false;
+  double alpha = 0.0;
+  std::vector<DevBuf> Amat;   // u: A = W^T X ; w: V (evecs of X^T X)
+  std::vector<DevBuf> E;      // u: exp(alpha A) ; w: unused
+  std::vector<DevBuf> P1, P2, Pc;  // w: spectral matrices
+};
+
+}  // namespace mera
+
+struct mera_ctx {
+  mera_config cfg{};
+  cudaStream_t s = nullptr;
+  int L = 0, nt = 0;
+  std::vector<int64_t> dims;
+  std::vector<int64_t> rows, cols, offs;  // tensor shapes and offsets in a flat tangent
+  int64_t total = 0;                      // flat tangent length
+  mera::TablePool pool;
+  std::vector<mera::Layer> layers;
+  mera::DevBuf Wcur, Wtry;                // points (flat)
+  mera::DevBuf h0;
+  std::vector<mera::DevBuf> h, rho;       // level operators h_0..h_L, rho_0..rho_L
+  mera::DevBuf x;                         // scale-invariant series
+  bool have_rho = false, have_x = false;
+  mera::DevBuf kbasis, ktmp, kcoef;       // Krylov workspace
+  mera::DevBuf scratch;                   // transient contraction buffers
+  mera::DevBuf gtmp[6];                   // geometry temporaries
+  mera::Reducer red;
+  mera::Eval ev[2];
+  int cur = 0;                            // index of the current point's Eval
+  mera::StepGeom geom;
+  // optimiser
+  std::vector<mera::DevBuf> mem_s, mem_y;
+  std::vector<double> mem_rho;
+  int mem_n = 0;
+  mera::DevBuf dir, dir2, tmpv, tmpv2;
+  double alpha_prev = 1.0;
+  int iters = 0;
+  int64_t launches = 0;
+  int64_t matvecs = 0;
+  std::string err;
+};
+
+namespace mera {
+namespace {
+
+using Ctx = mera_ctx;
+
+double* P(const DevBuf& b) { return b.as<double>(); }
+double* Wt(Ctx& c, DevBuf& flat, int i) { return P(flat) + c.offs[i]; }
+
+int64_t ipow(int64_t b, int e) {
+  int64_t r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+// ------------------------------------------------------ network binding ----
+void bind_leaves(Layer& ly, int side, const double* op, const double* u, const double* w) {
+  SideBufs& b = ly.buf[side];
+  b.leaf[0] = op;
+  for (int l : {1, 2, 3, 5}) b.leaf[l] = u;
+  for (int l : {4, 6, 7, 8, 9, 10}) b.leaf[l] = w;
+}
+
+void build_layers(Ctx& c) {
+  c.layers.resize(c.L + 1);
+  size_t scratch_need = 0;
+  for (int l = 0; l <= c.L; ++l) {
+    Layer& ly = c.layers[l];
+    ly.cf = c.dims[l];
+    ly.cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    for (int sd = 0; sd < 2; ++sd) {
+      ly.net[sd] = std::make_unique<SideNet>(sd == 0 ? 'L' : 'R', ly.cf, ly.cc, c.pool);
+      SideNet& net = *ly.net[sd];
+      // persistent node values: N1 N3 N4 N6 N7 N8 N9
+      for (int node : {11, 13, 14, 16, 17, 18, 19}) {
+        ly.own[sd].emplace_back(sizeof(double) * net.node_size(node));
+        ly.buf[sd].val[node] = P(ly.own[sd].back());
+      }
+      size_t need = 0;
+      for (int node : {12, 15}) need += net.node_size(node);
+      for (int node = 11; node < 20; ++node) need += net.node_size(node);
+      scratch_need = std::max(scratch_need, need);
+    }
+  }
+  c.scratch.alloc(sizeof(double) * scratch_need);
+  for (int l = 0; l <= c.L; ++l)
+    for (int sd = 0; sd < 2; ++sd) {
+      Layer& ly = c.layers[l];
+      SideNet& net = *ly.net[sd];
+      double* p = P(c.scratch);
+      for (int node : {12, 15}) {
+        ly.buf[sd].val[node] = p;
+        p += net.node_size(node);
+      }
+      for (int node = 11; node < 20; ++node) {
+        ly.buf[sd].adj[node] = p;
+        p += net.node_size(node);
+      }
+    }
+}
+
+// -------------------------------------------------------- superoperators ---
+// out = ao * out + af * Abar(op) (both sides), using layer l's tensors from point W.
+void ascend(Ctx& c, int l, const double* W, const double* op, double* out, double af, bool keep,
+            cudaStream_t s) {
+  Layer& ly = c.layers[l];
+  const double* u = W + c.offs[2 * l];
+  const double* w = W + c.offs[2 * l + 1];
+  for (int sd = 0; sd < 2; ++sd) {
+    bind_leaves(ly, sd, op, u, w);
+    ly.buf[sd].val[SideNet::ROOT] = out;
+    (void)keep;
+  }
+  // root written with alpha = af/2, the right side accumulating
+  for (int sd = 0; sd < 2; ++sd) {
+    SideNet& net = *ly.net[sd];
+    SideBufs& b = ly.buf[sd];
+    for (int node : {12, 13, 15, 17, 18}) {
+      GettCall g = net.fwd(node).proto;
+      const int lc = SideNet::left(node), rc = SideNet::right(node);
+      g.A = lc < SideNet::NLEAF ? b.leaf[lc] : b.val[lc];
+      g.B = rc < SideNet::NLEAF ? b.leaf[rc] : b.val[rc];
+      g.C = b.val[node];
+      gett_f64(g, s);
+    }
+    GettCall g = net.fwd(SideNet::ROOT).proto;
+    g.A = b.val[18];
+    g.B = b.val[19];
+    g.C = out;
+    g.alpha = 0.5 * af;
+    g.beta = 1.0;
+    gett_f64(g, s);
+  }
+}
+
+void prepare_layer(Ctx& c, int l, const double* W, cudaStream_t s) {
+  Layer& ly = c.layers[l];
+  const double* u = W + c.offs[2 * l];
+  const double* w = W + c.offs[2 * l + 1];
+  for (int sd = 0; sd < 2; ++sd) {
+    bind_leaves(ly, sd, nullptr, u, w);
+    side_prepare(*ly.net[sd], ly.buf[sd], s);
+  }
+}
+
+// out += af * Dbar(r) (both sides); operator-path reverse pass only.
+void descend(Ctx& c, int l, const double* r, double* out, double af, cudaStream_t s) {
+  Layer& ly = c.layers[l];
+  for (int sd = 0; sd < 2; ++sd) {
+    ly.buf[sd].adj[SideNet::ROOT] = const_cast<double*>(r);
+    side_backward(*ly.net[sd], ly.buf[sd], true, out, 0.5 * af, false, nullptr, nullptr, 0.0, s);
+  }
+}
+
+// ---------------------------------------------------------------- GMRES ----
+// Solve Op(x) = b (length n) with restarted GMRES(m), classical Gram-Schmidt
+// with one re-orthogonalisation; x holds the initial guess.  Returns the
+// number of operator applications; throws MERA_ERR_NOCONV if the relative
+// residual stays above tol after maxit applications.
+int gmres(Ctx& c, const std::function<void(const double*, double*)>& op, const double* b,
+          double* x, int64_t n, double tol, cudaStream_t s) {
+  const int m = std::max(2, c.cfg.krylov_dim);
+  const int maxit = std::max(m, c.cfg.krylov_maxiter);
+  double* V = P(c.kbasis);
+  double* w = P(c.ktmp);
+  const double bnorm = std::sqrt(c.red.dot(b, b, n, s));
+  if (bnorm == 0.0) {
+    fill(0.0, x, n, s);
+    return 0;
+  }
+  int applications = 0;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), h1(m + 1), h2(m + 1), y(m);
+  double best = INFINITY;
+  while (true) {
+    op(x, w);
+    ++applications;
+    axpby(1.0, b, -1.0, w, n, s);  // w = b - A x
+    const double beta = std::sqrt(c.red.dot(w, w, n, s));
+    if (beta <= tol * bnorm) return applications;
+    if (applications >= maxit || !(beta < 1e300)) {
+      throw Error(MERA_ERR_NOCONV, "GMRES: relative residual " + std::to_string(beta / bnorm));
+    }
+    if (beta >= best * 0.999999 && applications > 4 * m) {
+      // stagnation at the rounding floor
+      if (beta <= 1e3 * tol * bnorm) return applications;
+    }
+    best = std::min(best, beta);
+    axpby(1.0 / beta, w, 0.0, V, n, s);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < m; ++j) {
+      double* vj1 = V + (int64_t)(j + 1) * n;
+      op(V + (int64_t)j * n, vj1);
+      ++applications;
+      c.red.dots(V, n, j + 1, vj1, n, s, h1.data());
+      for (int i = 0; i <= j; ++i) h1[i] = -h1[i];
+      MERA_CUDA(cudaMemcpyAsync(c.kcoef.p, h1.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+      combine(V, n, j + 1, P(c.kcoef), vj1, n, 1.0, s);
+      c.red.dots(V, n, j + 1, vj1, n, s, h2.data());
+      for (int i = 0; i <= j; ++i) h2[i] = -h2[i];
+      MERA_CUDA(cudaMemcpyAsync(c.kcoef.p, h2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+      combine(V, n, j + 1, P(c.kcoef), vj1, n, 1.0, s);
+      for (int i = 0; i <= j; ++i) H[i * m + j] = -(h1[i] + h2[i]);
+      const double hn = std::sqrt(c.red.dot(vj1, vj1, n, s));
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0) scal(1.0 / hn, vj1, n, s);
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double a = H[j * m + j], bb = H[(j + 1) * m + j];
+      const double r = std::hypot(a, bb);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? bb / r : 0.0;
+      H[j * m + j] = r;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      if (std::fabs(g[j + 1]) <= 0.5 * tol * bnorm || hn == 0.0 || applications >= maxit) {
+        ++j;
+        break;
+      }
+    }
+    // back substitution
+    for (int i = j - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k < j; ++k) t -= H[i * m + k] * y[k];
+      y[i] = H[i * m + i] != 0 ? t / H[i * m + i] : 0.0;
+    }
+    MERA_CUDA(cudaMemcpyAsync(c.kcoef.p, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    combine(V, n, j, P(c.kcoef), x, n, 1.0, s);
+  }
+}
+
+// --------------------------------------------------------- energy / grad ---
+void project_tensor(Ctx& c, int i, const double* W, const double* D, double* G, cudaStream_t s) {
+  const int64_t n = c.rows[i], p = c.cols[i];
+  double* S = P(c.gtmp[0]);
+  gemm_f64('T', 'N', p, p, n, 1.0, W, p, D, p, 0.0, S, p, s);  // S = W^T D
+  const bool stiefel = (i % 2 == 0) || c.cfg.w_stiefel;
+  if (stiefel) symmetrize(S, p, s);                             // (S + S^T)/2
+  if (G != D) copy(G, D, n * p, s);
+  gemm_f64('N', 'N', n, p, p, -1.0, W, p, S, p, 1.0, G, p, s); // G = D - W S
+}
+
+void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
+
+// Full evaluation at point W into E.
+void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
+  const int L = c.L;
+  // up-sweep
+  copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6), s);
+  for (int l = 0; l <= L; ++l) prepare_layer(c, l, W, s);
+  for (int l = 0; l < L; ++l) {
+    const int64_t n3 = ipow(c.dims[l + 1], 3);
+    fill(0.0, P(c.h[l + 1]), n3 * n3, s);
+    ascend(c, l, W, P(c.h[l]), P(c.h[l + 1]), 1.0, true, s);
+    symmetrize(P(c.h[l + 1]), n3, s);
+  }
+  // scale-invariant layer
+  const int64_t cS = c.dims[L], n3 = ipow(cS, 3), n = n3 * n3;
+  double* rhoS = P(c.rho[L]);
+  if (!c.have_rho) {
+    fill(0.0, rhoS, n, s);
+    add_identity(1.0 / (double)n3, rhoS, n3, s);
+  }
+  double* bvec = P(c.gtmp[5]);
+  fill(0.0, bvec, n, s);
+  add_identity(1.0 / (double)n3, bvec, n3, s);
+  const double tol = c.cfg.krylov_tol;
+  auto op_rho = [&](const double* v, double* out) {
+    copy(out, v, n, s);
+    descend(c, L, v, out, -1.0, s);
+    const double tr = c.red.trace(v, n3, s);
+    axpy(tr, bvec, out, n, s);
+    ++c.matvecs;
+  };
+  gmres(c, op_rho, bvec, rhoS, n, tol, s);
+  const double tr = c.red.trace(rhoS, n3, s);
+  if (!(std::fabs(tr) > 0)) throw Error(MERA_ERR_NONFINITE, "fixed point has zero trace");
+  scal(1.0 / tr, rhoS, n, s);
+  symmetrize(rhoS, n3, s);
+  c.have_rho = true;
+  double* hL = P(c.h[L]);
+  double* xs = P(c.x);
+  if (!c.have_x) copy(xs, hL, n, s);
+  auto op_x = [&](const double* v, double* out) {
+    copy(out, v, n, s);
+    ascend(c, L, W, v, out, -1.0, false, s);
+    const double t = c.red.dot(v, rhoS, n, s);
+    add_identity(t, out, n3, s);
+    ++c.matvecs;
+  };
+  gmres(c, op_x, hL, xs, n, tol, s);
+  symmetrize(xs, n3, s);
+  c.have_x = true;
+  E.e = c.red.dot(hL, rhoS, n, s);
+  // down-sweep with environments
+  double* D = P(E.D);
+  fill(0.0, D, c.total, s);
+  for (int l = L; l >= 0; --l) {
+    Layer& ly = c.layers[l];
+    const double* u = W + c.offs[2 * l];
+    const double* w = W + c.offs[2 * l + 1];
+    const double* op = l < L ? P(c.h[l]) : xs;
+    const double* r = l < L ? P(c.rho[l + 1]) : rhoS;
+    const bool need_op = l < L;
+    if (need_op) fill(0.0, P(c.rho[l]), ipow(ly.cf, 6), s);
+    for (int sd = 0; sd < 2; ++sd) {
+      SideBufs& b = ly.buf[sd];
+      bind_leaves(ly, sd, op, u, w);
+      // forward with this layer's operator (keeps N3, N7, N8); output not needed
+      for (int node : {12, 13, 15, 17, 18}) {
+        GettCall g = ly.net[sd]->fwd(node).proto;
+        const int lc = SideNet::left(node), rc = SideNet::right(node);
+        g.A = lc < SideNet::NLEAF ? b.leaf[lc] : b.val[lc];
+        g.B = rc < SideNet::NLEAF ? b.leaf[rc] : b.val[rc];
+        g.C = b.val[node];
+        gett_f64(g, s);
+      }
+      b.adj[SideNet::ROOT] = const_cast<double*>(r);
+      side_backward(*ly.net[sd], b, need_op, need_op ? P(c.rho[l]) : nullptr, 0.5, true,
+                    D + c.offs[2 * l], D + c.offs[2 * l + 1], 1.0, s);
+    }
+    if (need_op) symmetrize(P(c.rho[l]), ipow(ly.cf, 3), s);
+  }
+  // projection
+  for (int i = 0; i < c.nt; ++i)
+    project_tensor(c, i, W + c.offs[i], D + c.offs[i], P(E.G) + c.offs[i], s);
+  E.delta.resize(c.nt);
+  bool finite = std::isfinite(E.e);
+  for (int i = 0; i < c.nt; ++i) {
+    const double* g = P(E.G) + c.offs[i];
+    E.delta[i] = std::sqrt(c.red.dot(g, g, c.rows[i] * c.cols[i], s));
+    finite = finite && std::isfinite(E.delta[i]);
+  }
+  if (!finite) throw Error(MERA_ERR_NONFINITE, "non-finite energy or gradient");
+  compute_rho_v(c, E, W, s);
+  E.eig_ready = false;
+  E.valid = true;
+}
+
+// rho_w: one-site marginal of the density matrix above the layer; rho_u:
+// W rho2 W^T on the pair of isometry outputs that u acts on (Sec. 4).
+void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s) {
+  for (int l = 0; l <= c.L; ++l) {
+    const int64_t cf = c.layers[l].cf, cc = c.layers[l].cc;
+    const double* r = l < c.L ? P(c.rho[l + 1]) : P(c.rho[c.L]);
+    const double* w = W + c.offs[2 * l + 1];
+    double* rw = P(E.rho_v[2 * l + 1]);
+    double* ru = P(E.rho_v[2 * l]);
+    marginal_1site_mid(r, cc, rw, s);
+    double* r2 = P(c.gtmp[1]);
+    marginal_2site_left(r, cc, r2, s);
+    // pairwise: T1[x0 x1 b A B] = w[x0 x1 a] r2[a b A B]
+    //           T2[x1 b B X1]   = T1 x w[x0 X1 A]
+    //           T3[x1 B X1 x2 x3] = T2 x w[x2 x3 b]
+    //           ru[x1 x2 X1 X2] = T3 x w[X2 x3 B]
+    auto D = [](std::vector<int> legs, std::vector<int64_t> ext) {
+      TDesc d;
+      d.legs = legs;
+      d.ext = ext;
+      d.stride.assign(legs.size(), 1);
+      for (size_t j = legs.size(); j-- > 1;) d.stride[j - 1] = d.stride[j] * ext[j];
+      return d;
+    };
+    enum { x0, x1, x2, x3, X1, X2, a, b, A, B };
+    TDesc wa = D({x0, x1, a}, {cf, cf, cc}), R2 = D({a, b, A, B}, {cc, cc, cc, cc});
+    TDesc T1 = D({x0, x1, b, A, B}, {cf, cf, cc, cc, cc});
+    TDesc wA = D({x0, X1, A}, {cf, cf, cc});
+    TDesc T2 = D({x1, b, B, X1}, {cf, cc, cc, cf});
+    TDesc wb = D({x2, x3, b}, {cf, cf, cc});
+    TDesc T3 = D({x1, B, X1, x2, x3}, {cf, cc, cf, cf, cf});
+    TDesc wB = D({X2, x3, B}, {cf, cf, cc});
+    TDesc RU = D({x1, x2, X1, X2}, {cf, cf, cf, cf});
+    double* t1 = P(c.gtmp[2]);
+    double* t2 = P(c.gtmp[3]);
+    double* t3 = P(c.gtmp[4]);
+    auto run = [&](const TDesc& A_, const TDesc& B_, const TDesc& C_, const double* pa,
+                   const double* pb, double* pc) {
+      GettCall g = make_plan(A_, B_, C_, c.pool).proto;
+      g.A = pa;
+      g.B = pb;
+      g.C = pc;
+      gett_f64(g, s);
+    };
+    run(wa, R2, T1, w, r2, t1);
+    run(T1, wA, T2, t1, w, t2);
+    run(T2, wb, T3, t2, w, t3);
+    run(T3, wB, RU, t3, w, ru);
+    symmetrize(ru, cf * cf, s);
+    symmetrize(rw, cc, s);
+  }
+}
+
+void ensure_eig(Ctx& c, Eval& E, cudaStream_t s) {
+  if (E.eig_ready) return;
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t p = c.cols[i];
+    double* A = P(c.gtmp[0]);
+    copy(A, P(E.rho_v[i]), p * p, s);
+    sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)p, s);
+  }
+  E.eig_ready = true;
+}
+
+// Xt = preconditioned X (per tensor), with E's density matrices and deltas.
+void precondition(Ctx& c, Eval& E, const double* W, const double* X, double* Xt, cudaStream_t s) {
+  if (!c.cfg.precond) {
+    if (Xt != X) copy(Xt, X, c.total, s);
+    return;
+  }
+  ensure_eig(c, E, s);
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t n = c.rows[i], p = c.cols[i];
+    const double* Wi = W + c.offs[i];
+    const double* Xi = X + c.offs[i];
+    double* Yi = Xt + c.offs[i];
+    const double* V = P(E.evec[i]);
+    double* lt = P(c.gtmp[5]);
+    const bool stiefel = (i % 2 == 0) || c.cfg.w_stiefel;
+    double* A = P(c.gtmp[0]);
+    double* T = P(c.gtmp[1]);
+    double* Rinv = P(c.gtmp[2]);
+    double* Z = P(c.gtmp[3]);
+    // regularised inverse (rho^2 + delta^2)^(-1/2) = V diag(1/lt) V^T
+    spectral_k<<<blocks(p), 256, 0, s>>>(P(E.eval[i]), (int)p, 3, 0.0, E.delta[i], lt);
+    vfvt_k<<<blocks(p * p), 256, 0, s>>>(V, lt, (int)p, Rinv);
+    count_launch(2);
+    if (stiefel) {
+      gemm_f64('T', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, A, p, s);   // A = W^T X
+      // Z = X - W A  (W_perp B part)
+      copy(Z, Xi, n * p, s);
+      gemm_f64('N', 'N', n, p, p, -1.0, Wi, p, A, p, 1.0, Z, p, s);
+      // At = V [2 (V^T A V)_ij / (lt_i + lt_j)] V^T
+      spectral_k<<<blocks(p), 256, 0, s>>>(P(E.eval[i]), (int)p, 4, 0.0, E.delta[i], lt);
+      count_launch();
+      gemm_f64('T', 'N', p, p, p, 1.0, V, p, A, p, 0.0, T, p, s);
+      gemm_f64('N', 'N', p, p, p, 1.0, T, p, V, p, 0.0, A, p, s);
+      sylvester_scale_k<<<blocks(p * p), 256, 0, s>>>(A, lt, (int)p);
+      count_launch();
+      gemm_f64('N', 'N', p, p, p, 1.0, V, p, A, p, 0.0, T, p, s);
+      gemm_f64('N', 'T', p, p, p, 1.0, T, p, V, p, 0.0, A, p, s);
+      // Yi = W At + Z Rinv
+      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, A, p, 0.0, Yi, p, s);
+      gemm_f64('N', 'N', n, p, p, 1.0, Z, p, Rinv, p, 1.0, Yi, p, s);
+    } else {
+      gemm_f64('N', 'N', n, p, p, 1.0, Xi, p, Rinv, p, 0.0, Yi, p, s);
+    }
+  }
+  MERA_CHECK_LAUNCH();
+}
+
+// ----------------------------------------------------------- geometry ------
+void expm_skew(Ctx& c, const double* A, double alpha, int64_t n, double* E, double* T1, double* T2,
+               cudaStream_t s) {
+  // scaling and squaring with a degree-16 Taylor polynomial (Horner form)
+  const double nrm = std::fabs(alpha) * std::sqrt(c.red.dot(A, A, n * n, s));
+  int sq = 0;
+  while (nrm / std::ldexp(1.0, sq) > 0.5) ++sq;
+  const double a = alpha / std::ldexp(1.0, sq);
+  const int q = 16;
+  // T1 = I + a A / q
+  axpby(a / q, A, 0.0, T1, n * n, s);
+  add_identity(1.0, T1, n, s);
+  for (int k = q - 1; k >= 1; --k) {
+    gemm_f64('N', 'N', n, n, n, a / k, A, n, T1, n, 0.0, T2, n, s);
+    add_identity(1.0, T2, n, s);
+    std::swap(T1, T2);
+  }
+  for (int k = 0; k < sq; ++k) {
+    gemm_f64('N', 'N', n, n, n, 1.0, T1, n, T1, n, 0.0, T2, n, s);
+    std::swap(T1, T2);
+  }
+  copy(E, T1, n * n, s);
+}
+
+// Newton-Schulz polar iteration X <- X (3 - X^T X)/2, in place (n x p).
+void polar_ns(Ctx& c, double* X, int64_t n, int64_t p, cudaStream_t s) {
+  double* S = P(c.gtmp[0]);
+  double* Y = P(c.gtmp[1]);
+  for (int it = 0; it < 2; ++it) {
+    gemm_f64('T', 'N', p, p, n, -0.5, X, p, X, p, 0.0, S, p, s);
+    add_identity(1.5, S, p, s);
+    gemm_f64('N', 'N', n, p, p, 1.0, X, p, S, p, 0.0, Y, p, s);
+    copy(X, Y, n * p, s);
+  }
+}
+
+// Fill c.geom for direction X at point W and step alpha.
+void make_geom(Ctx& c, const double* W, const double* X, double alpha, cudaStream_t s) {
+  StepGeom& g = c.geom;
+  g.alpha = alpha;
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t n = c.rows[i], p = c.cols[i];
+    const double* Wi = W + c.offs[i];
+    const double* Xi = X + c.offs[i];
+    const bool unitary = (n == p) && ((i % 2 == 0) || c.cfg.w_stiefel || true);
+    if (unitary) {
+      gemm_f64('T', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, P(g.Amat[i]), p, s);
+      expm_skew(c, P(g.Amat[i]), alpha, p, P(g.E[i]), P(c.gtmp[2]), P(c.gtmp[3]), s);
+    } else if (i % 2 == 1 && !c.cfg.w_stiefel) {
+      // Grassmann: X^T X = V S^2 V^T
+      double* Z = P(c.gtmp[0]);
+      double* ev = P(c.gtmp[5]);
+      gemm_f64('T', 'N', p, p, n, 1.0, Xi, p, Xi, p, 0.0, Z, p, s);
+      sym_eig(Z, P(g.Amat[i]), ev, (int)p, s);
+      double* f = P(c.gtmp[4]);
+      for (int kind = 0; kind < 3; ++kind) {
+        double* out = kind == 0 ? P(g.Pc[i]) : kind == 1 ? P(g.P1[i]) : P(g.P2[i]);
+        spectral_k<<<blocks(p), 256, 0, s>>>(ev, (int)p, kind, alpha, 0.0, f);
+        vfvt_k<<<blocks(p * p), 256, 0, s>>>(P(g.Amat[i]), f, (int)p, out);
+        count_launch(2);
+      }
+      MERA_CHECK_LAUNCH();
+    } else {
+      throw Error(MERA_ERR_UNSUPPORTED, "non-square Stiefel retraction not built");
+    }
+  }
+  g.valid = true;
+}
+
+// Wout = R_W(X, alpha) (re-isometrised); uses c.geom.
+void apply_retract(Ctx& c, const double* W, const double* X, double* Wout, cudaStream_t s) {
+  StepGeom& g = c.geom;
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t n = c.rows[i], p = c.cols[i];
+    const double* Wi = W + c.offs[i];
+    const double* Xi = X + c.offs[i];
+    double* Ri = Wout + c.offs[i];
+    if (n == p) {
+      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, P(g.E[i]), p, 0.0, Ri, p, s);
+    } else {
+      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, P(g.Pc[i]), p, 0.0, Ri, p, s);
+      gemm_f64('N', 'N', n, p, p, 1.0, Xi, p, P(g.P1[i]), p, 1.0, Ri, p, s);
+    }
+    polar_ns(c, Ri, n, p, s);
+  }
+}
+
+// Y <- T_W(Y, X, alpha), in place; uses c.geom.
+void apply_transport(Ctx& c, const double* W, const double* X, double* Y, cudaStream_t s) {
+  StepGeom& g = c.geom;
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t n = c.rows[i], p = c.cols[i];
+    const double* Wi = W + c.offs[i];
+    const double* Xi = X + c.offs[i];
+    double* Yi = Y + c.offs[i];
+    double* Z = P(c.gtmp[0]);
+    double* Z2 = P(c.gtmp[1]);
+    if (n == p) {
+      // W exp(aA) W^T Y
+      gemm_f64('T', 'N', p, p, n, 1.0, Wi, p, Yi, p, 0.0, Z, p, s);
+      gemm_f64('N', 'N', p, p, p, 1.0, P(g.E[i]), p, Z, p, 0.0, Z2, p, s);
+      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, Z2, p, 0.0, Yi, p, s);
+    } else {
+      // Y - W P1 (X^T Y) - X P2 (X^T Y)
+      gemm_f64('T', 'N', p, p, n, 1.0, Xi, p, Yi, p, 0.0, Z, p, s);
+      gemm_f64('N', 'N', p, p, p, 1.0, P(g.P1[i]), p, Z, p, 0.0, Z2, p, s);
+      gemm_f64('N', 'N', n, p, p, -1.0, Wi, p, Z2, p, 1.0, Yi, p, s);
+      gemm_f64('N', 'N', p, p, p, 1.0, P(g.P2[i]), p, Z, p, 0.0, Z2, p, s);
+      gemm_f64('N', 'N', n, p, p, -1.0, Xi, p, Z2, p, 1.0, Yi, p, s);
+    }
+  }
+}
+
+double inner(Ctx& c, const double* X, const double* Y, cudaStream_t s) {
+  return c.red.dot(X, Y, c.total, s);
+}
+
+// ------------------------------------------------------------ optimiser ----
+struct LsResult {
+  double alpha = 0, f = 0, df = 0;
+  int nev = 0;
+  bool ok = false, found = false;
+};
+
+// One trial: point Wtry = R(Wcur, d, a), evaluation into ev[1-cur],
+// dir2 = T(d).  Returns (f, df).
+std::pair<double, double> trial(Ctx& c, double a, cudaStream_t s) {
+  const double* W = P(c.Wcur);
+  make_geom(c, W, P(c.dir), a, s);
+  apply_retract(c, W, P(c.dir), P(c.Wtry), s);
+  Eval& E = c.ev[1 - c.cur];
+  double f, df;
+  try {
+    energy_grad(c, P(c.Wtry), E, s);
+    copy(P(c.dir2), P(c.dir), c.total, s);
+    apply_transport(c, W, P(c.dir), P(c.dir2), s);
+    f = E.e;
+    df = inner(c, P(E.G), P(c.dir2), s);
+  } catch (const Error& e) {
+    if (e.code != MERA_ERR_NONFINITE) throw;
+    f = INFINITY;
+    df = INFINITY;
+  }
+  return {f, df};
+}
+
+LsResult hager_zhang(Ctx& c, double f0, double df0, double a0, cudaStream_t s) {
+  const double delta = 0.1, sigma = 0.9, eps = 1e-6, theta = 0.5, gamma = 0.66, expand = 5.0;
+  const int maxeval = 20;
+  const double epsk = eps * std::fabs(f0);
+  struct Pt { double a, f, df; };
+  std::vector<Pt> hist;
+  LsResult res;
+  double last_a = NAN;
+  auto ev = [&](double a) -> Pt {
+    for (auto& p : hist)
+      if (p.a == a) return p;
+    if ((int)hist.size() >= maxeval) throw 1;
+    auto fd = trial(c, a, s);
+    last_a = a;
+    Pt p{a, fd.first, fd.second};
+    if (!std::isfinite(p.f) || !std::isfinite(p.df)) { p.f = INFINITY; p.df = INFINITY; }
+    hist.push_back(p);
+    const bool wolfe = (p.f - f0 <= delta * a * df0) && (p.df >= sigma * df0);
+    const bool approx = ((2 * delta - 1) * df0 >= p.df) && (p.df >= sigma * df0) && (p.f <= f0 + epsk);
+    if (wolfe || approx) throw 2;
+    return p;
+  };
+  auto dfof = [&](double a) { if (a == 0) return df0; for (auto& p : hist) if (p.a == a) return p.df; return df0; };
+  auto u3 = [&](double a, double b) -> std::pair<double, double> {
+    while (true) {
+      const double d = (1 - theta) * a + theta * b;
+      Pt p = ev(d);
+      if (p.df >= 0) return {a, d};
+      if (p.f <= f0 + epsk) a = d; else b = d;
+    }
+  };
+  auto update = [&](double a, double b, double cc) -> std::pair<double, double> {
+    if (!(a < cc && cc < b)) return {a, b};
+    Pt p = ev(cc);
+    if (p.df >= 0) return {a, cc};
+    if (p.f <= f0 + epsk) return {cc, b};
+    return u3(a, cc);
+  };
+  auto secant = [&](double a, double b) {
+    const double da = dfof(a), db = dfof(b);
+    if (db == da) return 0.5 * (a + b);
+    return (a * db - b * da) / (db - da);
+  };
+  int outcome = 0;
+  try {
+    double cc = a0;
+    Pt p = ev(cc);
+    double good = 0.0, a, b;
+    while (true) {
+      if (p.df >= 0) { a = good; b = cc; break; }
+      if (p.f > f0 + epsk) { auto ab = u3(0.0, cc); a = ab.first; b = ab.second; break; }
+      good = cc;
+      cc *= expand;
+      p = ev(cc);
+    }
+    while (true) {
+      const double cs = secant(a, b);
+      auto AB = update(a, b, cs);
+      if (cs == AB.second) AB = update(AB.first, AB.second, secant(b, AB.second));
+      else if (cs == AB.first) AB = update(AB.first, AB.second, secant(a, AB.first));
+      if (AB.second - AB.first > gamma * (b - a)) AB = update(AB.first, AB.second, 0.5 * (AB.first + AB.second));
+      a = AB.first;
+      b = AB.second;
+    }
+  } catch (int code) {
+    outcome = code;
+  }
+  res.nev = (int)hist.size();
+  if (outcome == 2) {
+    res.ok = true;
+    res.found = true;
+    res.alpha = last_a;
+    res.f = hist.back().f;
+    res.df = hist.back().df;
+    return res;
+  }
+  // best finite trial
+  double bf = INFINITY, ba = NAN;
+  for (auto& p : hist)
+    if (p.f < bf) { bf = p.f; ba = p.a; }
+  if (std::isfinite(bf)) {
+    res.found = true;
+    res.alpha = ba;
+    if (ba != last_a) trial(c, ba, s);  // re-evaluate to leave its state in place
+    res.f = c.ev[1 - c.cur].e;
+    res.df = NAN;
+  }
+  return res;
+}
+
+void ensure_current(Ctx& c, cudaStream_t s) {
+  if (!c.ev[c.cur].valid) energy_grad(c, P(c.Wcur), c.ev[c.cur], s);
+}
+
+void clear_history(Ctx& c) {
+  c.mem_n = 0;
+  c.mem_rho.clear();
+  c.alpha_prev = 1.0;
+}
+
+// Accept the last trial: transport history, move point.
+void accept(Ctx& c, cudaStream_t s) {
+  std::swap(c.Wcur, c.Wtry);
+  c.cur = 1 - c.cur;
+}
+
+void lbfgs_step(Ctx& c, mera_iter_info* info, cudaStream_t s) {
+  ensure_current(c, s);
+  const int64_t mv0 = c.matvecs;
+  Eval& E = c.ev[c.cur];
+  const double* W = P(c.Wcur);
+  double* G = P(E.G);
+  const int m = std::max(1, c.cfg.lbfgs_m);
+  // two-loop recursion, q in dir
+  double* q = P(c.dir);
+  copy(q, G, c.total, s);
+  std::vector<double> al(c.mem_n);
+  for (int i = c.mem_n - 1; i >= 0; --i) {
+    al[i] = c.mem_rho[i] * inner(c, P(c.mem_s[i]), q, s);
+    axpy(-al[i], P(c.mem_y[i]), q, c.total, s);
+  }
+  double gam = 1.0;
+  if (c.mem_n > 0) {
+    double* Py = P(c.tmpv);
+    precondition(c, E, W, P(c.mem_y[c.mem_n - 1]), Py, s);
+    gam = (1.0 / c.mem_rho[c.mem_n - 1]) / inner(c, P(c.mem_y[c.mem_n - 1]), Py, s);
+  }
+  precondition(c, E, W, q, P(c.tmpv), s);
+  axpby(gam, P(c.tmpv), 0.0, q, c.total, s);
+  for (int i = 0; i < c.mem_n; ++i) {
+    const double b = c.mem_rho[i] * inner(c, P(c.mem_y[i]), q, s);
+    axpy(al[i] - b, P(c.mem_s[i]), q, c.total, s);
+  }
+  scal(-1.0, q, c.total, s);
+  double df0 = inner(c, G, q, s);
+  if (!(df0 < 0)) {
+    clear_history(c);
+    precondition(c, E, W, G, q, s);
+    scal(-1.0, q, c.total, s);
+    df0 = inner(c, G, q, s);
+  }
+  const double f0 = E.e;
+  LsResult ls = hager_zhang(c, f0, df0, 1.0, s);
+  info->n_evals = ls.nev;
+  info->ls_ok = ls.ok;
+  if (!ls.found || (!ls.ok && ls.f >= f0)) {
+    clear_history(c);
+    info->alpha = 0.0;
+    info->energy = f0;
+    info->gnorm = std::sqrt(inner(c, G, G, s));
+    info->iter = ++c.iters;
+    info->krylov_matvecs = (int)(c.matvecs - mv0);
+    return;
+  }
+  // c.geom holds the accepted alpha's quantities, dir2 = T(d)
+  const double a = ls.alpha;
+  for (int i = 0; i < c.mem_n; ++i) {
+    apply_transport(c, W, P(c.dir), P(c.mem_s[i]), s);
+    apply_transport(c, W, P(c.dir), P(c.mem_y[i]), s);
+  }
+  // s_new = a T(d), y_new = G' - T(G)
+  double* Tg = P(c.tmpv);
+  copy(Tg, G, c.total, s);
+  apply_transport(c, W, P(c.dir), Tg, s);
+  Eval& En = c.ev[1 - c.cur];
+  if (c.mem_n == m) {
+    // drop the oldest pair (rotate buffers)
+    DevBuf s0 = std::move(c.mem_s[0]), y0 = std::move(c.mem_y[0]);
+    for (int i = 0; i + 1 < m; ++i) {
+      c.mem_s[i] = std::move(c.mem_s[i + 1]);
+      c.mem_y[i] = std::move(c.mem_y[i + 1]);
+    }
+    c.mem_s[m - 1] = std::move(s0);
+    c.mem_y[m - 1] = std::move(y0);
+    c.mem_rho.erase(c.mem_rho.begin());
+    c.mem_n--;
+  }
+  double* sn = P(c.mem_s[c.mem_n]);
+  double* yn = P(c.mem_y[c.mem_n]);
+  axpby(a, P(c.dir2), 0.0, sn, c.total, s);
+  copy(yn, P(En.G), c.total, s);
+  axpy(-1.0, Tg, yn, c.total, s);
+  const double sy = inner(c, sn, yn, s);
+  const double ss = inner(c, sn, sn, s), yy = inner(c, yn, yn, s);
+  if (sy > 1e-16 * std::sqrt(ss * yy)) {
+    c.mem_rho.push_back(1.0 / sy);
+    c.mem_n++;
+  }
+  accept(c, s);
+  Eval& Ec = c.ev[c.cur];
+  info->alpha = a;
+  info->energy = Ec.e;
+  info->gnorm = std::sqrt(inner(c, P(Ec.G), P(Ec.G), s));
+  info->iter = ++c.iters;
+  info->krylov_matvecs = (int)(c.matvecs - mv0);
+}
+
+void cg_step(Ctx& c, mera_iter_info* info, cudaStream_t s) {
+  ensure_current(c, s);
+  const int64_t mv0 = c.matvecs;
+  Eval& E = c.ev[c.cur];
+  const double* W = P(c.Wcur);
+  double* G = P(E.G);
+  double* d = P(c.dir);
+  // c.mem_n == 1 means dir holds the previous (transported) direction
+  if (c.mem_n == 0) {
+    precondition(c, E, W, G, d, s);
+    scal(-1.0, d, c.total, s);
+  }
+  double df0 = inner(c, G, d, s);
+  if (!(df0 < 0)) {
+    precondition(c, E, W, G, d, s);
+    scal(-1.0, d, c.total, s);
+    df0 = inner(c, G, d, s);
+  }
+  const double f0 = E.e;
+  LsResult ls = hager_zhang(c, f0, df0, c.alpha_prev, s);
+  info->n_evals = ls.nev;
+  info->ls_ok = ls.ok;
+  if (!ls.found || (!ls.ok && ls.f >= f0)) {
+    c.mem_n = 0;
+    info->alpha = 0.0;
+    info->energy = f0;
+    info->gnorm = std::sqrt(inner(c, G, G, s));
+    info->iter = ++c.iters;
+    info->krylov_matvecs = (int)(c.matvecs - mv0);
+    return;
+  }
+  const double a = ls.alpha;
+  Eval& En = c.ev[1 - c.cur];
+  // y = G' - T(G)
+  double* y = P(c.tmpv);
+  copy(y, G, c.total, s);
+  apply_transport(c, W, d, y, s);
+  axpby(1.0, P(En.G), -1.0, y, c.total, s);
+  const double* Wn = P(c.Wtry);
+  double* Pg = P(c.tmpv2);
+  precondition(c, En, Wn, P(En.G), Pg, s);
+  double* d2 = P(c.dir2);
+  const double dy = inner(c, d2, y, s);
+  double beta = 0.0;
+  if (dy != 0.0) {
+    double* Py = P(c.mem_s.empty() ? c.tmpv : c.mem_s[0]);
+    precondition(c, En, Wn, y, Py, s);
+    beta = (inner(c, y, Pg, s) - 2.0 * inner(c, y, Py, s) * inner(c, d2, P(En.G), s) / dy) / dy;
+  }
+  const double dn = std::sqrt(inner(c, d2, d2, s));
+  const double gn = std::sqrt(inner(c, P(En.G), P(En.G), s));
+  beta = std::max(beta, -1.0 / (dn * std::min(0.01, gn)));
+  // new direction d = -Pg + beta T(d)
+  axpby(-1.0, Pg, beta, d2, c.total, s);
+  copy(d, d2, c.total, s);
+  c.mem_n = 1;
+  c.alpha_prev = a;
+  accept(c, s);
+  info->alpha = a;
+  info->energy = c.ev[c.cur].e;
+  info->gnorm = gn;
+  info->iter = ++c.iters;
+  info->krylov_matvecs = (int)(c.matvecs - mv0);
+}
+
+// ------------------------------------------------------------ creation -----
+void check_isometric(Ctx& c, const double* W, cudaStream_t s) {
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t n = c.rows[i], p = c.cols[i];
+    double* S = P(c.gtmp[0]);
+    gemm_f64('T', 'N', p, p, n, 1.0, W + c.offs[i], p, W + c.offs[i], p, 0.0, S, p, s);
+    add_identity(-1.0, S, p, s);
+    const double r = std::sqrt(c.red.dot(S, S, p * p, s));
+    if (!(r < 1e-10)) throw Error(MERA_ERR_NOT_ISOMETRIC, "tensor " + std::to_string(i) + " has |W^T W - 1| = " + std::to_string(r));
+  }
+}
+
+void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
+  c.cfg = cfg;
+  c.s = s;
+  if (cfg.d_b < 2 || cfg.chi < 2 || cfg.n_trans < 1) throw Error(MERA_ERR_ARG, "bad d_b/chi/n_trans");
+  if (cfg.dtype != MERA_F64) throw Error(MERA_ERR_UNSUPPORTED, "only MERA_F64 is built");
+  if (cfg.prec != MERA_PREC_FP64) throw Error(MERA_ERR_UNSUPPORTED, "only MERA_PREC_FP64 is built");
+  c.L = cfg.n_trans;
+  c.dims.push_back(cfg.d_b);
+  for (int l = 0; l < c.L; ++l) c.dims.push_back(std::min<int64_t>(cfg.chi, c.dims.back() * c.dims.back()));
+  if (c.dims.back() != cfg.chi) throw Error(MERA_ERR_ARG, "transition layers do not reach chi");
+  c.nt = 2 * (c.L + 1);
+  int64_t off = 0;
+  for (int l = 0; l <= c.L; ++l) {
+    const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    c.rows.push_back(cf * cf); c.cols.push_back(cf * cf); c.offs.push_back(off); off += cf * cf * cf * cf;
+    c.rows.push_back(cf * cf); c.cols.push_back(cc);      c.offs.push_back(off); off += cf * cf * cc;
+  }
+  c.total = off;
+  build_layers(c);
+  const size_t tb = sizeof(double) * c.total;
+  c.Wcur.alloc(tb);
+  c.Wtry.alloc(tb);
+  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 6));
+  MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
+  for (int l = 0; l <= c.L; ++l) {
+    c.h.emplace_back(sizeof(double) * ipow(c.dims[l], 6));
+    c.rho.emplace_back(sizeof(double) * ipow(c.dims[l], 6));
+  }
+  const int64_t nS = ipow(cfg.chi, 6);
+  c.x.alloc(sizeof(double) * nS);
+  c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));
+  c.ktmp.alloc(sizeof(double) * nS);
+  c.kcoef.alloc(sizeof(double) * (cfg.krylov_dim + 2));
+  c.red.init(std::max(8, cfg.krylov_dim + 2));
+  // geometry temporaries: max over tensors / rho_u builders
+  int64_t gmax = nS;  // bvec in gtmp[5] also used for chi^6 vectors
+  for (int l = 0; l <= c.L; ++l) {
+    const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    gmax = std::max({gmax, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
+                     cf * cc * cc * cf, cf * cc * cf * cf * cf});
+  }
+  for (auto& b : c.gtmp) b.alloc(sizeof(double) * gmax);
+  for (auto& E : c.ev) {
+    E.G.alloc(tb);
+    E.D.alloc(tb);
+    for (int i = 0; i < c.nt; ++i) {
+      const int64_t p = c.cols[i];
+      E.rho_v.emplace_back(sizeof(double) * p * p);
+      E.evec.emplace_back(sizeof(double) * p * p);
+      E.eval.emplace_back(sizeof(double) * p);
+    }
+  }
+  StepGeom& g = c.geom;
+  for (int i = 0; i < c.nt; ++i) {
+    const int64_t p = c.cols[i];
+    g.Amat.emplace_back(sizeof(double) * p * p);
+    g.E.emplace_back(sizeof(double) * p * p);
+    g.P1.emplace_back(sizeof(double) * p * p);
+    g.P2.emplace_back(sizeof(double) * p * p);
+    g.Pc.emplace_back(sizeof(double) * p * p);
+  }
+  const int m = std::max(1, cfg.lbfgs_m);
+  for (int i = 0; i < m; ++i) {
+    c.mem_s.emplace_back(tb);
+    c.mem_y.emplace_back(tb);
+  }
+  c.dir.alloc(tb);
+  c.dir2.alloc(tb);
+  c.tmpv.alloc(tb);
+  c.tmpv2.alloc(tb);
+  // default point: u = 1, w = first columns
+  std::vector<double> host(c.total, 0.0);
+  for (int i = 0; i < c.nt; ++i)
+    for (int64_t k = 0; k < std::min(c.rows[i], c.cols[i]); ++k) host[c.offs[i] + k * c.cols[i] + k] = 1.0;
+  MERA_CUDA(cudaMemcpyAsync(c.Wcur.p, host.data(), tb, cudaMemcpyHostToDevice, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+}  // namespace mera
+
+// ================================================================ C ABI ====
+using mera::Error;
+
+namespace {
+struct Guard {
+  mera_t m;
+  explicit Guard(mera_t mm) : m(mm) { mera::g_launch_counter = mm ? &mm->launches : nullptr; }
+  ~Guard() { mera::g_launch_counter = nullptr; }
+};
+
+template <class F>
+int wrap(mera_t m, F&& f) {
+  Guard g(m);
+  try {
+    f();
+    return MERA_OK;
+  } catch (const Error& e) {
+    if (m) m->err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (m) m->err = "host allocation failed";
+    return MERA_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (m) m->err = e.what();
+    return MERA_ERR_CUDA;
+  }
+}
+
+void copy_in(mera_t m, const void* const* arr, double* flat) {
+  for (int i = 0; i < m->nt; ++i) {
+    if (!arr[i]) throw Error(MERA_ERR_ARG, "null tensor pointer");
+    MERA_CUDA(cudaMemcpyAsync(flat + m->offs[i], arr[i], sizeof(double) * m->rows[i] * m->cols[i],
+                              cudaMemcpyDefault, m->s));
+  }
+}
+void copy_out(mera_t m, const double* flat, void* const* arr) {
+  for (int i = 0; i < m->nt; ++i) {
+    if (!arr[i]) throw Error(MERA_ERR_ARG, "null tensor pointer");
+    MERA_CUDA(cudaMemcpyAsync(arr[i], flat + m->offs[i], sizeof(double) * m->rows[i] * m->cols[i],
+                              cudaMemcpyDefault, m->s));
+  }
+  MERA_CUDA(cudaStreamSynchronize(m->s));
+}
+}  // namespace
+
+extern "C" {
+
+void mera_config_default(mera_config* c, int d_b, int chi, int n_trans) {
+  std::memset(c, 0, sizeof(*c));
+  c->d_b = d_b;
+  c->chi = chi;
+  c->n_trans = n_trans;
+  c->dtype = MERA_F64;
+  c->prec = MERA_PREC_FP64;
+  c->w_stiefel = 0;
+  c->precond = 1;
+  c->krylov_dim = 20;
+  c->krylov_maxiter = 2000;
+  c->krylov_tol = 1e-14;
+  c->recompute_env = 0;
+  c->lbfgs_m = 8;
+}
+
+int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out) {
+  if (!cfg || !h3 || !out) return MERA_ERR_ARG;
+  mera_t m = new (std::nothrow) mera_ctx();
+  if (!m) return MERA_ERR_OOM;
+  int rc = wrap(m, [&] { mera::create(*m, *cfg, h3, static_cast<cudaStream_t>(stream)); });
+  if (rc != MERA_OK) {
+    delete m;
+    *out = nullptr;
+    return rc;
+  }
+  *out = m;
+  return MERA_OK;
+}
+
+int mera_destroy(mera_t m) {
+  if (!m) return MERA_ERR_ARG;
+  cudaStreamSynchronize(m->s);
+  delete m;
+  return MERA_OK;
+}
+
+int mera_num_tensors(mera_t m) { return m ? m->nt : MERA_ERR_ARG; }
+
+int mera_tensor_shape(mera_t m, int i, int64_t* rows, int64_t* cols) {
+  if (!m || i < 0 || i >= m->nt || !rows || !cols) return MERA_ERR_ARG;
+  *rows = m->rows[i];
+  *cols = m->cols[i];
+  return MERA_OK;
+}
+
+int mera_set_tensors(mera_t m, const void* const* t) {
+  if (!m || !t) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    copy_in(m, t, mera::P(m->Wtry));
+    mera::check_isometric(*m, mera::P(m->Wtry), m->s);
+    std::swap(m->Wcur, m->Wtry);
+    m->ev[0].valid = m->ev[1].valid = false;
+    mera::clear_history(*m);
+    m->iters = 0;
+  });
+}
+
+int mera_get_tensors(mera_t m, void* const* t) {
+  if (!m || !t) return MERA_ERR_ARG;
+  return wrap(m, [&] { copy_out(m, mera::P(m->Wcur), t); });
+}
+
+int mera_energy_grad(mera_t m, double* energy, void* const* grad, void* const* deriv) {
+  if (!m) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    mera::Eval& E = m->ev[m->cur];
+    mera::energy_grad(*m, mera::P(m->Wcur), E, m->s);
+    if (energy) *energy = E.e;
+    if (grad) copy_out(m, mera::P(E.G), grad);
+    if (deriv) copy_out(m, mera::P(E.D), deriv);
+    MERA_CUDA(cudaStreamSynchronize(m->s));
+  });
+}
+
+int mera_project(mera_t m, const void* const* D, void* const* G) {
+  if (!m || !D || !G) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    copy_in(m, D, mera::P(m->tmpv));
+    for (int i = 0; i < m->nt; ++i)
+      mera::project_tensor(*m, i, mera::P(m->Wcur) + m->offs[i], mera::P(m->tmpv) + m->offs[i],
+                           mera::P(m->tmpv2) + m->offs[i], m->s);
+    copy_out(m, mera::P(m->tmpv2), G);
+  });
+}
+
+int mera_inner(mera_t m, const void* const* X, const void* const* Y, double* out) {
+  if (!m || !X || !Y || !out) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    copy_in(m, X, mera::P(m->tmpv));
+    copy_in(m, Y, mera::P(m->tmpv2));
+    *out = mera::inner(*m, mera::P(m->tmpv), mera::P(m->tmpv2), m->s);
+  });
+}
+
+int mera_transport(mera_t m, const void* const* X, double alpha, void* const* Y) {
+  if (!m || !X || !Y) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    copy_in(m, X, mera::P(m->dir2));
+    copy_in(m, (const void* const*)Y, mera::P(m->tmpv));
+    mera::make_geom(*m, mera::P(m->Wcur), mera::P(m->dir2), alpha, m->s);
+    mera::apply_transport(*m, mera::P(m->Wcur), mera::P(m->dir2), mera::P(m->tmpv), m->s);
+    copy_out(m, mera::P(m->tmpv), Y);
+  });
+}
+
+int mera_retract(mera_t m, const void* const* X, double alpha, void* const* Xprime) {
+  if (!m || !X) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    copy_in(m, X, mera::P(m->dir2));
+    mera::make_geom(*m, mera::P(m->Wcur), mera::P(m->dir2), alpha, m->s);
+    mera::apply_retract(*m, mera::P(m->Wcur), mera::P(m->dir2), mera::P(m->Wtry), m->s);
+    if (Xprime) {
+      mera::copy(mera::P(m->tmpv), mera::P(m->dir2), m->total, m->s);
+      mera::apply_transport(*m, mera::P(m->Wcur), mera::P(m->dir2), mera::P(m->tmpv), m->s);
+      copy_out(m, mera::P(m->tmpv), Xprime);
+    }
+    MERA_CUDA(cudaStreamSynchronize(m->s));
+    std::swap(m->Wcur, m->Wtry);
+    m->ev[0].valid = m->ev[1].valid = false;
+    mera::clear_history(*m);
+  });
+}
+
+int mera_precondition(mera_t m, const void* const* X, void* const* Xt) {
+  if (!m || !X || !Xt) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    mera::Eval& E = m->ev[m->cur];
+    if (!E.valid) throw Error(MERA_ERR_ARG, "mera_precondition needs a prior mera_energy_grad");
+    copy_in(m, X, mera::P(m->tmpv));
+    mera::precondition(*m, E, mera::P(m->Wcur), mera::P(m->tmpv), mera::P(m->tmpv2), m->s);
+    copy_out(m, mera::P(m->tmpv2), Xt);
+  });
+}
+
+int mera_lbfgs_step(mera_t m, mera_iter_info* info) {
+  if (!m || !info) return MERA_ERR_ARG;
+  return wrap(m, [&] { mera::lbfgs_step(*m, info, m->s); });
+}
+
+int mera_cg_step(mera_t m, mera_iter_info* info) {
+  if (!m || !info) return MERA_ERR_ARG;
+  return wrap(m, [&] { mera::cg_step(*m, info, m->s); });
+}
+
+int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
+  if (!m || !o || !r) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    std::memset(r, 0, sizeof(*r));
+    mera::ensure_current(*m, m->s);
+    mera_iter_info info{};
+    double gn = std::sqrt(mera::inner(*m, mera::P(m->ev[m->cur].G), mera::P(m->ev[m->cur].G), m->s));
+    r->n_evals = 1;
+    for (int it = 0; it < o->maxiter && !(gn < o->gtol); ++it) {
+      if (o->method == 1) mera::cg_step(*m, &info, m->s);
+      else mera::lbfgs_step(*m, &info, m->s);
+      gn = info.gnorm;
+      r->iters++;
+      r->n_evals += info.n_evals;
+    }
+    r->energy = m->ev[m->cur].e;
+    r->gnorm = gn;
+    r->converged = gn < o->gtol;
+  });
+}
+
+size_t mera_footprint_bytes(const mera_config* cfg) {
+  if (!cfg) return 0;
+  // tensors (points, gradients, history) + level operators + Krylov + nets
+  std::vector<int64_t> dims{cfg->d_b};
+  for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
+  int64_t total = 0, ops = 0, nets = 0, scratch = 0;
+  for (size_t l = 0; l < dims.size(); ++l) {
+    const int64_t f = dims[l], c = l + 1 < dims.size() ? dims[l + 1] : dims[l];
+    total += f * f * f * f + f * f * c;
+    ops += 2 * mera::ipow(f, 6);
+    const int64_t node6 = std::max({mera::ipow(f, 6), mera::ipow(f, 4) * c * c, f * f * mera::ipow(c, 4)});
+    nets += 2 * (4 * node6 + 2 * mera::ipow(f, 4) * c);
+    scratch = std::max(scratch, mera::ipow(f, 6) * c * 2 + 6 * node6);
+  }
+  const int64_t nS = mera::ipow(cfg->chi, 6);
+  const int64_t krylov = nS * (cfg->krylov_dim + 3);
+  const int64_t tangents = total * (2 * std::max(1, cfg->lbfgs_m) + 10);
+  return sizeof(double) * (size_t)(tangents + ops + krylov + nets + scratch + 6 * nS);
+}
+
+int64_t mera_launch_count(mera_t m) { return m ? m->launches : 0; }
+
+const char* mera_strerror(int code) {
+  switch (code) {
+    case MERA_OK: return "ok";
+    case MERA_ERR_ARG: return "invalid argument";
+    case MERA_ERR_OOM: return "out of device memory";
+    case MERA_ERR_NONFINITE: return "non-finite energy or gradient";
+    case MERA_ERR_NOCONV: return "iteration did not converge";
+    case MERA_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case MERA_ERR_NOT_ISOMETRIC: return "tensor is not isometric";
+    case MERA_ERR_CUDA: return "CUDA runtime error";
+    case MERA_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+const char* mera_last_error(mera_t m) { return m ? m->err.c_str() : ""; }
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Contraction-tree executor for the binary MERA superoperators.
+#pragma once
+#include "common.h"
+#include <map>
+#include <memory>
+#include <string>
+
+namespace mera {
+
+// A dense tensor layout: leg labels with extents and element strides.
+struct TDesc {
+  std::vector<int> legs;
+  std::vector<int64_t> ext;
+  std::vector<int64_t> stride;
+  int64_t size() const {
+    int64_t s = 1;
+    for (auto e : ext) s *= e;
+    return s;
+  }
+  int find(int leg) const {
+    for (size_t i = 0; i < legs.size(); ++i)
+      if (legs[i] == leg) return (int)i;
+    return -1;
+  }
+};
+
+// Device-resident offset tables, deduplicated by content.
+class TablePool {
+ public:
+  const int64_t* get(const std::vector<int64_t>& host);
+  size_t bytes() const { return bytes_; }
+
+ private:
+  std::map<std::vector<int64_t>, DevBuf> tables_;
+  size_t bytes_ = 0;
+};
+
+// One pairwise contraction C = A x B, all index bookkeeping precomputed.
+struct GemmPlan {
+  GettCall proto;  // tables/strides/sizes; data pointers filled at run time
+  double flops() const { return 2.0 * proto.M * proto.N * proto.K; }
+};
+GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool);
+
+// Ascending network of one side (A_L or A_R) of one layer.  Node numbering:
+// 0..10 leaves (0 = operator; 1,3 = conj u; 2,5 = u; 4,7,9 = conj w;
+// 6,8,10 = w), 11..20 internal nodes N1..N10 (20 = root = the ascended
+// operator with legs [a b c A B C]).
+class SideNet {
+ public:
+  static constexpr int NLEAF = 11, NNODE = 21, ROOT = 20;
+  SideNet(char side, int64_t chi_f, int64_t chi_c, TablePool& pool);
+
+  // Size (elements) of each internal node value and of each adjoint.
+  int64_t node_size(int i) const { return desc_[i].size(); }
+  static int left(int i) { return kids_[i - NLEAF][0]; }
+  static int right(int i) { return kids_[i - NLEAF][1]; }
+
+  // Forward/backward plans.
+  const GemmPlan& fwd(int node) const { return fwd_[node - NLEAF]; }
+  const GemmPlan& bwd_left(int node) const { return bwdl_[node - NLEAF]; }
+  const GemmPlan& bwd_right(int node) const { return bwdr_[node - NLEAF]; }
+  double forward_flops() const;
+  char side() const { return side_; }
+
+  static const int kids_[10][2];
+
+ private:
+  char side_;
+  TDesc desc_[NNODE];
+  GemmPlan fwd_[10], bwdl_[10], bwdr_[10];
+};
+
+// Buffers bound to a SideNet for one evaluation.
+struct SideBufs {
+  const double* leaf[SideNet::NLEAF] = {};  // leaf values (operator, u, conj u, w, conj w)
+  double* val[SideNet::NNODE] = {};          // internal node values (root = output)
+  double* adj[SideNet::NNODE] = {};          // adjoints (root = seed)
+};
+
+// Subtrees that do not contain the operator leaf: N1, N4, N6, N9.
+void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s);
+// Operator-dependent forward pass N2, N3, N5, N7, N8, root.
+void side_forward(const SideNet& net, SideBufs& b, cudaStream_t s);
+// Reverse pass from the root adjoint.  need_op: adjoint of the operator
+// (descending map) into op_out (alpha_op, accumulated); need_env: adjoints of
+// the conjugated u/w copies accumulated into du/dw with alpha_env.
+void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out, double alpha_op,
+                   bool need_env, double* du, double* dw, double alpha_env, cudaStream_t s);
+
+}  // namespace mera

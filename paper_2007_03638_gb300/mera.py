@@ -1,0 +1,261 @@
+"""Python binding of libmera (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts arrays to
+pointers and back.  Arrays may be NumPy arrays (host memory) or torch
+tensors (host or CUDA); outputs are NumPy arrays unless ``device=True``, in
+which case they are CUDA torch tensors.  If the compiled library is missing
+the import fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmera.so")
+
+MERA_F64, MERA_C128 = 0, 1
+PREC_FP64, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
+
+ERRORS = {
+    -1: "MERA_ERR_ARG", -2: "MERA_ERR_OOM", -3: "MERA_ERR_NONFINITE", -4: "MERA_ERR_NOCONV",
+    -5: "MERA_ERR_DEVICE_TIMEOUT", -6: "MERA_ERR_NOT_ISOMETRIC", -7: "MERA_ERR_CUDA",
+    -8: "MERA_ERR_UNSUPPORTED",
+}
+
+
+class MeraError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("d_b", C.c_int), ("chi", C.c_int), ("n_trans", C.c_int), ("dtype", C.c_int),
+                ("prec", C.c_int), ("w_stiefel", C.c_int), ("precond", C.c_int),
+                ("krylov_dim", C.c_int), ("krylov_maxiter", C.c_int), ("krylov_tol", C.c_double),
+                ("recompute_env", C.c_int), ("lbfgs_m", C.c_int)]
+
+
+class IterInfo(C.Structure):
+    _fields_ = [("iter", C.c_int), ("energy", C.c_double), ("gnorm", C.c_double),
+                ("alpha", C.c_double), ("n_evals", C.c_int), ("ls_ok", C.c_int),
+                ("krylov_matvecs", C.c_int)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("method", C.c_int), ("maxiter", C.c_int), ("gtol", C.c_double)]
+
+
+class SolveResult(C.Structure):
+    _fields_ = [("iters", C.c_int), ("n_evals", C.c_int), ("energy", C.c_double),
+                ("gnorm", C.c_double), ("converged", C.c_int)]
+
+
+EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tensors",
+           "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_energy_grad",
+           "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
+           "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
+           "mera_launch_count", "mera_strerror", "mera_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmera.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmera.so not built ({path}); run paper_2007_03638_gb300.build.build()")
+    L = C.CDLL(path)
+    vpp = C.POINTER(C.c_void_p)
+    sig = {
+        "mera_config_default": (None, [C.POINTER(Config), C.c_int, C.c_int, C.c_int]),
+        "mera_create": (C.c_int, [C.POINTER(Config), C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+        "mera_destroy": (C.c_int, [C.c_void_p]),
+        "mera_num_tensors": (C.c_int, [C.c_void_p]),
+        "mera_tensor_shape": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "mera_set_tensors": (C.c_int, [C.c_void_p, vpp]),
+        "mera_get_tensors": (C.c_int, [C.c_void_p, vpp]),
+        "mera_energy_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), vpp, vpp]),
+        "mera_project": (C.c_int, [C.c_void_p, vpp, vpp]),
+        "mera_inner": (C.c_int, [C.c_void_p, vpp, vpp, C.POINTER(C.c_double)]),
+        "mera_transport": (C.c_int, [C.c_void_p, vpp, C.c_double, vpp]),
+        "mera_retract": (C.c_int, [C.c_void_p, vpp, C.c_double, vpp]),
+        "mera_precondition": (C.c_int, [C.c_void_p, vpp, vpp]),
+        "mera_lbfgs_step": (C.c_int, [C.c_void_p, C.POINTER(IterInfo)]),
+        "mera_cg_step": (C.c_int, [C.c_void_p, C.POINTER(IterInfo)]),
+        "mera_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
+        "mera_footprint_bytes": (C.c_size_t, [C.POINTER(Config)]),
+        "mera_launch_count": (C.c_int64, [C.c_void_p]),
+        "mera_strerror": (C.c_char_p, [C.c_int]),
+        "mera_last_error": (C.c_char_p, [C.c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def default_config(d_b, chi, n_trans, **kw) -> Config:
+    L = load()
+    cfg = Config()
+    L.mera_config_default(C.byref(cfg), d_b, chi, n_trans)
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def footprint_bytes(cfg: Config) -> int:
+    return int(load().mera_footprint_bytes(C.byref(cfg)))
+
+
+def _ptr(a):
+    """Data pointer of a contiguous float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("expected a C-contiguous float64 array")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _ptrs(arrs, keep):
+    out = (C.c_void_p * len(arrs))()
+    for i, a in enumerate(arrs):
+        if isinstance(a, np.ndarray) and (a.dtype != np.float64 or not a.flags.c_contiguous):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        out[i] = _ptr(a)
+    return out
+
+
+class Mera:
+    """One optimisation problem (a ``mera_t``) bound to a CUDA stream."""
+
+    def __init__(self, cfg: Config, h3, stream=None):
+        self.L = load()
+        self.cfg = cfg
+        h = np.ascontiguousarray(h3, dtype=np.float64) if isinstance(h3, np.ndarray) else h3
+        handle = C.c_void_p()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:
+                stream = 0
+        rc = self.L.mera_create(C.byref(cfg), C.c_void_p(_ptr(h)), C.c_void_p(stream), C.byref(handle))
+        if rc != 0:
+            raise MeraError(rc, self.L.mera_strerror(rc).decode())
+        self.h = handle
+        self.n = self.L.mera_num_tensors(self.h)
+        self.shapes = []
+        for i in range(self.n):
+            r, c = C.c_int64(), C.c_int64()
+            self.L.mera_tensor_shape(self.h, i, C.byref(r), C.byref(c))
+            self.shapes.append((r.value, c.value))
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MeraError(rc, self.L.mera_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mera_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _alloc(self, device):
+        if device:
+            import torch
+            return [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes]
+        return [np.empty(s) for s in self.shapes]
+
+    # ---- C ABI mirrors ------------------------------------------------------
+    def set_tensors(self, tensors):
+        keep = []
+        self._check(self.L.mera_set_tensors(self.h, _ptrs(tensors, keep)))
+
+    def get_tensors(self, device=False):
+        out = self._alloc(device)
+        keep = []
+        self._check(self.L.mera_get_tensors(self.h, _ptrs(out, keep)))
+        return out
+
+    def energy_grad(self, device=False, deriv=False):
+        e = C.c_double()
+        G = self._alloc(device)
+        keep = []
+        D = self._alloc(device) if deriv else None
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep),
+                                            _ptrs(D, keep) if deriv else None))
+        return (e.value, G, D) if deriv else (e.value, G)
+
+    def energy(self):
+        e = C.c_double()
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), None, None))
+        return e.value
+
+    def project(self, D, device=False):
+        G = self._alloc(device)
+        keep = []
+        self._check(self.L.mera_project(self.h, _ptrs(D, keep), _ptrs(G, keep)))
+        return G
+
+    def inner(self, X, Y):
+        out = C.c_double()
+        keep = []
+        self._check(self.L.mera_inner(self.h, _ptrs(X, keep), _ptrs(Y, keep), C.byref(out)))
+        return out.value
+
+    def transport(self, X, alpha, Y):
+        keep = []
+        Yc = [np.array(y, dtype=np.float64, copy=True) if isinstance(y, np.ndarray) else y.clone() for y in Y]
+        self._check(self.L.mera_transport(self.h, _ptrs(X, keep), float(alpha), _ptrs(Yc, keep)))
+        return Yc
+
+    def retract(self, X, alpha, want_xprime=False):
+        keep = []
+        Xp = self._alloc(False) if want_xprime else None
+        self._check(self.L.mera_retract(self.h, _ptrs(X, keep), float(alpha),
+                                        _ptrs(Xp, keep) if want_xprime else None))
+        return Xp
+
+    def precondition(self, X):
+        keep = []
+        out = self._alloc(False)
+        self._check(self.L.mera_precondition(self.h, _ptrs(X, keep), _ptrs(out, keep)))
+        return out
+
+    def lbfgs_step(self):
+        info = IterInfo()
+        self._check(self.L.mera_lbfgs_step(self.h, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in IterInfo._fields_}
+
+    def cg_step(self):
+        info = IterInfo()
+        self._check(self.L.mera_cg_step(self.h, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in IterInfo._fields_}
+
+    def solve(self, maxiter=100, gtol=1e-6, method=0):
+        o = SolveOpts(method, maxiter, gtol)
+        r = SolveResult()
+        self._check(self.L.mera_solve(self.h, C.byref(o), C.byref(r)))
+        return {f: getattr(r, f) for f, _ in SolveResult._fields_}
+
+    def launch_count(self):
+        return int(self.L.mera_launch_count(self.h))

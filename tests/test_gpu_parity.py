@@ -1,0 +1,174 @@
+"""GPU (CUDA, FP64 path) against the CPU FP64 oracle, element by element,
+through the C ABI.  Tolerance: 1e-12 relative (normwise per tensor) for the
+FP64 path."""
+import numpy as np
+import pytest
+
+from oracle import geometry as geo
+from oracle import mera as om
+from oracle import optim as oo
+from paper_2007_03638_gb300 import inputs as inp
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def gm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03638_gb300 import build as b
+    b.build()
+    from paper_2007_03638_gb300 import mera
+    return mera
+
+
+def _ham(d_b, kind="ising", seed=0):
+    if kind == "ising":
+        bond = inp.ising_bond(1.0)
+    elif kind == "xxz":
+        bond = inp.xxz_bond(1.0)
+    else:
+        rng = np.random.default_rng(seed)
+        a = rng.standard_normal((d_b**3, d_b**3))
+        return 0.5 * (a + a.T)
+    return inp.three_site_blocked(bond) if d_b == 4 else inp.three_site_unblocked(bond)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _flat(us, ws):
+    return [t for p in zip(us, ws) for t in p]
+
+
+CASES = [
+    (4, 4, 2, "ising", 0),   # config-1 shapes
+    (4, 4, 2, "xxz", 3),
+    (2, 3, 2, "ising", 1),   # ragged tiles: dims 2,3,3
+    (3, 5, 2, "random", 2),  # odd dims 3,5,5
+    (4, 8, 3, "ising", 4),   # config-2 chi=8
+]
+
+
+@pytest.mark.parametrize("d_b,chi,L,kind,seed", CASES)
+def test_energy_grad_parity(gm, d_b, chi, L, kind, seed):
+    us, ws = inp.random_mera(d_b, chi, L, seed=seed)
+    h3 = _ham(d_b, kind, seed)
+    m = gm.Mera(gm.default_config(d_b, chi, L), h3)
+    m.set_tensors(_flat(us, ws))
+    e, G, D = m.energy_grad(deriv=True)
+    e_ref, ds, _ = om.energy_grad(h3, us, ws)
+    assert abs(e - e_ref) <= TOL * max(1.0, abs(e_ref)), (e, e_ref)
+    pt = _flat(us, ws)
+    for i, (W, d_ref) in enumerate(zip(pt, ds)):
+        kind_i = geo.STIEFEL if i % 2 == 0 else geo.GRASSMANN
+        g_ref = geo.project(W, d_ref, kind_i)
+        assert _rel(D[i], d_ref) < TOL, (i, _rel(D[i], d_ref))
+        if np.abs(g_ref).max() > 1e-13:
+            assert np.abs(G[i] - g_ref).max() < TOL * np.abs(d_ref).max(), i
+    # second call reuses the Krylov warm starts: same result
+    e2, G2 = m.energy_grad()
+    assert abs(e2 - e) <= 1e-13 * max(1, abs(e))
+    assert max(np.abs(a - b).max() for a, b in zip(G, G2)) < 1e-12 * max(np.abs(g).max() for g in G)
+
+
+@pytest.mark.slow
+def test_energy_grad_parity_chi12(gm):
+    """Config-2 chi=12 (3 transition layers), one seed."""
+    us, ws = inp.random_mera(4, 12, 3, seed=5)
+    h3 = _ham(4)
+    m = gm.Mera(gm.default_config(4, 12, 3), h3)
+    m.set_tensors(_flat(us, ws))
+    e, G, D = m.energy_grad(deriv=True)
+    e_ref, ds, _ = om.energy_grad(h3, us, ws)
+    assert abs(e - e_ref) <= TOL * abs(e_ref)
+    for i in range(len(ds)):
+        assert _rel(D[i], ds[i]) < TOL, i
+
+
+def test_product_state(gm):
+    """Closed form: u = 1, w|k> = |k>|0> gives e = 2 <00|bond|00> per bottom site."""
+    us, ws = inp.product_state_mera(4, 2)
+    m = gm.Mera(gm.default_config(4, 4, 2), _ham(4, "xxz"))
+    m.set_tensors(_flat(us, ws))
+    assert abs(m.energy() / 2 - 1.0) < 1e-12
+
+
+def test_not_isometric_rejected(gm):
+    us, ws = inp.random_mera(4, 4, 2, seed=0)
+    m = gm.Mera(gm.default_config(4, 4, 2), _ham(4))
+    bad = _flat(us, ws)
+    bad[1] = bad[1] * 1.01
+    with pytest.raises(gm.MeraError) as ex:
+        m.set_tensors(bad)
+    assert ex.value.code == -6
+    m.set_tensors(_flat(us, ws))  # object still usable
+    assert np.isfinite(m.energy())
+
+
+def test_geometry_parity(gm):
+    us, ws = inp.random_mera(4, 4, 2, seed=7)
+    pt = _flat(us, ws)
+    h3 = _ham(4)
+    m = gm.Mera(gm.default_config(4, 4, 2), h3)
+    m.set_tensors(pt)
+    rng = np.random.default_rng(1)
+    kinds = [geo.STIEFEL if i % 2 == 0 else geo.GRASSMANN for i in range(len(pt))]
+    Draw = [rng.standard_normal(t.shape) for t in pt]
+    X = m.project(Draw)
+    X_ref = [geo.project(W, d, k) for W, d, k in zip(pt, Draw, kinds)]
+    for a, b in zip(X, X_ref):
+        assert np.abs(a - b).max() < 1e-13
+    Y = [geo.project(W, rng.standard_normal(W.shape), k) for W, k in zip(pt, kinds)]
+    assert abs(m.inner(X, Y) - geo.inner(X_ref, Y)) < 1e-12 * abs(geo.inner(X_ref, Y))
+    alpha = 0.3
+    TY = m.transport(X_ref, alpha, Y)
+    for W, x, y, ty in zip(pt, X_ref, Y, TY):
+        assert np.abs(ty - geo.transport(W, x, alpha, y)).max() < 1e-12
+    # preconditioner with the density matrices of this point
+    e, G = m.energy_grad()
+    e_ref, ds, info = om.energy_grad(h3, us, ws)
+    rv = om.tensor_density_matrices(info["rho"], ws)
+    Gr = [geo.project(W, d, k) for W, d, k in zip(pt, ds, kinds)]
+    deltas = [float(np.linalg.norm(g)) for g in Gr]
+    Xt = m.precondition(X_ref)
+    for W, x, r, dl, k, xt in zip(pt, X_ref, rv, deltas, kinds, Xt):
+        ref = geo.precondition(W, x, r, dl, k)
+        assert np.abs(xt - ref).max() < 1e-11 * max(1, np.abs(ref).max())
+    Xp = m.retract(X_ref, alpha, want_xprime=True)
+    Wn = m.get_tensors()
+    for W, x, wn, xp in zip(pt, X_ref, Wn, Xp):
+        assert np.abs(wn - geo.polar(geo.retract(W, x, alpha))).max() < 1e-12
+        assert np.abs(xp - geo.transport(W, x, alpha, x)).max() < 1e-12
+        assert np.abs(wn.T @ wn - np.eye(wn.shape[1])).max() < 1e-14
+
+
+def test_lbfgs_matches_oracle_trajectory(gm):
+    """Config-1 shapes: the first L-BFGS iterations of the GPU follow the
+    oracle's energies (same starting point, same algorithm)."""
+    us, ws = inp.random_mera(4, 4, 2, seed=0)
+    h3 = _ham(4)
+    m = gm.Mera(gm.default_config(4, 4, 2), h3)
+    m.set_tensors(_flat(us, ws))
+    got = [m.lbfgs_step() for _ in range(8)]
+    prob = oo.MeraProblem(h3)
+    _, _, hist = oo.lbfgs(prob, _flat(us, ws), m=8, maxiter=9)
+    ref = [h["energy"] for h in hist[1:9]]
+    for g, r in zip(got, ref):
+        assert abs(g["energy"] - r) < 1e-9 * abs(r), (g, r)
+    # isometry kept
+    for t in m.get_tensors():
+        assert np.abs(t.T @ t - np.eye(t.shape[1])).max() < 1e-13
+
+
+def test_cg_decreases(gm):
+    us, ws = inp.random_mera(4, 4, 2, seed=2)
+    m = gm.Mera(gm.default_config(4, 4, 2), _ham(4, "xxz"))
+    m.set_tensors(_flat(us, ws))
+    e0 = m.energy()
+    es = [m.cg_step()["energy"] for _ in range(6)]
+    assert es[-1] < e0
+    assert all(b <= a + 1e-12 for a, b in zip(es, es[1:]))
