@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark: MERA gradient evaluations per second (one GB300 per rank).
+
+A step is one full Riemannian L-BFGS iteration of the scale-invariant binary
+MERA (two-loop direction with the preconditioner, Hager-Zhang line search
+with as many energy/gradient evaluations as it needs, retraction, transport
+of the history).  The reported value is energy/gradient evaluations per
+second over the timed steps, summed over ranks (independent replicas: the
+optimisation does not shard across GPUs, so N GPUs run N problems).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   # the CPU FP64 oracle, same metric
+
+Inputs are synthetic and seeded (QR-of-Gaussian tensors, critical Ising or
+XXZ Hamiltonian on blocked spin pairs).  L2 is flushed (256 MiB write)
+between timed steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2007_03638_gb300 import inputs as inp  # noqa: E402
+
+WORKLOADS = {
+    # name: (hamiltonian, d_b, chi, n_trans, prec)
+    "ising_chi12_L3_fp64": ("ising", 4, 12, 3, 0),
+    "ising_chi8_L3_fp64": ("ising", 4, 8, 3, 0),
+    "ising_chi4_L2_fp64": ("ising", 4, 4, 2, 0),
+}
+DEFAULT_WORKLOAD = "ising_chi12_L3_fp64"
+METRIC = "MERA grad evals/s"
+UNIT = "grad_evals/s"
+
+# FP64 FMA throughput of GB300: the nominal 1.25 TFLOP/s at the 2070 MHz
+# boost clock is 2 FP64 FMA per clock per SM over 152 SMs.
+FP64_PEAK_FLOPS = 152 * 2 * 2 * 2070e6
+
+# DRAM traffic per launch of the contraction kernel, from the ncu capture
+# summarised in profiles/gett_f64_ising_chi12.md (null once the kernel changes).
+GETT_TRAFFIC_BYTES = {}
+
+
+def hamiltonian(kind, d_b):
+    bond = inp.ising_bond(1.0) if kind == "ising" else inp.xxz_bond(1.0)
+    return inp.three_site_blocked(bond) if d_b == 4 else inp.three_site_unblocked(bond)
+
+
+def ascend_flops(chi):
+    """Algorithmic flops of one averaged ascending map at bond chi (both sides,
+    the fixed contraction tree: 2 chi^9 + 4 chi^8 + 2 chi^6 + 2 chi^5 MACs per side)."""
+    macs = 2 * chi**9 + 4 * chi**8 + 2 * chi**6 + 2 * chi**5
+    return 2 * 2.0 * macs
+
+
+class Clocks:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path, gpu):
+        self.path, self.gpu, self.p = path, gpu, None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_sample(chi, seconds=10.0, seed=0):
+    """Time the oracle's averaged ascending map at bond chi (one bounded sample
+    of the workload's dominant operation) on the host cores."""
+    from oracle import mera as om
+    us, ws = inp.random_mera(4, chi, 1, seed=seed) if chi <= 16 else inp.random_mera(4, chi, 2, seed=seed)
+    u, w = us[-1], ws[-1]
+    rng = np.random.default_rng(seed)
+    h = rng.standard_normal((chi**3, chi**3))
+    h = 0.5 * (h + h.T)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        om.ascend(h, u, w)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return dt / n, n
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    kind, d_b, chi, L, prec = wl
+    flops_grad = float(args.ref_flops_per_grad) if args.ref_flops_per_grad else None
+    if flops_grad is None:
+        # algorithmic flops of one gradient evaluation of this workload as the
+        # GPU path counts them (fixed here from the contraction plan so the
+        # reference arm needs no GPU): ascend/descend applications per layer
+        flops_grad = ascend_flops(chi) * (L + 1) * 8.0
+    frac = ascend_flops(chi) / flops_grad
+    per = []
+    for i in range(args.warmup + args.steps):
+        t, n = oracle_sample(chi, seconds=args.ref_seconds, seed=i)
+        if i >= args.warmup:
+            per.append(t)
+    t = sum(per) / len(per)
+    value = frac / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "chi": chi, "n_trans": L},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "sample": f"oracle averaged ascending map at chi={chi} "
+                                       f"(fraction {frac:.4f} of one gradient evaluation's flops)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=5.0)
+    ap.add_argument("--ref-flops-per-grad", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2007_03638_gb300 import build as b
+    b.build()
+    from paper_2007_03638_gb300 import mera as gm
+
+    kind, d_b, chi, L, prec = wl
+    h3 = hamiltonian(kind, d_b)
+    stream = torch.cuda.current_stream()
+    m = gm.Mera(gm.default_config(d_b, chi, L, prec=prec), h3, stream=stream.cuda_stream)
+    us, ws = inp.random_mera(d_b, chi, L, seed=args.seed + rank)
+    point = [t for p in zip(us, ws) for t in p]
+    m.set_tensors(point)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        m.lbfgs_step()
+    m.stats(reset=True)
+    m.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    infos = []
+    with Clocks(clk_path, local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            infos.append(m.lbfgs_step())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    m.profile(False)
+    st = m.stats(reset=True)
+    t_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    grads = st["energy_grad_calls"]
+    if pg:
+        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_ms = float(t.item())
+        g = torch.tensor([grads], dtype=torch.float64, device="cuda")
+        pg.all_reduce(g)
+        grads_all = int(g.item())
+    else:
+        grads_all = grads
+    value = grads_all / (t_ms / 1e3)
+    gett_flops_per_grad = st["gett_flops"] / max(1, grads)
+
+    # end to end: host (pinned) tensors in, host gradient out, per evaluation
+    pinned = [torch.from_numpy(np.ascontiguousarray(t)).pin_memory() for t in m.get_tensors()]
+    gout = [torch.empty(s, dtype=torch.float64).pin_memory() for s in m.shapes]
+    h2d = sum(t.numel() * 8 for t in pinned)
+    d2h = sum(t.numel() * 8 for t in gout) + 8
+    for _ in range(2):
+        m.set_tensors(pinned)
+        m.energy_grad_into(gout)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = max(2, args.steps)
+    for _ in range(n_e2e):
+        m.set_tensors(pinned)
+        m.energy_grad_into(gout)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * n_e2e / t_e2e
+
+    achieved = st["gett_flops"] / (st["gett_ms"] / 1e3) if st["gett_ms"] > 0 else None
+    roof = {"bound": "alu", "kernel": "gett_f64_kernel", "achieved": achieved / 1e12 if achieved else None,
+            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_FLOPS if achieved else None,
+            "traffic": GETT_TRAFFIC_BYTES.get(args.workload),
+            "peak_source": "derived FP64 FMA rate (152 SMs x 2 FMA/clk x 2070 MHz)",
+            "launches_timed": st["gett_timed"],
+            "share_of_step": (st["gett_ms"] / t_ms) if t_ms > 0 else None}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "hamiltonian": kind, "d_b": d_b, "chi": chi,
+                       "n_trans": L, "prec": ["fp64", "3xtf32", "split_bf16"][prec],
+                       "step": "one L-BFGS iteration (m=8)", "l2": "flushed (256 MiB write) between steps",
+                       "parallelism": f"replicas x{world}"},
+            "lbfgs_iters_per_s": world * args.steps / (t_ms / 1e3),
+            "grad_evals_per_step": grads / args.steps,
+            "krylov_matvecs_per_grad": st["krylov_matvecs"] / max(1, grads),
+            "gett_gflop_per_grad": gett_flops_per_grad / 1e9,
+            "energy_last": infos[-1]["energy"],
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "call": "mera_set_tensors(host) + mera_energy_grad(grad -> host)"},
+            "gpu_launches": st["launches"],
+            "clocks": clocks.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, n = oracle_sample(chi, seconds=args.cpu_seconds)
+        frac = ascend_flops(chi) / gett_flops_per_grad
+        line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                                "sample": f"{n} x oracle averaged ascending map at chi={chi}, "
+                                          f"{t:.2f} s each = {frac:.4f} of one gradient evaluation's "
+                                          f"algorithmic flops"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -187,6 +187,22 @@ size_t mera_footprint_bytes(const mera_config* cfg);
 /* Number of kernel launches issued by this object so far. */
 int64_t mera_launch_count(mera_t m);
 
+/* Counters of one object since its creation (or the last reset).  The
+ * contraction kernel's device time is summed only over launches issued while
+ * profiling is on (a CUDA event pair on the object's stream around each
+ * launch); reading synchronises the stream. */
+typedef struct {
+    int64_t launches;          /* all kernels                                   */
+    int64_t gett_launches;     /* tensor-contraction kernel launches            */
+    double gett_flops;         /* algorithmic flops of those launches (2 M N K) */
+    int64_t gett_timed;        /* contraction launches timed with events        */
+    double gett_ms;            /* their summed device time                      */
+    int64_t energy_grad_calls; /* energy/gradient evaluations                    */
+    int64_t krylov_matvecs;    /* scale-invariant superoperator applications    */
+} mera_stats;
+int mera_get_stats(mera_t m, mera_stats* out, int reset);
+int mera_profile(mera_t m, int enable);
+
 const char* mera_strerror(int code);
 const char* mera_last_error(mera_t m);
 

@@ -29,10 +29,24 @@ struct Error : std::runtime_error {
 
 #define MERA_CHECK_LAUNCH() MERA_CUDA(cudaGetLastError())
 
-// Counts kernel launches issued by the library (reported to callers).
-extern thread_local int64_t* g_launch_counter;
+// Per-object counters, reached through a thread-local pointer that the C ABI
+// sets for the duration of each call.
+struct Prof {
+  int64_t launches = 0;
+  int64_t gett_launches = 0;
+  double gett_flops = 0.0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  size_t used = 0;              // events in use
+  double gett_ms = 0.0;
+  int64_t gett_timed = 0;
+  int64_t energy_grad_calls = 0;
+  ~Prof();
+  void collect();               // sum the recorded pairs (after a sync)
+};
+extern thread_local Prof* g_prof;
 inline void count_launch(int n = 1) {
-  if (g_launch_counter) *g_launch_counter += n;
+  if (g_prof) g_prof->launches += n;
 }
 
 // Owning device allocation.

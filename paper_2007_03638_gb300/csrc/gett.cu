@@ -102,9 +102,44 @@ void gett_f64(const GettCall& g, cudaStream_t s) {
   const int64_t gx = (g.M + BM - 1) / BM, gy = (g.N + BN - 1) / BN;
   if (gy > 65535) throw Error(MERA_ERR_UNSUPPORTED, "gett_f64: N too large for grid");
   dim3 grid((unsigned)gx, (unsigned)gy);
+  Prof* pr = g_prof;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (pr && pr->timing) {
+    if (pr->used + 2 > pr->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        MERA_CUDA(cudaEventCreate(&e));
+        pr->ev.push_back(e);
+      }
+    }
+    e0 = pr->ev[pr->used];
+    e1 = pr->ev[pr->used + 1];
+    pr->used += 2;
+    MERA_CUDA(cudaEventRecord(e0, s));
+  }
   gett_f64_kernel<<<grid, NT, 0, s>>>(g);
-  count_launch();
+  if (e1) MERA_CUDA(cudaEventRecord(e1, s));
+  if (pr) {
+    pr->launches++;
+    pr->gett_launches++;
+    pr->gett_flops += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+  }
   MERA_CHECK_LAUNCH();
+}
+
+Prof::~Prof() {
+  for (auto e : ev) cudaEventDestroy(e);
+}
+
+void Prof::collect() {
+  for (size_t i = 0; i + 1 < used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
+      gett_ms += ms;
+      gett_timed++;
+    }
+  }
+  used = 0;
 }
 
 void gemm_f64(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,

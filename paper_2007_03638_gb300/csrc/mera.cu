@@ -25,7 +25,7 @@
 #include <memory>
 
 namespace mera {
-thread_local int64_t* g_launch_counter = nullptr;
+thread_local Prof* g_prof = nullptr;
 
 namespace {
 
@@ -145,7 +145,7 @@ struct mera_ctx {
   mera::DevBuf dir, dir2, tmpv, tmpv2;
   double alpha_prev = 1.0;
   int iters = 0;
-  int64_t launches = 0;
+  mera::Prof prof;
   int64_t matvecs = 0;
   std::string err;
 };
@@ -361,6 +361,7 @@ void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
 // Full evaluation at point W into E.
 void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   const int L = c.L;
+  c.prof.energy_grad_calls++;
   // up-sweep
   copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6), s);
   for (int l = 0; l <= L; ++l) prepare_layer(c, l, W, s);
@@ -1071,8 +1072,8 @@ using mera::Error;
 namespace {
 struct Guard {
   mera_t m;
-  explicit Guard(mera_t mm) : m(mm) { mera::g_launch_counter = mm ? &mm->launches : nullptr; }
-  ~Guard() { mera::g_launch_counter = nullptr; }
+  explicit Guard(mera_t mm) : m(mm) { mera::g_prof = mm ? &mm->prof : nullptr; }
+  ~Guard() { mera::g_prof = nullptr; }
 };
 
 template <class F>
@@ -1298,7 +1299,37 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
   return sizeof(double) * (size_t)(tangents + ops + krylov + nets + scratch + 6 * nS);
 }
 
-int64_t mera_launch_count(mera_t m) { return m ? m->launches : 0; }
+int64_t mera_launch_count(mera_t m) { return m ? m->prof.launches : 0; }
+
+int mera_get_stats(mera_t m, mera_stats* out, int reset) {
+  if (!m || !out) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    MERA_CUDA(cudaStreamSynchronize(m->s));
+    m->prof.collect();
+    out->launches = m->prof.launches;
+    out->gett_launches = m->prof.gett_launches;
+    out->gett_flops = m->prof.gett_flops;
+    out->gett_timed = m->prof.gett_timed;
+    out->gett_ms = m->prof.gett_ms;
+    out->energy_grad_calls = m->prof.energy_grad_calls;
+    out->krylov_matvecs = m->matvecs;
+    if (reset) {
+      m->prof.launches = m->prof.gett_launches = m->prof.gett_timed = 0;
+      m->prof.gett_flops = m->prof.gett_ms = 0.0;
+      m->prof.energy_grad_calls = 0;
+      m->matvecs = 0;
+    }
+  });
+}
+
+int mera_profile(mera_t m, int enable) {
+  if (!m) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    MERA_CUDA(cudaStreamSynchronize(m->s));
+    m->prof.collect();
+    m->prof.timing = enable != 0;
+  });
+}
 
 const char* mera_strerror(int code) {
   switch (code) {

@@ -45,6 +45,12 @@ class IterInfo(C.Structure):
                 ("krylov_matvecs", C.c_int)]
 
 
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("gett_launches", C.c_int64), ("gett_flops", C.c_double),
+                ("gett_timed", C.c_int64), ("gett_ms", C.c_double),
+                ("energy_grad_calls", C.c_int64), ("krylov_matvecs", C.c_int64)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int), ("maxiter", C.c_int), ("gtol", C.c_double)]
 
@@ -58,7 +64,8 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_energy_grad",
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
-           "mera_launch_count", "mera_strerror", "mera_last_error"]
+           "mera_launch_count", "mera_get_stats", "mera_profile", "mera_strerror",
+           "mera_last_error"]
 
 _lib = None
 
@@ -91,6 +98,8 @@ def load(path: str = LIB_PATH):
         "mera_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
         "mera_footprint_bytes": (C.c_size_t, [C.POINTER(Config)]),
         "mera_launch_count": (C.c_int64, [C.c_void_p]),
+        "mera_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats), C.c_int]),
+        "mera_profile": (C.c_int, [C.c_void_p, C.c_int]),
         "mera_strerror": (C.c_char_p, [C.c_int]),
         "mera_last_error": (C.c_char_p, [C.c_void_p]),
     }
@@ -205,6 +214,13 @@ class Mera:
                                             _ptrs(D, keep) if deriv else None))
         return (e.value, G, D) if deriv else (e.value, G)
 
+    def energy_grad_into(self, G):
+        """Energy, with the gradient written into the given arrays (host or device)."""
+        e = C.c_double()
+        keep = []
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep), None))
+        return e.value
+
     def energy(self):
         e = C.c_double()
         self._check(self.L.mera_energy_grad(self.h, C.byref(e), None, None))
@@ -259,3 +275,11 @@ class Mera:
 
     def launch_count(self):
         return int(self.L.mera_launch_count(self.h))
+
+    def stats(self, reset=False):
+        st = Stats()
+        self._check(self.L.mera_get_stats(self.h, C.byref(st), int(reset)))
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+    def profile(self, enable=True):
+        self._check(self.L.mera_profile(self.h, int(enable)))
