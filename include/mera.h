@@ -203,6 +203,26 @@ typedef struct {
 int mera_get_stats(mera_t m, mera_stats* out, int reset);
 int mera_profile(mera_t m, int enable);
 
+/* Allocation-free batched dot products, for callers that cannot allocate
+ * device memory (a host application that owns the whole GPU memory and
+ * gives the library no allocator, or code that must not trigger the device
+ * synchronisation of cudaMalloc).  Needs no mera_t; calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   out[i] = sum_{j<n} X[i*ldx + j] * y[j],   i < k,
+ * in the same fixed reduction order as the library's own dot products.
+ * X, y: device pointers (doubles); out: host or device pointer to k doubles;
+ * stream: a cudaStream_t (NULL = default stream); returns after the results
+ * are in out.  Limits: 1 <= k <= 32 (MERA_ERR_ARG beyond), ldx >= n if k > 1.
+ * Scratch: a fixed file-scope device array of 32*608+32 doubles (about
+ * 152 KiB) held by every GPU that loads the library until exit.  The first
+ * call on a device looks up that array's device address (make it before any
+ * stream capture).  All calls share the array and it keeps the last call's
+ * partial sums: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  The paper has no
+ * counterpart of this entry point. */
+int mera_dots_noalloc(const double* X, int64_t ldx, int k, const double* y, int64_t n, double* out,
+                      void* stream);
+
 const char* mera_strerror(int code);
 const char* mera_last_error(mera_t m);
 

@@ -3,6 +3,7 @@
 // pass in a fixed order), axpy-type updates, symmetrisation and the partial
 // traces that give the per-tensor density matrices.
 #include "common.h"
+#include <mutex>
 
 namespace mera {
 
@@ -260,3 +261,57 @@ int check_finite(const double* x, int64_t n, cudaStream_t s) {
 }
 
 }  // namespace mera
+
+// ------------------------------------------- allocation-free dot products --
+// Some callers cannot allocate device memory at all (a host application that
+// owns every byte of the GPU and hands out no allocator, code running where
+// cudaMalloc's implicit device synchronisation is not allowed).  For them
+// mera_dots_noalloc computes the same deterministic batched dot products as
+// the library's reducer without a mera_t and without allocating: the
+// per-block partial sums live in this file-scope device array, which every
+// GPU that loads the library holds until the process exits.
+namespace mera {
+namespace {
+constexpr int NOALLOC_MAX_K = 32;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_K * RBLOCKS + NOALLOC_MAX_K];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+}  // namespace mera
+
+extern "C" int mera_dots_noalloc(const double* X, int64_t ldx, int k, const double* y, int64_t n,
+                                 double* out, void* stream) {
+  using namespace mera;
+  if (!X || !y || !out || k < 1 || n < 0) return MERA_ERR_ARG;
+  if (k > NOALLOC_MAX_K) return MERA_ERR_ARG;
+  if (k > 1 && ldx < n) return MERA_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MERA_ERR_CUDA;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MERA_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  {
+    // one-time set-up per device, with that device current: host code holds
+    // only a stand-in for the array, so its device address is looked up
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MERA_ERR_CUDA;
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  double* partial = static_cast<double*>(base);
+  double* result = partial + (int64_t)NOALLOC_MAX_K * RBLOCKS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = (int)std::min<int64_t>(RBLOCKS, std::max<int64_t>(1, (n + RT - 1) / RT));
+  // every partial slot read below is written by this call, so nothing needs clearing
+  dots_partial<<<dim3(nb, k), RT, 0, s>>>(X, ldx, y, n, partial);
+  finish_partial<<<k, RT, 0, s>>>(partial, nb, result);
+  if (cudaGetLastError() != cudaSuccess) return MERA_ERR_CUDA;
+  if (cudaMemcpyAsync(out, result, sizeof(double) * k, cudaMemcpyDefault, s) != cudaSuccess)
+    return MERA_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return MERA_ERR_CUDA;
+  return MERA_OK;
+}
+

@@ -64,8 +64,8 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_energy_grad",
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
-           "mera_launch_count", "mera_get_stats", "mera_profile", "mera_strerror",
-           "mera_last_error"]
+           "mera_launch_count", "mera_get_stats", "mera_profile", "mera_dots_noalloc",
+           "mera_strerror", "mera_last_error"]
 
 _lib = None
 
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
         "mera_launch_count": (C.c_int64, [C.c_void_p]),
         "mera_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats), C.c_int]),
         "mera_profile": (C.c_int, [C.c_void_p, C.c_int]),
+        "mera_dots_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                        C.c_void_p, C.c_void_p]),
         "mera_strerror": (C.c_char_p, [C.c_int]),
         "mera_last_error": (C.c_char_p, [C.c_void_p]),
     }
@@ -122,6 +124,20 @@ def default_config(d_b, chi, n_trans, **kw) -> Config:
 
 def footprint_bytes(cfg: Config) -> int:
     return int(load().mera_footprint_bytes(C.byref(cfg)))
+
+
+def dots_noalloc(X, y, k, n, ldx, out, stream=0):
+    """Allocation-free batched dot products (see mera_dots_noalloc in mera.h):
+    X, y device arrays (torch CUDA tensors or raw pointers), out: host or device
+    array of k doubles.  Raises MeraError on a bad size."""
+    L = load()
+    xp = X if isinstance(X, int) else _ptr(X)
+    yp = y if isinstance(y, int) else _ptr(y)
+    rc = L.mera_dots_noalloc(C.c_void_p(xp), int(ldx), int(k), C.c_void_p(yp), int(n),
+                             C.c_void_p(_ptr(out)), C.c_void_p(stream))
+    if rc != 0:
+        raise MeraError(rc, L.mera_strerror(rc).decode())
+    return out
 
 
 def _ptr(a):
