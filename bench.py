@@ -187,6 +187,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--ref-flops-per-grad", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--energy-once", action="store_true",
+                    help="set the seeded point, run one energy/gradient evaluation and exit (profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -213,6 +215,9 @@ def main():
     us, ws = inp.random_mera(d_b, chi, L, seed=args.seed + rank)
     point = [t for p in zip(us, ws) for t in p]
     m.set_tensors(point)
+    if args.energy_once:
+        print(json.dumps({"workload": args.workload, "energy": m.energy(), "launches": m.launch_count()}))
+        return
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         m.lbfgs_step()

@@ -203,6 +203,16 @@ typedef struct {
 int mera_get_stats(mera_t m, mera_stats* out, int reset);
 int mera_profile(mera_t m, int enable);
 
+/* C = A B for row-major double matrices A (M x K), B (K x N), C (M x N) on
+ * the device, with the contraction arithmetic of the given mera_prec:
+ * FP64 (the FP64 contraction kernel) or the tensor-core kernel with 3xTF32 /
+ * split-BF16 operands and FP32 accumulation.  Exposes the arithmetic of each
+ * mode for checking (Sec. 4 contractions are built from this product);
+ * allocates its temporary operand planes.  MERA_ERR_DEVICE_TIMEOUT if a
+ * bounded device-side wait expired. */
+int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C,
+              void* stream);
+
 /* Allocation-free batched dot products, for callers that cannot allocate
  * device memory (a host application that owns the whole GPU memory and
  * gives the library no allocator, or code that must not trigger the device

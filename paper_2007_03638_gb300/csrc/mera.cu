@@ -17,6 +17,7 @@
 //   optimiser     L-BFGS two-loop / Hager-Zhang CG, Hager-Zhang line search
 #include "common.h"
 #include "tn.h"
+#include "tc_gemm.h"
 
 #include <algorithm>
 #include <cmath>
@@ -1347,5 +1348,38 @@ const char* mera_strerror(int code) {
 }
 
 const char* mera_last_error(mera_t m) { return m ? m->err.c_str() : ""; }
+
+int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C,
+              void* stream) {
+  if (M < 0 || N < 0 || K < 1 || !A || !B || !C) return MERA_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return wrap(nullptr, [&] {
+    if (prec == MERA_PREC_FP64) {
+      mera::gemm_f64('N', 'N', M, N, K, 1.0, A, K, B, N, 0.0, C, N, s);
+      MERA_CUDA(cudaStreamSynchronize(s));
+      return;
+    }
+    if (prec != MERA_PREC_3XTF32 && prec != MERA_PREC_SPLIT_BF16) throw Error(MERA_ERR_ARG, "bad precision");
+    const int kind = prec == MERA_PREC_3XTF32 ? mera::tc::KIND_TF32 : mera::tc::KIND_BF16;
+    const int elem = kind == mera::tc::KIND_TF32 ? 4 : 2;
+    const int64_t Kp = mera::tc::padded_k(K, kind);
+    const int64_t Mp = mera::tc::round_up(std::max<int64_t>(M, 1), 128), Np = mera::tc::round_up(std::max<int64_t>(N, 1), 128);
+    mera::DevBuf ah(elem * Mp * Kp), al(elem * Mp * Kp), bh(elem * Np * Kp), bl(elem * Np * Kp), err(sizeof(int));
+    MERA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    mera::tc::pack_split(A, true, nullptr, K, nullptr, 1, M, K, Mp, Kp, kind, ah.p, al.p, s);
+    mera::tc::pack_split(B, true, nullptr, 1, nullptr, N, N, K, Np, Kp, kind, bh.p, bl.p, s);
+    mera::tc::TcEpilogue ep;
+    ep.C = C;
+    ep.c_f64 = 1;
+    ep.cms = N;
+    ep.cns = 1;
+    ep.err = err.as<int>();
+    mera::tc::gemm_packed(kind, M, N, Kp, ah.p, al.p, Mp, bh.p, bl.p, Np, ep, s);
+    int e = 0;
+    MERA_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MERA_CUDA(cudaStreamSynchronize(s));
+    if (e) throw Error(MERA_ERR_DEVICE_TIMEOUT, "tensor-core GEMM: a bounded wait expired");
+  });
+}
 
 }  // extern "C"

@@ -1,0 +1,404 @@
+// Tensor-core contraction kernel for the mixed-precision path (sm_103a).
+//
+// C[cm[m] + cn[n]] = alpha * sum_k A[m,k] B[k,n] + beta * C[..]
+// with the operands split into two tensor-core-precision planes,
+// x = hi + lo (hi = round(x), lo = round(x - hi)), and the product evaluated
+// as hi*hi + hi*lo + lo*hi with FP32 accumulation:
+//   3xTF32      kind::tf32, hi/lo TF32 (~22 significant bits per operand)
+//   split-BF16  kind::f16 with BF16 planes (~16 significant bits)
+//
+// Data flow per CTA (one 128 x BN output tile):
+//   * operands are packed beforehand (pack_split) into K-major planes
+//     [rows x Kp] (Kp a multiple of the 128-byte K block), zero padded;
+//   * warp 0 (one elected lane) streams K blocks of all four planes with TMA
+//     (2-D tiled, 128-byte swizzle) into a STAGES-deep shared-memory ring,
+//     completion tracked by mbarrier transaction counts;
+//   * warp 1 (one elected lane) issues tcgen05.mma (M=128, N=BN) for the three
+//     products into one FP32 accumulator in tensor memory and frees each ring
+//     slot with tcgen05.commit;
+//   * all four warps drain the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = tile rows) and scatter through the offset tables.
+// Every mbarrier wait is bounded (about one second of %globaltimer); on
+// expiry the CTA records an error code, stops issuing, waits (bounded) for
+// its own copies and MMAs, frees its tensor memory and returns.
+#include "common.h"
+#include "tc_gemm.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <mutex>
+
+namespace mera {
+namespace tc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int STAGES = 3;
+constexpr int KB_BYTES = 128;               // K block = one 128-byte swizzle row
+constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits: 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile with 128-byte swizzle, rows
+// of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)(16 >> 4) << 16;                   // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  if (KIND == KIND_TF32) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M=128, N=BN.
+template <int KIND, int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4)                                   // D format: F32
+         | ((KIND == KIND_TF32 ? 2u : 1u) << 7)      // A format: TF32 / BF16
+         | ((KIND == KIND_TF32 ? 2u : 1u) << 10)     // B format
+         | ((uint32_t)(BN >> 3) << 17)               // N / 8
+         | ((uint32_t)(BM >> 4) << 24);              // M / 16
+}
+
+struct Smem {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t accum;
+  uint32_t tmem;
+  int abort;
+};
+
+template <int KIND, int BN>
+__global__ __launch_bounds__(128, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
+                                                         const __grid_constant__ CUtensorMap a_lo,
+                                                         const __grid_constant__ CUtensorMap b_hi,
+                                                         const __grid_constant__ CUtensorMap b_lo,
+                                                         TcEpilogue ep) {
+  constexpr int A_BYTES = BM * KB_BYTES;   // one plane, one K block
+  constexpr int B_BYTES = BN * KB_BYTES;
+  constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int KSTEP_BYTES = KIND == KIND_TF32 ? 32 : 32;  // bytes of K per MMA (8 tf32 / 16 bf16)
+  constexpr int KSTEPS = KB_BYTES / KSTEP_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem* S = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM;
+  const int64_t n0 = (int64_t)blockIdx.y * BN;
+  const int kblocks = ep.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&S->full[s], 1);
+      mbar_init(&S->empty[s], 1);
+    }
+    mbar_init(&S->accum, 1);
+    S->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S->tmem;
+
+  int issued_loads = 0;   // K blocks whose TMA was issued (producer)
+  int issued_mma = 0;     // K blocks whose MMAs were issued (MMA warp)
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES) {
+        if (!mbar_wait(&S->empty[s], ((kb / STAGES) - 1) & 1)) { atomicExch(&S->abort, 1); break; }
+      }
+      if (*(volatile int*)&S->abort) break;
+      uint8_t* st = base + s * STAGE_BYTES;
+      mbar_expect_tx(&S->full[s], STAGE_BYTES);
+      const int kx = kb * (KB_BYTES / (KIND == KIND_TF32 ? 4 : 2));
+      tma_load_2d(&a_hi, &S->full[s], st, kx, (int)m0);
+      tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, (int)m0);
+      tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, (int)n0);
+      tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, (int)n0);
+      issued_loads = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t ID = idesc<KIND, BN>();
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&S->full[s], (kb / STAGES) & 1)) { atomicExch(&S->abort, 1); break; }
+      if (*(volatile int*)&S->abort) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(base + s * STAGE_BYTES);
+      const uint32_t ahi = st, alo = st + A_BYTES, bhi = st + 2 * A_BYTES, blo = st + 2 * A_BYTES + B_BYTES;
+#pragma unroll
+      for (int k = 0; k < KSTEPS; ++k) {
+        const uint32_t off = k * KSTEP_BYTES;
+        const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+        // small products first, the dominant one last
+        mma<KIND>(tmem, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, acc0);
+        mma<KIND>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
+        mma<KIND>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
+      }
+      mma_commit(&S->empty[s]);
+      issued_mma = kb + 1;
+    }
+    mma_commit(&S->accum);
+  }
+  __syncwarp();
+  // epilogue: wait for the accumulator
+  bool ok = mbar_wait(&S->accum, 0);
+  if (!ok) atomicExch(&S->abort, 1);
+  __syncthreads();
+  const bool aborted = *(volatile int*)&S->abort != 0;
+  if (!aborted) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = warp * 32 + lane;
+    const int64_t m = m0 + row;
+    const bool mvalid = m < ep.M;
+    const int64_t crow = mvalid ? (ep.cm ? ep.cm[m] : m * ep.cms) : 0;
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (mvalid) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t n = n0 + c0 + j;
+          if (n < ep.N) {
+            const int64_t idx = crow + (ep.cn ? ep.cn[n] : n * ep.cns);
+            const double v = ep.alpha * (double)__uint_as_float(r[j]);
+            if (ep.c_f64) {
+              double* C = static_cast<double*>(ep.C);
+              C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+            } else {
+              float* C = static_cast<float*>(ep.C);
+              C[idx] = (float)(ep.beta != 0.0 ? fma(ep.beta, (double)C[idx], v) : v);
+            }
+          }
+        }
+      }
+    }
+  } else {
+    if (threadIdx.x == 0) atomicExch(ep.err, 1);
+    // drain: wait (bounded) for this CTA's outstanding copies and MMAs
+    if (warp == 0 && lane == 0) {
+      for (int kb = 0; kb < issued_loads; ++kb) mbar_wait(&S->full[kb % STAGES], (kb / STAGES) & 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+  (void)issued_mma;
+}
+
+// ----------------------------------------------------------------- packing -
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// hi/lo planes [Rp x Kp] (row-major, K fastest) of src[r_off[r] + k_off[k]].
+template <typename Src, int KIND>
+__global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt, int64_t rs,
+                                  const int64_t* __restrict__ kt, int64_t ks, int64_t R, int64_t K,
+                                  int64_t Rp, int64_t Kp, void* hi, void* lo) {
+  const int64_t total = Rp * Kp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / Kp, k = i % Kp;
+    double v = 0.0;
+    if (r < R && k < K) v = (double)src[(rt ? rt[r] : r * rs) + (kt ? kt[k] : k * ks)];
+    if (KIND == KIND_TF32) {
+      const float h = tf32_round((float)v);
+      const float l = tf32_round((float)(v - (double)h));
+      static_cast<float*>(hi)[i] = h;
+      static_cast<float*>(lo)[i] = l;
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+      const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+      static_cast<__nv_bfloat16*>(hi)[i] = h;
+      static_cast<__nv_bfloat16*>(lo)[i] = l;
+    }
+  }
+}
+
+// ------------------------------------------------------------- host side ---
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+void load_encode() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) throw Error(MERA_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+}
+
+CUtensorMap make_map(const void* ptr, int64_t rows, int64_t kp, int elem, int box_rows) {
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)(kp * elem)};
+  const cuuint32_t box[2] = {(cuuint32_t)(KB_BYTES / elem), (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((kp * elem) & 15))
+    throw Error(MERA_ERR_ARG, "tensor map: base or row pitch not 16-byte aligned");
+  CUresult r = g_encode(&m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(MERA_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+template <int KIND, int BN>
+size_t smem_bytes() {
+  return 1024 + (size_t)STAGES * (2 * BM * KB_BYTES + 2 * BN * KB_BYTES) + sizeof(Smem) + 64;
+}
+
+template <int KIND, int BN>
+void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
+            const TcEpilogue& ep, int64_t mt, int64_t nt, cudaStream_t s) {
+  static bool attr_set[64] = {};
+  int dev = 0;
+  MERA_CUDA(cudaGetDevice(&dev));
+  const size_t sm = smem_bytes<KIND, BN>();
+  if (dev < 64 && !attr_set[dev]) {
+    MERA_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr_set[dev] = true;
+  }
+  if (nt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: N too large for grid");
+  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)mt, (unsigned)nt), 128, sm, s>>>(ah, al, bh, bl, ep);
+}
+
+}  // namespace
+
+int64_t padded_k(int64_t K, int kind) {
+  const int64_t kb = KB_BYTES / (kind == KIND_TF32 ? 4 : 2);
+  return (K + kb - 1) / kb * kb;
+}
+
+void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
+                int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, cudaStream_t s) {
+  const int64_t total = Rp * Kp;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
+  if (kind == KIND_TF32) {
+    if (src_f64)
+      pack_split_kernel<double, KIND_TF32><<<blocks, threads, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+    else
+      pack_split_kernel<float, KIND_TF32><<<blocks, threads, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+  } else {
+    if (src_f64)
+      pack_split_kernel<double, KIND_BF16><<<blocks, threads, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+    else
+      pack_split_kernel<float, KIND_BF16><<<blocks, threads, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+  }
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+
+void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo, int64_t Mp,
+                 const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep_in, cudaStream_t s) {
+  load_encode();
+  const int elem = kind == KIND_TF32 ? 4 : 2;
+  const int bn = 128;
+  TcEpilogue ep = ep_in;
+  ep.M = M;
+  ep.N = N;
+  ep.kblocks = (int)(Kp / (KB_BYTES / elem));
+  CUtensorMap ah = make_map(a_hi, Mp, Kp, elem, BM), al = make_map(a_lo, Mp, Kp, elem, BM);
+  CUtensorMap bh = make_map(b_hi, Np, Kp, elem, bn), bl = make_map(b_lo, Np, Kp, elem, bn);
+  const int64_t mt = (M + BM - 1) / BM, nt = (N + bn - 1) / bn;
+  if (Mp < mt * BM || Np < nt * bn) throw Error(MERA_ERR_ARG, "gemm_packed: operand padding too small");
+  if (kind == KIND_TF32)
+    launch<KIND_TF32, 128>(ah, al, bh, bl, ep, mt, nt, s);
+  else
+    launch<KIND_BF16, 128>(ah, al, bh, bl, ep, mt, nt, s);
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+
+}  // namespace tc
+}  // namespace mera

@@ -1,0 +1,43 @@
+// Tensor-core (tcgen05) contraction path: operand packing and the GEMM.
+#pragma once
+#include "common.h"
+#include <cuda_bf16.h>
+
+namespace mera {
+namespace tc {
+
+enum { KIND_TF32 = 0, KIND_BF16 = 1 };
+
+// Output side of one tensor-core contraction (offset tables as in GettCall).
+struct TcEpilogue {
+  int64_t M = 0, N = 0;
+  int kblocks = 0;
+  double alpha = 1.0, beta = 0.0;
+  const int64_t* cm = nullptr;
+  int64_t cms = 0;
+  const int64_t* cn = nullptr;
+  int64_t cns = 0;
+  void* C = nullptr;
+  int c_f64 = 0;       // 1: C is double, 0: float
+  int* err = nullptr;  // set to 1 by a CTA whose bounded wait expired
+};
+
+// K rounded up to the 128-byte K block of the kind (32 TF32 / 64 BF16 values).
+int64_t padded_k(int64_t K, int kind);
+
+// Split src[r_off(r) + k_off(k)] (r < R, k < K; zero elsewhere) into hi/lo
+// planes of [Rp x Kp] row-major tensor-core values.
+void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt,
+                int64_t ks, int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi,
+                void* lo, cudaStream_t s);
+
+// C tile loop over packed planes: A [Mp x Kp], B [Np x Kp] (both K-major),
+// Mp a multiple of 128 covering M, Np a multiple of 128 covering N.
+void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo,
+                 int64_t Mp, const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep,
+                 cudaStream_t s);
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace tc
+}  // namespace mera

@@ -65,7 +65,7 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
            "mera_launch_count", "mera_get_stats", "mera_profile", "mera_dots_noalloc",
-           "mera_strerror", "mera_last_error"]
+           "mera_gemm", "mera_strerror", "mera_last_error"]
 
 _lib = None
 
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
         "mera_profile": (C.c_int, [C.c_void_p, C.c_int]),
         "mera_dots_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
                                         C.c_void_p, C.c_void_p]),
+        "mera_gemm": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
         "mera_strerror": (C.c_char_p, [C.c_int]),
         "mera_last_error": (C.c_char_p, [C.c_void_p]),
     }
@@ -138,6 +140,21 @@ def dots_noalloc(X, y, k, n, ldx, out, stream=0):
     if rc != 0:
         raise MeraError(rc, L.mera_strerror(rc).decode())
     return out
+
+
+def gemm(prec, A, B, C, stream=0):
+    """C = A B (device float64 row-major tensors) in the arithmetic of ``prec``."""
+    L = load()
+    M, K = A.shape
+    N = B.shape[1]
+    rc = L.mera_gemm(int(prec), M, N, K, C_void(A), C_void(B), C_void(C), C.c_void_p(stream))
+    if rc != 0:
+        raise MeraError(rc, L.mera_strerror(rc).decode())
+    return C
+
+
+def C_void(a):
+    return C.c_void_p(_ptr(a))
 
 
 def _ptr(a):

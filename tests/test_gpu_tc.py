@@ -1,0 +1,39 @@
+"""Tensor-core contraction kernel (tcgen05, 3xTF32 / split-BF16 with FP32
+accumulation) against an FP64 product, through the C ABI (mera_gemm)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(128, 128, 32), (200, 130, 70), (1, 1, 1), (1024, 512, 1000), (4100, 257, 2049)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03638_gb300 import build as b
+    b.build()
+    from paper_2007_03638_gb300 import mera as gm
+    return torch, gm
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 4e-6), (2, 2e-4)])
+def test_gemm_modes(env, shape, prec, tol):
+    torch, gm = env
+    M, N, K = shape
+    rng = np.random.default_rng(M + 7 * N + 13 * K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    ref = A @ B
+    Ad = torch.from_numpy(A).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    Cd = torch.full((M, N), float("nan"), dtype=torch.float64, device="cuda")
+    gm.gemm(prec, Ad, Bd, Cd)
+    C = Cd.cpu().numpy()
+    assert np.all(np.isfinite(C))
+    # error relative to the natural scale of the entries (sqrt(K) for N(0,1) data)
+    err = np.abs(C - ref).max() / np.sqrt(K)
+    assert err < tol, (prec, shape, err)
