@@ -125,13 +125,19 @@ __host__ __device__ constexpr uint32_t idesc() {
 struct Smem {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
-  uint64_t accum;
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
   uint32_t tmem;
   int abort;
 };
 
+// Warp roles (192 threads): warp 0 TMA producer, warp 1 MMA issuer, warps
+// 2..5 promote/epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// The tensor cores' FP32 accumulation truncates, so each K block is
+// accumulated into a fresh tensor-memory buffer (two buffers alternate) and
+// folded into FP32 registers with round-to-nearest adds by the epilogue warps.
 template <int KIND, int BN>
-__global__ __launch_bounds__(128, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
+__global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
                                                          const __grid_constant__ CUtensorMap a_lo,
                                                          const __grid_constant__ CUtensorMap b_hi,
                                                          const __grid_constant__ CUtensorMap b_lo,
@@ -139,8 +145,9 @@ __global__ __launch_bounds__(128, 1) void tc_gemm_kernel(const __grid_constant__
   constexpr int A_BYTES = BM * KB_BYTES;   // one plane, one K block
   constexpr int B_BYTES = BN * KB_BYTES;
   constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  constexpr int KSTEP_BYTES = KIND == KIND_TF32 ? 32 : 32;  // bytes of K per MMA (8 tf32 / 16 bf16)
+  constexpr int KSTEP_BYTES = 32;          // bytes of K per MMA (8 tf32 / 16 bf16)
   constexpr int KSTEPS = KB_BYTES / KSTEP_BYTES;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Smem* S = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
@@ -154,13 +161,16 @@ __global__ __launch_bounds__(128, 1) void tc_gemm_kernel(const __grid_constant__
       mbar_init(&S->full[s], 1);
       mbar_init(&S->empty[s], 1);
     }
-    mbar_init(&S->accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S->acc_full[b], 1);
+      mbar_init(&S->acc_empty[b], 4);  // one arrival per epilogue warp
+    }
     S->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem)),
-                 "r"(BN));
+                 "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -168,105 +178,117 @@ __global__ __launch_bounds__(128, 1) void tc_gemm_kernel(const __grid_constant__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S->tmem;
 
-  int issued_loads = 0;   // K blocks whose TMA was issued (producer)
-  int issued_mma = 0;     // K blocks whose MMAs were issued (MMA warp)
-  if (warp == 0 && lane == 0) {
-    // producer
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES) {
-        if (!mbar_wait(&S->empty[s], ((kb / STAGES) - 1) & 1)) { atomicExch(&S->abort, 1); break; }
+  int issued_loads = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&S->empty[s], ((kb / STAGES) - 1) & 1)) {
+          atomicExch(&S->abort, 1);
+          break;
+        }
+        if (*(volatile int*)&S->abort) break;
+        uint8_t* st = base + s * STAGE_BYTES;
+        mbar_expect_tx(&S->full[s], STAGE_BYTES);
+        const int kx = kb * (KB_BYTES / (KIND == KIND_TF32 ? 4 : 2));
+        tma_load_2d(&a_hi, &S->full[s], st, kx, (int)m0);
+        tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, (int)m0);
+        tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, (int)n0);
+        tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, (int)n0);
+        issued_loads = kb + 1;
       }
-      if (*(volatile int*)&S->abort) break;
-      uint8_t* st = base + s * STAGE_BYTES;
-      mbar_expect_tx(&S->full[s], STAGE_BYTES);
-      const int kx = kb * (KB_BYTES / (KIND == KIND_TF32 ? 4 : 2));
-      tma_load_2d(&a_hi, &S->full[s], st, kx, (int)m0);
-      tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, (int)m0);
-      tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, (int)n0);
-      tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, (int)n0);
-      issued_loads = kb + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t ID = idesc<KIND, BN>();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t ID = idesc<KIND, BN>();
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % STAGES, b = kb & 1;
+        if (!mbar_wait(&S->full[s], (kb / STAGES) & 1)) { atomicExch(&S->abort, 1); break; }
+        if (kb >= 2 && !mbar_wait(&S->acc_empty[b], ((kb >> 1) - 1) & 1)) { atomicExch(&S->abort, 1); break; }
+        if (*(volatile int*)&S->abort) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(base + s * STAGE_BYTES);
+        const uint32_t ahi = st, alo = st + A_BYTES, bhi = st + 2 * A_BYTES, blo = st + 2 * A_BYTES + B_BYTES;
+        const uint32_t dt = tmem + (uint32_t)(b * BN);
+#pragma unroll
+        for (int k = 0; k < KSTEPS; ++k) {
+          const uint32_t off = k * KSTEP_BYTES;
+          // small products first, the dominant one last
+          mma<KIND>(dt, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, k > 0 ? 1u : 0u);
+          mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
+          mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
+        }
+        mma_commit(&S->empty[s]);
+        mma_commit(&S->acc_full[b]);
+      }
+    }
+  } else {
+    // promotion and epilogue
+    const int q = warp & 3;                    // TMEM lane quarter
+    const int row = q * 32 + lane;
+    float acc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    bool ok = true;
     for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(&S->full[s], (kb / STAGES) & 1)) { atomicExch(&S->abort, 1); break; }
-      if (*(volatile int*)&S->abort) break;
+      const int b = kb & 1;
+      if (!mbar_wait(&S->acc_full[b], (kb >> 1) & 1)) { ok = false; break; }
+      if (*(volatile int*)&S->abort) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(base + s * STAGE_BYTES);
-      const uint32_t ahi = st, alo = st + A_BYTES, bhi = st + 2 * A_BYTES, blo = st + 2 * A_BYTES + B_BYTES;
 #pragma unroll
-      for (int k = 0; k < KSTEPS; ++k) {
-        const uint32_t off = k * KSTEP_BYTES;
-        const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-        // small products first, the dominant one last
-        mma<KIND>(tmem, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, acc0);
-        mma<KIND>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
-        mma<KIND>(tmem, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
       }
-      mma_commit(&S->empty[s]);
-      issued_mma = kb + 1;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
     }
-    mma_commit(&S->accum);
-  }
-  __syncwarp();
-  // epilogue: wait for the accumulator
-  bool ok = mbar_wait(&S->accum, 0);
-  if (!ok) atomicExch(&S->abort, 1);
-  __syncthreads();
-  const bool aborted = *(volatile int*)&S->abort != 0;
-  if (!aborted) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = warp * 32 + lane;
+    if (!ok) atomicExch(&S->abort, 1);
     const int64_t m = m0 + row;
-    const bool mvalid = m < ep.M;
-    const int64_t crow = mvalid ? (ep.cm ? ep.cm[m] : m * ep.cms) : 0;
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-            "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-            "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-            "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (mvalid) {
+    if (ok && m < ep.M) {
+      const int64_t crow = ep.cm ? ep.cm[m] : m * ep.cms;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t n = n0 + c0 + j;
-          if (n < ep.N) {
-            const int64_t idx = crow + (ep.cn ? ep.cn[n] : n * ep.cns);
-            const double v = ep.alpha * (double)__uint_as_float(r[j]);
-            if (ep.c_f64) {
-              double* C = static_cast<double*>(ep.C);
-              C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
-            } else {
-              float* C = static_cast<float*>(ep.C);
-              C[idx] = (float)(ep.beta != 0.0 ? fma(ep.beta, (double)C[idx], v) : v);
-            }
+      for (int j = 0; j < BN; ++j) {
+        const int64_t n = n0 + j;
+        if (n < ep.N) {
+          const int64_t idx = crow + (ep.cn ? ep.cn[n] : n * ep.cns);
+          const double v = ep.alpha * (double)acc[j];
+          if (ep.c_f64) {
+            double* C = static_cast<double*>(ep.C);
+            C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+          } else {
+            float* C = static_cast<float*>(ep.C);
+            C[idx] = (float)(ep.beta != 0.0 ? fma(ep.beta, (double)C[idx], v) : v);
           }
         }
       }
     }
-  } else {
+  }
+  __syncthreads();
+  if (*(volatile int*)&S->abort) {
     if (threadIdx.x == 0) atomicExch(ep.err, 1);
-    // drain: wait (bounded) for this CTA's outstanding copies and MMAs
-    if (warp == 0 && lane == 0) {
+    // drain this CTA's outstanding copies (bounded) before its memory goes away
+    if (warp == 0 && lane == 0)
       for (int kb = 0; kb < issued_loads; ++kb) mbar_wait(&S->full[kb % STAGES], (kb / STAGES) & 1);
-    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
-  (void)issued_mma;
 }
 
 // ----------------------------------------------------------------- packing -
@@ -349,7 +371,7 @@ void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
     attr_set[dev] = true;
   }
   if (nt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: N too large for grid");
-  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)mt, (unsigned)nt), 128, sm, s>>>(ah, al, bh, bl, ep);
+  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)mt, (unsigned)nt), 192, sm, s>>>(ah, al, bh, bl, ep);
 }
 
 }  // namespace

@@ -142,15 +142,15 @@ def dots_noalloc(X, y, k, n, ldx, out, stream=0):
     return out
 
 
-def gemm(prec, A, B, C, stream=0):
-    """C = A B (device float64 row-major tensors) in the arithmetic of ``prec``."""
+def gemm(prec, A, B, out, stream=0):
+    """out = A B (device float64 row-major tensors) in the arithmetic of ``prec``."""
     L = load()
     M, K = A.shape
     N = B.shape[1]
-    rc = L.mera_gemm(int(prec), M, N, K, C_void(A), C_void(B), C_void(C), C.c_void_p(stream))
+    rc = L.mera_gemm(int(prec), M, N, K, C_void(A), C_void(B), C_void(out), C.c_void_p(stream))
     if rc != 0:
         raise MeraError(rc, L.mera_strerror(rc).decode())
-    return C
+    return out
 
 
 def C_void(a):
