@@ -95,6 +95,7 @@ struct GettCall {
   GettOperand c;
   int64_t M = 0, N = 0, K = 0;
   double alpha = 1.0, beta = 0.0;
+  int a32 = 0, b32 = 0, c32 = 0;  // 1: operand stored as float (mixed-precision node buffers)
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 

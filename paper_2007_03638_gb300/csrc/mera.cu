@@ -134,6 +134,8 @@ struct mera_ctx {
   bool have_rho = false, have_x = false;
   mera::DevBuf kbasis, ktmp, kcoef;       // Krylov workspace
   mera::DevBuf scratch;                   // transient contraction buffers
+  mera::Exec ex;                          // contraction arithmetic
+  mera::DevBuf tc_ws, tc_err;             // tensor-core operand planes, wait-expiry flag
   mera::DevBuf gtmp[6];                   // geometry temporaries
   mera::Reducer red;
   mera::Eval ev[2];
@@ -175,7 +177,9 @@ void bind_leaves(Layer& ly, int side, const double* op, const double* u, const d
 
 void build_layers(Ctx& c) {
   c.layers.resize(c.L + 1);
-  size_t scratch_need = 0;
+  const bool mixed = c.cfg.prec != MERA_PREC_FP64;
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  size_t scratch_need = 0, ws_need = 0;
   for (int l = 0; l <= c.L; ++l) {
     Layer& ly = c.layers[l];
     ly.cf = c.dims[l];
@@ -185,63 +189,66 @@ void build_layers(Ctx& c) {
       SideNet& net = *ly.net[sd];
       // persistent node values: N1 N3 N4 N6 N7 N8 N9
       for (int node : {11, 13, 14, 16, 17, 18, 19}) {
-        ly.own[sd].emplace_back(sizeof(double) * net.node_size(node));
+        ly.own[sd].emplace_back(es * net.node_size(node));
         ly.buf[sd].val[node] = P(ly.own[sd].back());
       }
+      ly.buf[sd].f32 = mixed;
+      ly.buf[sd].ex = &c.ex;
       size_t need = 0;
       for (int node : {12, 15}) need += net.node_size(node);
       for (int node = 11; node < 20; ++node) need += net.node_size(node);
       scratch_need = std::max(scratch_need, need);
+      for (int node = SideNet::NLEAF; node < SideNet::NNODE; ++node)
+        for (const GemmPlan* p : {&net.fwd(node), &net.bwd_left(node), &net.bwd_right(node)})
+          ws_need = std::max(ws_need, tc_workspace_bytes(p->proto, c.cfg.prec));
     }
   }
-  c.scratch.alloc(sizeof(double) * scratch_need);
+  c.scratch.alloc(es * scratch_need);
+  c.ex.prec = c.cfg.prec;
+  if (mixed) {
+    c.tc_ws.alloc(ws_need);
+    c.tc_err.alloc(sizeof(int));
+    MERA_CUDA(cudaMemset(c.tc_err.p, 0, sizeof(int)));
+    c.ex.ws = c.tc_ws.p;
+    c.ex.ws_bytes = ws_need;
+    c.ex.err = c.tc_err.as<int>();
+  }
   for (int l = 0; l <= c.L; ++l)
     for (int sd = 0; sd < 2; ++sd) {
       Layer& ly = c.layers[l];
       SideNet& net = *ly.net[sd];
-      double* p = P(c.scratch);
+      char* p = static_cast<char*>(c.scratch.p);
       for (int node : {12, 15}) {
-        ly.buf[sd].val[node] = p;
-        p += net.node_size(node);
+        ly.buf[sd].val[node] = reinterpret_cast<double*>(p);
+        p += es * net.node_size(node);
       }
       for (int node = 11; node < 20; ++node) {
-        ly.buf[sd].adj[node] = p;
-        p += net.node_size(node);
+        ly.buf[sd].adj[node] = reinterpret_cast<double*>(p);
+        p += es * net.node_size(node);
       }
     }
 }
 
+void check_device_flag(Ctx& c, cudaStream_t s) {
+  if (!c.tc_err.p) return;
+  int e = 0;
+  MERA_CUDA(cudaMemcpyAsync(&e, c.tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+  if (e) {
+    MERA_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), s));
+    throw Error(MERA_ERR_DEVICE_TIMEOUT, "tensor-core contraction: a bounded device-side wait expired");
+  }
+}
+
 // -------------------------------------------------------- superoperators ---
 // out = ao * out + af * Abar(op) (both sides), using layer l's tensors from point W.
-void ascend(Ctx& c, int l, const double* W, const double* op, double* out, double af, bool keep,
-            cudaStream_t s) {
+void ascend(Ctx& c, int l, const double* W, const double* op, double* out, double af, cudaStream_t s) {
   Layer& ly = c.layers[l];
   const double* u = W + c.offs[2 * l];
   const double* w = W + c.offs[2 * l + 1];
   for (int sd = 0; sd < 2; ++sd) {
     bind_leaves(ly, sd, op, u, w);
-    ly.buf[sd].val[SideNet::ROOT] = out;
-    (void)keep;
-  }
-  // root written with alpha = af/2, the right side accumulating
-  for (int sd = 0; sd < 2; ++sd) {
-    SideNet& net = *ly.net[sd];
-    SideBufs& b = ly.buf[sd];
-    for (int node : {12, 13, 15, 17, 18}) {
-      GettCall g = net.fwd(node).proto;
-      const int lc = SideNet::left(node), rc = SideNet::right(node);
-      g.A = lc < SideNet::NLEAF ? b.leaf[lc] : b.val[lc];
-      g.B = rc < SideNet::NLEAF ? b.leaf[rc] : b.val[rc];
-      g.C = b.val[node];
-      gett_f64(g, s);
-    }
-    GettCall g = net.fwd(SideNet::ROOT).proto;
-    g.A = b.val[18];
-    g.B = b.val[19];
-    g.C = out;
-    g.alpha = 0.5 * af;
-    g.beta = 1.0;
-    gett_f64(g, s);
+    side_forward(*ly.net[sd], ly.buf[sd], out, 0.5 * af, 1.0, s);
   }
 }
 
@@ -292,9 +299,9 @@ int gmres(Ctx& c, const std::function<void(const double*, double*)>& op, const d
     if (applications >= maxit || !(beta < 1e300)) {
       throw Error(MERA_ERR_NOCONV, "GMRES: relative residual " + std::to_string(beta / bnorm));
     }
-    if (beta >= best * 0.999999 && applications > 4 * m) {
-      // stagnation at the rounding floor
-      if (beta <= 1e3 * tol * bnorm) return applications;
+    if (beta > 0.9 * best && applications > 2 * m && beta <= 100.0 * tol * bnorm) {
+      // no progress over a restart cycle: the residual is at the rounding floor
+      return applications;
     }
     best = std::min(best, beta);
     axpby(1.0 / beta, w, 0.0, V, n, s);
@@ -369,7 +376,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   for (int l = 0; l < L; ++l) {
     const int64_t n3 = ipow(c.dims[l + 1], 3);
     fill(0.0, P(c.h[l + 1]), n3 * n3, s);
-    ascend(c, l, W, P(c.h[l]), P(c.h[l + 1]), 1.0, true, s);
+    ascend(c, l, W, P(c.h[l]), P(c.h[l + 1]), 1.0, s);
     symmetrize(P(c.h[l + 1]), n3, s);
   }
   // scale-invariant layer
@@ -382,7 +389,10 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   double* bvec = P(c.gtmp[5]);
   fill(0.0, bvec, n, s);
   add_identity(1.0 / (double)n3, bvec, n3, s);
-  const double tol = c.cfg.krylov_tol;
+  // the residual of a Krylov solve cannot fall below the rounding level of
+  // the contractions that apply the superoperator
+  const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
+  const double tol = std::max(c.cfg.krylov_tol, floor_tol);
   auto op_rho = [&](const double* v, double* out) {
     copy(out, v, n, s);
     descend(c, L, v, out, -1.0, s);
@@ -401,7 +411,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   if (!c.have_x) copy(xs, hL, n, s);
   auto op_x = [&](const double* v, double* out) {
     copy(out, v, n, s);
-    ascend(c, L, W, v, out, -1.0, false, s);
+    ascend(c, L, W, v, out, -1.0, s);
     const double t = c.red.dot(v, rhoS, n, s);
     add_identity(t, out, n3, s);
     ++c.matvecs;
@@ -425,14 +435,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
       SideBufs& b = ly.buf[sd];
       bind_leaves(ly, sd, op, u, w);
       // forward with this layer's operator (keeps N3, N7, N8); output not needed
-      for (int node : {12, 13, 15, 17, 18}) {
-        GettCall g = ly.net[sd]->fwd(node).proto;
-        const int lc = SideNet::left(node), rc = SideNet::right(node);
-        g.A = lc < SideNet::NLEAF ? b.leaf[lc] : b.val[lc];
-        g.B = rc < SideNet::NLEAF ? b.leaf[rc] : b.val[rc];
-        g.C = b.val[node];
-        gett_f64(g, s);
-      }
+      side_forward(*ly.net[sd], b, nullptr, 0.0, 0.0, s);
       b.adj[SideNet::ROOT] = const_cast<double*>(r);
       side_backward(*ly.net[sd], b, need_op, need_op ? P(c.rho[l]) : nullptr, 0.5, true,
                     D + c.offs[2 * l], D + c.offs[2 * l + 1], 1.0, s);
@@ -449,6 +452,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
     E.delta[i] = std::sqrt(c.red.dot(g, g, c.rows[i] * c.cols[i], s));
     finite = finite && std::isfinite(E.delta[i]);
   }
+  check_device_flag(c, s);
   if (!finite) throw Error(MERA_ERR_NONFINITE, "non-finite energy or gradient");
   compute_rho_v(c, E, W, s);
   E.eig_ready = false;
@@ -991,7 +995,8 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.s = s;
   if (cfg.d_b < 2 || cfg.chi < 2 || cfg.n_trans < 1) throw Error(MERA_ERR_ARG, "bad d_b/chi/n_trans");
   if (cfg.dtype != MERA_F64) throw Error(MERA_ERR_UNSUPPORTED, "only MERA_F64 is built");
-  if (cfg.prec != MERA_PREC_FP64) throw Error(MERA_ERR_UNSUPPORTED, "only MERA_PREC_FP64 is built");
+  if (cfg.prec != MERA_PREC_FP64 && cfg.prec != MERA_PREC_3XTF32 && cfg.prec != MERA_PREC_SPLIT_BF16)
+    throw Error(MERA_ERR_ARG, "unknown precision mode");
   c.L = cfg.n_trans;
   c.dims.push_back(cfg.d_b);
   for (int l = 0; l < c.L; ++l) c.dims.push_back(std::min<int64_t>(cfg.chi, c.dims.back() * c.dims.back()));

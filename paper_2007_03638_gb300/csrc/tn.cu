@@ -14,6 +14,7 @@
 // forward plus one reverse pass cost 5.3 chi^9 per side instead of
 // 15 chi^9 for separate ascending, descending and ten environment networks.
 #include "tn.h"
+#include "tc_gemm.h"
 #include <algorithm>
 #include <cstring>
 
@@ -221,34 +222,105 @@ double SideNet::forward_flops() const {
   return f;
 }
 
+size_t tc_workspace_bytes(const GettCall& g, int prec) {
+  if (prec == MERA_PREC_FP64) return 0;
+  const int kind = prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
+  const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
+  const int64_t Kp = tc::padded_k(g.K, kind);
+  const int64_t Mp = tc::round_up(g.M, 128), Np = tc::round_up(g.N, 128);
+  return 4 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp;
+}
+
+void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return;
+  if (ex.prec == MERA_PREC_FP64) {
+    if (g.a32 || g.b32 || g.c32) throw Error(MERA_ERR_ARG, "contract: float operand in the FP64 path");
+    gett_f64(g, s);
+    return;
+  }
+  const int kind = ex.prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
+  const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
+  const int64_t Kp = tc::padded_k(g.K, kind);
+  const int64_t Mp = tc::round_up(g.M, 128), Np = tc::round_up(g.N, 128);
+  if (tc_workspace_bytes(g, ex.prec) > ex.ws_bytes) throw Error(MERA_ERR_ARG, "contract: workspace too small");
+  auto align = [](size_t o) { return (o + 1023) & ~size_t(1023); };
+  char* w = static_cast<char*>(ex.ws);
+  size_t o = 0;
+  void* ah = w + o; o = align(o + elem * Mp * Kp);
+  void* al = w + o; o = align(o + elem * Mp * Kp);
+  void* bh = w + o; o = align(o + elem * Np * Kp);
+  void* bl = w + o;
+  // A rows = M group, A columns = K group; B rows (of the packed K-major plane) = N group
+  tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, s);
+  tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, s);
+  tc::TcEpilogue ep;
+  ep.alpha = g.alpha;
+  ep.beta = g.beta;
+  ep.cm = g.c.t0;
+  ep.cms = g.c.s0;
+  ep.cn = g.c.t1;
+  ep.cns = g.c.s1;
+  ep.C = g.C;
+  ep.c_f64 = g.c32 ? 0 : 1;
+  ep.err = ex.err;
+  Prof* pr = g_prof;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (pr && pr->timing) {
+    if (pr->used + 2 > pr->ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        MERA_CUDA(cudaEventCreate(&e));
+        pr->ev.push_back(e);
+      }
+    }
+    e0 = pr->ev[pr->used];
+    e1 = pr->ev[pr->used + 1];
+    pr->used += 2;
+    MERA_CUDA(cudaEventRecord(e0, s));
+  }
+  tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s);
+  if (e1) MERA_CUDA(cudaEventRecord(e1, s));
+  if (pr) {
+    pr->gett_launches++;
+    pr->gett_flops += 2.0 * (double)g.M * (double)g.N * (double)g.K;
+  }
+}
+
 namespace {
-void run(const GemmPlan& p, const double* A, const double* B, double* C, double alpha, double beta,
-         cudaStream_t s) {
+// Run one plan; operand precision follows the buffer kind (leaf/external = double,
+// internal node = float in mixed mode).
+void run(const SideBufs& b, const GemmPlan& p, const double* A, bool a_int, const double* B, bool b_int,
+         double* C, bool c_int, double alpha, double beta, cudaStream_t s) {
   GettCall g = p.proto;
   g.A = A;
   g.B = B;
   g.C = C;
   g.alpha = alpha;
   g.beta = beta;
-  gett_f64(g, s);
+  g.a32 = b.f32 && a_int;
+  g.b32 = b.f32 && b_int;
+  g.c32 = b.f32 && c_int;
+  contract(g, *b.ex, s);
 }
 inline const double* value(const SideBufs& b, int node) {
   return node < SideNet::NLEAF ? b.leaf[node] : b.val[node];
 }
+inline bool internal(int node) { return node >= SideNet::NLEAF && node != SideNet::ROOT; }
 }  // namespace
 
 void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
   for (int node : {11, 14, 16, 19}) {
-    run(net.fwd(node), value(b, SideNet::left(node)), value(b, SideNet::right(node)), b.val[node],
-        1.0, 0.0, s);
+    const int l = SideNet::left(node), r = SideNet::right(node);
+    run(b, net.fwd(node), value(b, l), internal(l), value(b, r), internal(r), b.val[node], true, 1.0, 0.0, s);
   }
 }
 
-void side_forward(const SideNet& net, SideBufs& b, cudaStream_t s) {
-  for (int node : {12, 13, 15, 17, 18, 20}) {
-    run(net.fwd(node), value(b, SideNet::left(node)), value(b, SideNet::right(node)), b.val[node],
-        1.0, 0.0, s);
+void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, double beta, cudaStream_t s) {
+  for (int node : {12, 13, 15, 17, 18}) {
+    const int l = SideNet::left(node), r = SideNet::right(node);
+    run(b, net.fwd(node), value(b, l), internal(l), value(b, r), internal(r), b.val[node], true, 1.0, 0.0, s);
   }
+  if (out) run(b, net.fwd(SideNet::ROOT), b.val[18], true, b.val[19], true, out, false, alpha, beta, s);
 }
 
 void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out, double alpha_op,
@@ -277,10 +349,12 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
       } else {
         out = b.adj[c];
       }
+      const bool dn_int = node != SideNet::ROOT;
+      const bool out_int = c >= SideNet::NLEAF;
       if (side == 0)
-        run(net.bwd_left(node), dn, value(b, r), out, alpha, beta, s);
+        run(b, net.bwd_left(node), dn, dn_int, value(b, r), internal(r), out, out_int, alpha, beta, s);
       else
-        run(net.bwd_right(node), value(b, l), dn, out, alpha, beta, s);
+        run(b, net.bwd_right(node), value(b, l), internal(l), dn, dn_int, out, out_int, alpha, beta, s);
     }
   }
 }

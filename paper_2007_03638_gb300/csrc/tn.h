@@ -71,17 +71,34 @@ class SideNet {
   GemmPlan fwd_[10], bwdl_[10], bwdr_[10];
 };
 
-// Buffers bound to a SideNet for one evaluation.
+// How contractions run: FP64 kernel, or tensor cores (3xTF32 / split-BF16)
+// with operands packed into the workspace.
+struct Exec {
+  int prec = MERA_PREC_FP64;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int* err = nullptr;  // device flag set by an expired bounded wait
+};
+void contract(const GettCall& g, const Exec& ex, cudaStream_t s);
+size_t tc_workspace_bytes(const GettCall& g, int prec);
+
+// Buffers bound to a SideNet for one evaluation.  Leaves, root output,
+// operator adjoint and u/w adjoints are double; internal node values and
+// adjoints are float when f32 is set (mixed precision).
 struct SideBufs {
   const double* leaf[SideNet::NLEAF] = {};  // leaf values (operator, u, conj u, w, conj w)
   double* val[SideNet::NNODE] = {};          // internal node values (root = output)
   double* adj[SideNet::NNODE] = {};          // adjoints (root = seed)
+  bool f32 = false;
+  const Exec* ex = nullptr;
 };
 
 // Subtrees that do not contain the operator leaf: N1, N4, N6, N9.
 void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s);
-// Operator-dependent forward pass N2, N3, N5, N7, N8, root.
-void side_forward(const SideNet& net, SideBufs& b, cudaStream_t s);
+// Operator-dependent forward pass N2, N3, N5, N7, N8 (kept for the reverse
+// pass) and, if out != nullptr, the root: out = beta*out + alpha*A_side(op).
+void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, double beta,
+                  cudaStream_t s);
 // Reverse pass from the root adjoint.  need_op: adjoint of the operator
 // (descending map) into op_out (alpha_op, accumulated); need_env: adjoints of
 // the conjugated u/w copies accumulated into du/dw with alpha_env.

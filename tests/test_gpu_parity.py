@@ -172,3 +172,31 @@ def test_cg_decreases(gm):
     es = [m.cg_step()["energy"] for _ in range(6)]
     assert es[-1] < e0
     assert all(b <= a + 1e-12 for a, b in zip(es, es[1:]))
+
+
+MIXED = [
+    (1, 2e-6, 4, 4, 2, "ising", 0),
+    (1, 2e-6, 4, 8, 3, "xxz", 1),
+    (1, 2e-6, 3, 5, 2, "random", 2),
+    (2, 2e-4, 4, 4, 2, "ising", 0),
+    (2, 2e-4, 4, 8, 3, "ising", 3),
+]
+
+
+@pytest.mark.parametrize("prec,tol,d_b,chi,L,kind,seed", MIXED)
+def test_energy_grad_mixed_precision(gm, prec, tol, d_b, chi, L, kind, seed):
+    """Tensor-core path (1 = 3xTF32, 2 = split-BF16; FP32 accumulation, FP64
+    Krylov solves and reductions) against the FP64 oracle."""
+    us, ws = inp.random_mera(d_b, chi, L, seed=seed)
+    h3 = _ham(d_b, kind, seed)
+    m = gm.Mera(gm.default_config(d_b, chi, L, prec=prec), h3)
+    m.set_tensors(_flat(us, ws))
+    e, G, D = m.energy_grad(deriv=True)
+    e_ref, ds, _ = om.energy_grad(h3, us, ws)
+    err_e = abs(e - e_ref) / max(1.0, abs(e_ref))
+    err_d = max(_rel(D[i], ds[i]) for i in range(len(ds)))
+    print(f"prec={prec} chi={chi}: energy rel err {err_e:.2e}, max derivative rel err {err_d:.2e}")
+    assert err_e < tol
+    assert err_d < 10 * tol
+    st = m.stats()
+    assert st["gett_launches"] > 0
