@@ -34,10 +34,18 @@ sys.path.insert(0, ROOT)
 from paper_2007_03638_gb300 import inputs as inp  # noqa: E402
 
 WORKLOADS = {
-    # name: (hamiltonian, d_b, chi, n_trans, prec)
+    # name: (hamiltonian, d_b, chi, n_trans, prec)  prec: 0 FP64, 1 3xTF32, 2 split-BF16
     "ising_chi12_L3_fp64": ("ising", 4, 12, 3, 0),
     "ising_chi8_L3_fp64": ("ising", 4, 8, 3, 0),
     "ising_chi4_L2_fp64": ("ising", 4, 4, 2, 0),
+    "ising_chi12_L3_3xtf32": ("ising", 4, 12, 3, 1),
+    "ising_chi12_L3_bf16": ("ising", 4, 12, 3, 2),
+    "xxz_chi16_L3_3xtf32": ("xxz", 4, 16, 3, 1),
+    "xxz_chi16_L3_bf16": ("xxz", 4, 16, 3, 2),
+    "xxz_chi24_L3_3xtf32": ("xxz", 4, 24, 3, 1),
+    "xxz_chi24_L3_bf16": ("xxz", 4, 24, 3, 2),
+    "xxz_chi32_L3_3xtf32": ("xxz", 4, 32, 3, 1),
+    "xxz_chi32_L3_bf16": ("xxz", 4, 32, 3, 2),
 }
 DEFAULT_WORKLOAD = "ising_chi12_L3_fp64"
 METRIC = "MERA grad evals/s"
@@ -46,6 +54,20 @@ UNIT = "grad_evals/s"
 # FP64 FMA throughput of GB300: the nominal 1.25 TFLOP/s at the 2070 MHz
 # boost clock is 2 FP64 FMA per clock per SM over 152 SMs.
 FP64_PEAK_FLOPS = 152 * 2 * 2 * 2070e6
+
+# Tensor-core peaks: the measured dense BF16 GEMM rate (MEASURED_PEAKS.json,
+# burst) and TF32 from it by the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s).
+def tensor_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        j = json.load(open(path))
+        bf16 = float(j["bf16_tflops"]) * 1e12
+        src = "measured bf16 (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        bf16 = 1.9e15
+        src = "fallback bf16 1.9 PFLOP/s"
+    return {2: (bf16, src), 1: (bf16 * 1.1 / 2.25, src + " x nominal tf32/bf16 ratio 1.1/2.25")}
+
 
 # DRAM traffic per launch of the contraction kernel, from the ncu capture
 # summarised in profiles/gett_f64_ising_chi12.md (null once the kernel changes).
@@ -281,16 +303,24 @@ def main():
     e2e_value = world * n_e2e / t_e2e
 
     achieved = st["gett_flops"] / (st["gett_ms"] / 1e3) if st["gett_ms"] > 0 else None
-    roof = {"bound": "alu", "kernel": "gett_f64_kernel", "achieved": achieved / 1e12 if achieved else None,
-            "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_FLOPS if achieved else None,
+    if prec == 0:
+        peak, psrc, kname, bound = FP64_PEAK_FLOPS, "derived FP64 FMA rate (152 SMs x 2 FMA/clk x 2070 MHz)", \
+            "gett_f64_kernel", "alu"
+    else:
+        peak, psrc = tensor_peaks()[prec]
+        kname, bound = "tc_gemm_kernel (%s)" % ("3xTF32" if prec == 1 else "split-BF16"), "tensor"
+    roof = {"bound": bound, "kernel": kname, "achieved": achieved / 1e12 if achieved else None,
+            "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None,
             "traffic": GETT_TRAFFIC_BYTES.get(args.workload),
-            "peak_source": "derived FP64 FMA rate (152 SMs x 2 FMA/clk x 2070 MHz)",
+            "peak_source": psrc,
+            "flops_counted": "algorithmic 2*M*N*K per contraction (each split mode issues 3 tensor-core products per MAC)",
             "launches_timed": st["gett_timed"],
             "share_of_step": (st["gett_ms"] / t_ms) if t_ms > 0 else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ["f64", "tf32x3+f32acc (f64 Krylov/geometry)", "bf16x3+f32acc (f64 Krylov/geometry)"][prec], "data": "synthetic",
             "config": {"workload": args.workload, "hamiltonian": kind, "d_b": d_b, "chi": chi,
                        "n_trans": L, "prec": ["fp64", "3xtf32", "split_bf16"][prec],
                        "step": "one L-BFGS iteration (m=8)", "l2": "flushed (256 MiB write) between steps",
