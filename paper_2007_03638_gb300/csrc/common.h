@@ -96,6 +96,7 @@ struct GettCall {
   int64_t M = 0, N = 0, K = 0;
   double alpha = 1.0, beta = 0.0;
   int a32 = 0, b32 = 0, c32 = 0;  // 1: operand stored as float (mixed-precision node buffers)
+  int a_rfast = 0, b_rfast = 0;   // 1: the operand's stride-1 leg is in its row group (M for A, N for B)
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 
@@ -138,5 +139,8 @@ int check_finite(const double* x, int64_t n, cudaStream_t s);   // 1 if all fini
 // Symmetric eigendecomposition of an n x n matrix (in place -> eigenvalues in
 // evals_dev, eigenvectors as columns of V), cyclic parallel Jacobi in one CTA.
 void sym_eig(double* A, double* V, double* evals, int n, cudaStream_t s);
+// Same, optionally warm-started: with warm, V holds an orthogonal basis that
+// A was already rotated into, and the result accumulates onto it.
+void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, cudaStream_t s);
 
 }  // namespace mera

@@ -141,6 +141,8 @@ struct mera_ctx {
   mera::Eval ev[2];
   int cur = 0;                            // index of the current point's Eval
   mera::StepGeom geom;
+  std::vector<mera::DevBuf> eig_cache;    // last eigenvectors of each rho_v (warm starts)
+  std::vector<int> eig_uses;
   // optimiser
   std::vector<mera::DevBuf> mem_s, mem_y;
   std::vector<double> mem_rho;
@@ -517,8 +519,22 @@ void ensure_eig(Ctx& c, Eval& E, cudaStream_t s) {
   for (int i = 0; i < c.nt; ++i) {
     const int64_t p = c.cols[i];
     double* A = P(c.gtmp[0]);
-    copy(A, P(E.rho_v[i]), p * p, s);
-    sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)p, s);
+    if (p > 64 && c.eig_uses[i] > 0 && c.eig_uses[i] < 25) {
+      // warm start: rotate rho into the previous eigenbasis, which leaves it
+      // nearly diagonal, and continue the Jacobi sweeps from there
+      double* T = P(c.gtmp[1]);
+      double* Vc = P(c.eig_cache[i]);
+      gemm_f64('N', 'N', p, p, p, 1.0, P(E.rho_v[i]), p, Vc, p, 0.0, T, p, s);
+      gemm_f64('T', 'N', p, p, p, 1.0, Vc, p, T, p, 0.0, A, p, s);
+      copy(P(E.evec[i]), Vc, p * p, s);
+      sym_eig_from(A, P(E.evec[i]), P(E.eval[i]), (int)p, true, s);
+      c.eig_uses[i]++;
+    } else {
+      copy(A, P(E.rho_v[i]), p * p, s);
+      sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)p, s);
+      c.eig_uses[i] = 1;
+    }
+    if (p > 64) copy(P(c.eig_cache[i]), P(E.evec[i]), p * p, s);
   }
   E.eig_ready = true;
 }
@@ -1044,8 +1060,10 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     }
   }
   StepGeom& g = c.geom;
+  c.eig_uses.assign(c.nt, 0);
   for (int i = 0; i < c.nt; ++i) {
     const int64_t p = c.cols[i];
+    c.eig_cache.emplace_back(sizeof(double) * p * p);
     g.Amat.emplace_back(sizeof(double) * p * p);
     g.E.emplace_back(sizeof(double) * p * p);
     g.P1.emplace_back(sizeof(double) * p * p);
@@ -1371,8 +1389,8 @@ int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const 
     const int64_t Mp = mera::tc::round_up(std::max<int64_t>(M, 1), 128), Np = mera::tc::round_up(std::max<int64_t>(N, 1), 128);
     mera::DevBuf ah(elem * Mp * Kp), al(elem * Mp * Kp), bh(elem * Np * Kp), bl(elem * Np * Kp), err(sizeof(int));
     MERA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    mera::tc::pack_split(A, true, nullptr, K, nullptr, 1, M, K, Mp, Kp, kind, ah.p, al.p, s);
-    mera::tc::pack_split(B, true, nullptr, 1, nullptr, N, N, K, Np, Kp, kind, bh.p, bl.p, s);
+    mera::tc::pack_split(A, true, nullptr, K, nullptr, 1, M, K, Mp, Kp, kind, ah.p, al.p, false, s);
+    mera::tc::pack_split(B, true, nullptr, 1, nullptr, N, N, K, Np, Kp, kind, bh.p, bl.p, true, s);
     mera::tc::TcEpilogue ep;
     ep.C = C;
     ep.c_f64 = 1;

@@ -257,23 +257,36 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
     }
     if (!ok) atomicExch(&S->abort, 1);
-    const int64_t m = m0 + row;
-    if (ok && m < ep.M) {
-      const int64_t crow = ep.cm ? ep.cm[m] : m * ep.cms;
+    // stores: each warp stages 32x32 chunks of its rows through shared memory
+    // (the ring is idle once the last accumulator has been read), so a warp
+    // writes 32 consecutive columns of one row per instruction
+    if (ok) {
+      float* tile = reinterpret_cast<float*>(base) + q * (32 * 33);
+      (void)row;
 #pragma unroll
-      for (int j = 0; j < BN; ++j) {
-        const int64_t n = n0 + j;
-        if (n < ep.N) {
-          const int64_t idx = crow + (ep.cn ? ep.cn[n] : n * ep.cns);
-          const double v = ep.alpha * (double)acc[j];
-          if (ep.c_f64) {
-            double* C = static_cast<double*>(ep.C);
-            C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
-          } else {
-            float* C = static_cast<float*>(ep.C);
-            C[idx] = (float)(ep.beta != 0.0 ? fma(ep.beta, (double)C[idx], v) : v);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = acc[c0 + j];
+        __syncwarp();
+        const int64_t n = n0 + c0 + lane;
+        const bool nvalid = n < ep.N;
+        const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
+        for (int j = 0; j < 32; ++j) {
+          const int64_t m = m0 + q * 32 + j;
+          if (m >= ep.M) break;
+          if (nvalid) {
+            const int64_t idx = (ep.cm ? ep.cm[m] : m * ep.cms) + coff;
+            const double v = ep.alpha * (double)tile[j * 33 + lane];
+            if (ep.c_f64) {
+              double* C = static_cast<double*>(ep.C);
+              C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+            } else {
+              float* C = static_cast<float*>(ep.C);
+              C[idx] = (float)(ep.beta != 0.0 ? fma(ep.beta, (double)C[idx], v) : v);
+            }
           }
         }
+        __syncwarp();
       }
     }
   }
@@ -320,6 +333,41 @@ __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __
       static_cast<__nv_bfloat16*>(hi)[i] = h;
       static_cast<__nv_bfloat16*>(lo)[i] = l;
     }
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void store_split(double v, void* hi, void* lo, int64_t i) {
+  if (KIND == KIND_TF32) {
+    const float h = tf32_round((float)v);
+    static_cast<float*>(hi)[i] = h;
+    static_cast<float*>(lo)[i] = tf32_round((float)(v - (double)h));
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    static_cast<__nv_bfloat16*>(hi)[i] = h;
+    static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+  }
+}
+
+// Same packing through a 32x32 shared-memory tile: reads run along r (the
+// source's stride-1 direction), writes along k.
+template <typename Src, int KIND>
+__global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt,
+                                        int64_t rs, const int64_t* __restrict__ kt, int64_t ks, int64_t R,
+                                        int64_t K, int64_t Rp, int64_t Kp, void* hi, void* lo) {
+  __shared__ Src tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const int64_t r = r0 + tx;
+  const int64_t roff = r < R ? (rt ? rt[r] : r * rs) : 0;
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t k = k0 + j;
+    tile[j][tx] = (r < R && k < K) ? src[roff + (kt ? kt[k] : k * ks)] : (Src)0;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t rr = r0 + j, kk = k0 + tx;
+    if (rr < Rp && kk < Kp) store_split<KIND>((double)tile[tx][j], hi, lo, rr * Kp + kk);
   }
 }
 
@@ -382,7 +430,26 @@ int64_t padded_k(int64_t K, int kind) {
 }
 
 void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
-                int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, cudaStream_t s) {
+                int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, bool rows_fast,
+                cudaStream_t s) {
+  if (rows_fast) {
+    if ((Rp + 31) / 32 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: too many rows");
+    const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((Rp + 31) / 32)), blk(32, 8);
+    if (kind == KIND_TF32) {
+      if (src_f64)
+        pack_split_tiled_kernel<double, KIND_TF32><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      else
+        pack_split_tiled_kernel<float, KIND_TF32><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+    } else {
+      if (src_f64)
+        pack_split_tiled_kernel<double, KIND_BF16><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      else
+        pack_split_tiled_kernel<float, KIND_BF16><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+    }
+    count_launch();
+    MERA_CHECK_LAUNCH();
+    return;
+  }
   const int64_t total = Rp * Kp;
   const int threads = 256;
   const unsigned blocks = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 152 * 32);

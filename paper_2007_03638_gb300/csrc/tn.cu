@@ -119,6 +119,16 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
   g.M = m;
   g.N = n;
   g.K = k;
+  // orientation hints for operand packing: where is each operand's stride-1 leg?
+  auto fast_leg = [](const TDesc& t) {
+    int best = -1;
+    for (size_t j = 0; j < t.legs.size(); ++j)
+      if (t.ext[j] > 1 && (best < 0 || t.stride[j] < t.stride[best])) best = (int)j;
+    return best < 0 ? -1 : t.legs[best];
+  };
+  const int fa = fast_leg(A), fb = fast_leg(B);
+  g.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
+  g.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
   return p;
 }
 
@@ -251,8 +261,8 @@ void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
   void* bh = w + o; o = align(o + elem * Np * Kp);
   void* bl = w + o;
   // A rows = M group, A columns = K group; B rows (of the packed K-major plane) = N group
-  tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, s);
-  tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, s);
+  tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s);
+  tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s);
   tc::TcEpilogue ep;
   ep.alpha = g.alpha;
   ep.beta = g.beta;

@@ -200,3 +200,31 @@ def test_energy_grad_mixed_precision(gm, prec, tol, d_b, chi, L, kind, seed):
     assert err_d < 10 * tol
     st = m.stats()
     assert st["gett_launches"] > 0
+
+
+def test_preconditioner_large_rho_warm_start(gm):
+    """rho_u of the scale-invariant layer is 81 x 81 (d_b=3, chi=9): the
+    eigen-decomposition runs on the multi-CTA Jacobi path; the second
+    evaluation (after a retraction) starts from the previous eigenbasis."""
+    us, ws = inp.random_mera(3, 9, 1, seed=11)
+    h3 = _ham(3, "random", 4)
+    m = gm.Mera(gm.default_config(3, 9, 1), h3)
+    pt = _flat(us, ws)
+    m.set_tensors(pt)
+    kinds = [geo.STIEFEL if i % 2 == 0 else geo.GRASSMANN for i in range(len(pt))]
+    rng = np.random.default_rng(2)
+    for rep in range(2):
+        e, G = m.energy_grad()
+        us_c, ws_c = pt[0::2], pt[1::2]
+        e_ref, ds, info = om.energy_grad(h3, us_c, ws_c)
+        assert abs(e - e_ref) < 1e-12 * max(1, abs(e_ref))
+        rv = om.tensor_density_matrices(info["rho"], ws_c)
+        Gr = [geo.project(W, d, k) for W, d, k in zip(pt, ds, kinds)]
+        X = [geo.project(W, rng.standard_normal(W.shape), k) for W, k in zip(pt, kinds)]
+        Xt = m.precondition(X)
+        for W, x, r, g, k, xt in zip(pt, X, rv, Gr, kinds, Xt):
+            ref = geo.precondition(W, x, r, float(np.linalg.norm(g)), k)
+            assert np.abs(xt - ref).max() < 1e-10 * max(1, np.abs(ref).max()), rep
+        step = [-0.05 * g for g in G]
+        m.retract(step, 1.0)
+        pt = m.get_tensors()
