@@ -91,6 +91,10 @@ typedef struct {
     int recompute_env; /* 1: recompute the ascending intermediates in the
                           gradient pass instead of keeping them (less memory)  */
     int lbfgs_m;       /* L-BFGS memory length                                 */
+    int b_chunk;       /* slice length of the middle coarse leg in the chi^9
+                          contraction chain (must divide the coarse bond
+                          dimension; 0 = automatic: no slicing while the
+                          7-leg intermediate has at most 2^30 entries)        */
 } mera_config;
 
 /* Fill *cfg with defaults for (d_b, chi, n_trans): F64, FP64 contractions,

@@ -131,6 +131,7 @@ struct mera_ctx {
   mera::DevBuf h0;
   std::vector<mera::DevBuf> h, rho;       // level operators h_0..h_L, rho_0..rho_L
   mera::DevBuf x;                         // scale-invariant series
+  mera::DevBuf bvec;                      // right-hand side 1/chi^3 of the fixed-point solve
   bool have_rho = false, have_x = false;
   mera::DevBuf kbasis, ktmp, kcoef;       // Krylov workspace
   mera::DevBuf scratch;                   // transient contraction buffers
@@ -177,6 +178,17 @@ void bind_leaves(Layer& ly, int side, const double* op, const double* u, const d
   for (int l : {4, 6, 7, 8, 9, 10}) b.leaf[l] = w;
 }
 
+// Slice length of the coarse leg b: keep the 7-leg intermediate (chi_f^6 * b
+// entries) at most 2^30 entries per slice.
+int64_t choose_chunk(int64_t cf, int64_t cc) {
+  const int64_t f6 = ipow(cf, 6);
+  if (f6 * cc <= (int64_t)1 << 30) return 0;
+  int64_t nb = 1;
+  for (int64_t d = 1; d <= cc; ++d)
+    if (cc % d == 0 && f6 * d <= (int64_t)1 << 30) nb = d;
+  return nb;
+}
+
 void build_layers(Ctx& c) {
   c.layers.resize(c.L + 1);
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
@@ -186,23 +198,27 @@ void build_layers(Ctx& c) {
     Layer& ly = c.layers[l];
     ly.cf = c.dims[l];
     ly.cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    int64_t chunk = choose_chunk(ly.cf, ly.cc);
+    if (c.cfg.b_chunk > 0) {
+      if (ly.cc % c.cfg.b_chunk) throw Error(MERA_ERR_ARG, "b_chunk must divide every coarse bond dimension");
+      chunk = c.cfg.b_chunk < ly.cc ? c.cfg.b_chunk : 0;
+    }
     for (int sd = 0; sd < 2; ++sd) {
-      ly.net[sd] = std::make_unique<SideNet>(sd == 0 ? 'L' : 'R', ly.cf, ly.cc, c.pool);
+      ly.net[sd] = std::make_unique<SideNet>(sd == 0 ? 'L' : 'R', ly.cf, ly.cc, c.pool, chunk);
       SideNet& net = *ly.net[sd];
       // persistent node values: N1 N3 N4 N6 N7 N8 N9
       for (int node : {11, 13, 14, 16, 17, 18, 19}) {
-        ly.own[sd].emplace_back(es * net.node_size(node));
+        ly.own[sd].emplace_back(es * net.alloc_size(node));
         ly.buf[sd].val[node] = P(ly.own[sd].back());
       }
       ly.buf[sd].f32 = mixed;
       ly.buf[sd].ex = &c.ex;
       size_t need = 0;
-      for (int node : {12, 15}) need += net.node_size(node);
-      for (int node = 11; node < 20; ++node) need += net.node_size(node);
+      for (int node : {12, 15}) need += net.alloc_size(node);
+      for (int node = 11; node < 20; ++node) need += net.alloc_size(node);
       scratch_need = std::max(scratch_need, need);
-      for (int node = SideNet::NLEAF; node < SideNet::NNODE; ++node)
-        for (const GemmPlan* p : {&net.fwd(node), &net.bwd_left(node), &net.bwd_right(node)})
-          ws_need = std::max(ws_need, tc_workspace_bytes(p->proto, c.cfg.prec));
+      for (const GemmPlan* p : net.executed_plans())
+        ws_need = std::max(ws_need, tc_workspace_bytes(p->proto, c.cfg.prec));
     }
   }
   c.scratch.alloc(es * scratch_need);
@@ -222,11 +238,11 @@ void build_layers(Ctx& c) {
       char* p = static_cast<char*>(c.scratch.p);
       for (int node : {12, 15}) {
         ly.buf[sd].val[node] = reinterpret_cast<double*>(p);
-        p += es * net.node_size(node);
+        p += es * net.alloc_size(node);
       }
       for (int node = 11; node < 20; ++node) {
         ly.buf[sd].adj[node] = reinterpret_cast<double*>(p);
-        p += es * net.node_size(node);
+        p += es * net.alloc_size(node);
       }
     }
 }
@@ -388,7 +404,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
     fill(0.0, rhoS, n, s);
     add_identity(1.0 / (double)n3, rhoS, n3, s);
   }
-  double* bvec = P(c.gtmp[5]);
+  double* bvec = P(c.bvec);
   fill(0.0, bvec, n, s);
   add_identity(1.0 / (double)n3, bvec, n3, s);
   // the residual of a Krylov solve cannot fall below the rounding level of
@@ -1042,7 +1058,8 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.kcoef.alloc(sizeof(double) * (cfg.krylov_dim + 2));
   c.red.init(std::max(8, cfg.krylov_dim + 2));
   // geometry temporaries: max over tensors / rho_u builders
-  int64_t gmax = nS;  // bvec in gtmp[5] also used for chi^6 vectors
+  c.bvec.alloc(sizeof(double) * nS);
+  int64_t gmax = 1;
   for (int l = 0; l <= c.L; ++l) {
     const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
     gmax = std::max({gmax, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
@@ -1151,6 +1168,7 @@ void mera_config_default(mera_config* c, int d_b, int chi, int n_trans) {
   c->krylov_tol = 1e-14;
   c->recompute_env = 0;
   c->lbfgs_m = 8;
+  c->b_chunk = 0;
 }
 
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out) {

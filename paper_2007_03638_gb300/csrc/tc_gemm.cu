@@ -152,8 +152,10 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Smem* S = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * BM;
-  const int64_t n0 = (int64_t)blockIdx.y * BN;
+  // N tiles vary fastest across the grid: CTAs running together share one A
+  // tile (the larger operand in the chi^9 steps), which is then read once from DRAM
+  const int64_t n0 = (int64_t)blockIdx.x * BN;
+  const int64_t m0 = (int64_t)blockIdx.y * BM;
   const int kblocks = ep.kblocks;
 
   if (threadIdx.x == 0) {
@@ -418,8 +420,8 @@ void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
     MERA_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr_set[dev] = true;
   }
-  if (nt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: N too large for grid");
-  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)mt, (unsigned)nt), 192, sm, s>>>(ah, al, bh, bl, ep);
+  if (mt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: M too large for grid");
+  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)nt, (unsigned)mt), 192, sm, s>>>(ah, al, bh, bl, ep);
 }
 
 }  // namespace

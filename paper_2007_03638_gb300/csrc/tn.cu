@@ -146,7 +146,7 @@ const int SideNet::kids_[10][2] = {
     {18, 19},  // N10 = N8 x N9 = ascended operator
 };
 
-SideNet::SideNet(char side, int64_t cf, int64_t cc, TablePool& pool) : side_(side) {
+SideNet::SideNet(char side, int64_t cf, int64_t cc, TablePool& pool, int64_t chunk) : side_(side) {
   // leg names -> ids; coarse legs a b c (conj side) A B C (plain side)
   std::map<std::string, int> id;
   auto L = [&](const char* names) {
@@ -224,6 +224,49 @@ SideNet::SideNet(char side, int64_t cf, int64_t cc, TablePool& pool) : side_(sid
     bwdl_[k] = make_plan(dnode, desc_[r], dl, pool);
     bwdr_[k] = make_plan(desc_[l], dnode, desc_[r], pool);
   }
+  cc_ = cc;
+  if (chunk > 0 && chunk < cc) {
+    if (cc % chunk) throw Error(MERA_ERR_ARG, "SideNet: chunk must divide the coarse dimension");
+    sliced_ = true;
+    nb_ = chunk;
+    const int b = id.at("b");
+    auto view = [&](const TDesc& d) {  // same strides, leg b restricted to one slice
+      TDesc v = d;
+      v.ext[d.find(b)] = chunk;
+      return v;
+    };
+    const TDesc& n3 = desc_[13];
+    const TDesc& n4 = desc_[14];
+    const TDesc& n6 = desc_[16];
+    const TDesc& n7 = desc_[17];
+    std::vector<int64_t> e5 = desc_[15].ext;
+    e5[desc_[15].find(b)] = chunk;
+    n5c_ = make_desc(desc_[15].legs, e5);
+    sb4_ = n4.stride[n4.find(b)];
+    sb7_ = n7.stride[n7.find(b)];
+    f5c_ = make_plan(n3, view(n4), n5c_, pool);
+    f7c_ = make_plan(n5c_, n6, view(n7), pool);
+    b7c_ = make_plan(view(n7), n6, n5c_, pool);
+    b5lc_ = make_plan(n5c_, view(n4), n3, pool);
+    b5rc_ = make_plan(n3, n5c_, view(n4), pool);
+  }
+}
+
+std::vector<const GemmPlan*> SideNet::executed_plans() const {
+  std::vector<const GemmPlan*> v;
+  for (int node = NLEAF; node < NNODE; ++node) {
+    if (sliced_ && (node == 15 || node == 17)) {
+      // only the sliced chi^9 chain runs; N7's other child (N6) gets no adjoint
+      continue;
+    }
+    v.push_back(&fwd(node));
+    v.push_back(&bwd_left(node));
+    v.push_back(&bwd_right(node));
+  }
+  if (sliced_) {
+    for (const GemmPlan* p : {&f5c_, &f7c_, &b7c_, &b5lc_, &b5rc_}) v.push_back(p);
+  }
+  return v;
 }
 
 double SideNet::forward_flops() const {
@@ -316,6 +359,11 @@ inline const double* value(const SideBufs& b, int node) {
   return node < SideNet::NLEAF ? b.leaf[node] : b.val[node];
 }
 inline bool internal(int node) { return node >= SideNet::NLEAF && node != SideNet::ROOT; }
+// Advance a node pointer by `off` elements of its storage type.
+inline double* offp(const SideBufs& b, const double* p, int64_t off) {
+  char* c = reinterpret_cast<char*>(const_cast<double*>(p));
+  return reinterpret_cast<double*>(c + off * (b.f32 ? 4 : 8));
+}
 }  // namespace
 
 void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
@@ -327,6 +375,17 @@ void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
 
 void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, double beta, cudaStream_t s) {
   for (int node : {12, 13, 15, 17, 18}) {
+    if (net.sliced() && node == 15) {
+      // N5 = N3 x N4 and N7 = N5 x N6 one slice of the coarse leg b at a time
+      for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
+        run(b, net.f5c(), b.val[13], true, offp(b, b.val[14], b0 * net.b_stride_n4()), true, b.val[15], true,
+            1.0, 0.0, s);
+        run(b, net.f7c(), b.val[15], true, b.val[16], true, offp(b, b.val[17], b0 * net.b_stride_n7()), true,
+            1.0, 0.0, s);
+      }
+      continue;
+    }
+    if (net.sliced() && node == 17) continue;
     const int l = SideNet::left(node), r = SideNet::right(node);
     run(b, net.fwd(node), value(b, l), internal(l), value(b, r), internal(r), b.val[node], true, 1.0, 0.0, s);
   }
@@ -345,6 +404,21 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
     need[node] = need[SideNet::left(node)] || need[SideNet::right(node)];
   for (int node = SideNet::ROOT; node >= SideNet::NLEAF; --node) {
     if (!need[node]) continue;
+    if (net.sliced() && node == 15) continue;  // handled with N7 below
+    if (net.sliced() && node == 17) {
+      // dN5 one slice of b at a time, consumed at once by N5's children
+      for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
+        run(b, net.b7c(), offp(b, b.adj[17], b0 * net.b_stride_n7()), true, b.val[16], true, b.adj[15], true,
+            1.0, 0.0, s);
+        if (need[13])
+          run(b, net.b5lc(), b.adj[15], true, offp(b, b.val[14], b0 * net.b_stride_n4()), true, b.adj[13], true,
+              1.0, b0 == 0 ? 0.0 : 1.0, s);
+        if (need[14])
+          run(b, net.b5rc(), b.val[13], true, b.adj[15], true, offp(b, b.adj[14], b0 * net.b_stride_n4()), true,
+              1.0, 0.0, s);
+      }
+      continue;
+    }
     const int l = SideNet::left(node), r = SideNet::right(node);
     const double* dn = b.adj[node];
     for (int side = 0; side < 2; ++side) {

@@ -49,10 +49,26 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
 class SideNet {
  public:
   static constexpr int NLEAF = 11, NNODE = 21, ROOT = 20;
-  SideNet(char side, int64_t chi_f, int64_t chi_c, TablePool& pool);
+  // chunk: slice length of the middle coarse leg b in the chi^9 chain
+  // (N4 -> N5 -> N7 forward, dN7 -> dN5 -> dN3, dN4 backward); 0 = no slicing.
+  SideNet(char side, int64_t chi_f, int64_t chi_c, TablePool& pool, int64_t chunk = 0);
 
   // Size (elements) of each internal node value and of each adjoint.
   int64_t node_size(int i) const { return desc_[i].size(); }
+  // Elements a buffer for node i must hold (the 7-leg N5 only one slice).
+  int64_t alloc_size(int i) const { return (sliced_ && i == 15) ? n5c_.size() : desc_[i].size(); }
+  // Every plan that evaluations execute.
+  std::vector<const GemmPlan*> executed_plans() const;
+  bool sliced() const { return sliced_; }
+  int64_t chunk() const { return nb_; }
+  int64_t coarse() const { return cc_; }
+  int64_t b_stride_n4() const { return sb4_; }
+  int64_t b_stride_n7() const { return sb7_; }
+  const GemmPlan& f5c() const { return f5c_; }
+  const GemmPlan& f7c() const { return f7c_; }
+  const GemmPlan& b7c() const { return b7c_; }
+  const GemmPlan& b5lc() const { return b5lc_; }
+  const GemmPlan& b5rc() const { return b5rc_; }
   static int left(int i) { return kids_[i - NLEAF][0]; }
   static int right(int i) { return kids_[i - NLEAF][1]; }
 
@@ -69,6 +85,10 @@ class SideNet {
   char side_;
   TDesc desc_[NNODE];
   GemmPlan fwd_[10], bwdl_[10], bwdr_[10];
+  bool sliced_ = false;
+  int64_t nb_ = 0, cc_ = 0, sb4_ = 0, sb7_ = 0;
+  TDesc n5c_;
+  GemmPlan f5c_, f7c_, b7c_, b5lc_, b5rc_;
 };
 
 // How contractions run: FP64 kernel, or tensor cores (3xTF32 / split-BF16)

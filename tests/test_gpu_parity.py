@@ -228,3 +228,20 @@ def test_preconditioner_large_rho_warm_start(gm):
         step = [-0.05 * g for g in G]
         m.retract(step, 1.0)
         pt = m.get_tensors()
+
+
+@pytest.mark.parametrize("prec,chunk,tol", [(0, 2, 1e-12), (0, 4, 1e-12), (1, 2, 2e-6)])
+def test_sliced_chain_parity(gm, prec, chunk, tol):
+    """The chi^9 chain evaluated one slice of the middle coarse leg at a time
+    (as at chi=32) gives the oracle's energy and derivatives (chi=8)."""
+    us, ws = inp.random_mera(4, 8, 3, seed=6)
+    h3 = _ham(4, "xxz")
+    m = gm.Mera(gm.default_config(4, 8, 3, prec=prec, b_chunk=chunk), h3)
+    m.set_tensors(_flat(us, ws))
+    e, G, D = m.energy_grad(deriv=True)
+    e_ref, ds, _ = om.energy_grad(h3, us, ws)
+    assert abs(e - e_ref) <= tol * max(1.0, abs(e_ref))
+    for i in range(len(ds)):
+        assert _rel(D[i], ds[i]) < 10 * tol, i
+    with pytest.raises(gm.MeraError):
+        gm.Mera(gm.default_config(4, 8, 3, b_chunk=3), h3)
