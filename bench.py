@@ -34,20 +34,31 @@ sys.path.insert(0, ROOT)
 from paper_2007_03638_gb300 import inputs as inp  # noqa: E402
 
 WORKLOADS = {
-    # name: (hamiltonian, d_b, chi, n_trans, prec)  prec: 0 FP64, 1 3xTF32, 2 split-BF16
-    "ising_chi12_L3_fp64": ("ising", 4, 12, 3, 0),
-    "ising_chi8_L3_fp64": ("ising", 4, 8, 3, 0),
-    "ising_chi4_L2_fp64": ("ising", 4, 4, 2, 0),
-    "ising_chi12_L3_3xtf32": ("ising", 4, 12, 3, 1),
-    "ising_chi12_L3_bf16": ("ising", 4, 12, 3, 2),
-    "xxz_chi16_L3_3xtf32": ("xxz", 4, 16, 3, 1),
-    "xxz_chi16_L3_bf16": ("xxz", 4, 16, 3, 2),
-    "xxz_chi24_L3_3xtf32": ("xxz", 4, 24, 3, 1),
-    "xxz_chi24_L3_bf16": ("xxz", 4, 24, 3, 2),
-    "xxz_chi32_L3_3xtf32": ("xxz", 4, 32, 3, 1),
-    "xxz_chi32_L3_bf16": ("xxz", 4, 32, 3, 2),
+    # name: (hamiltonian, d_b, chi, n_trans, prec, extra config)
+    # prec: 0 FP64, 1 3xTF32, 2 split-BF16
+    "ising_chi4_L2_fp64": ("ising", 4, 4, 2, 0, {}),
+    "ising_chi8_L3_fp64": ("ising", 4, 8, 3, 0, {}),
+    "ising_chi12_L3_fp64": ("ising", 4, 12, 3, 0, {}),
+    "ising_chi12_L3_3xtf32": ("ising", 4, 12, 3, 1, {}),
+    "ising_chi12_L3_bf16": ("ising", 4, 12, 3, 2, {}),
+    "xxz_chi16_L3_3xtf32": ("xxz", 4, 16, 3, 1, {"lbfgs_m": 16}),
+    "xxz_chi16_L3_bf16": ("xxz", 4, 16, 3, 2, {"lbfgs_m": 16}),
+    "xxz_chi24_L3_3xtf32": ("xxz", 4, 24, 3, 1, {"lbfgs_m": 16}),
+    "xxz_chi24_L3_bf16": ("xxz", 4, 24, 3, 2, {"lbfgs_m": 16}),
+    "xxz_chi32_L3_3xtf32": ("xxz", 4, 32, 3, 1, {"lbfgs_m": 16, "krylov_dim": 4}),
+    "xxz_chi32_L3_bf16": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4}),
 }
-DEFAULT_WORKLOAD = "ising_chi12_L3_fp64"
+DEFAULT_WORKLOAD = "xxz_chi32_L3_bf16"
+# Algorithmic flops of one energy/gradient evaluation as the GPU path counts
+# them inside L-BFGS steps (measured by this script's own GPU runs); used only
+# to express the reference arm's bounded sample in gradient evaluations.
+FLOPS_PER_GRAD = {
+    "xxz_chi32_L3_bf16": 3.3e15, "xxz_chi32_L3_3xtf32": 3.3e15,
+    "xxz_chi24_L3_3xtf32": 4.7e14, "xxz_chi24_L3_bf16": 4.7e14,
+    "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13,
+    "ising_chi12_L3_fp64": 1.6e12, "ising_chi12_L3_3xtf32": 1.13e12, "ising_chi12_L3_bf16": 1.13e12,
+    "ising_chi8_L3_fp64": 5e10, "ising_chi4_L2_fp64": 1.2e8,
+}
 METRIC = "MERA grad evals/s"
 UNIT = "grad_evals/s"
 
@@ -79,10 +90,15 @@ def hamiltonian(kind, d_b):
     return inp.three_site_blocked(bond) if d_b == 4 else inp.three_site_unblocked(bond)
 
 
-def ascend_flops(chi):
-    """Algorithmic flops of one averaged ascending map at bond chi (both sides,
-    the fixed contraction tree: 2 chi^9 + 4 chi^8 + 2 chi^6 + 2 chi^5 MACs per side)."""
-    macs = 2 * chi**9 + 4 * chi**8 + 2 * chi**6 + 2 * chi**5
+def ascend_flops(cf, cc=None):
+    """Algorithmic flops of one averaged ascending map of a layer with fine
+    bond cf and coarse bond cc (both sides; the library's contraction tree,
+    whose ten steps cost cf^3cc^2, cf^8, cf^8, cf^5cc, cf^8cc, cf^5cc, cf^7cc^2,
+    cf^4cc^4, cf^3cc^2, cf^2cc^6 multiply-adds; 2 chi^9 + 4 chi^8 + ... at cf = cc)."""
+    cc = cf if cc is None else cc
+    f, c = float(cf), float(cc)
+    macs = (f**3 * c**2 + 2 * f**8 + f**5 * c + f**8 * c + f**5 * c + f**7 * c**2 + f**4 * c**4
+            + f**3 * c**2 + f**2 * c**6)
     return 2 * 2.0 * macs
 
 
@@ -134,14 +150,25 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def oracle_sample(chi, seconds=10.0, seed=0):
-    """Time the oracle's averaged ascending map at bond chi (one bounded sample
-    of the workload's dominant operation) on the host cores."""
+def sample_layer(d_b, chi, L):
+    """The largest layer of the workload whose oracle ascending map stays a
+    bounded (seconds-scale) sample: the scale-invariant layer up to chi=16,
+    otherwise transition layer 1."""
+    dims = inp.layer_dims(d_b, chi, L)
+    if chi <= 16:
+        return L, dims[L], dims[L]
+    return 1, dims[1], dims[2]
+
+
+def oracle_sample(d_b, chi, L, seconds=10.0, seed=0):
+    """Time the oracle's averaged ascending map of one layer of the workload
+    (seeded tensors of that layer, random symmetric operator) on the host cores."""
     from oracle import mera as om
-    us, ws = inp.random_mera(4, chi, 1, seed=seed) if chi <= 16 else inp.random_mera(4, chi, 2, seed=seed)
-    u, w = us[-1], ws[-1]
+    layer, cf, cc = sample_layer(d_b, chi, L)
+    us, ws = inp.random_mera(d_b, chi, L, seed=seed)
+    u, w = us[layer], ws[layer]
     rng = np.random.default_rng(seed)
-    h = rng.standard_normal((chi**3, chi**3))
+    h = rng.standard_normal((cf**3, cf**3))
     h = 0.5 * (h + h.T)
     n, t0 = 0, time.perf_counter()
     while True:
@@ -150,7 +177,7 @@ def oracle_sample(chi, seconds=10.0, seed=0):
         dt = time.perf_counter() - t0
         if dt >= seconds:
             break
-    return dt / n, n
+    return dt / n, n, layer, cf, cc
 
 
 def host_cores():
@@ -171,28 +198,24 @@ def run_reference(args, wl):
     world, rank, _ = dist_setup()
     if rank != 0:
         return
-    kind, d_b, chi, L, prec = wl
-    flops_grad = float(args.ref_flops_per_grad) if args.ref_flops_per_grad else None
-    if flops_grad is None:
-        # algorithmic flops of one gradient evaluation of this workload as the
-        # GPU path counts them (fixed here from the contraction plan so the
-        # reference arm needs no GPU): ascend/descend applications per layer
-        flops_grad = ascend_flops(chi) * (L + 1) * 8.0
-    frac = ascend_flops(chi) / flops_grad
+    kind, d_b, chi, L, prec, extra = wl
+    flops_grad = args.ref_flops_per_grad or FLOPS_PER_GRAD[args.workload]
     per = []
     for i in range(args.warmup + args.steps):
-        t, n = oracle_sample(chi, seconds=args.ref_seconds, seed=i)
+        t, n, layer, cf, cc = oracle_sample(d_b, chi, L, seconds=args.ref_seconds, seed=i)
         if i >= args.warmup:
             per.append(t)
+    frac = ascend_flops(cf, cc) / flops_grad
     t = sum(per) / len(per)
     value = frac / t
+    sample = (f"oracle (NumPy FP64) averaged ascending map of layer {layer} (chi {cf}->{cc}), "
+              f"{t:.2f} s each = {frac:.3g} of one gradient evaluation's algorithmic flops ({flops_grad:.3g})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "chi": chi, "n_trans": L},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                             "sample": f"oracle averaged ascending map at chi={chi} "
-                                       f"(fraction {frac:.4f} of one gradient evaluation's flops)"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -200,7 +223,7 @@ def run_reference(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
@@ -230,10 +253,10 @@ def main():
     b.build()
     from paper_2007_03638_gb300 import mera as gm
 
-    kind, d_b, chi, L, prec = wl
+    kind, d_b, chi, L, prec, extra = wl
     h3 = hamiltonian(kind, d_b)
     stream = torch.cuda.current_stream()
-    m = gm.Mera(gm.default_config(d_b, chi, L, prec=prec), h3, stream=stream.cuda_stream)
+    m = gm.Mera(gm.default_config(d_b, chi, L, prec=prec, **extra), h3, stream=stream.cuda_stream)
     us, ws = inp.random_mera(d_b, chi, L, seed=args.seed + rank)
     point = [t for p in zip(us, ws) for t in p]
     m.set_tensors(point)
@@ -323,7 +346,7 @@ def main():
             "dtype": ["f64", "tf32x3+f32acc (f64 Krylov/geometry)", "bf16x3+f32acc (f64 Krylov/geometry)"][prec], "data": "synthetic",
             "config": {"workload": args.workload, "hamiltonian": kind, "d_b": d_b, "chi": chi,
                        "n_trans": L, "prec": ["fp64", "3xtf32", "split_bf16"][prec],
-                       "step": "one L-BFGS iteration (m=8)", "l2": "flushed (256 MiB write) between steps",
+                       "step": "one L-BFGS iteration (m=%d)" % extra.get("lbfgs_m", 8), "l2": "flushed (256 MiB write) between steps",
                        "parallelism": f"replicas x{world}"},
             "lbfgs_iters_per_s": world * args.steps / (t_ms / 1e3),
             "grad_evals_per_step": grads / args.steps,
@@ -336,12 +359,12 @@ def main():
             "gpu_launches": st["launches"],
             "clocks": clocks.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, n = oracle_sample(chi, seconds=args.cpu_seconds)
-        frac = ascend_flops(chi) / gett_flops_per_grad
+        t, n, layer, cf, cc = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds)
+        frac = ascend_flops(cf, cc) / gett_flops_per_grad
         line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                                "sample": f"{n} x oracle averaged ascending map at chi={chi}, "
-                                          f"{t:.2f} s each = {frac:.4f} of one gradient evaluation's "
-                                          f"algorithmic flops"}
+                                "sample": f"{n} x oracle (NumPy FP64) averaged ascending map of layer {layer} "
+                                          f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient "
+                                          f"evaluation's algorithmic flops"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

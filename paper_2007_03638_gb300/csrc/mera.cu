@@ -1322,23 +1322,45 @@ int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
 }
 
 size_t mera_footprint_bytes(const mera_config* cfg) {
-  if (!cfg) return 0;
-  // tensors (points, gradients, history) + level operators + Krylov + nets
-  std::vector<int64_t> dims{cfg->d_b};
-  for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
-  int64_t total = 0, ops = 0, nets = 0, scratch = 0;
-  for (size_t l = 0; l < dims.size(); ++l) {
-    const int64_t f = dims[l], c = l + 1 < dims.size() ? dims[l + 1] : dims[l];
-    total += f * f * f * f + f * f * c;
-    ops += 2 * mera::ipow(f, 6);
-    const int64_t node6 = std::max({mera::ipow(f, 6), mera::ipow(f, 4) * c * c, f * f * mera::ipow(c, 4)});
-    nets += 2 * (4 * node6 + 2 * mera::ipow(f, 4) * c);
-    scratch = std::max(scratch, mera::ipow(f, 6) * c * 2 + 6 * node6);
+  if (!cfg || cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
+  try {
+    // mirror of the allocations made by mera_create, with plans built dry
+    std::vector<int64_t> dims{cfg->d_b};
+    for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
+    if (dims.back() != cfg->chi) return 0;
+    const bool mixed = cfg->prec != MERA_PREC_FP64;
+    const size_t es = mixed ? 4 : 8;
+    mera::TablePool pool(true);
+    size_t bytes = 0, scratch = 0, ws = 0, total = 0, gmax = 1;
+    for (size_t l = 0; l < dims.size(); ++l) {
+      const int64_t cf = dims[l], cc = l + 1 < dims.size() ? dims[l + 1] : dims[l];
+      int64_t chunk = mera::choose_chunk(cf, cc);
+      if (cfg->b_chunk > 0) chunk = cfg->b_chunk < cc ? cfg->b_chunk : 0;
+      total += cf * cf * cf * cf + cf * cf * cc;
+      bytes += 2 * 8 * (size_t)mera::ipow(cf, 6);  // h_l, rho_l
+      gmax = std::max<size_t>({gmax, (size_t)(cf * cf * cf * cf), (size_t)(cc * cc * cc * cc),
+                               (size_t)(cf * cf * cc * cc * cc), (size_t)(cf * cc * cc * cf),
+                               (size_t)(cf * cc * cf * cf * cf)});
+      for (char sd : {'L', 'R'}) {
+        mera::SideNet net(sd, cf, cc, pool, chunk);
+        for (int node : {11, 13, 14, 16, 17, 18, 19}) bytes += es * net.alloc_size(node);
+        size_t need = 0;
+        for (int node : {12, 15}) need += net.alloc_size(node);
+        for (int node = 11; node < 20; ++node) need += net.alloc_size(node);
+        scratch = std::max(scratch, es * need);
+        for (const mera::GemmPlan* p : net.executed_plans())
+          ws = std::max(ws, mera::tc_workspace_bytes(p->proto, cfg->prec));
+      }
+    }
+    const size_t nS = (size_t)mera::ipow(cfg->chi, 6);
+    bytes += scratch + ws + pool.bytes();
+    bytes += 8 * nS * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);  // basis, tmp, x, bvec
+    bytes += 8 * gmax * 6;
+    bytes += 8 * (size_t)total * (size_t)(2 * std::max(1, cfg->lbfgs_m) + 2 + 4 + 4);
+    return bytes;
+  } catch (...) {
+    return 0;
   }
-  const int64_t nS = mera::ipow(cfg->chi, 6);
-  const int64_t krylov = nS * (cfg->krylov_dim + 3);
-  const int64_t tangents = total * (2 * std::max(1, cfg->lbfgs_m) + 10);
-  return sizeof(double) * (size_t)(tangents + ops + krylov + nets + scratch + 6 * nS);
 }
 
 int64_t mera_launch_count(mera_t m) { return m ? m->prof.launches : 0; }

@@ -27,10 +27,13 @@ struct TDesc {
 // Device-resident offset tables, deduplicated by content.
 class TablePool {
  public:
+  // dry: count the bytes tables would take, allocate nothing (footprint queries)
+  explicit TablePool(bool dry = false) : dry_(dry) {}
   const int64_t* get(const std::vector<int64_t>& host);
   size_t bytes() const { return bytes_; }
 
  private:
+  bool dry_ = false;
   std::map<std::vector<int64_t>, DevBuf> tables_;
   size_t bytes_ = 0;
 };
