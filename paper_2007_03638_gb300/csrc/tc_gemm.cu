@@ -122,11 +122,13 @@ __host__ __device__ constexpr uint32_t idesc() {
          | ((uint32_t)(BM >> 4) << 24);              // M / 16
 }
 
+constexpr int NACC = 4;  // tensor-memory accumulator buffers (4 x 128 columns)
+
 struct Smem {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
-  uint64_t acc_full[2];
-  uint64_t acc_empty[2];
+  uint64_t acc_full[NACC];
+  uint64_t acc_empty[NACC];
   uint32_t tmem;
   int abort;
 };
@@ -135,7 +137,8 @@ struct Smem {
 // 2..5 promote/epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
 // The tensor cores' FP32 accumulation truncates, so each K block is
 // accumulated into a fresh tensor-memory buffer (two buffers alternate) and
-// folded into FP32 registers with round-to-nearest adds by the epilogue warps.
+// folded into FP32 registers with round-to-nearest adds by the epilogue warps;
+// NACC buffers let the MMAs run up to NACC-1 K blocks ahead of the folding.
 template <int KIND, int BN>
 __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
                                                          const __grid_constant__ CUtensorMap a_lo,
@@ -147,7 +150,7 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
   constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   constexpr int KSTEP_BYTES = 32;          // bytes of K per MMA (8 tf32 / 16 bf16)
   constexpr int KSTEPS = KB_BYTES / KSTEP_BYTES;
-  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t TMEM_COLS = NACC * BN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Smem* S = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
@@ -163,7 +166,7 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
       mbar_init(&S->full[s], 1);
       mbar_init(&S->empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NACC; ++b) {
       mbar_init(&S->acc_full[b], 1);
       mbar_init(&S->acc_empty[b], 4);  // one arrival per epilogue warp
     }
@@ -204,9 +207,9 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     if (lane == 0) {
       constexpr uint32_t ID = idesc<KIND, BN>();
       for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % STAGES, b = kb & 1;
+        const int s = kb % STAGES, b = kb % NACC;
         if (!mbar_wait(&S->full[s], (kb / STAGES) & 1)) { atomicExch(&S->abort, 1); break; }
-        if (kb >= 2 && !mbar_wait(&S->acc_empty[b], ((kb >> 1) - 1) & 1)) { atomicExch(&S->abort, 1); break; }
+        if (kb >= NACC && !mbar_wait(&S->acc_empty[b], ((kb / NACC) - 1) & 1)) { atomicExch(&S->abort, 1); break; }
         if (*(volatile int*)&S->abort) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = smem_u32(base + s * STAGE_BYTES);
@@ -233,13 +236,14 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     for (int j = 0; j < BN; ++j) acc[j] = 0.f;
     bool ok = true;
     for (int kb = 0; kb < kblocks; ++kb) {
-      const int b = kb & 1;
-      if (!mbar_wait(&S->acc_full[b], (kb >> 1) & 1)) { ok = false; break; }
+      const int b = kb % NACC;
+      if (!mbar_wait(&S->acc_full[b], (kb / NACC) & 1)) { ok = false; break; }
       if (*(volatile int*)&S->abort) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t r[32];
+      for (int c0 = 0; c0 < BN; c0 += 64) {
+        // two 32-column loads in flight, one wait
+        uint32_t r[64];
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -250,9 +254,18 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
               "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
               "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]),
+              "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]),
+              "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]),
+              "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]),
+              "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+            : "r"(taddr + 32u));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+        for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(r[j]);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -264,7 +277,9 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     // writes 32 consecutive columns of one row per instruction
     if (ok) {
       float* tile = reinterpret_cast<float*>(base) + q * (32 * 33);
-      (void)row;
+      // lane i holds the output offset of row q*32 + i; rows are broadcast by shuffle
+      const int64_t mrow = m0 + row;
+      const int64_t my_off = mrow < ep.M ? (ep.cm ? ep.cm[mrow] : mrow * ep.cms) : 0;
 #pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 32) {
 #pragma unroll
@@ -275,9 +290,10 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
         const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
         for (int j = 0; j < 32; ++j) {
           const int64_t m = m0 + q * 32 + j;
+          const int64_t roff = __shfl_sync(0xffffffffu, my_off, j);
           if (m >= ep.M) break;
           if (nvalid) {
-            const int64_t idx = (ep.cm ? ep.cm[m] : m * ep.cms) + coff;
+            const int64_t idx = roff + coff;
             const double v = ep.alpha * (double)tile[j * 33 + lane];
             if (ep.c_f64) {
               double* C = static_cast<double*>(ep.C);
