@@ -186,6 +186,8 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
   int issued_loads = 0;
   if (warp == 0) {
     if (lane == 0) {
+      for (const CUtensorMap* mp : {&a_hi, &a_lo, &b_hi, &b_lo})
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mp)) : "memory");
       for (int kb = 0; kb < kblocks; ++kb) {
         const int s = kb % STAGES;
         if (kb >= STAGES && !mbar_wait(&S->empty[s], ((kb / STAGES) - 1) & 1)) {
@@ -277,9 +279,13 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     // writes 32 consecutive columns of one row per instruction
     if (ok) {
       float* tile = reinterpret_cast<float*>(base) + q * (32 * 33);
-      // lane i holds the output offset of row q*32 + i; rows are broadcast by shuffle
+      // lane i holds the output offset of row q*32 + i; rows are broadcast by
+      // shuffle; the row loop is fully unrolled so 32 load/store pairs are in flight
       const int64_t mrow = m0 + row;
       const int64_t my_off = mrow < ep.M ? (ep.cm ? ep.cm[mrow] : mrow * ep.cms) : 0;
+      const unsigned rowmask = __ballot_sync(0xffffffffu, mrow < ep.M);
+      const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0;
+      const double alpha = ep.alpha, beta = ep.beta;
 #pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 32) {
 #pragma unroll
@@ -288,19 +294,18 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
         const int64_t n = n0 + c0 + lane;
         const bool nvalid = n < ep.N;
         const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int64_t m = m0 + q * 32 + j;
-          const int64_t roff = __shfl_sync(0xffffffffu, my_off, j);
-          if (m >= ep.M) break;
-          if (nvalid) {
-            const int64_t idx = roff + coff;
-            const double v = ep.alpha * (double)tile[j * 33 + lane];
-            if (ep.c_f64) {
+          const int64_t idx = __shfl_sync(0xffffffffu, my_off, j) + coff;
+          const float t = tile[j * 33 + lane];
+          if (nvalid && ((rowmask >> j) & 1u)) {
+            const double v = alpha * (double)t;
+            if (f64out) {
               double* C = static_cast<double*>(ep.C);
-              C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+              C[idx] = acc_c ? fma(beta, C[idx], v) : v;
             } else {
               float* C = static_cast<float*>(ep.C);
-              C[idx] = (float)(ep.beta != 0.0 ? fma(ep.beta, (double)C[idx], v) : v);
+              C[idx] = (float)(acc_c ? fma(beta, (double)C[idx], v) : v);
             }
           }
         }
