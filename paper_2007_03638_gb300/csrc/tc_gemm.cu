@@ -133,14 +133,18 @@ struct Smem {
   int abort;
 };
 
-// Warp roles (192 threads): warp 0 TMA producer, warp 1 MMA issuer, warps
-// 2..5 promote/epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+// Warp roles (320 threads): warp 0 TMA producer, warp 1 MMA issuer, warps
+// 2..9 promote/epilogue: warp w reads TMEM lanes 32*(w%4)..+31 (its rows) and
+// columns 64*((w-2)/4)..+63 of the accumulator.
 // The tensor cores' FP32 accumulation truncates, so each K block is
 // accumulated into a fresh tensor-memory buffer (two buffers alternate) and
 // folded into FP32 registers with round-to-nearest adds by the epilogue warps;
 // NACC buffers let the MMAs run up to NACC-1 K blocks ahead of the folding.
+constexpr int EPI_WARPS = 8;
+constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
+
 template <int KIND, int BN>
-__global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
+__global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
                                                          const __grid_constant__ CUtensorMap a_lo,
                                                          const __grid_constant__ CUtensorMap b_hi,
                                                          const __grid_constant__ CUtensorMap b_lo,
@@ -151,6 +155,10 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
   constexpr int KSTEP_BYTES = 32;          // bytes of K per MMA (8 tf32 / 16 bf16)
   constexpr int KSTEPS = KB_BYTES / KSTEP_BYTES;
   constexpr uint32_t TMEM_COLS = NACC * BN;
+  // K blocks accumulated in one tensor-memory buffer before it is folded:
+  // one for TF32 (the truncation error then stays near FP32 level), two for
+  // BF16 (its split error, ~1e-5, dominates the truncation of 128 products)
+  constexpr int PROMOTE = KIND == KIND_TF32 ? 1 : 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   Smem* S = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
@@ -168,7 +176,7 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(&S->acc_full[b], 1);
-      mbar_init(&S->acc_empty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&S->acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
     }
     S->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -209,9 +217,15 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     if (lane == 0) {
       constexpr uint32_t ID = idesc<KIND, BN>();
       for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % STAGES, b = kb % NACC;
+        const int s = kb % STAGES;
+        const int g = kb / PROMOTE, b = g % NACC;
+        const bool first = (kb % PROMOTE) == 0;
+        const bool last = (kb % PROMOTE) == PROMOTE - 1 || kb == kblocks - 1;
         if (!mbar_wait(&S->full[s], (kb / STAGES) & 1)) { atomicExch(&S->abort, 1); break; }
-        if (kb >= NACC && !mbar_wait(&S->acc_empty[b], ((kb / NACC) - 1) & 1)) { atomicExch(&S->abort, 1); break; }
+        if (first && g >= NACC && !mbar_wait(&S->acc_empty[b], ((g / NACC) - 1) & 1)) {
+          atomicExch(&S->abort, 1);
+          break;
+        }
         if (*(volatile int*)&S->abort) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = smem_u32(base + s * STAGE_BYTES);
@@ -221,32 +235,35 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
         for (int k = 0; k < KSTEPS; ++k) {
           const uint32_t off = k * KSTEP_BYTES;
           // small products first, the dominant one last
-          mma<KIND>(dt, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, k > 0 ? 1u : 0u);
+          mma<KIND>(dt, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, (first && k == 0) ? 0u : 1u);
           mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
           mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
         }
         mma_commit(&S->empty[s]);
-        mma_commit(&S->acc_full[b]);
+        if (last) mma_commit(&S->acc_full[b]);
       }
     }
   } else {
     // promotion and epilogue
     const int q = warp & 3;                    // TMEM lane quarter
+    const int half = (warp - 2) >> 2;          // column half of the accumulator
+    constexpr int HC = BN / 2;                 // columns per epilogue warp
     const int row = q * 32 + lane;
-    float acc[BN];
+    float acc[HC];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    for (int j = 0; j < HC; ++j) acc[j] = 0.f;
     bool ok = true;
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int b = kb % NACC;
-      if (!mbar_wait(&S->acc_full[b], (kb / NACC) & 1)) { ok = false; break; }
+    const int groups = (kblocks + PROMOTE - 1) / PROMOTE;
+    for (int g = 0; g < groups; ++g) {
+      const int b = g % NACC;
+      if (!mbar_wait(&S->acc_full[b], (g / NACC) & 1)) { ok = false; break; }
       if (*(volatile int*)&S->abort) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 64) {
+      for (int c0 = 0; c0 < HC; c0 += 64) {
         // two 32-column loads in flight, one wait
         uint32_t r[64];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -278,7 +295,7 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
     // (the ring is idle once the last accumulator has been read), so a warp
     // writes 32 consecutive columns of one row per instruction
     if (ok) {
-      float* tile = reinterpret_cast<float*>(base) + q * (32 * 33);
+      float* tile = reinterpret_cast<float*>(base) + (warp - 2) * (32 * 33);
       // lane i holds the output offset of row q*32 + i; rows are broadcast by
       // shuffle; the row loop is fully unrolled so 32 load/store pairs are in flight
       const int64_t mrow = m0 + row;
@@ -287,11 +304,11 @@ __global__ __launch_bounds__(192, 1) void tc_gemm_kernel(const __grid_constant__
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0;
       const double alpha = ep.alpha, beta = ep.beta;
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < HC; c0 += 32) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = acc[c0 + j];
         __syncwarp();
-        const int64_t n = n0 + c0 + lane;
+        const int64_t n = n0 + half * HC + c0 + lane;
         const bool nvalid = n < ep.N;
         const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
 #pragma unroll
@@ -442,7 +459,7 @@ void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
     attr_set[dev] = true;
   }
   if (mt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: M too large for grid");
-  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)nt, (unsigned)mt), 192, sm, s>>>(ah, al, bh, bl, ep);
+  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)nt, (unsigned)mt), NTHREADS, sm, s>>>(ah, al, bh, bl, ep);
 }
 
 }  // namespace
