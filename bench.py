@@ -220,6 +220,37 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Reduced serving stream: Poisson arrivals at 50/s, Ising
+    h ~ U[0.5,1.5] or XXZ Delta ~ U[0,2], chi from --serve-chis, 3xTF32, stop
+    at |G| < 1e-6 or --serve-maxiter iterations."""
+    import torch
+    from paper_2007_03638_gb300 import build as b
+    b.build()
+    from paper_2007_03638_gb300 import serve
+    chis = tuple(int(x) for x in args.serve_chis.split(","))
+    reqs = serve.poisson_stream(args.serve_n, rate=50.0, chis=chis, seed=args.seed)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+    warm = serve.poisson_stream(2, rate=1000.0, chis=chis[:1], seed=args.seed + 99)
+    serve.run_stream(warm, budget, workers=2, maxiter=2)
+    mixed = serve.run_stream(reqs, budget, workers=args.serve_workers, maxiter=args.serve_maxiter)
+    seq = serve.run_sequential(reqs, maxiter=args.serve_maxiter)
+    same = all(a["iters"] == b_["iters"] and abs(a["energy"] - b_["energy"]) <= 1e-12 * max(1, abs(b_["energy"]))
+               for a, b_ in zip(mixed["results"], seq["results"]))
+    line = {"metric": "serve solves/s", "value": mixed["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "poisson_stream", "requests": args.serve_n, "rate_per_s": 50.0,
+                       "chis": list(chis), "maxiter": args.serve_maxiter, "gtol": 1e-6, "prec": "3xtf32",
+                       "workers": args.serve_workers, "budget_bytes": budget},
+            "p50_latency_s": mixed["p50_latency_s"], "p99_latency_s": mixed["p99_latency_s"],
+            "sequential": {"solves_per_s": seq["solves_per_s"], "p50_latency_s": seq["p50_latency_s"],
+                           "p99_latency_s": seq["p99_latency_s"]},
+            "same_results_alone_and_mixed": same,
+            "iterations_total": sum(r["iters"] for r in mixed["results"])}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -232,12 +263,22 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=5.0)
     ap.add_argument("--ref-flops-per-grad", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload: a seeded Poisson request stream through the native server, "
+                         "against the same stream solved one request at a time")
+    ap.add_argument("--serve-n", type=int, default=48)
+    ap.add_argument("--serve-chis", default="4,8,12")
+    ap.add_argument("--serve-maxiter", type=int, default=40)
+    ap.add_argument("--serve-workers", type=int, default=6)
     ap.add_argument("--energy-once", action="store_true",
                     help="set the seeded point, run one energy/gradient evaluation and exit (profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = WORKLOADS[args.workload]
+    if args.serve:
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args, wl)
         return

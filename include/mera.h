@@ -207,6 +207,41 @@ typedef struct {
 int mera_get_stats(mera_t m, mera_stats* out, int reset);
 int mera_profile(mera_t m, int enable);
 
+/* ---------------------------------------------------------------- serving --
+ * Many optimisations on one GPU (no counterpart in the paper; the request
+ * stream of the serving workload).  Requests are queued in arrival order and
+ * admitted while their device footprint (mera_footprint_bytes) fits in the
+ * memory budget; each admitted request owns a mera_t on its own stream, so
+ * its state stays on the device until it finishes, and n_workers host
+ * threads take turns stepping the running requests one iteration at a time
+ * (their kernels overlap on the GPU).  A request stops when |G| < gtol or
+ * after maxiter iterations.  Results do not depend on the mix. */
+typedef struct mera_server* mera_server_t;
+
+typedef struct {
+    int state;        /* 0 queued, 1 running, 2 done, 3 failed                 */
+    int error;        /* MERA_ERR_* of a failed request                         */
+    int iters;        /* iterations done                                         */
+    int n_evals;      /* energy/gradient evaluations                             */
+    double energy;    /* energy per bottom site after the last iteration         */
+    double gnorm;     /* |G| after the last iteration                            */
+    double t_submit;  /* seconds since the server started                        */
+    double t_admit;   /* -1 until admitted                                       */
+    double t_done;    /* -1 until finished                                       */
+    size_t bytes;     /* device footprint the request was admitted with          */
+} mera_request_status;
+
+int mera_server_create(size_t mem_budget_bytes, int n_workers, mera_server_t* out);
+/* Copies cfg, h3 and the starting tensors (host pointers) into the queue.
+ * method: 0 L-BFGS, 1 CG.  MERA_ERR_OOM if the request alone exceeds the budget. */
+int mera_server_submit(mera_server_t sv, const mera_config* cfg, const void* h3, const void* const* tensors,
+                       int method, double gtol, int maxiter, int64_t* id);
+int mera_server_poll(mera_server_t sv, int64_t id, mera_request_status* st);
+/* Wait until every submitted request has finished (MERA_ERR_NOCONV on timeout). */
+int mera_server_wait(mera_server_t sv, double timeout_s);
+/* Stop the workers after their current step; unfinished requests are dropped. */
+int mera_server_destroy(mera_server_t sv);
+
 /* C = A B for row-major double matrices A (M x K), B (K x N), C (M x N) on
  * the device, with the contraction arithmetic of the given mera_prec:
  * FP64 (the FP64 contraction kernel) or the tensor-core kernel with 3xTF32 /

@@ -1,0 +1,252 @@
+// Serving loop: many MERA optimisations on one GPU.
+//
+// Requests (a Hamiltonian, a starting point, a stopping rule) are queued in
+// arrival order.  A request is admitted when its device footprint
+// (mera_footprint_bytes) fits in the memory budget next to the requests that
+// are already running; it then gets its own mera_t on its own CUDA stream,
+// so its tensors, Krylov warm starts and L-BFGS history stay on the device
+// until it finishes.  Worker threads take turns over the running requests,
+// one L-BFGS (or CG) iteration at a time, so the kernels of different
+// requests overlap on the GPU while each request's host-side control (line
+// search, Krylov scalars) waits only for its own stream.  A request's
+// arithmetic does not depend on what else is running (every kernel has a
+// fixed reduction order), so its result is the same alone and in the mix.
+#include "common.h"
+#include "../../include/mera.h"
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Request {
+  int64_t id = 0;
+  mera_config cfg{};
+  std::vector<char> h3;
+  std::vector<std::vector<char>> tensors;
+  double gtol = 1e-6;
+  int maxiter = 100;
+  int method = 0;
+  size_t bytes = 0;
+  // run state
+  mera_t m = nullptr;
+  cudaStream_t stream = nullptr;
+  int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+  bool busy = false;
+  int iters = 0, n_evals = 0, error = 0;
+  double energy = 0.0, gnorm = 0.0;
+  clk::time_point t_submit, t_admit, t_done;
+};
+
+}  // namespace
+
+struct mera_server {
+  size_t budget = 0;
+  size_t in_use = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int64_t> queue;                          // waiting, arrival order
+  std::map<int64_t, std::unique_ptr<Request>> reqs;   // all requests
+  std::vector<int64_t> running;
+  size_t rr = 0;
+  int64_t next_id = 1;
+  bool stop = false;
+  int device = 0;
+  std::vector<std::thread> workers;
+  int64_t done = 0, failed = 0, submitted = 0;
+  clk::time_point t0 = clk::now();
+};
+
+namespace {
+
+void finish(mera_server* sv, Request& r, int err) {
+  r.state = err ? 3 : 2;
+  r.error = err;
+  r.t_done = clk::now();
+  if (r.m) mera_destroy(r.m);
+  r.m = nullptr;
+  if (r.stream) cudaStreamDestroy(r.stream);
+  r.stream = nullptr;
+  r.h3.clear();
+  r.tensors.clear();
+  sv->in_use -= r.bytes;
+  if (err) sv->failed++; else sv->done++;
+}
+
+// Admit queued requests in arrival order while they fit (caller holds mu).
+void admit_locked(mera_server* sv) {
+  while (!sv->queue.empty()) {
+    Request& r = *sv->reqs[sv->queue.front()];
+    if (sv->in_use + r.bytes > sv->budget && !sv->running.empty()) break;  // wait for memory
+    sv->queue.pop_front();
+    sv->in_use += r.bytes;
+    r.state = 1;
+    r.t_admit = clk::now();
+    sv->running.push_back(r.id);
+  }
+}
+
+void worker(mera_server* sv) {
+  cudaSetDevice(sv->device);
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    if (sv->stop) return;  // destroy: leave running requests to the destructor
+    admit_locked(sv);
+    // pick the next running request that no other worker is stepping
+    Request* pick = nullptr;
+    for (size_t k = 0; k < sv->running.size(); ++k) {
+      Request& r = *sv->reqs[sv->running[(sv->rr + k) % sv->running.size()]];
+      if (!r.busy) {
+        pick = &r;
+        sv->rr = (sv->rr + k + 1) % std::max<size_t>(1, sv->running.size());
+        break;
+      }
+    }
+    if (!pick) {
+      sv->cv.wait_for(lk, std::chrono::milliseconds(20));
+      continue;
+    }
+    Request& r = *pick;
+    r.busy = true;
+    lk.unlock();
+    int err = 0;
+    bool finished = false;
+    if (!r.m) {
+      // first turn: build the problem on its own stream and load its point
+      err = cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking) == cudaSuccess ? 0 : MERA_ERR_CUDA;
+      if (!err) err = mera_create(&r.cfg, r.h3.data(), r.stream, &r.m);
+      if (!err) {
+        std::vector<const void*> ptrs;
+        for (auto& t : r.tensors) ptrs.push_back(t.data());
+        err = mera_set_tensors(r.m, ptrs.data());
+      }
+    }
+    if (!err) {
+      mera_iter_info info{};
+      err = r.method == 1 ? mera_cg_step(r.m, &info) : mera_lbfgs_step(r.m, &info);
+      if (!err) {
+        r.iters++;
+        r.n_evals += info.n_evals;
+        r.energy = info.energy;
+        r.gnorm = info.gnorm;
+        finished = r.gnorm < r.gtol || r.iters >= r.maxiter;
+      }
+    }
+    lk.lock();
+    r.busy = false;
+    if (err || finished) {
+      for (size_t k = 0; k < sv->running.size(); ++k)
+        if (sv->running[k] == r.id) {
+          sv->running.erase(sv->running.begin() + k);
+          break;
+        }
+      finish(sv, r, err);
+      sv->cv.notify_all();
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mera_server_create(size_t mem_budget_bytes, int n_workers, mera_server_t* out) {
+  if (!out || n_workers < 1 || mem_budget_bytes == 0) return MERA_ERR_ARG;
+  auto* sv = new (std::nothrow) mera_server();
+  if (!sv) return MERA_ERR_OOM;
+  sv->budget = mem_budget_bytes;
+  cudaGetDevice(&sv->device);
+  for (int i = 0; i < n_workers; ++i) sv->workers.emplace_back(worker, sv);
+  *out = sv;
+  return MERA_OK;
+}
+
+int mera_server_submit(mera_server_t sv, const mera_config* cfg, const void* h3, const void* const* tensors,
+                       int method, double gtol, int maxiter, int64_t* id) {
+  if (!sv || !cfg || !h3 || !tensors || !id || maxiter < 1) return MERA_ERR_ARG;
+  auto r = std::make_unique<Request>();
+  r->cfg = *cfg;
+  r->bytes = mera_footprint_bytes(cfg);
+  if (r->bytes == 0) return MERA_ERR_ARG;
+  if (r->bytes > sv->budget) return MERA_ERR_OOM;
+  const int64_t n3 = (int64_t)cfg->d_b * cfg->d_b * cfg->d_b;
+  r->h3.assign(static_cast<const char*>(h3), static_cast<const char*>(h3) + sizeof(double) * n3 * n3);
+  std::vector<int64_t> dims{cfg->d_b};
+  for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
+  for (int l = 0; l <= cfg->n_trans; ++l) {
+    const int64_t cf = dims[l], cc = l < cfg->n_trans ? dims[l + 1] : dims[l];
+    const int64_t sz[2] = {cf * cf * cf * cf, cf * cf * cc};
+    for (int k = 0; k < 2; ++k) {
+      const char* p = static_cast<const char*>(tensors[2 * l + k]);
+      if (!p) return MERA_ERR_ARG;
+      r->tensors.emplace_back(p, p + sizeof(double) * sz[k]);
+    }
+  }
+  r->gtol = gtol;
+  r->maxiter = maxiter;
+  r->method = method;
+  r->t_submit = clk::now();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  r->id = sv->next_id++;
+  *id = r->id;
+  sv->queue.push_back(r->id);
+  sv->reqs.emplace(r->id, std::move(r));
+  sv->submitted++;
+  sv->cv.notify_all();
+  return MERA_OK;
+}
+
+int mera_server_poll(mera_server_t sv, int64_t id, mera_request_status* st) {
+  if (!sv || !st) return MERA_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return MERA_ERR_ARG;
+  const Request& r = *it->second;
+  auto sec = [&](clk::time_point t) { return std::chrono::duration<double>(t - sv->t0).count(); };
+  st->state = r.state;
+  st->error = r.error;
+  st->iters = r.iters;
+  st->n_evals = r.n_evals;
+  st->energy = r.energy;
+  st->gnorm = r.gnorm;
+  st->t_submit = sec(r.t_submit);
+  st->t_admit = r.state >= 1 ? sec(r.t_admit) : -1.0;
+  st->t_done = r.state >= 2 ? sec(r.t_done) : -1.0;
+  st->bytes = r.bytes;
+  return MERA_OK;
+}
+
+int mera_server_wait(mera_server_t sv, double timeout_s) {
+  if (!sv) return MERA_ERR_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  const auto until = clk::now() + std::chrono::duration<double>(timeout_s);
+  while (sv->done + sv->failed < sv->submitted) {
+    if (sv->cv.wait_until(lk, until) == std::cv_status::timeout) return MERA_ERR_NOCONV;
+  }
+  return MERA_OK;
+}
+
+int mera_server_destroy(mera_server_t sv) {
+  if (!sv) return MERA_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    // queued requests that never started are dropped
+    sv->queue.clear();
+    sv->cv.notify_all();
+  }
+  for (auto& t : sv->workers) t.join();
+  for (auto& kv : sv->reqs)
+    if (kv.second->m) finish(sv, *kv.second, MERA_ERR_ARG);
+  delete sv;
+  return MERA_OK;
+}
+
+}  // extern "C"

@@ -451,12 +451,16 @@ template <int KIND, int BN>
 void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
             const TcEpilogue& ep, int64_t mt, int64_t nt, cudaStream_t s) {
   static bool attr_set[64] = {};
+  static std::mutex attr_mu;
   int dev = 0;
   MERA_CUDA(cudaGetDevice(&dev));
   const size_t sm = smem_bytes<KIND, BN>();
-  if (dev < 64 && !attr_set[dev]) {
-    MERA_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr_set[dev] = true;
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+      MERA_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<KIND, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
   }
   if (mt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: M too large for grid");
   tc_gemm_kernel<KIND, BN><<<dim3((unsigned)nt, (unsigned)mt), NTHREADS, sm, s>>>(ah, al, bh, bl, ep);

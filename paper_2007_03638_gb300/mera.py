@@ -51,6 +51,12 @@ class Stats(C.Structure):
                 ("energy_grad_calls", C.c_int64), ("krylov_matvecs", C.c_int64)]
 
 
+class RequestStatus(C.Structure):
+    _fields_ = [("state", C.c_int), ("error", C.c_int), ("iters", C.c_int), ("n_evals", C.c_int),
+                ("energy", C.c_double), ("gnorm", C.c_double), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("bytes", C.c_size_t)]
+
+
 class SolveOpts(C.Structure):
     _fields_ = [("method", C.c_int), ("maxiter", C.c_int), ("gtol", C.c_double)]
 
@@ -65,7 +71,8 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
            "mera_launch_count", "mera_get_stats", "mera_profile", "mera_dots_noalloc",
-           "mera_gemm", "mera_strerror", "mera_last_error"]
+           "mera_gemm", "mera_strerror", "mera_last_error", "mera_server_create",
+           "mera_server_submit", "mera_server_poll", "mera_server_wait", "mera_server_destroy"]
 
 _lib = None
 
@@ -104,6 +111,12 @@ def load(path: str = LIB_PATH):
                                         C.c_void_p, C.c_void_p]),
         "mera_gemm": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p]),
+        "mera_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),
+        "mera_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Config), C.c_void_p, vpp, C.c_int,
+                                         C.c_double, C.c_int, C.POINTER(C.c_int64)]),
+        "mera_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
+        "mera_server_wait": (C.c_int, [C.c_void_p, C.c_double]),
+        "mera_server_destroy": (C.c_int, [C.c_void_p]),
         "mera_strerror": (C.c_char_p, [C.c_int]),
         "mera_last_error": (C.c_char_p, [C.c_void_p]),
     }
