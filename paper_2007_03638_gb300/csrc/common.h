@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <string>
 #include <vector>
+#include <map>
 #include <stdexcept>
 
 #include "../../include/mera.h"
@@ -138,9 +139,14 @@ int check_finite(const double* x, int64_t n, cudaStream_t s);   // 1 if all fini
 // --------------------------------------------------------- small linalg ----
 // Symmetric eigendecomposition of an n x n matrix (in place -> eigenvalues in
 // evals_dev, eigenvectors as columns of V), cyclic parallel Jacobi in one CTA.
-void sym_eig(double* A, double* V, double* evals, int n, cudaStream_t s);
+// Scratch of the eigensolver, kept by its owner so that no call allocates.
+struct EigWork {
+  DevBuf small, cs, red;
+  std::map<int, DevBuf> sched;  // round-robin schedule per matrix size
+};
+void sym_eig(double* A, double* V, double* evals, int n, EigWork& w, cudaStream_t s);
 // Same, optionally warm-started: with warm, V holds an orthogonal basis that
 // A was already rotated into, and the result accumulates onto it.
-void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, cudaStream_t s);
+void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, EigWork& w, cudaStream_t s);
 
 }  // namespace mera

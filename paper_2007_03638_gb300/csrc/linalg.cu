@@ -229,31 +229,41 @@ std::vector<int2> schedule(int n) {
 }
 }  // namespace
 
-void sym_eig(double* A, double* V, double* evals, int n, cudaStream_t s) {
-  sym_eig_from(A, V, evals, n, false, s);
+void sym_eig(double* A, double* V, double* evals, int n, EigWork& w, cudaStream_t s) {
+  sym_eig_from(A, V, evals, n, false, w, s);
 }
 
 // Symmetric eigendecomposition by cyclic Jacobi.  If warm, V holds an
 // orthogonal starting basis that A has already been rotated into (A is then
 // nearly diagonal); on exit V holds the accumulated eigenvectors.
-void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, cudaStream_t s) {
+void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, EigWork& w, cudaStream_t s) {
   if (n <= 0) return;
   if (n <= 64) {
     // small problems: one CTA does every sweep
     if (warm) throw Error(MERA_ERR_ARG, "sym_eig_from: warm start needs n > 64");
     const int m = (n + 1) & ~1;
-    DevBuf scratch(sizeof(double) * m + sizeof(int) * m);
-    jacobi_kernel<<<1, JT, 0, s>>>(A, V, evals, n, 40, scratch.as<double>(),
-                                   reinterpret_cast<int*>(scratch.as<char>() + sizeof(double) * m));
+    const size_t need = sizeof(double) * m + sizeof(int) * m;
+    if (w.small.bytes < need) w.small.alloc(need);
+    jacobi_kernel<<<1, JT, 0, s>>>(A, V, evals, n, 40, w.small.as<double>(),
+                                   reinterpret_cast<int*>(w.small.as<char>() + sizeof(double) * m));
     count_launch();
     MERA_CHECK_LAUNCH();
     MERA_CUDA(cudaStreamSynchronize(s));
     return;
   }
   const int m = (n + 1) & ~1, h = m / 2;
-  const std::vector<int2> sched = schedule(n);
-  DevBuf dpairs(sizeof(int2) * sched.size()), dcs(sizeof(double2) * h), dred(2 * sizeof(double));
-  MERA_CUDA(cudaMemcpyAsync(dpairs.p, sched.data(), sizeof(int2) * sched.size(), cudaMemcpyHostToDevice, s));
+  if (!w.sched.count(n)) {
+    const std::vector<int2> sched = schedule(n);
+    DevBuf b(sizeof(int2) * sched.size());
+    MERA_CUDA(cudaMemcpyAsync(b.p, sched.data(), sizeof(int2) * sched.size(), cudaMemcpyHostToDevice, s));
+    MERA_CUDA(cudaStreamSynchronize(s));
+    w.sched.emplace(n, std::move(b));
+  }
+  if (w.cs.bytes < sizeof(double2) * h) w.cs.alloc(sizeof(double2) * h);
+  if (w.red.bytes < 2 * sizeof(double)) w.red.alloc(2 * sizeof(double));
+  DevBuf& dpairs = w.sched.at(n);
+  DevBuf& dcs = w.cs;
+  DevBuf& dred = w.red;
   if (!warm) {
     eye_k<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(V, n);
     count_launch();

@@ -143,6 +143,7 @@ struct mera_ctx {
   int cur = 0;                            // index of the current point's Eval
   mera::StepGeom geom;
   std::vector<mera::DevBuf> eig_cache;    // last eigenvectors of each rho_v (warm starts)
+  mera::EigWork eigw;                      // Jacobi scratch
   std::vector<int> eig_uses;
   // optimiser
   std::vector<mera::DevBuf> mem_s, mem_y;
@@ -226,7 +227,8 @@ void build_layers(Ctx& c) {
   if (mixed) {
     c.tc_ws.alloc(ws_need);
     c.tc_err.alloc(sizeof(int));
-    MERA_CUDA(cudaMemset(c.tc_err.p, 0, sizeof(int)));
+    MERA_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.s));
+    MERA_CUDA(cudaStreamSynchronize(c.s));
     c.ex.ws = c.tc_ws.p;
     c.ex.ws_bytes = ws_need;
     c.ex.err = c.tc_err.as<int>();
@@ -543,11 +545,11 @@ void ensure_eig(Ctx& c, Eval& E, cudaStream_t s) {
       gemm_f64('N', 'N', p, p, p, 1.0, P(E.rho_v[i]), p, Vc, p, 0.0, T, p, s);
       gemm_f64('T', 'N', p, p, p, 1.0, Vc, p, T, p, 0.0, A, p, s);
       copy(P(E.evec[i]), Vc, p * p, s);
-      sym_eig_from(A, P(E.evec[i]), P(E.eval[i]), (int)p, true, s);
+      sym_eig_from(A, P(E.evec[i]), P(E.eval[i]), (int)p, true, c.eigw, s);
       c.eig_uses[i]++;
     } else {
       copy(A, P(E.rho_v[i]), p * p, s);
-      sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)p, s);
+      sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)p, c.eigw, s);
       c.eig_uses[i] = 1;
     }
     if (p > 64) copy(P(c.eig_cache[i]), P(E.evec[i]), p * p, s);
@@ -655,7 +657,7 @@ void make_geom(Ctx& c, const double* W, const double* X, double alpha, cudaStrea
       double* Z = P(c.gtmp[0]);
       double* ev = P(c.gtmp[5]);
       gemm_f64('T', 'N', p, p, n, 1.0, Xi, p, Xi, p, 0.0, Z, p, s);
-      sym_eig(Z, P(g.Amat[i]), ev, (int)p, s);
+      sym_eig(Z, P(g.Amat[i]), ev, (int)p, c.eigw, s);
       double* f = P(c.gtmp[4]);
       for (int kind = 0; kind < 3; ++kind) {
         double* out = kind == 0 ? P(g.Pc[i]) : kind == 1 ? P(g.P1[i]) : P(g.P2[i]);
@@ -1029,6 +1031,7 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   if (cfg.dtype != MERA_F64) throw Error(MERA_ERR_UNSUPPORTED, "only MERA_F64 is built");
   if (cfg.prec != MERA_PREC_FP64 && cfg.prec != MERA_PREC_3XTF32 && cfg.prec != MERA_PREC_SPLIT_BF16)
     throw Error(MERA_ERR_ARG, "unknown precision mode");
+  c.pool.set_stream(s);
   c.L = cfg.n_trans;
   c.dims.push_back(cfg.d_b);
   for (int l = 0; l < c.L; ++l) c.dims.push_back(std::min<int64_t>(cfg.chi, c.dims.back() * c.dims.back()));

@@ -29,7 +29,8 @@ const int64_t* TablePool::get(const std::vector<int64_t>& host) {
   auto it = tables_.find(host);
   if (it != tables_.end()) return it->second.as<int64_t>();
   DevBuf buf(sizeof(int64_t) * host.size());
-  MERA_CUDA(cudaMemcpy(buf.p, host.data(), sizeof(int64_t) * host.size(), cudaMemcpyHostToDevice));
+  MERA_CUDA(cudaMemcpyAsync(buf.p, host.data(), sizeof(int64_t) * host.size(), cudaMemcpyHostToDevice, stream_));
+  MERA_CUDA(cudaStreamSynchronize(stream_));
   bytes_ += buf.bytes;
   const int64_t* p = buf.as<int64_t>();
   tables_.emplace(host, std::move(buf));

@@ -29,11 +29,14 @@ class TablePool {
  public:
   // dry: count the bytes tables would take, allocate nothing (footprint queries)
   explicit TablePool(bool dry = false) : dry_(dry) {}
+  // uploads are issued on this stream (ordered with the owner's kernels)
+  void set_stream(cudaStream_t s) { stream_ = s; }
   const int64_t* get(const std::vector<int64_t>& host);
   size_t bytes() const { return bytes_; }
 
  private:
   bool dry_ = false;
+  cudaStream_t stream_ = nullptr;
   std::map<std::vector<int64_t>, DevBuf> tables_;
   size_t bytes_ = 0;
 };
