@@ -229,6 +229,7 @@ typedef struct {
     double t_admit;   /* -1 until admitted                                       */
     double t_done;    /* -1 until finished                                       */
     size_t bytes;     /* device footprint the request was admitted with          */
+    char message[160];/* detail of a failure (mera_last_error of the request)    */
 } mera_request_status;
 
 int mera_server_create(size_t mem_budget_bytes, int n_workers, mera_server_t* out);

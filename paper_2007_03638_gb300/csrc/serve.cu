@@ -15,6 +15,8 @@
 #include "../../include/mera.h"
 
 #include <chrono>
+#include <cstdio>
+#include <string>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -41,6 +43,7 @@ struct Request {
   int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
   bool busy = false;
   int iters = 0, n_evals = 0, error = 0;
+  std::string message;
   double energy = 0.0, gnorm = 0.0;
   clk::time_point t_submit, t_admit, t_done;
 };
@@ -139,6 +142,7 @@ void worker(mera_server* sv) {
         finished = r.gnorm < r.gtol || r.iters >= r.maxiter;
       }
     }
+    if (err) r.message = r.m ? mera_last_error(r.m) : "creation failed";
     lk.lock();
     r.busy = false;
     if (err || finished) {
@@ -220,6 +224,7 @@ int mera_server_poll(mera_server_t sv, int64_t id, mera_request_status* st) {
   st->t_admit = r.state >= 1 ? sec(r.t_admit) : -1.0;
   st->t_done = r.state >= 2 ? sec(r.t_done) : -1.0;
   st->bytes = r.bytes;
+  std::snprintf(st->message, sizeof(st->message), "%s", r.message.c_str());
   return MERA_OK;
 }
 

@@ -155,15 +155,21 @@ const int SideNet::kids_[10][2] = {
 SideNet::SideNet(char side, int64_t cf, int64_t cc, TablePool& pool, int64_t chunk) : side_(side) {
   // leg names -> ids; coarse legs a b c (conj side) A B C (plain side)
   std::map<std::string, int> id;
-  auto L = [&](const char* names) {
+  auto L = [&](const char* names) {  // split on spaces (re-entrant: objects are built concurrently)
     std::vector<int> v;
-    char buf[512];
-    std::strncpy(buf, names, sizeof(buf) - 1);
-    buf[sizeof(buf) - 1] = 0;
-    for (char* t = std::strtok(buf, " "); t; t = std::strtok(nullptr, " ")) {
-      auto it = id.find(t);
-      if (it == id.end()) it = id.emplace(t, (int)id.size()).first;
-      v.push_back(it->second);
+    std::string cur;
+    for (const char* p = names;; ++p) {
+      if (*p == ' ' || *p == 0) {
+        if (!cur.empty()) {
+          auto it = id.find(cur);
+          if (it == id.end()) it = id.emplace(cur, (int)id.size()).first;
+          v.push_back(it->second);
+          cur.clear();
+        }
+        if (*p == 0) break;
+      } else {
+        cur += *p;
+      }
     }
     return v;
   };

@@ -114,7 +114,8 @@ def run_stream(reqs, budget_bytes, workers=4, gtol=1e-6, maxiter=100, timeout=36
     res = [sv.poll(i) for i in ids]
     sv.close()
     lat = [x["t_done"] - x["t_submit"] for x in res]
-    return _summary(lat, wall, [{k: x[k] for k in ("state", "iters", "energy", "gnorm")} for x in res])
+    return _summary(lat, wall, [{k: x[k] for k in ("state", "iters", "energy", "gnorm", "error", "message")}
+                                for x in res])
 
 
 def run_sequential(reqs, gtol=1e-6, maxiter=100):
