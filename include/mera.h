@@ -88,8 +88,9 @@ typedef struct {
     int krylov_dim;    /* restart length of the scale-invariant Krylov solves  */
     int krylov_maxiter;/* max matrix-vector products per Krylov solve          */
     double krylov_tol; /* relative residual target of the Krylov solves        */
-    int recompute_env; /* 1: recompute the ascending intermediates in the
-                          gradient pass instead of keeping them (less memory)  */
+    int recompute_env; /* 1: recompute each transition layer's ascending
+                          intermediates in the gradient pass; 0: reuse the
+                          ones the up-sweep keeps per layer                    */
     int lbfgs_m;       /* L-BFGS memory length                                 */
     int b_chunk;       /* slice length of the middle coarse leg in the chi^9
                           contraction chain (must divide the coarse bond

@@ -454,8 +454,10 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
     for (int sd = 0; sd < 2; ++sd) {
       SideBufs& b = ly.buf[sd];
       bind_leaves(ly, sd, op, u, w);
-      // forward with this layer's operator (keeps N3, N7, N8); output not needed
-      side_forward(*ly.net[sd], b, nullptr, 0.0, 0.0, s);
+      // the reverse pass needs N3, N7, N8 for this layer's operator: the
+      // up-sweep left them in place for the transition layers (unless
+      // recomputation was asked for); the scale-invariant layer's operator is x
+      if (l == L || c.cfg.recompute_env) side_forward(*ly.net[sd], b, nullptr, 0.0, 0.0, s);
       b.adj[SideNet::ROOT] = const_cast<double*>(r);
       side_backward(*ly.net[sd], b, need_op, need_op ? P(c.rho[l]) : nullptr, 0.5, true,
                     D + c.offs[2 * l], D + c.offs[2 * l + 1], 1.0, s);

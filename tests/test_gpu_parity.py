@@ -245,3 +245,17 @@ def test_sliced_chain_parity(gm, prec, chunk, tol):
         assert _rel(D[i], ds[i]) < 10 * tol, i
     with pytest.raises(gm.MeraError):
         gm.Mera(gm.default_config(4, 8, 3, b_chunk=3), h3)
+
+
+def test_recompute_env_same_result(gm):
+    """Reusing the up-sweep's intermediates and recomputing them give the same gradient."""
+    us, ws = inp.random_mera(4, 8, 3, seed=8)
+    h3 = _ham(4, "xxz")
+    out = []
+    for rec in (0, 1):
+        m = gm.Mera(gm.default_config(4, 8, 3, recompute_env=rec), h3)
+        m.set_tensors(_flat(us, ws))
+        out.append(m.energy_grad(deriv=True))
+    assert out[0][0] == out[1][0]
+    for a, b in zip(out[0][2], out[1][2]):
+        assert np.array_equal(a, b)
