@@ -133,15 +133,20 @@ struct Smem {
   int abort;
 };
 
-// Warp roles (320 threads): warp 0 TMA producer, warp 1 MMA issuer, warps
-// 2..9 promote/epilogue: warp w reads TMEM lanes 32*(w%4)..+31 (its rows) and
-// columns 64*((w-2)/4)..+63 of the accumulator.
-// The tensor cores' FP32 accumulation truncates, so each K block is
-// accumulated into a fresh tensor-memory buffer (two buffers alternate) and
-// folded into FP32 registers with round-to-nearest adds by the epilogue warps;
-// NACC buffers let the MMAs run up to NACC-1 K blocks ahead of the folding.
+// Persistent kernel, one CTA per SM walking output tiles (N tiles fastest)
+// with a static stride.  Warp roles (320 threads): warp 0 TMA producer,
+// warp 1 MMA issuer, warps 2..9 fold and store (warp w reads TMEM lanes
+// 32*(w%4)..+31 = its rows, columns 64*((w-2)/4)..+63 of the accumulator).
+// The shared-memory ring, the tensor-memory accumulator ring and their
+// barriers run on across tiles, so loads and MMAs of tile i+1 proceed while
+// tile i is being stored.
+// The tensor cores' FP32 accumulation truncates, so each group of PROMOTE K
+// blocks is accumulated into a fresh tensor-memory buffer and folded into
+// FP32 registers with round-to-nearest adds; NACC buffers let the MMAs run up
+// to NACC-1 groups ahead of the folding.
 constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
+constexpr int STG = 16;  // columns per staged store chunk
 
 template <int KIND, int BN>
 __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
@@ -159,15 +164,16 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   // one for TF32 (the truncation error then stays near FP32 level), two for
   // BF16 (its split error, ~1e-5, dominates the truncation of 128 products)
   constexpr int PROMOTE = KIND == KIND_TF32 ? 1 : 2;
+  constexpr int HC = BN / 2;               // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Smem* S = reinterpret_cast<Smem*>(base + STAGES * STAGE_BYTES);
+  float* staging = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
+  Smem* S = reinterpret_cast<Smem*>(staging + EPI_WARPS * 32 * (STG + 1));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // N tiles vary fastest across the grid: CTAs running together share one A
-  // tile (the larger operand in the chi^9 steps), which is then read once from DRAM
-  const int64_t n0 = (int64_t)blockIdx.x * BN;
-  const int64_t m0 = (int64_t)blockIdx.y * BM;
+  const int64_t ntn = (ep.N + BN - 1) / BN, ntm = (ep.M + BM - 1) / BM;
+  const int64_t ntiles = ntn * ntm;
   const int kblocks = ep.kblocks;
+  const int gpt = (kblocks + PROMOTE - 1) / PROMOTE;  // accumulator groups per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -191,132 +197,146 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S->tmem;
 
-  int issued_loads = 0;
+  int64_t issued_loads = 0;
   if (warp == 0) {
     if (lane == 0) {
       for (const CUtensorMap* mp : {&a_hi, &a_lo, &b_hi, &b_lo})
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mp)) : "memory");
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(&S->empty[s], ((kb / STAGES) - 1) & 1)) {
-          atomicExch(&S->abort, 1);
-          break;
+      int64_t kbg = 0;
+      bool stop = false;
+      for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const int m0 = (int)((t / ntn) * BM), n0 = (int)((t % ntn) * BN);
+        for (int kb = 0; kb < kblocks; ++kb, ++kbg) {
+          const int s = (int)(kbg % STAGES);
+          if (kbg >= STAGES && !mbar_wait(&S->empty[s], (uint32_t)((kbg / STAGES) - 1) & 1)) {
+            atomicExch(&S->abort, 1);
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)&S->abort) { stop = true; break; }
+          uint8_t* st = base + s * STAGE_BYTES;
+          mbar_expect_tx(&S->full[s], STAGE_BYTES);
+          const int kx = kb * (KB_BYTES / (KIND == KIND_TF32 ? 4 : 2));
+          tma_load_2d(&a_hi, &S->full[s], st, kx, m0);
+          tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, m0);
+          tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, n0);
+          tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, n0);
+          issued_loads = kbg + 1;
         }
-        if (*(volatile int*)&S->abort) break;
-        uint8_t* st = base + s * STAGE_BYTES;
-        mbar_expect_tx(&S->full[s], STAGE_BYTES);
-        const int kx = kb * (KB_BYTES / (KIND == KIND_TF32 ? 4 : 2));
-        tma_load_2d(&a_hi, &S->full[s], st, kx, (int)m0);
-        tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, (int)m0);
-        tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, (int)n0);
-        tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, (int)n0);
-        issued_loads = kb + 1;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t ID = idesc<KIND, BN>();
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % STAGES;
-        const int g = kb / PROMOTE, b = g % NACC;
-        const bool first = (kb % PROMOTE) == 0;
-        const bool last = (kb % PROMOTE) == PROMOTE - 1 || kb == kblocks - 1;
-        if (!mbar_wait(&S->full[s], (kb / STAGES) & 1)) { atomicExch(&S->abort, 1); break; }
-        if (first && g >= NACC && !mbar_wait(&S->acc_empty[b], ((g / NACC) - 1) & 1)) {
-          atomicExch(&S->abort, 1);
-          break;
-        }
-        if (*(volatile int*)&S->abort) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = smem_u32(base + s * STAGE_BYTES);
-        const uint32_t ahi = st, alo = st + A_BYTES, bhi = st + 2 * A_BYTES, blo = st + 2 * A_BYTES + B_BYTES;
-        const uint32_t dt = tmem + (uint32_t)(b * BN);
+      int64_t kbg = 0, gg = 0;
+      bool stop = false;
+      for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        for (int kb = 0; kb < kblocks; ++kb, ++kbg) {
+          const int s = (int)(kbg % STAGES);
+          const bool first = (kb % PROMOTE) == 0;
+          const bool last = (kb % PROMOTE) == PROMOTE - 1 || kb == kblocks - 1;
+          const int b = (int)(gg % NACC);
+          if (!mbar_wait(&S->full[s], (uint32_t)(kbg / STAGES) & 1)) { atomicExch(&S->abort, 1); stop = true; break; }
+          if (first && gg >= NACC && !mbar_wait(&S->acc_empty[b], (uint32_t)((gg / NACC) - 1) & 1)) {
+            atomicExch(&S->abort, 1);
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)&S->abort) { stop = true; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(base + s * STAGE_BYTES);
+          const uint32_t ahi = st, alo = st + A_BYTES, bhi = st + 2 * A_BYTES, blo = st + 2 * A_BYTES + B_BYTES;
+          const uint32_t dt = tmem + (uint32_t)(b * BN);
 #pragma unroll
-        for (int k = 0; k < KSTEPS; ++k) {
-          const uint32_t off = k * KSTEP_BYTES;
-          // small products first, the dominant one last
-          mma<KIND>(dt, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, (first && k == 0) ? 0u : 1u);
-          mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
-          mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
+          for (int k = 0; k < KSTEPS; ++k) {
+            const uint32_t off = k * KSTEP_BYTES;
+            // small products first, the dominant one last
+            mma<KIND>(dt, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, (first && k == 0) ? 0u : 1u);
+            mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
+            mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
+          }
+          mma_commit(&S->empty[s]);
+          if (last) {
+            mma_commit(&S->acc_full[b]);
+            ++gg;
+          }
         }
-        mma_commit(&S->empty[s]);
-        if (last) mma_commit(&S->acc_full[b]);
       }
     }
   } else {
-    // promotion and epilogue
+    // fold and store
     const int q = warp & 3;                    // TMEM lane quarter
     const int half = (warp - 2) >> 2;          // column half of the accumulator
-    constexpr int HC = BN / 2;                 // columns per epilogue warp
     const int row = q * 32 + lane;
-    float acc[HC];
-#pragma unroll
-    for (int j = 0; j < HC; ++j) acc[j] = 0.f;
+    float* stg = staging + (warp - 2) * 32 * (STG + 1);
+    int64_t gg = 0;
     bool ok = true;
-    const int groups = (kblocks + PROMOTE - 1) / PROMOTE;
-    for (int g = 0; g < groups; ++g) {
-      const int b = g % NACC;
-      if (!mbar_wait(&S->acc_full[b], (g / NACC) & 1)) { ok = false; break; }
-      if (*(volatile int*)&S->abort) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int64_t m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+      float acc[HC];
 #pragma unroll
-      for (int c0 = 0; c0 < HC; c0 += 64) {
-        // two 32-column loads in flight, one wait
-        uint32_t r[64];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]),
-              "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]),
-              "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]),
-              "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]),
-              "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-            : "r"(taddr + 32u));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int j = 0; j < HC; ++j) acc[j] = 0.f;
+      for (int g = 0; g < gpt; ++g, ++gg) {
+        const int b = (int)(gg % NACC);
+        if (!mbar_wait(&S->acc_full[b], (uint32_t)(gg / NACC) & 1)) { ok = false; break; }
+        if (*(volatile int*)&S->abort) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+        for (int c0 = 0; c0 < HC; c0 += 64) {
+          // two 32-column loads in flight, one wait
+          uint32_t r[64];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]),
+                "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]),
+                "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]),
+                "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]),
+                "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+              : "r"(taddr + 32u));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
-    }
-    if (!ok) atomicExch(&S->abort, 1);
-    // stores: each warp stages 32x32 chunks of its rows through shared memory
-    // (the ring is idle once the last accumulator has been read), so a warp
-    // writes 32 consecutive columns of one row per instruction
-    if (ok) {
-      float* tile = reinterpret_cast<float*>(base) + (warp - 2) * (32 * 33);
-      // lane i holds the output offset of row q*32 + i; rows are broadcast by
-      // shuffle; the row loop is fully unrolled so 32 load/store pairs are in flight
+      if (!ok) break;
+      // store: 16-column chunks staged through shared memory; lanes 0-15 and
+      // 16-31 write consecutive columns of two rows per instruction
       const int64_t mrow = m0 + row;
       const int64_t my_off = mrow < ep.M ? (ep.cm ? ep.cm[mrow] : mrow * ep.cms) : 0;
       const unsigned rowmask = __ballot_sync(0xffffffffu, mrow < ep.M);
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0;
       const double alpha = ep.alpha, beta = ep.beta;
+      const int cl = lane & 15, rsel = lane >> 4;
 #pragma unroll
-      for (int c0 = 0; c0 < HC; c0 += 32) {
+      for (int c0 = 0; c0 < HC; c0 += STG) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = acc[c0 + j];
+        for (int j = 0; j < STG; ++j) stg[lane * (STG + 1) + j] = acc[c0 + j];
         __syncwarp();
-        const int64_t n = n0 + half * HC + c0 + lane;
+        const int64_t n = n0 + half * HC + c0 + cl;
         const bool nvalid = n < ep.N;
         const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t idx = __shfl_sync(0xffffffffu, my_off, j) + coff;
-          const float t = tile[j * 33 + lane];
-          if (nvalid && ((rowmask >> j) & 1u)) {
-            const double v = alpha * (double)t;
+        for (int j = 0; j < 16; ++j) {
+          const int r = 2 * j + rsel;
+          const int64_t idx = __shfl_sync(0xffffffffu, my_off, r) + coff;
+          const float tv = stg[r * (STG + 1) + cl];
+          if (nvalid && ((rowmask >> r) & 1u)) {
+            const double v = alpha * (double)tv;
             if (f64out) {
               double* C = static_cast<double*>(ep.C);
               C[idx] = acc_c ? fma(beta, C[idx], v) : v;
@@ -329,13 +349,16 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
         __syncwarp();
       }
     }
+    if (!ok) atomicExch(&S->abort, 1);
   }
   __syncthreads();
   if (*(volatile int*)&S->abort) {
     if (threadIdx.x == 0) atomicExch(ep.err, 1);
-    // drain this CTA's outstanding copies (bounded) before its memory goes away
-    if (warp == 0 && lane == 0)
-      for (int kb = 0; kb < issued_loads; ++kb) mbar_wait(&S->full[kb % STAGES], (kb / STAGES) & 1);
+    // drain this CTA's copies still in flight (at most the last STAGES, bounded waits)
+    if (warp == 0 && lane == 0) {
+      const int64_t lo = issued_loads > STAGES ? issued_loads - STAGES : 0;
+      for (int64_t kb = lo; kb < issued_loads; ++kb) mbar_wait(&S->full[kb % STAGES], (uint32_t)(kb / STAGES) & 1);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -444,7 +467,21 @@ CUtensorMap make_map(const void* ptr, int64_t rows, int64_t kp, int elem, int bo
 
 template <int KIND, int BN>
 size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (2 * BM * KB_BYTES + 2 * BN * KB_BYTES) + sizeof(Smem) + 64;
+  return 1024 + (size_t)STAGES * (2 * BM * KB_BYTES + 2 * BN * KB_BYTES) +
+         sizeof(float) * EPI_WARPS * 32 * (STG + 1) + sizeof(Smem) + 64;
+}
+
+int num_sms() {
+  static int cached[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  MERA_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  int n = 0;
+  MERA_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
 }
 
 template <int KIND, int BN>
@@ -462,8 +499,9 @@ void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
       if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
   }
-  if (mt > 65535) throw Error(MERA_ERR_UNSUPPORTED, "tc_gemm: M too large for grid");
-  tc_gemm_kernel<KIND, BN><<<dim3((unsigned)nt, (unsigned)mt), NTHREADS, sm, s>>>(ah, al, bh, bl, ep);
+  const int64_t tiles = mt * nt;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms());
+  tc_gemm_kernel<KIND, BN><<<grid, NTHREADS, sm, s>>>(ah, al, bh, bl, ep);
 }
 
 }  // namespace
