@@ -194,6 +194,19 @@ def dist_setup():
     return world, rank, local
 
 
+def aggregate(t_ms, units, dist=None, device="cpu"):
+    """Whole-job numbers over ranks: the slowest rank's time and the summed
+    units (replicas: every rank solves its own problem)."""
+    if dist is None:
+        return t_ms, units
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(u.item()))
+
+
 def run_reference(args, wl):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -330,15 +343,7 @@ def main():
     st = m.stats(reset=True)
     t_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
     grads = st["energy_grad_calls"]
-    if pg:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_ms = float(t.item())
-        g = torch.tensor([grads], dtype=torch.float64, device="cuda")
-        pg.all_reduce(g)
-        grads_all = int(g.item())
-    else:
-        grads_all = grads
+    t_ms, grads_all = aggregate(t_ms, grads, pg, "cuda")
     value = grads_all / (t_ms / 1e3)
     gett_flops_per_grad = st["gett_flops"] / max(1, grads)
 
@@ -361,10 +366,7 @@ def main():
         m.energy_grad_into(gout)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e, _ = aggregate(t_e2e, 0, pg, "cuda")
     e2e_value = world * n_e2e / t_e2e
 
     achieved = st["gett_flops"] / (st["gett_ms"] / 1e3) if st["gett_ms"] > 0 else None

@@ -130,6 +130,10 @@ int mera_get_tensors(mera_t m, void* const* tensors);
  * refreshes the density matrices used by mera_precondition. */
 int mera_energy_grad(mera_t m, double* energy, void* const* grad, void* const* deriv);
 
+/* Energy per bottom site only (ascending maps, scale-invariant fixed point,
+ * Tr(h_L rho_S); Sec. 4, App. B): no environment series, no reverse pass. */
+int mera_energy(mera_t m, double* energy);
+
 /* G = projection of arbitrary D onto the tangent space at the current point. */
 int mera_project(mera_t m, const void* const* D, void* const* G);
 

@@ -385,11 +385,38 @@ void project_tensor(Ctx& c, int i, const double* W, const double* D, double* G, 
 }
 
 void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
+void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s);
+
+// Energy only: up-sweep, scale-invariant fixed point, e = Tr(h_L rho_S).
+double forward_energy(Ctx& c, const double* W, cudaStream_t s);
 
 // Full evaluation at point W into E.
 void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   const int L = c.L;
   c.prof.energy_grad_calls++;
+  E.e = forward_energy(c, W, s);
+  const int64_t cS = c.dims[L], n3 = ipow(cS, 3), n = n3 * n3;
+  const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
+  const double tol = std::max(c.cfg.krylov_tol, floor_tol);
+  double* rhoS = P(c.rho[L]);
+  double* hL = P(c.h[L]);
+  double* xs = P(c.x);
+  if (!c.have_x) copy(xs, hL, n, s);
+  auto op_x = [&](const double* v, double* out) {
+    copy(out, v, n, s);
+    ascend(c, L, W, v, out, -1.0, s);
+    const double t = c.red.dot(v, rhoS, n, s);
+    add_identity(t, out, n3, s);
+    ++c.matvecs;
+  };
+  gmres(c, op_x, hL, xs, n, tol, s);
+  symmetrize(xs, n3, s);
+  c.have_x = true;
+  gradient_pass(c, W, E, s);
+}
+
+double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
+  const int L = c.L;
   // up-sweep
   copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6), s);
   for (int l = 0; l <= L; ++l) prepare_layer(c, l, W, s);
@@ -426,20 +453,18 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   scal(1.0 / tr, rhoS, n, s);
   symmetrize(rhoS, n3, s);
   c.have_rho = true;
-  double* hL = P(c.h[L]);
+  const double e = c.red.dot(P(c.h[L]), rhoS, n, s);
+  check_device_flag(c, s);
+  if (!std::isfinite(e)) throw Error(MERA_ERR_NONFINITE, "non-finite energy");
+  return e;
+}
+
+// Reverse passes of every layer (environments, descending maps), projection
+// and the preconditioner's density matrices; needs forward_energy and x.
+void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
+  const int L = c.L;
+  double* rhoS = P(c.rho[L]);
   double* xs = P(c.x);
-  if (!c.have_x) copy(xs, hL, n, s);
-  auto op_x = [&](const double* v, double* out) {
-    copy(out, v, n, s);
-    ascend(c, L, W, v, out, -1.0, s);
-    const double t = c.red.dot(v, rhoS, n, s);
-    add_identity(t, out, n3, s);
-    ++c.matvecs;
-  };
-  gmres(c, op_x, hL, xs, n, tol, s);
-  symmetrize(xs, n3, s);
-  c.have_x = true;
-  E.e = c.red.dot(hL, rhoS, n, s);
   // down-sweep with environments
   double* D = P(E.D);
   fill(0.0, D, c.total, s);
@@ -1221,6 +1246,11 @@ int mera_set_tensors(mera_t m, const void* const* t) {
 int mera_get_tensors(mera_t m, void* const* t) {
   if (!m || !t) return MERA_ERR_ARG;
   return wrap(m, [&] { copy_out(m, mera::P(m->Wcur), t); });
+}
+
+int mera_energy(mera_t m, double* energy) {
+  if (!m || !energy) return MERA_ERR_ARG;
+  return wrap(m, [&] { *energy = mera::forward_energy(*m, mera::P(m->Wcur), m->s); });
 }
 
 int mera_energy_grad(mera_t m, double* energy, void* const* grad, void* const* deriv) {

@@ -67,7 +67,7 @@ class SolveResult(C.Structure):
                 ("gnorm", C.c_double), ("converged", C.c_int)]
 
 
-EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tensors",
+EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tensors", "mera_energy",
            "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_energy_grad",
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "mera_set_tensors": (C.c_int, [C.c_void_p, vpp]),
         "mera_get_tensors": (C.c_int, [C.c_void_p, vpp]),
         "mera_energy_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), vpp, vpp]),
+        "mera_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
         "mera_project": (C.c_int, [C.c_void_p, vpp, vpp]),
         "mera_inner": (C.c_int, [C.c_void_p, vpp, vpp, C.POINTER(C.c_double)]),
         "mera_transport": (C.c_int, [C.c_void_p, vpp, C.c_double, vpp]),
@@ -269,8 +270,15 @@ class Mera:
         return e.value
 
     def energy(self):
+        """Energy and gradient at the current point; returns the energy."""
         e = C.c_double()
         self._check(self.L.mera_energy_grad(self.h, C.byref(e), None, None))
+        return e.value
+
+    def energy_only(self):
+        """Energy alone (no environments)."""
+        e = C.c_double()
+        self._check(self.L.mera_energy(self.h, C.byref(e)))
         return e.value
 
     def project(self, D, device=False):
