@@ -32,8 +32,18 @@ namespace mera {
 namespace tc {
 namespace {
 
+#ifndef MERA_TC_PROMOTE_TF32
+#define MERA_TC_PROMOTE_TF32 1   // K blocks per folded accumulator group (compile-time tuning)
+#endif
+#ifndef MERA_TC_PROMOTE_BF16
+#define MERA_TC_PROMOTE_BF16 2
+#endif
+#ifndef MERA_TC_STAGES
+#define MERA_TC_STAGES 3
+#endif
+
 constexpr int BM = 128;
-constexpr int STAGES = 3;
+constexpr int STAGES = MERA_TC_STAGES;
 constexpr int KB_BYTES = 128;               // K block = one 128-byte swizzle row
 constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits: 1 s
 
@@ -165,7 +175,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   // K blocks accumulated in one tensor-memory buffer before it is folded:
   // one for TF32 (the truncation error then stays near FP32 level), two for
   // BF16 (its split error, ~1e-5, dominates the truncation of 128 products)
-  constexpr int PROMOTE = KIND == KIND_TF32 ? 1 : 2;
+  constexpr int PROMOTE = KIND == KIND_TF32 ? MERA_TC_PROMOTE_TF32 : MERA_TC_PROMOTE_BF16;
   constexpr int HC = BN / 2;               // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -323,6 +333,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       const unsigned rowmask = __ballot_sync(0xffffffffu, mrow < ep.M);
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0;
       const double alpha = ep.alpha, beta = ep.beta;
+      const float alpha_f = (float)ep.alpha, beta_f = (float)ep.beta;
       const int cl = lane & 15, rsel = lane >> 4;
 #pragma unroll
       for (int c0 = 0; c0 < HC; c0 += STG) {
@@ -338,13 +349,15 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           const int64_t idx = __shfl_sync(0xffffffffu, my_off, r) + coff;
           const float tv = stg[r * (STG + 1) + cl];
           if (nvalid && ((rowmask >> r) & 1u)) {
-            const double v = alpha * (double)tv;
             if (f64out) {
+              const double v = alpha * (double)tv;
               double* C = static_cast<double*>(ep.C);
               C[idx] = acc_c ? fma(beta, C[idx], v) : v;
             } else {
+              // float output: FP32 arithmetic (the FP64 pipe is a few ops per clock per SM)
               float* C = static_cast<float*>(ep.C);
-              C[idx] = (float)(acc_c ? fma(beta, (double)C[idx], v) : v);
+              const float v = alpha_f * tv;
+              C[idx] = acc_c ? fmaf(beta_f, C[idx], v) : v;
             }
           }
         }
@@ -376,31 +389,8 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// hi/lo planes [Rp x Kp] (row-major, K fastest) of src[r_off[r] + k_off[k]].
-template <typename Src, int KIND>
-__global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt, int64_t rs,
-                                  const int64_t* __restrict__ kt, int64_t ks, int64_t R, int64_t K,
-                                  int64_t Rp, int64_t Kp, void* hi, void* lo) {
-  const int64_t total = Rp * Kp;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / Kp, k = i % Kp;
-    double v = 0.0;
-    if (r < R && k < K) v = (double)src[(rt ? rt[r] : r * rs) + (kt ? kt[k] : k * ks)];
-    if (KIND == KIND_TF32) {
-      const float h = tf32_round((float)v);
-      const float l = tf32_round((float)(v - (double)h));
-      static_cast<float*>(hi)[i] = h;
-      static_cast<float*>(lo)[i] = l;
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-      const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-      static_cast<__nv_bfloat16*>(hi)[i] = h;
-      static_cast<__nv_bfloat16*>(lo)[i] = l;
-    }
-  }
-}
-
+// Split one value into its hi/lo planes.  Float sources stay in FP32
+// (x - hi is exact in FP32), double sources take the residual in FP64.
 template <int KIND>
 __device__ __forceinline__ void store_split(double v, void* hi, void* lo, int64_t i) {
   if (KIND == KIND_TF32) {
@@ -411,6 +401,33 @@ __device__ __forceinline__ void store_split(double v, void* hi, void* lo, int64_
     const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
     static_cast<__nv_bfloat16*>(hi)[i] = h;
     static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+  }
+}
+template <int KIND>
+__device__ __forceinline__ void store_split(float v, void* hi, void* lo, int64_t i) {
+  if (KIND == KIND_TF32) {
+    const float h = tf32_round(v);
+    static_cast<float*>(hi)[i] = h;
+    static_cast<float*>(lo)[i] = tf32_round(v - h);
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    static_cast<__nv_bfloat16*>(hi)[i] = h;
+    static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// hi/lo planes [Rp x Kp] (row-major, K fastest) of src[r_off[r] + k_off[k]].
+template <typename Src, int KIND>
+__global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt, int64_t rs,
+                                  const int64_t* __restrict__ kt, int64_t ks, int64_t R, int64_t K,
+                                  int64_t Rp, int64_t Kp, void* hi, void* lo) {
+  const int64_t total = Rp * Kp;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / Kp, k = i % Kp;
+    Src v = (Src)0;
+    if (r < R && k < K) v = src[(rt ? rt[r] : r * rs) + (kt ? kt[k] : k * ks)];
+    store_split<KIND>(v, hi, lo, i);
   }
 }
 
@@ -432,7 +449,7 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
   __syncthreads();
   for (int j = ty; j < 32; j += 8) {
     const int64_t rr = r0 + j, kk = k0 + tx;
-    if (rr < Rp && kk < Kp) store_split<KIND>((double)tile[tx][j], hi, lo, rr * Kp + kk);
+    if (rr < Rp && kk < Kp) store_split<KIND>(tile[tx][j], hi, lo, rr * Kp + kk);
   }
 }
 
