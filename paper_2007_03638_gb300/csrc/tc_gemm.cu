@@ -183,9 +183,14 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   Smem* S = reinterpret_cast<Smem*>(staging + EPI_WARPS * 32 * (STG + 1));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntn = (ep.N + BN - 1) / BN, ntm = (ep.M + BM - 1) / BM;
-  const int64_t ntiles = ntn * ntm;
-  const int kblocks = ep.kblocks;
-  const int gpt = (kblocks + PROMOTE - 1) / PROMOTE;  // accumulator groups per tile
+  const int64_t nt1 = ntn * ntm;               // output tiles
+  const int64_t ntiles = nt1 * ep.ksplit;      // work items (tile, K slice)
+  // K blocks of work item t: [kb_lo, kb_hi)
+  auto krange = [&](int64_t t, int& lo, int& hi) {
+    const int sp = (int)(t / nt1);
+    lo = ep.ksplit > 1 ? sp * ep.kbs : 0;
+    hi = ep.ksplit > 1 ? min(ep.kblocks, lo + ep.kbs) : ep.kblocks;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -217,8 +222,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       int64_t kbg = 0;
       bool stop = false;
       for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        const int m0 = (int)((t / ntn) * BM), n0 = (int)((t % ntn) * BN);
-        for (int kb = 0; kb < kblocks; ++kb, ++kbg) {
+        const int64_t tt = t % nt1;
+        const int m0 = (int)((tt / ntn) * BM), n0 = (int)((tt % ntn) * BN);
+        int klo, khi;
+        krange(t, klo, khi);
+        for (int kb = klo; kb < khi; ++kb, ++kbg) {
           const int s = (int)(kbg % STAGES);
           if (kbg >= STAGES && !mbar_wait(&S->empty[s], (uint32_t)((kbg / STAGES) - 1) & 1)) {
             atomicExch(&S->abort, 1);
@@ -243,10 +251,12 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       int64_t kbg = 0, gg = 0;
       bool stop = false;
       for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-        for (int kb = 0; kb < kblocks; ++kb, ++kbg) {
+        int klo, khi;
+        krange(t, klo, khi);
+        for (int kb = klo; kb < khi; ++kb, ++kbg) {
           const int s = (int)(kbg % STAGES);
-          const bool first = (kb % PROMOTE) == 0;
-          const bool last = (kb % PROMOTE) == PROMOTE - 1 || kb == kblocks - 1;
+          const bool first = ((kb - klo) % PROMOTE) == 0;
+          const bool last = ((kb - klo) % PROMOTE) == PROMOTE - 1 || kb == khi - 1;
           const int b = (int)(gg % NACC);
           if (!mbar_wait(&S->full[s], (uint32_t)(kbg / STAGES) & 1)) { atomicExch(&S->abort, 1); stop = true; break; }
           if (first && gg >= NACC && !mbar_wait(&S->acc_empty[b], (uint32_t)((gg / NACC) - 1) & 1)) {
@@ -284,7 +294,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
     int64_t gg = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int64_t m0 = (t / ntn) * BM, n0 = (t % ntn) * BN;
+      const int64_t tt = t % nt1;
+      const int64_t m0 = (tt / ntn) * BM, n0 = (tt % ntn) * BN;
+      int klo, khi;
+      krange(t, klo, khi);
+      const int gpt = (khi - klo + PROMOTE - 1) / PROMOTE;  // accumulator groups of this item
       float acc[HC];
 #pragma unroll
       for (int j = 0; j < HC; ++j) acc[j] = 0.f;
@@ -332,6 +346,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       const int64_t my_off = mrow < ep.M ? (ep.cm ? ep.cm[mrow] : mrow * ep.cms) : 0;
       const unsigned rowmask = __ballot_sync(0xffffffffu, mrow < ep.M);
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0;
+      void* Cbase = ep.ksplit > 1 ? static_cast<void*>(static_cast<float*>(ep.C) + (t / nt1) * ep.split_stride)
+                                  : ep.C;
       const double alpha = ep.alpha, beta = ep.beta;
       const float alpha_f = (float)ep.alpha, beta_f = (float)ep.beta;
       const int cl = lane & 15, rsel = lane >> 4;
@@ -351,11 +367,11 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           if (nvalid && ((rowmask >> r) & 1u)) {
             if (f64out) {
               const double v = alpha * (double)tv;
-              double* C = static_cast<double*>(ep.C);
+              double* C = static_cast<double*>(Cbase);
               C[idx] = acc_c ? fma(beta, C[idx], v) : v;
             } else {
               // float output: FP32 arithmetic (the FP64 pipe is a few ops per clock per SM)
-              float* C = static_cast<float*>(ep.C);
+              float* C = static_cast<float*>(Cbase);
               const float v = alpha_f * tv;
               C[idx] = acc_c ? fmaf(beta_f, C[idx], v) : v;
             }
@@ -450,6 +466,28 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
   for (int j = ty; j < 32; j += 8) {
     const int64_t rr = r0 + j, kk = k0 + tx;
     if (rr < Rp && kk < Kp) store_split<KIND>(tile[tx][j], hi, lo, rr * Kp + kk);
+  }
+}
+
+// Sum of the split-K partials in a fixed order, then the real epilogue.
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit, int64_t M, int64_t N,
+                                     TcEpilogue ep) {
+  const int64_t total = M * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int sp = 0; sp < ksplit; ++sp) acc += part[(int64_t)sp * total + i];
+    const int64_t m = i / N, n = i % N;
+    const int64_t idx = (ep.cm ? ep.cm[m] : m * ep.cms) + (ep.cn ? ep.cn[n] : n * ep.cns);
+    if (ep.c_f64) {
+      double* C = static_cast<double*>(ep.C);
+      const double v = ep.alpha * (double)acc;
+      C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+    } else {
+      float* C = static_cast<float*>(ep.C);
+      const float v = (float)ep.alpha * acc;
+      C[idx] = ep.beta != 0.0 ? fmaf((float)ep.beta, C[idx], v) : v;
+    }
   }
 }
 
@@ -569,8 +607,29 @@ void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, co
   MERA_CHECK_LAUNCH();
 }
 
+namespace {
+constexpr int SPLITK_MAX = 8;
+// Number of K slices for an M x N x Kp product: only products whose output
+// tiles cover less than half of the GPU split, each slice keeping >= 16 K blocks.
+int choose_split(int64_t M, int64_t N, int64_t Kp, int kind) {
+  const int64_t tiles = ((M + BM - 1) / BM) * ((N + 127) / 128);
+  const int64_t kblocks = Kp / (KB_BYTES / (kind == KIND_TF32 ? 4 : 2));
+  const int nsm = 152;
+  if (tiles * 2 > nsm || kblocks < 32) return 1;
+  int64_t sp = (2 * nsm + tiles - 1) / tiles;
+  sp = std::min<int64_t>(std::min<int64_t>(sp, (int64_t)SPLITK_MAX), kblocks / 16);
+  return (int)std::max<int64_t>(sp, 1);
+}
+}  // namespace
+
+size_t splitk_bytes(int64_t M, int64_t N, int64_t Kp, int kind) {
+  const int sp = choose_split(M, N, Kp, kind);
+  return sp > 1 ? sizeof(float) * (size_t)sp * (size_t)M * (size_t)N : 0;
+}
+
 void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo, int64_t Mp,
-                 const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep_in, cudaStream_t s) {
+                 const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep_in, cudaStream_t s,
+                 float* splitk_ws, size_t splitk_ws_bytes) {
   load_encode();
   const int elem = kind == KIND_TF32 ? 4 : 2;
   const int bn = 128;
@@ -582,12 +641,36 @@ void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, c
   CUtensorMap bh = make_map(b_hi, Np, Kp, elem, bn), bl = make_map(b_lo, Np, Kp, elem, bn);
   const int64_t mt = (M + BM - 1) / BM, nt = (N + bn - 1) / bn;
   if (Mp < mt * BM || Np < nt * bn) throw Error(MERA_ERR_ARG, "gemm_packed: operand padding too small");
+  int sp = choose_split(M, N, Kp, kind);
+  if (sp > 1 && (!splitk_ws || splitk_ws_bytes < sizeof(float) * (size_t)sp * M * N)) sp = 1;
+  TcEpilogue run = ep;
+  if (sp > 1) {
+    run.ksplit = sp;
+    run.kbs = (ep.kblocks + sp - 1) / sp;
+    run.ksplit = (ep.kblocks + run.kbs - 1) / run.kbs;  // no empty slice
+    run.split_stride = M * N;
+    run.C = splitk_ws;
+    run.c_f64 = 0;
+    run.cm = nullptr;
+    run.cms = N;
+    run.cn = nullptr;
+    run.cns = 1;
+    run.alpha = 1.0;
+    run.beta = 0.0;
+  }
   if (kind == KIND_TF32)
-    launch<KIND_TF32, 128>(ah, al, bh, bl, ep, mt, nt, s);
+    launch<KIND_TF32, 128>(ah, al, bh, bl, run, mt * run.ksplit, nt, s);
   else
-    launch<KIND_BF16, 128>(ah, al, bh, bl, ep, mt, nt, s);
+    launch<KIND_BF16, 128>(ah, al, bh, bl, run, mt * run.ksplit, nt, s);
   count_launch();
   MERA_CHECK_LAUNCH();
+  if (sp > 1) {
+    const int64_t total = M * N;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(splitk_ws, run.ksplit, M, N, ep);
+    count_launch();
+    MERA_CHECK_LAUNCH();
+  }
 }
 
 }  // namespace tc

@@ -20,7 +20,14 @@ struct TcEpilogue {
   void* C = nullptr;
   int c_f64 = 0;       // 1: C is double, 0: float
   int* err = nullptr;  // set to 1 by a CTA whose bounded wait expired
+  // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
+  // writing a plain row-major partial at C + s * split_stride
+  int ksplit = 1, kbs = 0;
+  int64_t split_stride = 0;
 };
+
+// Bytes of split-K partials gemm_packed may use for an M x N product.
+size_t splitk_bytes(int64_t M, int64_t N, int64_t Kp, int kind);
 
 // K rounded up to the 128-byte K block of the kind (32 TF32 / 64 BF16 values).
 int64_t padded_k(int64_t K, int kind);
@@ -35,9 +42,11 @@ void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, co
 
 // C tile loop over packed planes: A [Mp x Kp], B [Np x Kp] (both K-major),
 // Mp a multiple of 128 covering M, Np a multiple of 128 covering N.
+// Products with too few output tiles to fill the GPU split K over several
+// CTAs (partials in splitk_ws, summed in a fixed order by a second kernel).
 void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo,
                  int64_t Mp, const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep,
-                 cudaStream_t s);
+                 cudaStream_t s, float* splitk_ws = nullptr, size_t splitk_ws_bytes = 0);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

@@ -293,7 +293,7 @@ size_t tc_workspace_bytes(const GettCall& g, int prec) {
   const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
   const int64_t Kp = tc::padded_k(g.K, kind);
   const int64_t Mp = tc::round_up(g.M, 128), Np = tc::round_up(g.N, 128);
-  return 4 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp;
+  return 5 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind);
 }
 
 void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
@@ -314,7 +314,9 @@ void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
   void* ah = w + o; o = align(o + elem * Mp * Kp);
   void* al = w + o; o = align(o + elem * Mp * Kp);
   void* bh = w + o; o = align(o + elem * Np * Kp);
-  void* bl = w + o;
+  void* bl = w + o; o = align(o + elem * Np * Kp);
+  float* part = reinterpret_cast<float*>(w + o);
+  const size_t part_bytes = ex.ws_bytes > o ? ex.ws_bytes - o : 0;
   // A rows = M group, A columns = K group; B rows (of the packed K-major plane) = N group
   tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s);
   tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s);
@@ -343,7 +345,7 @@ void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
     pr->used += 2;
     MERA_CUDA(cudaEventRecord(e0, s));
   }
-  tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s);
+  tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (e1) MERA_CUDA(cudaEventRecord(e1, s));
   if (pr) {
     pr->gett_launches++;

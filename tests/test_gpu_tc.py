@@ -5,7 +5,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(128, 128, 32), (200, 130, 70), (1, 1, 1), (1024, 512, 1000), (4100, 257, 2049)]
+SHAPES = [(128, 128, 32), (200, 130, 70), (1, 1, 1), (1024, 512, 1000), (4100, 257, 2049),
+          (256, 200, 40000), (100, 130, 9000)]  # the last two split K
 
 
 @pytest.fixture(scope="module")
