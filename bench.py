@@ -161,10 +161,12 @@ def sample_layer(d_b, chi, L):
 
 
 def oracle_sample(d_b, chi, L, seconds=10.0, seed=0):
-    """Time the oracle's averaged ascending map of one layer of the workload
-    (seeded tensors of that layer, random symmetric operator) on the host cores."""
+    """Time the oracle's ascending map of one layer of the workload (seeded
+    tensors of that layer, random symmetric operator) on the host cores: both
+    sides up to chi=16, the left side A_L alone above (half the flops)."""
     from oracle import mera as om
     layer, cf, cc = sample_layer(d_b, chi, L)
+    one_side = chi > 16
     us, ws = inp.random_mera(d_b, chi, L, seed=seed)
     u, w = us[layer], ws[layer]
     rng = np.random.default_rng(seed)
@@ -172,12 +174,15 @@ def oracle_sample(d_b, chi, L, seconds=10.0, seed=0):
     h = 0.5 * (h + h.T)
     n, t0 = 0, time.perf_counter()
     while True:
-        om.ascend(h, u, w)
+        if one_side:
+            om.ascend_side(h, u, w, "L")
+        else:
+            om.ascend(h, u, w)
         n += 1
         dt = time.perf_counter() - t0
         if dt >= seconds:
             break
-    return dt / n, n, layer, cf, cc
+    return dt / n, n, layer, cf, cc, (0.5 if one_side else 1.0)
 
 
 def host_cores():
@@ -215,13 +220,13 @@ def run_reference(args, wl):
     flops_grad = args.ref_flops_per_grad or FLOPS_PER_GRAD[args.workload]
     per = []
     for i in range(args.warmup + args.steps):
-        t, n, layer, cf, cc = oracle_sample(d_b, chi, L, seconds=args.ref_seconds, seed=i)
+        t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.ref_seconds, seed=i)
         if i >= args.warmup:
             per.append(t)
-    frac = ascend_flops(cf, cc) / flops_grad
+    frac = part * ascend_flops(cf, cc) / flops_grad
     t = sum(per) / len(per)
     value = frac / t
-    sample = (f"oracle (NumPy FP64) averaged ascending map of layer {layer} (chi {cf}->{cc}), "
+    sample = (f"oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}ascending map of layer {layer} (chi {cf}->{cc}), "
               f"{t:.2f} s each = {frac:.3g} of one gradient evaluation's algorithmic flops ({flops_grad:.3g})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
@@ -403,10 +408,11 @@ def main():
             "gpu_launches": st["launches"],
             "clocks": clocks.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, n, layer, cf, cc = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds)
-        frac = ascend_flops(cf, cc) / gett_flops_per_grad
+        t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds)
+        frac = part * ascend_flops(cf, cc) / gett_flops_per_grad
         line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                                "sample": f"{n} x oracle (NumPy FP64) averaged ascending map of layer {layer} "
+                                "sample": f"{n} x oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}"
+                                          f"ascending map of layer {layer} "
                                           f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient "
                                           f"evaluation's algorithmic flops"}
     if rank == 0:
