@@ -27,7 +27,13 @@
  *         w^dag w = 1 (w_L is chi^2 x chi).
  * Tangent vectors, partial derivatives and gradients use the same shapes.
  * mera_tensor_shape() reports them.  Element type: double (MERA_F64) or
- * interleaved complex double (MERA_C128).
+ * interleaved complex double (MERA_C128: real part first, the layout of C99
+ * double _Complex).  Complex problems (a Hamiltonian or tensors with
+ * imaginary parts) run with prec = MERA_PREC_FP64 only; mera_create returns
+ * MERA_ERR_UNSUPPORTED for a complex problem in a mixed-precision mode.  For
+ * complex data the inner product of the tangent space is Re Tr(X^dag Y) and
+ * the projections, retractions and preconditioner use conjugate transposes
+ * where the real case has transposes (Sec. 2.3, Sec. 3).
  *
  * Pointers
  * --------

@@ -152,6 +152,118 @@ __global__ void finite_k(const double* __restrict__ x, int64_t n, int* flag) {
     if (!isfinite(x[i])) *flag = 0;
 }
 
+
+// conj(x) . y for interleaved complex arrays: partial[0*nb + b] real, [1*nb + b] imaginary
+__global__ void cdot_partial(const double2* __restrict__ x, const double2* __restrict__ y, int64_t n,
+                             double* __restrict__ partial) {
+  double sr = 0.0, si = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * RT + threadIdx.x; j < n; j += (int64_t)gridDim.x * RT) {
+    const double2 a = x[j], b = y[j];
+    sr = fma(a.x, b.x, fma(a.y, b.y, sr));
+    si = fma(a.x, b.y, fma(-a.y, b.x, si));
+  }
+  sr = block_sum(sr);
+  si = block_sum(si);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sr;
+    partial[gridDim.x + blockIdx.x] = si;
+  }
+}
+
+__global__ void ctrace_partial(const double2* __restrict__ a, int64_t n, double* __restrict__ partial) {
+  double sr = 0.0, si = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * RT + threadIdx.x; j < n; j += (int64_t)gridDim.x * RT) {
+    sr += a[j * n + j].x;
+    si += a[j * n + j].y;
+  }
+  sr = block_sum(sr);
+  si = block_sum(si);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sr;
+    partial[gridDim.x + blockIdx.x] = si;
+  }
+}
+
+__global__ void hermitize_k(double2* x, int64_t n) {
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  __shared__ double2 t1[32][33], t2[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = bi * 32 + r, j = bj * 32 + tx;
+    t1[r][tx] = (i < n && j < n) ? x[i * n + j] : make_double2(0.0, 0.0);
+    int64_t i2 = bj * 32 + r, j2 = bi * 32 + tx;
+    t2[r][tx] = (i2 < n && j2 < n) ? x[i2 * n + j2] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    int64_t i = bi * 32 + r, j = bj * 32 + tx;
+    // (x + x^dag)/2: element (i,j) averages x_ij with conj(x_ji)
+    const double2 a = t1[r][tx], b = t2[tx][r];
+    if (i < n && j < n) x[i * n + j] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+    int64_t i2 = bj * 32 + r, j2 = bi * 32 + tx;
+    const double2 c = t2[r][tx], d = t1[tx][r];
+    if (bi != bj && i2 < n && j2 < n) x[i2 * n + j2] = make_double2(0.5 * (c.x + d.x), 0.5 * (c.y - d.y));
+  }
+}
+
+__global__ void add_identity_c_k(double re, double im, double2* x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i * n + i].x += re;
+    x[i * n + i].y += im;
+  }
+}
+
+__global__ void marg1c_k(const double2* __restrict__ r, int64_t c, double2* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c * c) return;
+  const int64_t b = idx / c, B = idx % c;
+  const int64_t n3 = c * c * c;
+  double2 s = make_double2(0.0, 0.0);
+  for (int64_t a = 0; a < c; ++a)
+    for (int64_t d = 0; d < c; ++d) {
+      const double2 v = r[(a * c * c + b * c + d) * n3 + (a * c * c + B * c + d)];
+      s.x += v.x;
+      s.y += v.y;
+    }
+  out[idx] = s;
+}
+
+__global__ void marg2c_k(const double2* __restrict__ r, int64_t c, double2* __restrict__ out) {
+  const int64_t c2 = c * c;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c2 * c2) return;
+  const int64_t ab = idx / c2, AB = idx % c2;
+  const int64_t n3 = c2 * c;
+  double2 s = make_double2(0.0, 0.0);
+  for (int64_t d = 0; d < c; ++d) {
+    const double2 v = r[(ab * c + d) * n3 + (AB * c + d)];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[idx] = s;
+}
+
+__global__ void embed_k(const double2* __restrict__ z, int64_t n, double* __restrict__ e) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  const double2 v = z[idx];
+  const int64_t m = 2 * n;
+  e[i * m + j] = v.x;
+  e[i * m + n + j] = -v.y;
+  e[(n + i) * m + j] = v.y;
+  e[(n + i) * m + n + j] = v.x;
+}
+
+__global__ void extract_k(const double* __restrict__ e, int64_t n, double2* __restrict__ z) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  const int64_t i = idx / n, j = idx % n;
+  const int64_t m = 2 * n;
+  z[idx] = make_double2(e[i * m + j], e[(n + i) * m + j]);
+}
+
 inline int grid_for(int64_t n, int threads = 256) {
   int64_t b = (n + threads - 1) / threads;
   if (b > 152 * 16) b = 152 * 16;
@@ -260,6 +372,67 @@ int check_finite(const double* x, int64_t n, cudaStream_t s) {
   return one;
 }
 
+
+void Reducer::dot_c(const double* x, const double* y, int64_t n, cudaStream_t s, double* re, double* im) {
+  int nb = (int)std::min<int64_t>(nblocks, std::max<int64_t>(1, (n + RT - 1) / RT));
+  cdot_partial<<<nb, RT, 0, s>>>(reinterpret_cast<const double2*>(x), reinterpret_cast<const double2*>(y), n,
+                                 partial.as<double>());
+  finish_partial<<<2, RT, 0, s>>>(partial.as<double>(), nb, result.as<double>());
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  double r[2];
+  MERA_CUDA(cudaMemcpyAsync(r, result.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+  *re = r[0];
+  *im = r[1];
+}
+
+void Reducer::trace_c(const double* a, int64_t n, cudaStream_t s, double* re, double* im) {
+  int nb = (int)std::min<int64_t>(nblocks, std::max<int64_t>(1, (n + RT - 1) / RT));
+  ctrace_partial<<<nb, RT, 0, s>>>(reinterpret_cast<const double2*>(a), n, partial.as<double>());
+  finish_partial<<<2, RT, 0, s>>>(partial.as<double>(), nb, result.as<double>());
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  double r[2];
+  MERA_CUDA(cudaMemcpyAsync(r, result.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+  *re = r[0];
+  *im = r[1];
+}
+
+void hermitize(double* x, int64_t n, cudaStream_t s) {
+  const unsigned nt = (unsigned)((n + 31) / 32);
+  hermitize_k<<<dim3(nt, nt), dim3(32, 8), 0, s>>>(reinterpret_cast<double2*>(x), n);
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+void add_identity_c(double re, double im, double* x, int64_t n, cudaStream_t s) {
+  add_identity_c_k<<<grid_for(n), 256, 0, s>>>(re, im, reinterpret_cast<double2*>(x), n);
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+void marginal_1site_mid_c(const double* r, int64_t c, double* out, cudaStream_t s) {
+  marg1c_k<<<(unsigned)((c * c + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(r), c,
+                                                          reinterpret_cast<double2*>(out));
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+void marginal_2site_left_c(const double* r, int64_t c, double* out, cudaStream_t s) {
+  marg2c_k<<<(unsigned)((c * c * c * c + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(r), c,
+                                                                   reinterpret_cast<double2*>(out));
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+void embed_complex(const double* z, int64_t n, double* e, cudaStream_t s) {
+  embed_k<<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(z), n, e);
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
+void extract_complex(const double* e, int64_t n, double* z, cudaStream_t s) {
+  extract_k<<<(unsigned)((n * n + 255) / 256), 256, 0, s>>>(e, n, reinterpret_cast<double2*>(z));
+  count_launch();
+  MERA_CHECK_LAUNCH();
+}
 }  // namespace mera
 
 // ------------------------------------------- allocation-free dot products --

@@ -97,15 +97,19 @@ struct GettCall {
   int64_t M = 0, N = 0, K = 0;
   double alpha = 1.0, beta = 0.0;
   int a32 = 0, b32 = 0, c32 = 0;  // 1: operand stored as float (mixed-precision node buffers)
+  int cplx = 0;                   // 1: interleaved complex elements (offsets count complex elements)
+  int a_conj = 0, b_conj = 0;     // complex: use the complex conjugate of the operand
   int a_rfast = 0, b_rfast = 0;   // 1: the operand's stride-1 leg is in its row group (M for A, N for B)
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 
 // Plain row-major matrix product C = alpha op(A) op(B) + beta C with
-// op = identity or transpose ('N'/'T'); leading dimensions are row strides.
+// op = identity, transpose or conjugate transpose ('N'/'T'/'C'); leading
+// dimensions are row strides in elements; cplx: interleaved complex data
+// (alpha, beta real).
 void gemm_f64(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha,
               const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
-              double* C, int64_t ldc, cudaStream_t s);
+              double* C, int64_t ldc, cudaStream_t s, bool cplx = false);
 
 // ---------------------------------------------------------- BLAS-1 etc ----
 // Deterministic reductions: fixed grid, fixed per-thread ranges, two passes.
@@ -120,6 +124,9 @@ struct Reducer {
             double* out_host);
   double dot(const double* x, const double* y, int64_t n, cudaStream_t s);
   double trace(const double* a, int64_t n, cudaStream_t s);  // n x n matrix
+  // complex: sum_j conj(x_j) y_j of n interleaved complex elements; trace of a complex matrix
+  void dot_c(const double* x, const double* y, int64_t n, cudaStream_t s, double* re, double* im);
+  void trace_c(const double* a, int64_t n, cudaStream_t s, double* re, double* im);
 };
 void axpy(double a, const double* x, double* y, int64_t n, cudaStream_t s);          // y += a x
 void axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t s); // y = a x + b y
@@ -135,6 +142,15 @@ void copy(double* dst, const double* src, int64_t n, cudaStream_t s);
 void marginal_1site_mid(const double* r, int64_t c, double* out, cudaStream_t s);  // c x c
 void marginal_2site_left(const double* r, int64_t c, double* out, cudaStream_t s); // c^2 x c^2
 int check_finite(const double* x, int64_t n, cudaStream_t s);   // 1 if all finite
+// ---- interleaved complex helpers (n = matrix order / element count) ----
+void hermitize(double* x, int64_t n, cudaStream_t s);                      // x = (x + x^dag)/2
+void add_identity_c(double re, double im, double* x, int64_t n, cudaStream_t s);
+void marginal_1site_mid_c(const double* r, int64_t c, double* out, cudaStream_t s);
+void marginal_2site_left_c(const double* r, int64_t c, double* out, cudaStream_t s);
+// real symmetric embedding [[Re, -Im], [Im, Re]] of a complex n x n matrix (2n x 2n)
+void embed_complex(const double* z, int64_t n, double* e, cudaStream_t s);
+// complex n x n matrix from the left block column of a 2n x 2n embedding
+void extract_complex(const double* e, int64_t n, double* z, cudaStream_t s);
 
 // --------------------------------------------------------- small linalg ----
 // Symmetric eigendecomposition of an n x n matrix (in place -> eigenvalues in

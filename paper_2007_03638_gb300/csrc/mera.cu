@@ -78,11 +78,6 @@ __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, doubl
   out[i] = r;
 }
 
-__global__ void add_scaled_identity_dev_k(double* x, int64_t n, const double* scale, double f) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i * n + i] += f * (*scale);
-}
-
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -121,6 +116,8 @@ struct StepGeom {
 struct mera_ctx {
   mera_config cfg{};
   cudaStream_t s = nullptr;
+  bool cplx = false;                      // interleaved complex128 data
+  int rs = 1;                             // reals per element (1 or 2)
   int L = 0, nt = 0;
   std::vector<int64_t> dims;
   std::vector<int64_t> rows, cols, offs;  // tensor shapes and offsets in a flat tangent
@@ -163,12 +160,24 @@ namespace {
 using Ctx = mera_ctx;
 
 double* P(const DevBuf& b) { return b.as<double>(); }
-double* Wt(Ctx& c, DevBuf& flat, int i) { return P(flat) + c.offs[i]; }
 
 int64_t ipow(int64_t b, int e) {
   int64_t r = 1;
   while (e-- > 0) r *= b;
   return r;
+}
+
+// element-type helpers: x = (x + x^dag)/2, x += a 1, matrix products whose
+// 'C' operands are conjugate-transposed (plain transposes for real data)
+void herm(Ctx& c, double* x, int64_t n, cudaStream_t s) {
+  if (c.cplx) hermitize(x, n, s); else symmetrize(x, n, s);
+}
+void add_id(Ctx& c, double a, double* x, int64_t n, cudaStream_t s) {
+  if (c.cplx) add_identity_c(a, 0.0, x, n, s); else add_identity(a, x, n, s);
+}
+void mm(Ctx& c, char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda,
+        const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t s) {
+  gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, c.cplx);
 }
 
 // ------------------------------------------------------ network binding ----
@@ -193,7 +202,7 @@ int64_t choose_chunk(int64_t cf, int64_t cc) {
 void build_layers(Ctx& c) {
   c.layers.resize(c.L + 1);
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
-  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  const size_t es = (mixed ? sizeof(float) : sizeof(double)) * c.rs;
   size_t scratch_need = 0, ws_need = 0;
   for (int l = 0; l <= c.L; ++l) {
     Layer& ly = c.layers[l];
@@ -213,6 +222,7 @@ void build_layers(Ctx& c) {
         ly.buf[sd].val[node] = P(ly.own[sd].back());
       }
       ly.buf[sd].f32 = mixed;
+      ly.buf[sd].cplx = c.cplx;
       ly.buf[sd].ex = &c.ex;
       size_t need = 0;
       for (int node : {12, 15}) need += net.alloc_size(node);
@@ -377,11 +387,11 @@ int gmres(Ctx& c, const std::function<void(const double*, double*)>& op, const d
 void project_tensor(Ctx& c, int i, const double* W, const double* D, double* G, cudaStream_t s) {
   const int64_t n = c.rows[i], p = c.cols[i];
   double* S = P(c.gtmp[0]);
-  gemm_f64('T', 'N', p, p, n, 1.0, W, p, D, p, 0.0, S, p, s);  // S = W^T D
+  mm(c, 'C', 'N', p, p, n, 1.0, W, p, D, p, 0.0, S, p, s);     // S = W^dag D
   const bool stiefel = (i % 2 == 0) || c.cfg.w_stiefel;
-  if (stiefel) symmetrize(S, p, s);                             // (S + S^T)/2
-  if (G != D) copy(G, D, n * p, s);
-  gemm_f64('N', 'N', n, p, p, -1.0, W, p, S, p, 1.0, G, p, s); // G = D - W S
+  if (stiefel) herm(c, S, p, s);                                // (S + S^dag)/2
+  if (G != D) copy(G, D, n * p * c.rs, s);
+  mm(c, 'N', 'N', n, p, p, -1.0, W, p, S, p, 1.0, G, p, s);    // G = D - W S
 }
 
 void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
@@ -401,16 +411,23 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   double* rhoS = P(c.rho[L]);
   double* hL = P(c.h[L]);
   double* xs = P(c.x);
-  if (!c.have_x) copy(xs, hL, n, s);
+  const int64_t nr = n * c.rs;  // reals per chi^6 operator
+  if (!c.have_x) copy(xs, hL, nr, s);
   auto op_x = [&](const double* v, double* out) {
-    copy(out, v, n, s);
+    copy(out, v, nr, s);
     ascend(c, L, W, v, out, -1.0, s);
-    const double t = c.red.dot(v, rhoS, n, s);
-    add_identity(t, out, n3, s);
+    // Tr(v rho) = sum_ij v_ij conj(rho_ij) for hermitian rho
+    if (c.cplx) {
+      double tr, ti;
+      c.red.dot_c(rhoS, v, n, s, &tr, &ti);
+      add_identity_c(tr, ti, out, n3, s);
+    } else {
+      add_identity(c.red.dot(v, rhoS, n, s), out, n3, s);
+    }
     ++c.matvecs;
   };
-  gmres(c, op_x, hL, xs, n, tol, s);
-  symmetrize(xs, n3, s);
+  gmres(c, op_x, hL, xs, nr, tol, s);
+  herm(c, xs, n3, s);
   c.have_x = true;
   gradient_pass(c, W, E, s);
 }
@@ -418,42 +435,50 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
 double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
   const int L = c.L;
   // up-sweep
-  copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6), s);
+  copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6) * c.rs, s);
   for (int l = 0; l <= L; ++l) prepare_layer(c, l, W, s);
   for (int l = 0; l < L; ++l) {
     const int64_t n3 = ipow(c.dims[l + 1], 3);
-    fill(0.0, P(c.h[l + 1]), n3 * n3, s);
+    fill(0.0, P(c.h[l + 1]), n3 * n3 * c.rs, s);
     ascend(c, l, W, P(c.h[l]), P(c.h[l + 1]), 1.0, s);
-    symmetrize(P(c.h[l + 1]), n3, s);
+    herm(c, P(c.h[l + 1]), n3, s);
   }
   // scale-invariant layer
-  const int64_t cS = c.dims[L], n3 = ipow(cS, 3), n = n3 * n3;
+  const int64_t cS = c.dims[L], n3 = ipow(cS, 3), n = n3 * n3, nr = n * c.rs;
   double* rhoS = P(c.rho[L]);
   if (!c.have_rho) {
-    fill(0.0, rhoS, n, s);
-    add_identity(1.0 / (double)n3, rhoS, n3, s);
+    fill(0.0, rhoS, nr, s);
+    add_id(c, 1.0 / (double)n3, rhoS, n3, s);
   }
   double* bvec = P(c.bvec);
-  fill(0.0, bvec, n, s);
-  add_identity(1.0 / (double)n3, bvec, n3, s);
+  fill(0.0, bvec, nr, s);
+  add_id(c, 1.0 / (double)n3, bvec, n3, s);
   // the residual of a Krylov solve cannot fall below the rounding level of
   // the contractions that apply the superoperator
   const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
   const double tol = std::max(c.cfg.krylov_tol, floor_tol);
   auto op_rho = [&](const double* v, double* out) {
-    copy(out, v, n, s);
+    copy(out, v, nr, s);
     descend(c, L, v, out, -1.0, s);
-    const double tr = c.red.trace(v, n3, s);
-    axpy(tr, bvec, out, n, s);
+    // + Tr(v) b, b = 1/chi^3
+    if (c.cplx) {
+      double tr, ti;
+      c.red.trace_c(v, n3, s, &tr, &ti);
+      add_identity_c(tr / (double)n3, ti / (double)n3, out, n3, s);
+    } else {
+      axpy(c.red.trace(v, n3, s), bvec, out, n, s);
+    }
     ++c.matvecs;
   };
-  gmres(c, op_rho, bvec, rhoS, n, tol, s);
-  const double tr = c.red.trace(rhoS, n3, s);
+  gmres(c, op_rho, bvec, rhoS, nr, tol, s);
+  double tr = 0.0, ti = 0.0;
+  if (c.cplx) c.red.trace_c(rhoS, n3, s, &tr, &ti); else tr = c.red.trace(rhoS, n3, s);
   if (!(std::fabs(tr) > 0)) throw Error(MERA_ERR_NONFINITE, "fixed point has zero trace");
-  scal(1.0 / tr, rhoS, n, s);
-  symmetrize(rhoS, n3, s);
+  scal(1.0 / tr, rhoS, nr, s);
+  herm(c, rhoS, n3, s);
   c.have_rho = true;
-  const double e = c.red.dot(P(c.h[L]), rhoS, n, s);
+  // Tr(h rho) = Re sum_ij h_ij conj(rho_ij): the real dot product of the arrays
+  const double e = c.red.dot(P(c.h[L]), rhoS, nr, s);
   check_device_flag(c, s);
   if (!std::isfinite(e)) throw Error(MERA_ERR_NONFINITE, "non-finite energy");
   return e;
@@ -475,7 +500,7 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
     const double* op = l < L ? P(c.h[l]) : xs;
     const double* r = l < L ? P(c.rho[l + 1]) : rhoS;
     const bool need_op = l < L;
-    if (need_op) fill(0.0, P(c.rho[l]), ipow(ly.cf, 6), s);
+    if (need_op) fill(0.0, P(c.rho[l]), ipow(ly.cf, 6) * c.rs, s);
     for (int sd = 0; sd < 2; ++sd) {
       SideBufs& b = ly.buf[sd];
       bind_leaves(ly, sd, op, u, w);
@@ -487,7 +512,7 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
       side_backward(*ly.net[sd], b, need_op, need_op ? P(c.rho[l]) : nullptr, 0.5, true,
                     D + c.offs[2 * l], D + c.offs[2 * l + 1], 1.0, s);
     }
-    if (need_op) symmetrize(P(c.rho[l]), ipow(ly.cf, 3), s);
+    if (need_op) herm(c, P(c.rho[l]), ipow(ly.cf, 3), s);
   }
   // projection
   for (int i = 0; i < c.nt; ++i)
@@ -496,7 +521,7 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   bool finite = std::isfinite(E.e);
   for (int i = 0; i < c.nt; ++i) {
     const double* g = P(E.G) + c.offs[i];
-    E.delta[i] = std::sqrt(c.red.dot(g, g, c.rows[i] * c.cols[i], s));
+    E.delta[i] = std::sqrt(c.red.dot(g, g, c.rows[i] * c.cols[i] * c.rs, s));
     finite = finite && std::isfinite(E.delta[i]);
   }
   check_device_flag(c, s);
@@ -515,9 +540,14 @@ void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s) {
     const double* w = W + c.offs[2 * l + 1];
     double* rw = P(E.rho_v[2 * l + 1]);
     double* ru = P(E.rho_v[2 * l]);
-    marginal_1site_mid(r, cc, rw, s);
     double* r2 = P(c.gtmp[1]);
-    marginal_2site_left(r, cc, r2, s);
+    if (c.cplx) {
+      marginal_1site_mid_c(r, cc, rw, s);
+      marginal_2site_left_c(r, cc, r2, s);
+    } else {
+      marginal_1site_mid(r, cc, rw, s);
+      marginal_2site_left(r, cc, r2, s);
+    }
     // pairwise: T1[x0 x1 b A B] = w[x0 x1 a] r2[a b A B]
     //           T2[x1 b B X1]   = T1 x w[x0 X1 A]
     //           T3[x1 B X1 x2 x3] = T2 x w[x2 x3 b]
@@ -543,43 +573,55 @@ void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s) {
     double* t2 = P(c.gtmp[3]);
     double* t3 = P(c.gtmp[4]);
     auto run = [&](const TDesc& A_, const TDesc& B_, const TDesc& C_, const double* pa,
-                   const double* pb, double* pc) {
+                   const double* pb, double* pc, bool conj_b) {
       GettCall g = make_plan(A_, B_, C_, c.pool).proto;
       g.A = pa;
       g.B = pb;
       g.C = pc;
+      g.cplx = c.cplx;
+      g.b_conj = c.cplx && conj_b;
       gett_f64(g, s);
     };
-    run(wa, R2, T1, w, r2, t1);
-    run(T1, wA, T2, t1, w, t2);
-    run(T2, wb, T3, t2, w, t3);
-    run(T3, wB, RU, t3, w, ru);
-    symmetrize(ru, cf * cf, s);
-    symmetrize(rw, cc, s);
+    // rho_u = W rho2 W^dag: the two isometries on the bra side are conjugated
+    run(wa, R2, T1, w, r2, t1, false);
+    run(T1, wA, T2, t1, w, t2, true);
+    run(T2, wb, T3, t2, w, t3, false);
+    run(T3, wB, RU, t3, w, ru, true);
+    herm(c, ru, cf * cf, s);
+    herm(c, rw, cc, s);
   }
 }
 
+// Eigendecomposition of every rho_v.  Complex hermitian matrices are
+// decomposed through their real symmetric embedding [[Re, -Im], [Im, Re]]
+// (order 2p): any real function of the matrix is the embedding of the
+// same function of the complex matrix.
 void ensure_eig(Ctx& c, Eval& E, cudaStream_t s) {
   if (E.eig_ready) return;
   for (int i = 0; i < c.nt; ++i) {
-    const int64_t p = c.cols[i];
+    const int64_t p = c.cols[i], q = p * c.rs;  // order of the (embedded) problem
     double* A = P(c.gtmp[0]);
-    if (p > 64 && c.eig_uses[i] > 0 && c.eig_uses[i] < 25) {
+    double* src = P(E.rho_v[i]);
+    if (c.cplx) {
+      embed_complex(P(E.rho_v[i]), p, P(c.gtmp[4]), s);
+      src = P(c.gtmp[4]);
+    }
+    if (q > 64 && c.eig_uses[i] > 0 && c.eig_uses[i] < 25) {
       // warm start: rotate rho into the previous eigenbasis, which leaves it
       // nearly diagonal, and continue the Jacobi sweeps from there
       double* T = P(c.gtmp[1]);
       double* Vc = P(c.eig_cache[i]);
-      gemm_f64('N', 'N', p, p, p, 1.0, P(E.rho_v[i]), p, Vc, p, 0.0, T, p, s);
-      gemm_f64('T', 'N', p, p, p, 1.0, Vc, p, T, p, 0.0, A, p, s);
-      copy(P(E.evec[i]), Vc, p * p, s);
-      sym_eig_from(A, P(E.evec[i]), P(E.eval[i]), (int)p, true, c.eigw, s);
+      gemm_f64('N', 'N', q, q, q, 1.0, src, q, Vc, q, 0.0, T, q, s);
+      gemm_f64('T', 'N', q, q, q, 1.0, Vc, q, T, q, 0.0, A, q, s);
+      copy(P(E.evec[i]), Vc, q * q, s);
+      sym_eig_from(A, P(E.evec[i]), P(E.eval[i]), (int)q, true, c.eigw, s);
       c.eig_uses[i]++;
     } else {
-      copy(A, P(E.rho_v[i]), p * p, s);
-      sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)p, c.eigw, s);
+      copy(A, src, q * q, s);
+      sym_eig(A, P(E.evec[i]), P(E.eval[i]), (int)q, c.eigw, s);
       c.eig_uses[i] = 1;
     }
-    if (p > 64) copy(P(c.eig_cache[i]), P(E.evec[i]), p * p, s);
+    if (q > 64) copy(P(c.eig_cache[i]), P(E.evec[i]), q * q, s);
   }
   E.eig_ready = true;
 }
@@ -592,7 +634,7 @@ void precondition(Ctx& c, Eval& E, const double* W, const double* X, double* Xt,
   }
   ensure_eig(c, E, s);
   for (int i = 0; i < c.nt; ++i) {
-    const int64_t n = c.rows[i], p = c.cols[i];
+    const int64_t n = c.rows[i], p = c.cols[i], q = p * c.rs;
     const double* Wi = W + c.offs[i];
     const double* Xi = X + c.offs[i];
     double* Yi = Xt + c.offs[i];
@@ -603,29 +645,42 @@ void precondition(Ctx& c, Eval& E, const double* W, const double* X, double* Xt,
     double* T = P(c.gtmp[1]);
     double* Rinv = P(c.gtmp[2]);
     double* Z = P(c.gtmp[3]);
+    double* Em = P(c.gtmp[4]);
     // regularised inverse (rho^2 + delta^2)^(-1/2) = V diag(1/lt) V^T
-    spectral_k<<<blocks(p), 256, 0, s>>>(P(E.eval[i]), (int)p, 3, 0.0, E.delta[i], lt);
-    vfvt_k<<<blocks(p * p), 256, 0, s>>>(V, lt, (int)p, Rinv);
+    spectral_k<<<blocks(q), 256, 0, s>>>(P(E.eval[i]), (int)q, 3, 0.0, E.delta[i], lt);
+    vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, lt, (int)q, c.cplx ? Em : Rinv);
     count_launch(2);
+    if (c.cplx) extract_complex(Em, p, Rinv, s);
     if (stiefel) {
-      gemm_f64('T', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, A, p, s);   // A = W^T X
+      mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, A, p, s);   // A = W^dag X
       // Z = X - W A  (W_perp B part)
-      copy(Z, Xi, n * p, s);
-      gemm_f64('N', 'N', n, p, p, -1.0, Wi, p, A, p, 1.0, Z, p, s);
-      // At = V [2 (V^T A V)_ij / (lt_i + lt_j)] V^T
-      spectral_k<<<blocks(p), 256, 0, s>>>(P(E.eval[i]), (int)p, 4, 0.0, E.delta[i], lt);
+      copy(Z, Xi, n * p * c.rs, s);
+      mm(c, 'N', 'N', n, p, p, -1.0, Wi, p, A, p, 1.0, Z, p, s);
+      // At = V [2 (V^T A V)_ij / (lt_i + lt_j)] V^T  (on the embedding for complex data)
+      spectral_k<<<blocks(q), 256, 0, s>>>(P(E.eval[i]), (int)q, 4, 0.0, E.delta[i], lt);
       count_launch();
-      gemm_f64('T', 'N', p, p, p, 1.0, V, p, A, p, 0.0, T, p, s);
-      gemm_f64('N', 'N', p, p, p, 1.0, T, p, V, p, 0.0, A, p, s);
-      sylvester_scale_k<<<blocks(p * p), 256, 0, s>>>(A, lt, (int)p);
+      const double* Ain = A;
+      if (c.cplx) {
+        embed_complex(A, p, Em, s);
+        Ain = Em;
+      }
+      gemm_f64('T', 'N', q, q, q, 1.0, V, q, Ain, q, 0.0, T, q, s);
+      double* U2 = c.cplx ? Em : A;
+      gemm_f64('N', 'N', q, q, q, 1.0, T, q, V, q, 0.0, U2, q, s);
+      sylvester_scale_k<<<blocks(q * q), 256, 0, s>>>(U2, lt, (int)q);
       count_launch();
-      gemm_f64('N', 'N', p, p, p, 1.0, V, p, A, p, 0.0, T, p, s);
-      gemm_f64('N', 'T', p, p, p, 1.0, T, p, V, p, 0.0, A, p, s);
+      gemm_f64('N', 'N', q, q, q, 1.0, V, q, U2, q, 0.0, T, q, s);
+      if (c.cplx) {
+        gemm_f64('N', 'T', q, q, q, 1.0, T, q, V, q, 0.0, Em, q, s);
+        extract_complex(Em, p, A, s);
+      } else {
+        gemm_f64('N', 'T', q, q, q, 1.0, T, q, V, q, 0.0, A, q, s);
+      }
       // Yi = W At + Z Rinv
-      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, A, p, 0.0, Yi, p, s);
-      gemm_f64('N', 'N', n, p, p, 1.0, Z, p, Rinv, p, 1.0, Yi, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, A, p, 0.0, Yi, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Z, p, Rinv, p, 1.0, Yi, p, s);
     } else {
-      gemm_f64('N', 'N', n, p, p, 1.0, Xi, p, Rinv, p, 0.0, Yi, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Xi, p, Rinv, p, 0.0, Yi, p, s);
     }
   }
   MERA_CHECK_LAUNCH();
@@ -635,35 +690,36 @@ void precondition(Ctx& c, Eval& E, const double* W, const double* X, double* Xt,
 void expm_skew(Ctx& c, const double* A, double alpha, int64_t n, double* E, double* T1, double* T2,
                cudaStream_t s) {
   // scaling and squaring with a degree-16 Taylor polynomial (Horner form)
-  const double nrm = std::fabs(alpha) * std::sqrt(c.red.dot(A, A, n * n, s));
+  const int64_t nr = n * n * c.rs;
+  const double nrm = std::fabs(alpha) * std::sqrt(c.red.dot(A, A, nr, s));
   int sq = 0;
   while (nrm / std::ldexp(1.0, sq) > 0.5) ++sq;
   const double a = alpha / std::ldexp(1.0, sq);
   const int q = 16;
   // T1 = I + a A / q
-  axpby(a / q, A, 0.0, T1, n * n, s);
-  add_identity(1.0, T1, n, s);
+  axpby(a / q, A, 0.0, T1, nr, s);
+  add_id(c, 1.0, T1, n, s);
   for (int k = q - 1; k >= 1; --k) {
-    gemm_f64('N', 'N', n, n, n, a / k, A, n, T1, n, 0.0, T2, n, s);
-    add_identity(1.0, T2, n, s);
+    mm(c, 'N', 'N', n, n, n, a / k, A, n, T1, n, 0.0, T2, n, s);
+    add_id(c, 1.0, T2, n, s);
     std::swap(T1, T2);
   }
   for (int k = 0; k < sq; ++k) {
-    gemm_f64('N', 'N', n, n, n, 1.0, T1, n, T1, n, 0.0, T2, n, s);
+    mm(c, 'N', 'N', n, n, n, 1.0, T1, n, T1, n, 0.0, T2, n, s);
     std::swap(T1, T2);
   }
-  copy(E, T1, n * n, s);
+  copy(E, T1, nr, s);
 }
 
-// Newton-Schulz polar iteration X <- X (3 - X^T X)/2, in place (n x p).
+// Newton-Schulz polar iteration X <- X (3 - X^dag X)/2, in place (n x p).
 void polar_ns(Ctx& c, double* X, int64_t n, int64_t p, cudaStream_t s) {
   double* S = P(c.gtmp[0]);
   double* Y = P(c.gtmp[1]);
   for (int it = 0; it < 2; ++it) {
-    gemm_f64('T', 'N', p, p, n, -0.5, X, p, X, p, 0.0, S, p, s);
-    add_identity(1.5, S, p, s);
-    gemm_f64('N', 'N', n, p, p, 1.0, X, p, S, p, 0.0, Y, p, s);
-    copy(X, Y, n * p, s);
+    mm(c, 'C', 'N', p, p, n, -0.5, X, p, X, p, 0.0, S, p, s);
+    add_id(c, 1.5, S, p, s);
+    mm(c, 'N', 'N', n, p, p, 1.0, X, p, S, p, 0.0, Y, p, s);
+    copy(X, Y, n * p * c.rs, s);
   }
 }
 
@@ -672,25 +728,30 @@ void make_geom(Ctx& c, const double* W, const double* X, double alpha, cudaStrea
   StepGeom& g = c.geom;
   g.alpha = alpha;
   for (int i = 0; i < c.nt; ++i) {
-    const int64_t n = c.rows[i], p = c.cols[i];
+    const int64_t n = c.rows[i], p = c.cols[i], q = p * c.rs;
     const double* Wi = W + c.offs[i];
     const double* Xi = X + c.offs[i];
-    const bool unitary = (n == p) && ((i % 2 == 0) || c.cfg.w_stiefel || true);
-    if (unitary) {
-      gemm_f64('T', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, P(g.Amat[i]), p, s);
+    if (n == p) {
+      mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, P(g.Amat[i]), p, s);
       expm_skew(c, P(g.Amat[i]), alpha, p, P(g.E[i]), P(c.gtmp[2]), P(c.gtmp[3]), s);
     } else if (i % 2 == 1 && !c.cfg.w_stiefel) {
-      // Grassmann: X^T X = V S^2 V^T
+      // Grassmann: X^dag X = V S^2 V^dag (through the real embedding for complex data)
       double* Z = P(c.gtmp[0]);
       double* ev = P(c.gtmp[5]);
-      gemm_f64('T', 'N', p, p, n, 1.0, Xi, p, Xi, p, 0.0, Z, p, s);
-      sym_eig(Z, P(g.Amat[i]), ev, (int)p, c.eigw, s);
-      double* f = P(c.gtmp[4]);
+      mm(c, 'C', 'N', p, p, n, 1.0, Xi, p, Xi, p, 0.0, Z, p, s);
+      if (c.cplx) {
+        embed_complex(Z, p, P(c.gtmp[4]), s);
+        copy(Z, P(c.gtmp[4]), q * q, s);
+      }
+      sym_eig(Z, P(g.Amat[i]), ev, (int)q, c.eigw, s);
+      double* f = P(c.gtmp[1]);
+      double* F = P(c.gtmp[4]);
       for (int kind = 0; kind < 3; ++kind) {
         double* out = kind == 0 ? P(g.Pc[i]) : kind == 1 ? P(g.P1[i]) : P(g.P2[i]);
-        spectral_k<<<blocks(p), 256, 0, s>>>(ev, (int)p, kind, alpha, 0.0, f);
-        vfvt_k<<<blocks(p * p), 256, 0, s>>>(P(g.Amat[i]), f, (int)p, out);
+        spectral_k<<<blocks(q), 256, 0, s>>>(ev, (int)q, kind, alpha, 0.0, f);
+        vfvt_k<<<blocks(q * q), 256, 0, s>>>(P(g.Amat[i]), f, (int)q, c.cplx ? F : out);
         count_launch(2);
+        if (c.cplx) extract_complex(F, p, out, s);
       }
       MERA_CHECK_LAUNCH();
     } else {
@@ -709,10 +770,10 @@ void apply_retract(Ctx& c, const double* W, const double* X, double* Wout, cudaS
     const double* Xi = X + c.offs[i];
     double* Ri = Wout + c.offs[i];
     if (n == p) {
-      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, P(g.E[i]), p, 0.0, Ri, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, P(g.E[i]), p, 0.0, Ri, p, s);
     } else {
-      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, P(g.Pc[i]), p, 0.0, Ri, p, s);
-      gemm_f64('N', 'N', n, p, p, 1.0, Xi, p, P(g.P1[i]), p, 1.0, Ri, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, P(g.Pc[i]), p, 0.0, Ri, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Xi, p, P(g.P1[i]), p, 1.0, Ri, p, s);
     }
     polar_ns(c, Ri, n, p, s);
   }
@@ -729,17 +790,17 @@ void apply_transport(Ctx& c, const double* W, const double* X, double* Y, cudaSt
     double* Z = P(c.gtmp[0]);
     double* Z2 = P(c.gtmp[1]);
     if (n == p) {
-      // W exp(aA) W^T Y
-      gemm_f64('T', 'N', p, p, n, 1.0, Wi, p, Yi, p, 0.0, Z, p, s);
-      gemm_f64('N', 'N', p, p, p, 1.0, P(g.E[i]), p, Z, p, 0.0, Z2, p, s);
-      gemm_f64('N', 'N', n, p, p, 1.0, Wi, p, Z2, p, 0.0, Yi, p, s);
+      // W exp(aA) W^dag Y
+      mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Yi, p, 0.0, Z, p, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, P(g.E[i]), p, Z, p, 0.0, Z2, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, Z2, p, 0.0, Yi, p, s);
     } else {
-      // Y - W P1 (X^T Y) - X P2 (X^T Y)
-      gemm_f64('T', 'N', p, p, n, 1.0, Xi, p, Yi, p, 0.0, Z, p, s);
-      gemm_f64('N', 'N', p, p, p, 1.0, P(g.P1[i]), p, Z, p, 0.0, Z2, p, s);
-      gemm_f64('N', 'N', n, p, p, -1.0, Wi, p, Z2, p, 1.0, Yi, p, s);
-      gemm_f64('N', 'N', p, p, p, 1.0, P(g.P2[i]), p, Z, p, 0.0, Z2, p, s);
-      gemm_f64('N', 'N', n, p, p, -1.0, Xi, p, Z2, p, 1.0, Yi, p, s);
+      // Y - W P1 (X^dag Y) - X P2 (X^dag Y)
+      mm(c, 'C', 'N', p, p, n, 1.0, Xi, p, Yi, p, 0.0, Z, p, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, P(g.P1[i]), p, Z, p, 0.0, Z2, p, s);
+      mm(c, 'N', 'N', n, p, p, -1.0, Wi, p, Z2, p, 1.0, Yi, p, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, P(g.P2[i]), p, Z, p, 0.0, Z2, p, s);
+      mm(c, 'N', 'N', n, p, p, -1.0, Xi, p, Z2, p, 1.0, Yi, p, s);
     }
   }
 }
@@ -1044,9 +1105,9 @@ void check_isometric(Ctx& c, const double* W, cudaStream_t s) {
   for (int i = 0; i < c.nt; ++i) {
     const int64_t n = c.rows[i], p = c.cols[i];
     double* S = P(c.gtmp[0]);
-    gemm_f64('T', 'N', p, p, n, 1.0, W + c.offs[i], p, W + c.offs[i], p, 0.0, S, p, s);
-    add_identity(-1.0, S, p, s);
-    const double r = std::sqrt(c.red.dot(S, S, p * p, s));
+    mm(c, 'C', 'N', p, p, n, 1.0, W + c.offs[i], p, W + c.offs[i], p, 0.0, S, p, s);
+    add_id(c, -1.0, S, p, s);
+    const double r = std::sqrt(c.red.dot(S, S, p * p * c.rs, s));
     if (!(r < 1e-10)) throw Error(MERA_ERR_NOT_ISOMETRIC, "tensor " + std::to_string(i) + " has |W^T W - 1| = " + std::to_string(r));
   }
 }
@@ -1055,7 +1116,11 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.cfg = cfg;
   c.s = s;
   if (cfg.d_b < 2 || cfg.chi < 2 || cfg.n_trans < 1) throw Error(MERA_ERR_ARG, "bad d_b/chi/n_trans");
-  if (cfg.dtype != MERA_F64) throw Error(MERA_ERR_UNSUPPORTED, "only MERA_F64 is built");
+  if (cfg.dtype != MERA_F64 && cfg.dtype != MERA_C128) throw Error(MERA_ERR_ARG, "unknown dtype");
+  c.cplx = cfg.dtype == MERA_C128;
+  c.rs = c.cplx ? 2 : 1;
+  if (c.cplx && cfg.prec != MERA_PREC_FP64)
+    throw Error(MERA_ERR_UNSUPPORTED, "complex tensors run in the FP64 path only");
   if (cfg.prec != MERA_PREC_FP64 && cfg.prec != MERA_PREC_3XTF32 && cfg.prec != MERA_PREC_SPLIT_BF16)
     throw Error(MERA_ERR_ARG, "unknown precision mode");
   c.pool.set_stream(s);
@@ -1067,21 +1132,21 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   int64_t off = 0;
   for (int l = 0; l <= c.L; ++l) {
     const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
-    c.rows.push_back(cf * cf); c.cols.push_back(cf * cf); c.offs.push_back(off); off += cf * cf * cf * cf;
-    c.rows.push_back(cf * cf); c.cols.push_back(cc);      c.offs.push_back(off); off += cf * cf * cc;
+    c.rows.push_back(cf * cf); c.cols.push_back(cf * cf); c.offs.push_back(off); off += cf * cf * cf * cf * c.rs;
+    c.rows.push_back(cf * cf); c.cols.push_back(cc);      c.offs.push_back(off); off += cf * cf * cc * c.rs;
   }
   c.total = off;
   build_layers(c);
   const size_t tb = sizeof(double) * c.total;
   c.Wcur.alloc(tb);
   c.Wtry.alloc(tb);
-  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 6));
+  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 6) * c.rs);
   MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
   for (int l = 0; l <= c.L; ++l) {
-    c.h.emplace_back(sizeof(double) * ipow(c.dims[l], 6));
-    c.rho.emplace_back(sizeof(double) * ipow(c.dims[l], 6));
+    c.h.emplace_back(sizeof(double) * ipow(c.dims[l], 6) * c.rs);
+    c.rho.emplace_back(sizeof(double) * ipow(c.dims[l], 6) * c.rs);
   }
-  const int64_t nS = ipow(cfg.chi, 6);
+  const int64_t nS = ipow(cfg.chi, 6) * c.rs;  // reals of one chi^6 operator
   c.x.alloc(sizeof(double) * nS);
   c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));
   c.ktmp.alloc(sizeof(double) * nS);
@@ -1095,27 +1160,28 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     gmax = std::max({gmax, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
                      cf * cc * cc * cf, cf * cc * cf * cf * cf});
   }
+  gmax *= c.cplx ? 4 : 1;  // complex data and 2p x 2p real embeddings
   for (auto& b : c.gtmp) b.alloc(sizeof(double) * gmax);
   for (auto& E : c.ev) {
     E.G.alloc(tb);
     E.D.alloc(tb);
     for (int i = 0; i < c.nt; ++i) {
-      const int64_t p = c.cols[i];
-      E.rho_v.emplace_back(sizeof(double) * p * p);
-      E.evec.emplace_back(sizeof(double) * p * p);
-      E.eval.emplace_back(sizeof(double) * p);
+      const int64_t p = c.cols[i], q = p * c.rs;
+      E.rho_v.emplace_back(sizeof(double) * p * p * c.rs);
+      E.evec.emplace_back(sizeof(double) * q * q);
+      E.eval.emplace_back(sizeof(double) * q);
     }
   }
   StepGeom& g = c.geom;
   c.eig_uses.assign(c.nt, 0);
   for (int i = 0; i < c.nt; ++i) {
-    const int64_t p = c.cols[i];
-    c.eig_cache.emplace_back(sizeof(double) * p * p);
-    g.Amat.emplace_back(sizeof(double) * p * p);
-    g.E.emplace_back(sizeof(double) * p * p);
-    g.P1.emplace_back(sizeof(double) * p * p);
-    g.P2.emplace_back(sizeof(double) * p * p);
-    g.Pc.emplace_back(sizeof(double) * p * p);
+    const int64_t p = c.cols[i], q = p * c.rs;
+    c.eig_cache.emplace_back(sizeof(double) * q * q);
+    g.Amat.emplace_back(sizeof(double) * q * q);
+    g.E.emplace_back(sizeof(double) * p * p * c.rs);
+    g.P1.emplace_back(sizeof(double) * p * p * c.rs);
+    g.P2.emplace_back(sizeof(double) * p * p * c.rs);
+    g.Pc.emplace_back(sizeof(double) * p * p * c.rs);
   }
   const int m = std::max(1, cfg.lbfgs_m);
   for (int i = 0; i < m; ++i) {
@@ -1129,7 +1195,8 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   // default point: u = 1, w = first columns
   std::vector<double> host(c.total, 0.0);
   for (int i = 0; i < c.nt; ++i)
-    for (int64_t k = 0; k < std::min(c.rows[i], c.cols[i]); ++k) host[c.offs[i] + k * c.cols[i] + k] = 1.0;
+    for (int64_t k = 0; k < std::min(c.rows[i], c.cols[i]); ++k)
+      host[c.offs[i] + (k * c.cols[i] + k) * c.rs] = 1.0;
   MERA_CUDA(cudaMemcpyAsync(c.Wcur.p, host.data(), tb, cudaMemcpyHostToDevice, s));
   MERA_CUDA(cudaStreamSynchronize(s));
 }
@@ -1168,14 +1235,14 @@ int wrap(mera_t m, F&& f) {
 void copy_in(mera_t m, const void* const* arr, double* flat) {
   for (int i = 0; i < m->nt; ++i) {
     if (!arr[i]) throw Error(MERA_ERR_ARG, "null tensor pointer");
-    MERA_CUDA(cudaMemcpyAsync(flat + m->offs[i], arr[i], sizeof(double) * m->rows[i] * m->cols[i],
+    MERA_CUDA(cudaMemcpyAsync(flat + m->offs[i], arr[i], sizeof(double) * m->rows[i] * m->cols[i] * m->rs,
                               cudaMemcpyDefault, m->s));
   }
 }
 void copy_out(mera_t m, const double* flat, void* const* arr) {
   for (int i = 0; i < m->nt; ++i) {
     if (!arr[i]) throw Error(MERA_ERR_ARG, "null tensor pointer");
-    MERA_CUDA(cudaMemcpyAsync(arr[i], flat + m->offs[i], sizeof(double) * m->rows[i] * m->cols[i],
+    MERA_CUDA(cudaMemcpyAsync(arr[i], flat + m->offs[i], sizeof(double) * m->rows[i] * m->cols[i] * m->rs,
                               cudaMemcpyDefault, m->s));
   }
   MERA_CUDA(cudaStreamSynchronize(m->s));
@@ -1364,15 +1431,16 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
     for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
     if (dims.back() != cfg->chi) return 0;
     const bool mixed = cfg->prec != MERA_PREC_FP64;
-    const size_t es = mixed ? 4 : 8;
+    const size_t rs = cfg->dtype == MERA_C128 ? 2 : 1;
+    const size_t es = (mixed ? 4 : 8) * rs;
     mera::TablePool pool(true);
     size_t bytes = 0, scratch = 0, ws = 0, total = 0, gmax = 1;
     for (size_t l = 0; l < dims.size(); ++l) {
       const int64_t cf = dims[l], cc = l + 1 < dims.size() ? dims[l + 1] : dims[l];
       int64_t chunk = mera::choose_chunk(cf, cc);
       if (cfg->b_chunk > 0) chunk = cfg->b_chunk < cc ? cfg->b_chunk : 0;
-      total += cf * cf * cf * cf + cf * cf * cc;
-      bytes += 2 * 8 * (size_t)mera::ipow(cf, 6);  // h_l, rho_l
+      total += (cf * cf * cf * cf + cf * cf * cc) * rs;
+      bytes += 2 * 8 * rs * (size_t)mera::ipow(cf, 6);  // h_l, rho_l
       gmax = std::max<size_t>({gmax, (size_t)(cf * cf * cf * cf), (size_t)(cc * cc * cc * cc),
                                (size_t)(cf * cf * cc * cc * cc), (size_t)(cf * cc * cc * cf),
                                (size_t)(cf * cc * cf * cf * cf)});
@@ -1387,10 +1455,10 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
           ws = std::max(ws, mera::tc_workspace_bytes(p->proto, cfg->prec));
       }
     }
-    const size_t nS = (size_t)mera::ipow(cfg->chi, 6);
+    const size_t nS = (size_t)mera::ipow(cfg->chi, 6) * rs;
     bytes += scratch + ws + pool.bytes();
     bytes += 8 * nS * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);  // basis, tmp, x, bvec
-    bytes += 8 * gmax * 6;
+    bytes += 8 * gmax * 6 * rs * rs;
     bytes += 8 * (size_t)total * (size_t)(2 * std::max(1, cfg->lbfgs_m) + 2 + 4 + 4);
     return bytes;
   } catch (...) {

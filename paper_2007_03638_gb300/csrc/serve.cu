@@ -181,7 +181,8 @@ int mera_server_submit(mera_server_t sv, const mera_config* cfg, const void* h3,
   if (r->bytes == 0) return MERA_ERR_ARG;
   if (r->bytes > sv->budget) return MERA_ERR_OOM;
   const int64_t n3 = (int64_t)cfg->d_b * cfg->d_b * cfg->d_b;
-  r->h3.assign(static_cast<const char*>(h3), static_cast<const char*>(h3) + sizeof(double) * n3 * n3);
+  const size_t es = sizeof(double) * (cfg->dtype == MERA_C128 ? 2 : 1);
+  r->h3.assign(static_cast<const char*>(h3), static_cast<const char*>(h3) + es * n3 * n3);
   std::vector<int64_t> dims{cfg->d_b};
   for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
   for (int l = 0; l <= cfg->n_trans; ++l) {
@@ -190,7 +191,7 @@ int mera_server_submit(mera_server_t sv, const mera_config* cfg, const void* h3,
     for (int k = 0; k < 2; ++k) {
       const char* p = static_cast<const char*>(tensors[2 * l + k]);
       if (!p) return MERA_ERR_ARG;
-      r->tensors.emplace_back(p, p + sizeof(double) * sz[k]);
+      r->tensors.emplace_back(p, p + es * sz[k]);
     }
   }
   r->gtol = gtol;

@@ -354,36 +354,44 @@ void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
 }
 
 namespace {
-// Run one plan; operand precision follows the buffer kind (leaf/external = double,
-// internal node = float in mixed mode).
-void run(const SideBufs& b, const GemmPlan& p, const double* A, bool a_int, const double* B, bool b_int,
-         double* C, bool c_int, double alpha, double beta, cudaStream_t s) {
+inline bool internal(int node) { return node >= SideNet::NLEAF && node != SideNet::ROOT; }
+// conjugated copies of u and w (bra side of <MERA| ... |MERA>)
+inline bool conj_leaf(int node) { return node == 1 || node == 3 || node == 4 || node == 7 || node == 9; }
+constexpr int EXT = -1;  // an external buffer (operator, seed, output): double, never conjugated
+
+// Run one plan.  Operands are identified by node id (or EXT): leaves and
+// externals are double, internal nodes float in mixed mode; conjugated
+// leaves are read conjugated.
+void run(const SideBufs& b, const GemmPlan& p, const double* A, int an, const double* B, int bn, double* C,
+         int cn, double alpha, double beta, cudaStream_t s) {
   GettCall g = p.proto;
   g.A = A;
   g.B = B;
   g.C = C;
   g.alpha = alpha;
   g.beta = beta;
-  g.a32 = b.f32 && a_int;
-  g.b32 = b.f32 && b_int;
-  g.c32 = b.f32 && c_int;
+  g.a32 = b.f32 && an != EXT && internal(an);
+  g.b32 = b.f32 && bn != EXT && internal(bn);
+  g.c32 = b.f32 && cn != EXT && internal(cn);
+  g.cplx = b.cplx;
+  g.a_conj = b.cplx && an != EXT && conj_leaf(an);
+  g.b_conj = b.cplx && bn != EXT && conj_leaf(bn);
   contract(g, *b.ex, s);
 }
 inline const double* value(const SideBufs& b, int node) {
   return node < SideNet::NLEAF ? b.leaf[node] : b.val[node];
 }
-inline bool internal(int node) { return node >= SideNet::NLEAF && node != SideNet::ROOT; }
 // Advance a node pointer by `off` elements of its storage type.
 inline double* offp(const SideBufs& b, const double* p, int64_t off) {
   char* c = reinterpret_cast<char*>(const_cast<double*>(p));
-  return reinterpret_cast<double*>(c + off * (b.f32 ? 4 : 8));
+  return reinterpret_cast<double*>(c + off * (b.f32 ? 4 : 8) * (b.cplx ? 2 : 1));
 }
 }  // namespace
 
 void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
   for (int node : {11, 14, 16, 19}) {
     const int l = SideNet::left(node), r = SideNet::right(node);
-    run(b, net.fwd(node), value(b, l), internal(l), value(b, r), internal(r), b.val[node], true, 1.0, 0.0, s);
+    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s);
   }
 }
 
@@ -392,18 +400,18 @@ void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, do
     if (net.sliced() && node == 15) {
       // N5 = N3 x N4 and N7 = N5 x N6 one slice of the coarse leg b at a time
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
-        run(b, net.f5c(), b.val[13], true, offp(b, b.val[14], b0 * net.b_stride_n4()), true, b.val[15], true,
+        run(b, net.f5c(), b.val[13], 13, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.val[15], 15,
             1.0, 0.0, s);
-        run(b, net.f7c(), b.val[15], true, b.val[16], true, offp(b, b.val[17], b0 * net.b_stride_n7()), true,
+        run(b, net.f7c(), b.val[15], 15, b.val[16], 16, offp(b, b.val[17], b0 * net.b_stride_n7()), 17,
             1.0, 0.0, s);
       }
       continue;
     }
     if (net.sliced() && node == 17) continue;
     const int l = SideNet::left(node), r = SideNet::right(node);
-    run(b, net.fwd(node), value(b, l), internal(l), value(b, r), internal(r), b.val[node], true, 1.0, 0.0, s);
+    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s);
   }
-  if (out) run(b, net.fwd(SideNet::ROOT), b.val[18], true, b.val[19], true, out, false, alpha, beta, s);
+  if (out) run(b, net.fwd(SideNet::ROOT), b.val[18], 18, b.val[19], 19, out, EXT, alpha, beta, s);
 }
 
 void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out, double alpha_op,
@@ -422,13 +430,13 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
     if (net.sliced() && node == 17) {
       // dN5 one slice of b at a time, consumed at once by N5's children
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
-        run(b, net.b7c(), offp(b, b.adj[17], b0 * net.b_stride_n7()), true, b.val[16], true, b.adj[15], true,
+        run(b, net.b7c(), offp(b, b.adj[17], b0 * net.b_stride_n7()), 17, b.val[16], 16, b.adj[15], 15,
             1.0, 0.0, s);
         if (need[13])
-          run(b, net.b5lc(), b.adj[15], true, offp(b, b.val[14], b0 * net.b_stride_n4()), true, b.adj[13], true,
+          run(b, net.b5lc(), b.adj[15], 15, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.adj[13], 13,
               1.0, b0 == 0 ? 0.0 : 1.0, s);
         if (need[14])
-          run(b, net.b5rc(), b.val[13], true, b.adj[15], true, offp(b, b.adj[14], b0 * net.b_stride_n4()), true,
+          run(b, net.b5rc(), b.val[13], 13, b.adj[15], 15, offp(b, b.adj[14], b0 * net.b_stride_n4()), 14,
               1.0, 0.0, s);
       }
       continue;
@@ -447,12 +455,14 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
       } else {
         out = b.adj[c];
       }
-      const bool dn_int = node != SideNet::ROOT;
-      const bool out_int = c >= SideNet::NLEAF;
+      // the adjoint of node is internal (node id) unless node is the root (seed rho: external);
+      // a leaf's adjoint goes to an external accumulator
+      const int dn_id = node != SideNet::ROOT ? node : EXT;
+      const int out_id = c >= SideNet::NLEAF ? c : EXT;
       if (side == 0)
-        run(b, net.bwd_left(node), dn, dn_int, value(b, r), internal(r), out, out_int, alpha, beta, s);
+        run(b, net.bwd_left(node), dn, dn_id, value(b, r), r, out, out_id, alpha, beta, s);
       else
-        run(b, net.bwd_right(node), value(b, l), internal(l), dn, dn_int, out, out_int, alpha, beta, s);
+        run(b, net.bwd_right(node), value(b, l), l, dn, dn_id, out, out_id, alpha, beta, s);
     }
   }
 }

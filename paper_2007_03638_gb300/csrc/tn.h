@@ -116,6 +116,7 @@ struct SideBufs {
   double* val[SideNet::NNODE] = {};          // internal node values (root = output)
   double* adj[SideNet::NNODE] = {};          // adjoints (root = seed)
   bool f32 = false;
+  bool cplx = false;   // interleaved complex data; conjugated leaves 1,3,4,7,9 read conjugated
   const Exec* ex = nullptr;
 };
 

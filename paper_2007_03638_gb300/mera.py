@@ -172,27 +172,30 @@ def C_void(a):
     return C.c_void_p(_ptr(a))
 
 
-def _ptr(a):
-    """Data pointer of a contiguous float64 numpy array or torch tensor."""
+def _ptr(a, dtype=None):
+    """Data pointer of a contiguous numpy array or torch tensor of float64
+    (or complex128) elements; ``dtype`` (a numpy dtype) pins the type."""
+    ok = (np.dtype(np.float64), np.dtype(np.complex128)) if dtype is None else (np.dtype(dtype),)
     if isinstance(a, np.ndarray):
-        if a.dtype != np.float64 or not a.flags.c_contiguous:
-            raise TypeError("expected a C-contiguous float64 array")
+        if a.dtype not in ok or not a.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {' or '.join(map(str, ok))} array")
         return a.ctypes.data
     import torch
     if isinstance(a, torch.Tensor):
-        if a.dtype != torch.float64 or not a.is_contiguous():
-            raise TypeError("expected a contiguous float64 tensor")
+        tmap = {torch.float64: np.dtype(np.float64), torch.complex128: np.dtype(np.complex128)}
+        if tmap.get(a.dtype) not in ok or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {' or '.join(map(str, ok))} tensor")
         return a.data_ptr()
     raise TypeError(f"unsupported array type {type(a)}")
 
 
-def _ptrs(arrs, keep):
+def _ptrs(arrs, keep, dtype=np.float64):
     out = (C.c_void_p * len(arrs))()
     for i, a in enumerate(arrs):
-        if isinstance(a, np.ndarray) and (a.dtype != np.float64 or not a.flags.c_contiguous):
-            a = np.ascontiguousarray(a, dtype=np.float64)
+        if isinstance(a, np.ndarray) and (a.dtype != dtype or not a.flags.c_contiguous):
+            a = np.ascontiguousarray(a, dtype=dtype)
         keep.append(a)
-        out[i] = _ptr(a)
+        out[i] = _ptr(a, dtype)
     return out
 
 
@@ -202,7 +205,8 @@ class Mera:
     def __init__(self, cfg: Config, h3, stream=None):
         self.L = load()
         self.cfg = cfg
-        h = np.ascontiguousarray(h3, dtype=np.float64) if isinstance(h3, np.ndarray) else h3
+        self.dtype = np.dtype(np.complex128 if cfg.dtype == MERA_C128 else np.float64)
+        h = np.ascontiguousarray(h3, dtype=self.dtype) if isinstance(h3, np.ndarray) else h3
         handle = C.c_void_p()
         if stream is None:
             try:
@@ -210,7 +214,8 @@ class Mera:
                 stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
             except ImportError:
                 stream = 0
-        rc = self.L.mera_create(C.byref(cfg), C.c_void_p(_ptr(h)), C.c_void_p(stream), C.byref(handle))
+        rc = self.L.mera_create(C.byref(cfg), C.c_void_p(_ptr(h, self.dtype)), C.c_void_p(stream),
+                                C.byref(handle))
         if rc != 0:
             raise MeraError(rc, self.L.mera_strerror(rc).decode())
         self.h = handle
@@ -239,18 +244,19 @@ class Mera:
     def _alloc(self, device):
         if device:
             import torch
-            return [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes]
-        return [np.empty(s) for s in self.shapes]
+            tdt = torch.complex128 if self.dtype == np.complex128 else torch.float64
+            return [torch.empty(s, dtype=tdt, device="cuda") for s in self.shapes]
+        return [np.empty(s, dtype=self.dtype) for s in self.shapes]
 
     # ---- C ABI mirrors ------------------------------------------------------
     def set_tensors(self, tensors):
         keep = []
-        self._check(self.L.mera_set_tensors(self.h, _ptrs(tensors, keep)))
+        self._check(self.L.mera_set_tensors(self.h, _ptrs(tensors, keep, self.dtype)))
 
     def get_tensors(self, device=False):
         out = self._alloc(device)
         keep = []
-        self._check(self.L.mera_get_tensors(self.h, _ptrs(out, keep)))
+        self._check(self.L.mera_get_tensors(self.h, _ptrs(out, keep, self.dtype)))
         return out
 
     def energy_grad(self, device=False, deriv=False):
@@ -258,15 +264,15 @@ class Mera:
         G = self._alloc(device)
         keep = []
         D = self._alloc(device) if deriv else None
-        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep),
-                                            _ptrs(D, keep) if deriv else None))
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype),
+                                            _ptrs(D, keep, self.dtype) if deriv else None))
         return (e.value, G, D) if deriv else (e.value, G)
 
     def energy_grad_into(self, G):
         """Energy, with the gradient written into the given arrays (host or device)."""
         e = C.c_double()
         keep = []
-        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep), None))
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype), None))
         return e.value
 
     def energy(self):
@@ -284,32 +290,35 @@ class Mera:
     def project(self, D, device=False):
         G = self._alloc(device)
         keep = []
-        self._check(self.L.mera_project(self.h, _ptrs(D, keep), _ptrs(G, keep)))
+        self._check(self.L.mera_project(self.h, _ptrs(D, keep, self.dtype), _ptrs(G, keep, self.dtype)))
         return G
 
     def inner(self, X, Y):
         out = C.c_double()
         keep = []
-        self._check(self.L.mera_inner(self.h, _ptrs(X, keep), _ptrs(Y, keep), C.byref(out)))
+        self._check(self.L.mera_inner(self.h, _ptrs(X, keep, self.dtype), _ptrs(Y, keep, self.dtype),
+                                      C.byref(out)))
         return out.value
 
     def transport(self, X, alpha, Y):
         keep = []
-        Yc = [np.array(y, dtype=np.float64, copy=True) if isinstance(y, np.ndarray) else y.clone() for y in Y]
-        self._check(self.L.mera_transport(self.h, _ptrs(X, keep), float(alpha), _ptrs(Yc, keep)))
+        Yc = [np.array(y, dtype=self.dtype, copy=True) if isinstance(y, np.ndarray) else y.clone() for y in Y]
+        self._check(self.L.mera_transport(self.h, _ptrs(X, keep, self.dtype), float(alpha),
+                                          _ptrs(Yc, keep, self.dtype)))
         return Yc
 
     def retract(self, X, alpha, want_xprime=False):
         keep = []
         Xp = self._alloc(False) if want_xprime else None
-        self._check(self.L.mera_retract(self.h, _ptrs(X, keep), float(alpha),
-                                        _ptrs(Xp, keep) if want_xprime else None))
+        self._check(self.L.mera_retract(self.h, _ptrs(X, keep, self.dtype), float(alpha),
+                                        _ptrs(Xp, keep, self.dtype) if want_xprime else None))
         return Xp
 
     def precondition(self, X):
         keep = []
         out = self._alloc(False)
-        self._check(self.L.mera_precondition(self.h, _ptrs(X, keep), _ptrs(out, keep)))
+        self._check(self.L.mera_precondition(self.h, _ptrs(X, keep, self.dtype),
+                                             _ptrs(out, keep, self.dtype)))
         return out
 
     def lbfgs_step(self):

@@ -32,9 +32,10 @@ class Server:
     def submit(self, cfg, h3, tensors, method=0, gtol=1e-6, maxiter=100) -> int:
         keep = []
         rid = C.c_int64()
-        h3 = np.ascontiguousarray(h3, dtype=np.float64)
+        dt = np.complex128 if cfg.dtype == gm.MERA_C128 else np.float64
+        h3 = np.ascontiguousarray(h3, dtype=dt)
         rc = self.L.mera_server_submit(self.h, C.byref(cfg), C.c_void_p(h3.ctypes.data),
-                                       gm._ptrs(tensors, keep), int(method), float(gtol), int(maxiter),
+                                       gm._ptrs(tensors, keep, dt), int(method), float(gtol), int(maxiter),
                                        C.byref(rid))
         if rc != 0:
             raise gm.MeraError(rc, self.L.mera_strerror(rc).decode())
