@@ -100,6 +100,13 @@ struct GettCall {
   int cplx = 0;                   // 1: interleaved complex elements (offsets count complex elements)
   int a_conj = 0, b_conj = 0;     // complex: use the complex conjugate of the operand
   int a_rfast = 0, b_rfast = 0;   // 1: the operand's stride-1 leg is in its row group (M for A, N for B)
+  // Output layout hints for the tensor-core epilogue, fixed by the plan:
+  // c_rows = 1: C's M-group offsets run contiguously through every aligned
+  //   group of 32 rows (off(m) = off(m - m % 32) + m % 32);
+  // c_vec = v (8, 4 or 1): N % v == 0, C's N-group offsets run contiguously
+  //   through every aligned group of v columns, and every M-group offset and
+  //   every group-start N offset is a multiple of v.
+  int c_rows = 0, c_vec = 1;
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 

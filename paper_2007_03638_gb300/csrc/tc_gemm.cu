@@ -299,6 +299,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       int klo, khi;
       krange(t, klo, khi);
       const int gpt = (khi - klo + PROMOTE - 1) / PROMOTE;  // accumulator groups of this item
+      // this lane's output row offset, loaded while the MMAs run
+      const int64_t mrow = m0 + row;
+      const bool rvalid = mrow < ep.M;
+      const int64_t my_off = rvalid ? (ep.cm ? ep.cm[mrow] : mrow * ep.cms) : 0;
       float acc[HC];
 #pragma unroll
       for (int j = 0; j < HC; ++j) acc[j] = 0.f;
@@ -340,44 +344,131 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
       }
       if (!ok) break;
-      // store: 16-column chunks staged through shared memory; lanes 0-15 and
-      // 16-31 write consecutive columns of two rows per instruction
-      const int64_t mrow = m0 + row;
-      const int64_t my_off = mrow < ep.M ? (ep.cm ? ep.cm[mrow] : mrow * ep.cms) : 0;
-      const unsigned rowmask = __ballot_sync(0xffffffffu, mrow < ep.M);
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0;
       void* Cbase = ep.ksplit > 1 ? static_cast<void*>(static_cast<float*>(ep.C) + (t / nt1) * ep.split_stride)
                                   : ep.C;
       const double alpha = ep.alpha, beta = ep.beta;
       const float alpha_f = (float)ep.alpha, beta_f = (float)ep.beta;
-      const int cl = lane & 15, rsel = lane >> 4;
+      const int64_t nbase = n0 + half * HC;  // first column of this warp's half
+      if (ep.mode == 1) {
+        // lanes = 32 consecutive rows = 32 consecutive elements: one
+        // coalesced 128-byte (float) store per column, no transpose
 #pragma unroll
-      for (int c0 = 0; c0 < HC; c0 += STG) {
+        for (int c0 = 0; c0 < HC; c0 += 16) {
+          int64_t co[16];
 #pragma unroll
-        for (int j = 0; j < STG; ++j) stg[lane * (STG + 1) + j] = acc[c0 + j];
-        __syncwarp();
-        const int64_t n = n0 + half * HC + c0 + cl;
-        const bool nvalid = n < ep.N;
-        const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
+          for (int j = 0; j < 16; ++j) {
+            const int64_t n = nbase + c0 + j;
+            co[j] = n < ep.N ? (ep.cn ? ep.cn[n] : n * ep.cns) : -1;
+          }
+          if (rvalid) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int r = 2 * j + rsel;
-          const int64_t idx = __shfl_sync(0xffffffffu, my_off, r) + coff;
-          const float tv = stg[r * (STG + 1) + cl];
-          if (nvalid && ((rowmask >> r) & 1u)) {
+            for (int j = 0; j < 16; ++j) {
+              if (co[j] < 0) continue;
+              const int64_t idx = my_off + co[j];
+              if (f64out) {
+                double* C = static_cast<double*>(Cbase);
+                const double v = alpha * (double)acc[c0 + j];
+                C[idx] = acc_c ? fma(beta, C[idx], v) : v;
+              } else {
+                float* C = static_cast<float*>(Cbase);
+                const float v = alpha_f * acc[c0 + j];
+                C[idx] = acc_c ? fmaf(beta_f, C[idx], v) : v;
+              }
+            }
+          }
+        }
+      } else if (ep.mode == 2 || ep.mode == 3) {
+        // float output, V consecutive aligned columns per vector: each lane
+        // writes its own row in 32-byte (V = 8) or 16-byte (V = 4) pieces
+        const int V = ep.mode == 2 ? 8 : 4;
+        float* C = static_cast<float*>(Cbase);
+        int64_t co[HC / 4];
+#pragma unroll
+        for (int c = 0; c < HC / 4; ++c) {
+          const int64_t n = nbase + (int64_t)c * V;
+          co[c] = (c * V < HC && n < ep.N) ? (ep.cn ? ep.cn[n] : n) : -1;
+        }
+        if (rvalid) {
+          if (V == 8) {
+#pragma unroll
+            for (int c = 0; c < HC / 8; ++c) {
+              if (co[c] < 0) continue;
+              float* p = C + my_off + co[c];
+              float v[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) v[j] = alpha_f * acc[8 * c + j];
+              if (acc_c) {
+                float o[8];
+                asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]),
+                               "=f"(o[7])
+                             : "l"(p));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = fmaf(beta_f, o[j], v[j]);
+              }
+              asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                           "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                           : "memory");
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < HC / 4; ++c) {
+              if (co[c] < 0) continue;
+              float4* p = reinterpret_cast<float4*>(C + my_off + co[c]);
+              float4 v = make_float4(alpha_f * acc[4 * c], alpha_f * acc[4 * c + 1], alpha_f * acc[4 * c + 2],
+                                     alpha_f * acc[4 * c + 3]);
+              if (acc_c) {
+                const float4 o = *p;
+                v.x = fmaf(beta_f, o.x, v.x);
+                v.y = fmaf(beta_f, o.y, v.y);
+                v.z = fmaf(beta_f, o.z, v.z);
+                v.w = fmaf(beta_f, o.w, v.w);
+              }
+              *p = v;
+            }
+          }
+        }
+      } else {
+        // any layout: 16-column chunks transposed through shared memory so
+        // that lanes 0-15 and 16-31 write 16 consecutive columns of two rows
+        const unsigned rowmask = __ballot_sync(0xffffffffu, rvalid);
+        const int cl = lane & 15, rsel = lane >> 4;
+#pragma unroll
+        for (int c0 = 0; c0 < HC; c0 += STG) {
+#pragma unroll
+          for (int j = 0; j < STG; ++j) stg[lane * (STG + 1) + j] = acc[c0 + j];
+          __syncwarp();
+          const int64_t n = nbase + c0 + cl;
+          const bool nvalid = n < ep.N;
+          const int64_t coff = nvalid ? (ep.cn ? ep.cn[n] : n * ep.cns) : 0;
+          // all shuffles and staged reads first, then the independent stores
+          int64_t ro[16];
+          float tv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int r = 2 * j + rsel;
+            ro[j] = __shfl_sync(0xffffffffu, my_off, r);
+            tv[j] = stg[r * (STG + 1) + cl];
+          }
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int r = 2 * j + rsel;
+            if (!nvalid || !((rowmask >> r) & 1u)) continue;
+            const int64_t idx = ro[j] + coff;
             if (f64out) {
-              const double v = alpha * (double)tv;
+              const double v = alpha * (double)tv[j];
               double* C = static_cast<double*>(Cbase);
               C[idx] = acc_c ? fma(beta, C[idx], v) : v;
             } else {
               // float output: FP32 arithmetic (the FP64 pipe is a few ops per clock per SM)
               float* C = static_cast<float*>(Cbase);
-              const float v = alpha_f * tv;
+              const float v = alpha_f * tv[j];
               C[idx] = acc_c ? fmaf(beta_f, C[idx], v) : v;
             }
           }
         }
-        __syncwarp();
       }
     }
     if (!ok) atomicExch(&S->abort, 1);
@@ -608,17 +699,34 @@ void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, co
 }
 
 namespace {
-constexpr int SPLITK_MAX = 8;
-// Number of K slices for an M x N x Kp product: only products whose output
-// tiles cover less than half of the GPU split, each slice keeping >= 16 K blocks.
+#ifndef MERA_TC_SPLITK_MAX
+#define MERA_TC_SPLITK_MAX 32
+#endif
+constexpr int SPLITK_MAX = MERA_TC_SPLITK_MAX;
+// Number of K slices for an M x N x Kp product.  Only products whose output
+// tiles cover less than half of the GPU split; each slice keeps >= 16 K
+// blocks.  Among the admissible counts the one whose work items fill the
+// SMs' last wave best is taken (the smallest of equally good ones).
 int choose_split(int64_t M, int64_t N, int64_t Kp, int kind) {
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + 127) / 128);
   const int64_t kblocks = Kp / (KB_BYTES / (kind == KIND_TF32 ? 4 : 2));
-  const int nsm = 152;
+  const int64_t nsm = 152;
   if (tiles * 2 > nsm || kblocks < 32) return 1;
-  int64_t sp = (2 * nsm + tiles - 1) / tiles;
-  sp = std::min<int64_t>(std::min<int64_t>(sp, (int64_t)SPLITK_MAX), kblocks / 16);
-  return (int)std::max<int64_t>(sp, 1);
+  const int64_t lo = (nsm + tiles - 1) / tiles;  // at least one wave
+  const int64_t hi = std::min<int64_t>((int64_t)SPLITK_MAX, kblocks / 16);
+  if (hi <= 1) return 1;
+  int64_t best = std::min(lo, hi);
+  double best_eff = 0.0;
+  for (int64_t sp = std::min(lo, hi); sp <= hi; ++sp) {
+    const int64_t items = tiles * sp, waves = (items + nsm - 1) / nsm;
+    const double eff = (double)items / (double)(waves * nsm);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = sp;
+    }
+    if (eff > 0.97) break;
+  }
+  return (int)best;
 }
 }  // namespace
 
@@ -657,7 +765,20 @@ void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, c
     run.cns = 1;
     run.alpha = 1.0;
     run.beta = 0.0;
+    run.rows = N == 1;
+    run.vec = N % 8 == 0 ? 8 : N % 4 == 0 ? 4 : 1;
   }
+  // store path: lanes = rows when rows are contiguous, else per-row vectors
+  // when the columns are (pointer alignment permitting), else the transpose
+  const uintptr_t cb = reinterpret_cast<uintptr_t>(run.C);
+  if (run.rows)
+    run.mode = 1;
+  else if (!run.c_f64 && run.vec == 8 && cb % 32 == 0)
+    run.mode = 2;
+  else if (!run.c_f64 && run.vec >= 4 && cb % 16 == 0)
+    run.mode = 3;
+  else
+    run.mode = 0;
   if (kind == KIND_TF32)
     launch<KIND_TF32, 128>(ah, al, bh, bl, run, mt * run.ksplit, nt, s);
   else

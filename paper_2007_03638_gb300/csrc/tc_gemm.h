@@ -19,6 +19,11 @@ struct TcEpilogue {
   int64_t cns = 0;
   void* C = nullptr;
   int c_f64 = 0;       // 1: C is double, 0: float
+  // layout hints (GettCall::c_rows / c_vec): rows = 1 when 32 consecutive
+  // rows are 32 consecutive elements; vec = v when v consecutive columns
+  // are v consecutive, v-aligned elements.  gemm_packed turns them into mode.
+  int rows = 0, vec = 1;
+  int mode = 0;        // store path: 0 staged transpose, 1 lanes = rows, 2/3 per-row 8/4-wide vectors
   int* err = nullptr;  // set to 1 by a CTA whose bounded wait expired
   // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
   // writing a plain row-major partial at C + s * split_stride

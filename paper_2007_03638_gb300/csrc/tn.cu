@@ -88,6 +88,37 @@ void set_group(const TDesc& t, const std::vector<int>& legs, TablePool& pool, co
   *count = n;
 }
 
+// Offsets of every index of a leg group (odometer over the group's legs, last fastest).
+std::vector<int64_t> all_offsets(const TDesc& t, const std::vector<int>& legs) {
+  std::vector<int64_t> ext, str;
+  int64_t n = 1;
+  for (int l : legs) {
+    const int j = t.find(l);
+    ext.push_back(t.ext[j]);
+    str.push_back(t.stride[j]);
+    n *= t.ext[j];
+  }
+  std::vector<int64_t> out(n);
+  std::vector<int64_t> idx(ext.size(), 0);
+  int64_t o = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    out[i] = o;
+    for (size_t j = ext.size(); j-- > 0;) {
+      if (++idx[j] < ext[j]) { o += str[j]; break; }
+      o -= str[j] * (ext[j] - 1);
+      idx[j] = 0;
+    }
+  }
+  return out;
+}
+
+// off(i) = off(i - i % r) + i % r for every i
+bool runs_of(const std::vector<int64_t>& off, int64_t r) {
+  for (size_t i = 0; i < off.size(); ++i)
+    if (off[i] != off[i - i % r] + (int64_t)(i % r)) return false;
+  return true;
+}
+
 TDesc make_desc(const std::vector<int>& legs, const std::vector<int64_t>& ext) {
   TDesc d;
   d.legs = legs;
@@ -135,6 +166,17 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
   const int fa = fast_leg(A), fb = fast_leg(B);
   g.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
   g.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
+  // output layout hints (see GettCall)
+  const std::vector<int64_t> om = all_offsets(C, M), on = all_offsets(C, N);
+  g.c_rows = runs_of(om, 32);
+  g.c_vec = 1;
+  for (int64_t v : {8, 4}) {
+    if (n % v || !runs_of(on, v)) continue;
+    bool ok = true;
+    for (int64_t o : om) ok = ok && o % v == 0;
+    for (size_t i = 0; i < on.size() && ok; i += v) ok = on[i] % v == 0;
+    if (ok) { g.c_vec = (int)v; break; }
+  }
   return p;
 }
 
@@ -329,6 +371,8 @@ void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
   ep.cns = g.c.s1;
   ep.C = g.C;
   ep.c_f64 = g.c32 ? 0 : 1;
+  ep.rows = g.c_rows;
+  ep.vec = g.c_vec;
   ep.err = ex.err;
   Prof* pr = g_prof;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
