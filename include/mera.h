@@ -217,6 +217,14 @@ typedef struct {
 } mera_stats;
 int mera_get_stats(mera_t m, mera_stats* out, int reset);
 int mera_profile(mera_t m, int enable);
+/* Write the per-shape table of the contractions timed while profiling was on
+ * (since creation or the last reset of mera_get_stats) to the file `path` as
+ * CSV lines "M,N,K,path,calls,ms,tflops": path 0 is the FP64 contraction
+ * kernel, otherwise 1000 * (1 + tensor-core kind: 0 TF32, 1 BF16) + 100 *
+ * epilogue store mode + 10 * cluster CTAs along M + cluster CTAs along N;
+ * tflops counts 2 M N K per call.  Synchronises the object's stream.
+ * MERA_ERR_ARG if the file cannot be written. */
+int mera_profile_dump(mera_t m, const char* path);
 
 /* ---------------------------------------------------------------- serving --
  * Many optimisations on one GPU (no counterpart in the paper; the request

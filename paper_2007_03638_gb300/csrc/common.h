@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <string>
 #include <vector>
+#include <array>
 #include <map>
 #include <stdexcept>
 
@@ -42,6 +43,18 @@ struct Prof {
   double gett_ms = 0.0;
   int64_t gett_timed = 0;
   int64_t energy_grad_calls = 0;
+  // per-shape table of the timed contractions: key = (M, N, K, path)
+  // with path = 0 FP64 GETT, else 1000 * kind + 100 * store mode + cluster
+  struct Shape {
+    int64_t calls = 0;
+    double ms = 0.0;
+  };
+  std::map<std::array<int64_t, 4>, Shape> shapes;
+  std::vector<std::array<int64_t, 4>> pending;  // key of each recorded pair
+  // Record an event pair around one contraction (if timing): call begin()
+  // before the launch and end() after it.
+  int64_t begin(int64_t M, int64_t N, int64_t K, cudaStream_t s);  // -1 when not timing
+  void end(int64_t pair, int64_t path, cudaStream_t s);
   ~Prof();
   void collect();               // sum the recorded pairs (after a sync)
 };
@@ -107,6 +120,9 @@ struct GettCall {
   //   through every aligned group of v columns, and every M-group offset and
   //   every group-start N offset is a multiple of v.
   int c_rows = 0, c_vec = 1;
+  // the same hints for the transposed product C^T = B^T A^T (roles of the
+  // M and N groups exchanged)
+  int c_rows_t = 0, c_vec_t = 1;
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 

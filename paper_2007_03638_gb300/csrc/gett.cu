@@ -194,25 +194,12 @@ void gett_f64(const GettCall& g, cudaStream_t s) {
   if (gy > 65535) throw Error(MERA_ERR_UNSUPPORTED, "gett_f64: N too large for grid");
   dim3 grid((unsigned)gx, (unsigned)gy);
   Prof* pr = g_prof;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (pr && pr->timing) {
-    if (pr->used + 2 > pr->ev.size()) {
-      for (int i = 0; i < 256; ++i) {
-        cudaEvent_t e;
-        MERA_CUDA(cudaEventCreate(&e));
-        pr->ev.push_back(e);
-      }
-    }
-    e0 = pr->ev[pr->used];
-    e1 = pr->ev[pr->used + 1];
-    pr->used += 2;
-    MERA_CUDA(cudaEventRecord(e0, s));
-  }
+  const int64_t pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
   if (g.cplx)
     gett_c128_kernel<<<grid, NT, 0, s>>>(g);
   else
     gett_f64_kernel<<<grid, NT, 0, s>>>(g);
-  if (e1) MERA_CUDA(cudaEventRecord(e1, s));
+  if (pr) pr->end(pair, 0, s);
   if (pr) {
     pr->launches++;
     pr->gett_launches++;
@@ -225,15 +212,41 @@ Prof::~Prof() {
   for (auto e : ev) cudaEventDestroy(e);
 }
 
+int64_t Prof::begin(int64_t M, int64_t N, int64_t K, cudaStream_t s) {
+  if (!timing) return -1;
+  if (used + 2 > ev.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      MERA_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+  }
+  const int64_t i = (int64_t)used;
+  used += 2;
+  MERA_CUDA(cudaEventRecord(ev[i], s));
+  pending.push_back({M, N, K, 0});
+  return i;
+}
+
+void Prof::end(int64_t pair, int64_t path, cudaStream_t s) {
+  if (pair < 0) return;
+  MERA_CUDA(cudaEventRecord(ev[pair + 1], s));
+  pending[pair / 2][3] = path;
+}
+
 void Prof::collect() {
   for (size_t i = 0; i + 1 < used; i += 2) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
       gett_ms += ms;
       gett_timed++;
+      Shape& sh = shapes[pending[i / 2]];
+      sh.calls++;
+      sh.ms += ms;
     }
   }
   used = 0;
+  pending.clear();
 }
 
 void gemm_f64(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,

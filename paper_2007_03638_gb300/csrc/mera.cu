@@ -1481,6 +1481,7 @@ int mera_get_stats(mera_t m, mera_stats* out, int reset) {
     out->energy_grad_calls = m->prof.energy_grad_calls;
     out->krylov_matvecs = m->matvecs;
     if (reset) {
+      m->prof.shapes.clear();
       m->prof.launches = m->prof.gett_launches = m->prof.gett_timed = 0;
       m->prof.gett_flops = m->prof.gett_ms = 0.0;
       m->prof.energy_grad_calls = 0;
@@ -1495,6 +1496,25 @@ int mera_profile(mera_t m, int enable) {
     MERA_CUDA(cudaStreamSynchronize(m->s));
     m->prof.collect();
     m->prof.timing = enable != 0;
+  });
+}
+
+int mera_profile_dump(mera_t m, const char* path) {
+  if (!m || !path) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    MERA_CUDA(cudaStreamSynchronize(m->s));
+    m->prof.collect();
+    FILE* f = std::fopen(path, "w");
+    if (!f) throw Error(MERA_ERR_ARG, std::string("cannot write ") + path);
+    std::fprintf(f, "M,N,K,path,calls,ms,tflops\n");
+    for (const auto& kv : m->prof.shapes) {
+      const auto& k = kv.first;
+      const double fl = 2.0 * (double)k[0] * (double)k[1] * (double)k[2] * (double)kv.second.calls;
+      std::fprintf(f, "%lld,%lld,%lld,%lld,%lld,%.4f,%.2f\n", (long long)k[0], (long long)k[1], (long long)k[2],
+                   (long long)k[3], (long long)kv.second.calls, kv.second.ms,
+                   kv.second.ms > 0 ? fl / (kv.second.ms * 1e9) : 0.0);
+    }
+    std::fclose(f);
   });
 }
 
@@ -1541,6 +1561,7 @@ int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const 
     ep.c_f64 = 1;
     ep.cms = N;
     ep.cns = 1;
+    ep.rows = N == 1;
     ep.err = err.as<int>();
     mera::tc::gemm_packed(kind, M, N, Kp, ah.p, al.p, Mp, bh.p, bl.p, Np, ep, s, part.as<float>(), skb);
     int e = 0;

@@ -24,6 +24,11 @@ struct TcEpilogue {
   // are v consecutive, v-aligned elements.  gemm_packed turns them into mode.
   int rows = 0, vec = 1;
   int mode = 0;        // store path: 0 staged transpose, 1 lanes = rows, 2/3 per-row 8/4-wide vectors
+  // float C with beta != 0 in modes 1-3 and alpha a power of two: each lane
+  // starts its register accumulator at (beta / alpha) C while the tile's MMAs
+  // run, and the store writes alpha * acc without reading C again
+  int preload = 0;
+  float bscale = 0.f;  // beta / alpha (exact: alpha is a power of two)
   int* err = nullptr;  // set to 1 by a CTA whose bounded wait expired
   // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
   // writing a plain row-major partial at C + s * split_stride
@@ -49,9 +54,11 @@ void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, co
 // Mp a multiple of 128 covering M, Np a multiple of 128 covering N.
 // Products with too few output tiles to fill the GPU split K over several
 // CTAs (partials in splitk_ws, summed in a fixed order by a second kernel).
-void gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo,
-                 int64_t Mp, const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep,
-                 cudaStream_t s, float* splitk_ws = nullptr, size_t splitk_ws_bytes = 0);
+// Returns the path taken: 100 * store mode + 10 * cluster CTAs along M +
+// cluster CTAs along N.
+int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo,
+                int64_t Mp, const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep,
+                cudaStream_t s, float* splitk_ws = nullptr, size_t splitk_ws_bytes = 0);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

@@ -166,17 +166,22 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
   const int fa = fast_leg(A), fb = fast_leg(B);
   g.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
   g.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
-  // output layout hints (see GettCall)
+  // output layout hints (see GettCall), for C = A B and for C^T = B^T A^T
   const std::vector<int64_t> om = all_offsets(C, M), on = all_offsets(C, N);
+  auto vec_of = [](const std::vector<int64_t>& rows, const std::vector<int64_t>& cols) {
+    for (int64_t v : {8, 4}) {
+      if ((int64_t)cols.size() % v || !runs_of(cols, v)) continue;
+      bool ok = true;
+      for (int64_t o : rows) ok = ok && o % v == 0;
+      for (size_t i = 0; i < cols.size() && ok; i += v) ok = cols[i] % v == 0;
+      if (ok) return (int)v;
+    }
+    return 1;
+  };
   g.c_rows = runs_of(om, 32);
-  g.c_vec = 1;
-  for (int64_t v : {8, 4}) {
-    if (n % v || !runs_of(on, v)) continue;
-    bool ok = true;
-    for (int64_t o : om) ok = ok && o % v == 0;
-    for (size_t i = 0; i < on.size() && ok; i += v) ok = on[i] % v == 0;
-    if (ok) { g.c_vec = (int)v; break; }
-  }
+  g.c_vec = vec_of(om, on);
+  g.c_rows_t = runs_of(on, 32);
+  g.c_vec_t = vec_of(on, om);
   return p;
 }
 
@@ -338,13 +343,45 @@ size_t tc_workspace_bytes(const GettCall& g, int prec) {
   return 5 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind);
 }
 
-void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return;
+namespace {
+// The transposed product C^T = B^T A^T: the same contraction with the roles
+// of A and B (and of the M and N groups) exchanged.
+GettCall transposed(const GettCall& g) {
+  GettCall h = g;
+  h.A = g.B;
+  h.B = g.A;
+  h.a.t0 = g.b.t1; h.a.s0 = g.b.s1;  // rows of A^T-side operand: B's N group
+  h.a.t1 = g.b.t0; h.a.s1 = g.b.s0;  // its K group
+  h.b.t0 = g.a.t1; h.b.s0 = g.a.s1;  // K group of the other: A's K group
+  h.b.t1 = g.a.t0; h.b.s1 = g.a.s0;  // its N group: A's M group
+  h.c.t0 = g.c.t1; h.c.s0 = g.c.s1;
+  h.c.t1 = g.c.t0; h.c.s1 = g.c.s0;
+  h.M = g.N;
+  h.N = g.M;
+  h.a32 = g.b32;
+  h.b32 = g.a32;
+  h.a_conj = g.b_conj;
+  h.b_conj = g.a_conj;
+  h.a_rfast = g.b_rfast;
+  h.b_rfast = g.a_rfast;
+  h.c_rows = g.c_rows_t;
+  h.c_vec = g.c_vec_t;
+  h.c_rows_t = g.c_rows;
+  h.c_vec_t = g.c_vec;
+  return h;
+}
+}  // namespace
+
+void contract(const GettCall& g0, const Exec& ex, cudaStream_t s) {
+  if (g0.M <= 0 || g0.N <= 0) return;
   if (ex.prec == MERA_PREC_FP64) {
-    if (g.a32 || g.b32 || g.c32) throw Error(MERA_ERR_ARG, "contract: float operand in the FP64 path");
-    gett_f64(g, s);
+    if (g0.a32 || g0.b32 || g0.c32) throw Error(MERA_ERR_ARG, "contract: float operand in the FP64 path");
+    gett_f64(g0, s);
     return;
   }
+  // tensor cores: take the orientation whose output columns run contiguously
+  // (the epilogue then writes whole 32-byte pieces of each row)
+  const GettCall g = (g0.c_vec < 8 && g0.c_vec_t > g0.c_vec) ? transposed(g0) : g0;
   const int kind = ex.prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
   const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
   const int64_t Kp = tc::padded_k(g.K, kind);
@@ -375,23 +412,10 @@ void contract(const GettCall& g, const Exec& ex, cudaStream_t s) {
   ep.vec = g.c_vec;
   ep.err = ex.err;
   Prof* pr = g_prof;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (pr && pr->timing) {
-    if (pr->used + 2 > pr->ev.size()) {
-      for (int i = 0; i < 256; ++i) {
-        cudaEvent_t e;
-        MERA_CUDA(cudaEventCreate(&e));
-        pr->ev.push_back(e);
-      }
-    }
-    e0 = pr->ev[pr->used];
-    e1 = pr->ev[pr->used + 1];
-    pr->used += 2;
-    MERA_CUDA(cudaEventRecord(e0, s));
-  }
-  tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
-  if (e1) MERA_CUDA(cudaEventRecord(e1, s));
+  const int64_t pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
+  const int path = tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (pr) {
+    pr->end(pair, 1000 * (kind + 1) + path, s);
     pr->gett_launches++;
     pr->gett_flops += 2.0 * (double)g.M * (double)g.N * (double)g.K;
   }

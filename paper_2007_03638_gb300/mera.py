@@ -71,7 +71,7 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_energy_grad",
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_solve", "mera_footprint_bytes",
-           "mera_launch_count", "mera_get_stats", "mera_profile", "mera_dots_noalloc",
+           "mera_launch_count", "mera_get_stats", "mera_profile", "mera_profile_dump", "mera_dots_noalloc",
            "mera_gemm", "mera_strerror", "mera_last_error", "mera_server_create",
            "mera_server_submit", "mera_server_poll", "mera_server_wait", "mera_server_destroy"]
 
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "mera_launch_count": (C.c_int64, [C.c_void_p]),
         "mera_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats), C.c_int]),
         "mera_profile": (C.c_int, [C.c_void_p, C.c_int]),
+        "mera_profile_dump": (C.c_int, [C.c_void_p, C.c_char_p]),
         "mera_dots_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
                                         C.c_void_p, C.c_void_p]),
         "mera_gemm": (C.c_int, [C.c_int, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
@@ -347,3 +348,7 @@ class Mera:
 
     def profile(self, enable=True):
         self._check(self.L.mera_profile(self.h, int(enable)))
+
+    def profile_dump(self, path):
+        """Per-shape table of the contractions timed while profiling (CSV)."""
+        self._check(self.L.mera_profile_dump(self.h, str(path).encode()))

@@ -38,3 +38,28 @@ def test_gemm_modes(env, shape, prec, tol):
     # error relative to the natural scale of the entries (sqrt(K) for N(0,1) data)
     err = np.abs(C - ref).max() / np.sqrt(K)
     assert err < tol, (prec, shape, err)
+
+
+# cluster shapes (CTAs along M x along N sharing operand tiles by multicast),
+# forced through MERA_TC_CLUSTER; odd tile counts leave padding CTAs that load
+# zeros and store nothing
+CLUSTER_SHAPES = [(200, 130, 70), (384, 384, 512), (4100, 257, 2049), (256, 200, 40000), (1, 300, 64)]
+
+
+@pytest.mark.parametrize("cluster", ["11", "12", "21", "22"])
+@pytest.mark.parametrize("shape", CLUSTER_SHAPES)
+@pytest.mark.parametrize("prec,tol", [(1, 4e-6), (2, 2e-4)])
+def test_gemm_cluster_shapes(env, monkeypatch, cluster, shape, prec, tol):
+    torch, gm = env
+    monkeypatch.setenv("MERA_TC_CLUSTER", cluster)
+    M, N, K = shape
+    rng = np.random.default_rng(M + 3 * N + 5 * K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    ref = A @ B
+    Cd = torch.full((M, N), float("nan"), dtype=torch.float64, device="cuda")
+    gm.gemm(prec, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), Cd)
+    C = Cd.cpu().numpy()
+    assert np.all(np.isfinite(C))
+    err = np.abs(C - ref).max() / np.sqrt(K)
+    assert err < tol, (cluster, prec, shape, err)
