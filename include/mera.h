@@ -222,7 +222,12 @@ int mera_profile(mera_t m, int enable);
  * CSV lines "M,N,K,path,calls,ms,tflops": path 0 is the FP64 contraction
  * kernel, otherwise 1000 * (1 + tensor-core kind: 0 TF32, 1 BF16) + 100 *
  * epilogue store mode + 10 * cluster CTAs along M + cluster CTAs along N;
- * tflops counts 2 M N K per call.  Synchronises the object's stream.
+ * tflops counts 2 M N K per call.  Rows with K = 0 time other phases:
+ * path 91xx / 92xx the packing of a tensor-core product's first / second
+ * operand into split planes (M, N = rows, packed length; xx = 10 if the
+ * source's stride-1 leg is a row leg, + 1 if the source is float), path
+ * 9300 one eigendecomposition of the preconditioner (M = N = order).
+ * Synchronises the object's stream.
  * MERA_ERR_ARG if the file cannot be written. */
 int mera_profile_dump(mera_t m, const char* path);
 

@@ -238,8 +238,10 @@ void Prof::collect() {
   for (size_t i = 0; i + 1 < used; i += 2) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) {
-      gett_ms += ms;
-      gett_timed++;
+      if (pending[i / 2][2] > 0) {  // contractions only (phases have K = 0)
+        gett_ms += ms;
+        gett_timed++;
+      }
       Shape& sh = shapes[pending[i / 2]];
       sh.calls++;
       sh.ms += ms;

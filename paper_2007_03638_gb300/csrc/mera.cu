@@ -134,6 +134,7 @@ struct mera_ctx {
   mera::DevBuf scratch;                   // transient contraction buffers
   mera::Exec ex;                          // contraction arithmetic
   mera::DevBuf tc_ws, tc_err;             // tensor-core operand planes, wait-expiry flag
+  mera::DevBuf tc_keep[2];                // packed planes of loop-invariant operands (sliced chain)
   mera::DevBuf gtmp[6];                   // geometry temporaries
   mera::Reducer red;
   mera::Eval ev[2];
@@ -203,7 +204,7 @@ void build_layers(Ctx& c) {
   c.layers.resize(c.L + 1);
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
   const size_t es = (mixed ? sizeof(float) : sizeof(double)) * c.rs;
-  size_t scratch_need = 0, ws_need = 0;
+  size_t scratch_need = 0, ws_need = 0, kneed[2] = {0, 0};
   for (int l = 0; l <= c.L; ++l) {
     Layer& ly = c.layers[l];
     ly.cf = c.dims[l];
@@ -230,6 +231,10 @@ void build_layers(Ctx& c) {
       scratch_need = std::max(scratch_need, need);
       for (const GemmPlan* p : net.executed_plans())
         ws_need = std::max(ws_need, tc_workspace_bytes(p->proto, c.cfg.prec));
+      size_t kn[2];
+      keep_need(net, c.cfg.prec, kn);
+      kneed[0] = std::max(kneed[0], kn[0]);
+      kneed[1] = std::max(kneed[1], kn[1]);
     }
   }
   c.scratch.alloc(es * scratch_need);
@@ -241,6 +246,12 @@ void build_layers(Ctx& c) {
     MERA_CUDA(cudaStreamSynchronize(c.s));
     c.ex.ws = c.tc_ws.p;
     c.ex.ws_bytes = ws_need;
+    for (int k = 0; k < 2; ++k)
+      if (kneed[k]) {
+        c.tc_keep[k].alloc(kneed[k]);
+        c.ex.keep[k] = c.tc_keep[k].p;
+        c.ex.keep_bytes[k] = kneed[k];
+      }
     c.ex.err = c.tc_err.as<int>();
   }
   for (int l = 0; l <= c.L; ++l)
@@ -600,6 +611,7 @@ void ensure_eig(Ctx& c, Eval& E, cudaStream_t s) {
   if (E.eig_ready) return;
   for (int i = 0; i < c.nt; ++i) {
     const int64_t p = c.cols[i], q = p * c.rs;  // order of the (embedded) problem
+    const int64_t pair = c.prof.begin(q, q, 0, s);
     double* A = P(c.gtmp[0]);
     double* src = P(E.rho_v[i]);
     if (c.cplx) {
@@ -622,6 +634,7 @@ void ensure_eig(Ctx& c, Eval& E, cudaStream_t s) {
       c.eig_uses[i] = 1;
     }
     if (q > 64) copy(P(c.eig_cache[i]), P(E.evec[i]), q * q, s);
+    c.prof.end(pair, 9300, s);
   }
   E.eig_ready = true;
 }
@@ -1434,7 +1447,7 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
     const size_t rs = cfg->dtype == MERA_C128 ? 2 : 1;
     const size_t es = (mixed ? 4 : 8) * rs;
     mera::TablePool pool(true);
-    size_t bytes = 0, scratch = 0, ws = 0, total = 0, gmax = 1;
+    size_t bytes = 0, scratch = 0, ws = 0, total = 0, gmax = 1, keep[2] = {0, 0};
     for (size_t l = 0; l < dims.size(); ++l) {
       const int64_t cf = dims[l], cc = l + 1 < dims.size() ? dims[l + 1] : dims[l];
       int64_t chunk = mera::choose_chunk(cf, cc);
@@ -1453,10 +1466,14 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
         scratch = std::max(scratch, es * need);
         for (const mera::GemmPlan* p : net.executed_plans())
           ws = std::max(ws, mera::tc_workspace_bytes(p->proto, cfg->prec));
+        size_t kn[2];
+        mera::keep_need(net, cfg->prec, kn);
+        keep[0] = std::max(keep[0], kn[0]);
+        keep[1] = std::max(keep[1], kn[1]);
       }
     }
     const size_t nS = (size_t)mera::ipow(cfg->chi, 6) * rs;
-    bytes += scratch + ws + pool.bytes();
+    bytes += scratch + ws + keep[0] + keep[1] + pool.bytes();
     bytes += 8 * nS * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);  // basis, tmp, x, bvec
     bytes += 8 * gmax * 6 * rs * rs;
     bytes += 8 * (size_t)total * (size_t)(2 * std::max(1, cfg->lbfgs_m) + 2 + 4 + 4);

@@ -606,67 +606,117 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// Split one value into its hi/lo planes.  Float sources stay in FP32
-// (x - hi is exact in FP32), double sources take the residual in FP64.
-template <int KIND>
-__device__ __forceinline__ void store_split(double v, void* hi, void* lo, int64_t i) {
+// Split 8 consecutive values of one plane row into hi/lo and write them as
+// one 16-byte (BF16) or 32-byte (TF32) piece per plane; i = row * Kp + k,
+// k a multiple of 8.
+template <int KIND, typename T>
+__device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo, int64_t i) {
   if (KIND == KIND_TF32) {
-    const float h = tf32_round((float)v);
-    static_cast<float*>(hi)[i] = h;
-    static_cast<float*>(lo)[i] = tf32_round((float)(v - (double)h));
+    float h[8], l[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      h[j] = tf32_round((float)v[j]);
+      l[j] = tf32_round((float)(v[j] - (T)h[j]));
+    }
+    float4* ph = reinterpret_cast<float4*>(static_cast<float*>(hi) + i);
+    float4* pl = reinterpret_cast<float4*>(static_cast<float*>(lo) + i);
+    ph[0] = make_float4(h[0], h[1], h[2], h[3]);
+    ph[1] = make_float4(h[4], h[5], h[6], h[7]);
+    pl[0] = make_float4(l[0], l[1], l[2], l[3]);
+    pl[1] = make_float4(l[4], l[5], l[6], l[7]);
   } else {
-    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-    static_cast<__nv_bfloat16*>(hi)[i] = h;
-    static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-  }
-}
-template <int KIND>
-__device__ __forceinline__ void store_split(float v, void* hi, void* lo, int64_t i) {
-  if (KIND == KIND_TF32) {
-    const float h = tf32_round(v);
-    static_cast<float*>(hi)[i] = h;
-    static_cast<float*>(lo)[i] = tf32_round(v - h);
-  } else {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    static_cast<__nv_bfloat16*>(hi)[i] = h;
-    static_cast<__nv_bfloat16*>(lo)[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    uint32_t h2[4], l2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat16 a = __float2bfloat16_rn((float)v[2 * j]), b = __float2bfloat16_rn((float)v[2 * j + 1]);
+      const __nv_bfloat16 la = __float2bfloat16_rn((float)(v[2 * j] - (T)__bfloat162float(a)));
+      const __nv_bfloat16 lb = __float2bfloat16_rn((float)(v[2 * j + 1] - (T)__bfloat162float(b)));
+      h2[j] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+      l2[j] = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+    }
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(hi) + i) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+    *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(lo) + i) = make_uint4(l2[0], l2[1], l2[2], l2[3]);
   }
 }
 
-// hi/lo planes [Rp x Kp] (row-major, K fastest) of src[r_off[r] + k_off[k]].
+// hi/lo planes [Rp x Kp] (row-major, K fastest) of src[r_off[r] + k_off[k]],
+// zero outside R x K.  Block 32 x 8: threadIdx.y picks one of 8 rows,
+// threadIdx.x 8 consecutive k (256 k per block row).  Reads run along k (the
+// source's stride-1 direction); an affine unit-stride k group with aligned
+// rows is read with vector loads.
 template <typename Src, int KIND>
 __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt, int64_t rs,
                                   const int64_t* __restrict__ kt, int64_t ks, int64_t R, int64_t K,
                                   int64_t Rp, int64_t Kp, void* hi, void* lo) {
-  const int64_t total = Rp * Kp;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / Kp, k = i % Kp;
-    Src v = (Src)0;
-    if (r < R && k < K) v = src[(rt ? rt[r] : r * rs) + (kt ? kt[k] : k * ks)];
-    store_split<KIND>(v, hi, lo, i);
+  const int64_t r = (int64_t)blockIdx.x * 8 + threadIdx.y;
+  const int64_t k0 = ((int64_t)blockIdx.y * 32 + threadIdx.x) * 8;
+  if (r >= Rp || k0 >= Kp) return;
+  Src v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = (Src)0;
+  if (r < R) {
+    const int64_t roff = rt ? rt[r] : r * rs;
+    constexpr int VW = 16 / sizeof(Src);  // elements per 16-byte load
+    if (!kt && ks == 1 && k0 + 8 <= K && (reinterpret_cast<uintptr_t>(src + roff + k0) & 15) == 0) {
+      const Src* p = src + roff + k0;
+#pragma unroll
+      for (int j = 0; j < 8; j += VW) {
+        if (sizeof(Src) == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(p + j);
+          v[j] = (Src)q.x; v[j + 1] = (Src)q.y; v[j + 2] = (Src)q.z; v[j + 3] = (Src)q.w;
+        } else {
+          const double2 q = *reinterpret_cast<const double2*>(p + j);
+          v[j] = (Src)q.x; v[j + 1] = (Src)q.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int64_t k = k0 + j;
+        if (k < K) v[j] = src[roff + (kt ? kt[k] : k * ks)];
+      }
+    }
   }
+  store_split8<KIND>(v, hi, lo, r * Kp + k0);
 }
 
-// Same packing through a 32x32 shared-memory tile: reads run along r (the
-// source's stride-1 direction), writes along k.
+// Same packing through a 64 x 64 shared-memory tile, for sources whose
+// stride-1 direction is r: reads run along r, writes along k (16 k per
+// thread and plane).  Block 256 threads.
 template <typename Src, int KIND>
 __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt,
                                         int64_t rs, const int64_t* __restrict__ kt, int64_t ks, int64_t R,
                                         int64_t K, int64_t Rp, int64_t Kp, void* hi, void* lo) {
-  __shared__ Src tile[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
-  const int64_t r = r0 + tx;
-  const int64_t roff = r < R ? (rt ? rt[r] : r * rs) : 0;
-  for (int j = ty; j < 32; j += 8) {
-    const int64_t k = k0 + j;
-    tile[j][tx] = (r < R && k < K) ? src[roff + (kt ? kt[k] : k * ks)] : (Src)0;
+  __shared__ Src tile[64][65];  // [k][r]
+  __shared__ int64_t roffs[64];
+  const int t = threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
+  if (t < 64) {
+    const int64_t r = r0 + t;
+    roffs[t] = r < R ? (rt ? rt[r] : r * rs) : -1;
   }
   __syncthreads();
-  for (int j = ty; j < 32; j += 8) {
-    const int64_t rr = r0 + j, kk = k0 + tx;
-    if (rr < Rp && kk < Kp) store_split<KIND>(tile[tx][j], hi, lo, rr * Kp + kk);
+  {
+    const int rl = t & 63;
+    const int64_t roff = roffs[rl];
+#pragma unroll 4
+    for (int kl = t >> 6; kl < 64; kl += 4) {
+      const int64_t k = k0 + kl;
+      tile[kl][rl] = (roff >= 0 && k < K) ? src[roff + (kt ? kt[k] : k * ks)] : (Src)0;
+    }
+  }
+  __syncthreads();
+  const int rl = t >> 2, kc = (t & 3) * 16;
+  const int64_t r = r0 + rl;
+  if (r >= Rp) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t k = k0 + kc + 8 * h;
+    if (k >= Kp) break;
+    Src v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = tile[kc + 8 * h + j][rl];
+    store_split8<KIND>(v, hi, lo, r * Kp + k);
   }
 }
 
@@ -799,37 +849,37 @@ int64_t padded_k(int64_t K, int kind) {
 void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
                 int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, bool rows_fast,
                 cudaStream_t s) {
+  if (Kp % 32 || Rp % 64) throw Error(MERA_ERR_ARG, "pack_split: Kp must be a multiple of 32, Rp of 64");
   if (rows_fast) {
-    if ((Rp + 31) / 32 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: too many rows");
-    const dim3 grid((unsigned)((Kp + 31) / 32), (unsigned)((Rp + 31) / 32)), blk(32, 8);
+    if (Rp / 64 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: too many rows");
+    const dim3 grid((unsigned)((Kp + 63) / 64), (unsigned)(Rp / 64));
     if (kind == KIND_TF32) {
       if (src_f64)
-        pack_split_tiled_kernel<double, KIND_TF32><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+        pack_split_tiled_kernel<double, KIND_TF32><<<grid, 256, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
       else
-        pack_split_tiled_kernel<float, KIND_TF32><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+        pack_split_tiled_kernel<float, KIND_TF32><<<grid, 256, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
     } else {
       if (src_f64)
-        pack_split_tiled_kernel<double, KIND_BF16><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+        pack_split_tiled_kernel<double, KIND_BF16><<<grid, 256, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
       else
-        pack_split_tiled_kernel<float, KIND_BF16><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+        pack_split_tiled_kernel<float, KIND_BF16><<<grid, 256, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
     }
     count_launch();
     MERA_CHECK_LAUNCH();
     return;
   }
-  const int64_t total = Rp * Kp;
-  const int threads = 256;
-  const unsigned blocks = (unsigned)std::min<int64_t>((total + threads - 1) / threads, 152 * 32);
+  if ((Kp + 255) / 256 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: K too long");
+  const dim3 grid((unsigned)(Rp / 8), (unsigned)((Kp + 255) / 256)), blk(32, 8);
   if (kind == KIND_TF32) {
     if (src_f64)
-      pack_split_kernel<double, KIND_TF32><<<blocks, threads, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_kernel<double, KIND_TF32><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
     else
-      pack_split_kernel<float, KIND_TF32><<<blocks, threads, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_kernel<float, KIND_TF32><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
   } else {
     if (src_f64)
-      pack_split_kernel<double, KIND_BF16><<<blocks, threads, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_kernel<double, KIND_BF16><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
     else
-      pack_split_kernel<float, KIND_BF16><<<blocks, threads, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_kernel<float, KIND_BF16><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
   }
   count_launch();
   MERA_CHECK_LAUNCH();

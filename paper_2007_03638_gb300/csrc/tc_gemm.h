@@ -45,7 +45,8 @@ int64_t padded_k(int64_t K, int kind);
 // Split src[r_off(r) + k_off(k)] (r < R, k < K; zero elsewhere) into hi/lo
 // planes of [Rp x Kp] row-major tensor-core values.
 // rows_fast: the source's stride-1 index runs along r (a tiled transpose keeps
-// both the reads and the plane writes coalesced).
+// both the reads and the plane writes coalesced).  Kp must be a multiple of
+// 32 and Rp of 64 (padded_k and round_up(., 128) give both).
 void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt,
                 int64_t ks, int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi,
                 void* lo, bool rows_fast, cudaStream_t s);

@@ -343,6 +343,22 @@ size_t tc_workspace_bytes(const GettCall& g, int prec) {
   return 5 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind);
 }
 
+size_t tc_keep_bytes(const GettCall& g, int prec, int side) {
+  if (prec == MERA_PREC_FP64 || side == 0) return 0;
+  const int kind = prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
+  const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
+  const int64_t Kp = tc::padded_k(g.K, kind);
+  const int64_t Rp = tc::round_up(side == 1 ? g.M : g.N, 128);
+  return 2048 + elem * 2 * (size_t)Rp * (size_t)Kp;
+}
+
+void keep_need(const SideNet& net, int prec, size_t need[2]) {
+  need[0] = need[1] = 0;
+  if (!net.sliced()) return;
+  need[0] = std::max(tc_keep_bytes(net.f5c().proto, prec, 1), tc_keep_bytes(net.b5rc().proto, prec, 1));
+  need[1] = std::max(tc_keep_bytes(net.f7c().proto, prec, 2), tc_keep_bytes(net.b7c().proto, prec, 2));
+}
+
 namespace {
 // The transposed product C^T = B^T A^T: the same contraction with the roles
 // of A and B (and of the M and N groups) exchanged.
@@ -372,7 +388,7 @@ GettCall transposed(const GettCall& g) {
 }
 }  // namespace
 
-void contract(const GettCall& g0, const Exec& ex, cudaStream_t s) {
+void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* keep) {
   if (g0.M <= 0 || g0.N <= 0) return;
   if (ex.prec == MERA_PREC_FP64) {
     if (g0.a32 || g0.b32 || g0.c32) throw Error(MERA_ERR_ARG, "contract: float operand in the FP64 path");
@@ -381,7 +397,10 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s) {
   }
   // tensor cores: take the orientation whose output columns run contiguously
   // (the epilogue then writes whole 32-byte pieces of each row)
-  const GettCall g = (g0.c_vec < 8 && g0.c_vec_t > g0.c_vec) ? transposed(g0) : g0;
+  const bool flip = g0.c_vec < 8 && g0.c_vec_t > g0.c_vec;
+  const GettCall g = flip ? transposed(g0) : g0;
+  int kside = keep ? keep->side : 0;  // kept operand, as a side of g
+  if (flip && kside) kside = 3 - kside;
   const int kind = ex.prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
   const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
   const int64_t Kp = tc::padded_k(g.K, kind);
@@ -396,9 +415,30 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s) {
   void* bl = w + o; o = align(o + elem * Np * Kp);
   float* part = reinterpret_cast<float*>(w + o);
   const size_t part_bytes = ex.ws_bytes > o ? ex.ws_bytes - o : 0;
+  if (kside) {
+    // the kept operand's planes live in their slot
+    const int slot = keep->slot;
+    if (slot < 0 || slot > 1 || !ex.keep[slot] || ex.keep_bytes[slot] < tc_keep_bytes(g, ex.prec, kside))
+      throw Error(MERA_ERR_ARG, "contract: keep slot missing or too small");
+    char* k = static_cast<char*>(ex.keep[slot]);
+    const int64_t Rp = kside == 1 ? Mp : Np;
+    (kside == 1 ? ah : bh) = k;
+    (kside == 1 ? al : bl) = k + align(elem * Rp * Kp);
+  }
+  const bool pack_a = !(kside == 1 && keep->valid), pack_b = !(kside == 2 && keep->valid);
   // A rows = M group, A columns = K group; B rows (of the packed K-major plane) = N group
-  tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s);
-  tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s);
+  Prof* pr = g_prof;
+  int64_t pair = -1;
+  if (pack_a) {
+    pair = pr ? pr->begin(g.M, g.K, 0, s) : -1;
+    tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s);
+    if (pr) pr->end(pair, 9100 + (g.a_rfast ? 10 : 0) + (g.a32 ? 1 : 0), s);
+  }
+  if (pack_b) {
+    pair = pr ? pr->begin(g.N, g.K, 0, s) : -1;
+    tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s);
+    if (pr) pr->end(pair, 9200 + (g.b_rfast ? 10 : 0) + (g.b32 ? 1 : 0), s);
+  }
   tc::TcEpilogue ep;
   ep.alpha = g.alpha;
   ep.beta = g.beta;
@@ -411,8 +451,7 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s) {
   ep.rows = g.c_rows;
   ep.vec = g.c_vec;
   ep.err = ex.err;
-  Prof* pr = g_prof;
-  const int64_t pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
+  pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
   const int path = tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (pr) {
     pr->end(pair, 1000 * (kind + 1) + path, s);
@@ -431,7 +470,7 @@ constexpr int EXT = -1;  // an external buffer (operator, seed, output): double,
 // externals are double, internal nodes float in mixed mode; conjugated
 // leaves are read conjugated.
 void run(const SideBufs& b, const GemmPlan& p, const double* A, int an, const double* B, int bn, double* C,
-         int cn, double alpha, double beta, cudaStream_t s) {
+         int cn, double alpha, double beta, cudaStream_t s, const Keep* keep = nullptr) {
   GettCall g = p.proto;
   g.A = A;
   g.B = B;
@@ -444,7 +483,7 @@ void run(const SideBufs& b, const GemmPlan& p, const double* A, int an, const do
   g.cplx = b.cplx;
   g.a_conj = b.cplx && an != EXT && conj_leaf(an);
   g.b_conj = b.cplx && bn != EXT && conj_leaf(bn);
-  contract(g, *b.ex, s);
+  contract(g, *b.ex, s, keep);
 }
 inline const double* value(const SideBufs& b, int node) {
   return node < SideNet::NLEAF ? b.leaf[node] : b.val[node];
@@ -467,11 +506,13 @@ void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, do
   for (int node : {12, 13, 15, 17, 18}) {
     if (net.sliced() && node == 15) {
       // N5 = N3 x N4 and N7 = N5 x N6 one slice of the coarse leg b at a time
+      // N3 and N6 are the same for every slice: their packed planes are kept
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
+        const Keep k3{1, 0, b0 > 0}, k6{2, 1, b0 > 0};
         run(b, net.f5c(), b.val[13], 13, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.val[15], 15,
-            1.0, 0.0, s);
+            1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr);
         run(b, net.f7c(), b.val[15], 15, b.val[16], 16, offp(b, b.val[17], b0 * net.b_stride_n7()), 17,
-            1.0, 0.0, s);
+            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr);
       }
       continue;
     }
@@ -497,15 +538,17 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
     if (net.sliced() && node == 15) continue;  // handled with N7 below
     if (net.sliced() && node == 17) {
       // dN5 one slice of b at a time, consumed at once by N5's children
+      // N6 and N3 are the same for every slice: their packed planes are kept
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
+        const Keep k6{2, 1, b0 > 0}, k3{1, 0, b0 > 0};
         run(b, net.b7c(), offp(b, b.adj[17], b0 * net.b_stride_n7()), 17, b.val[16], 16, b.adj[15], 15,
-            1.0, 0.0, s);
+            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr);
         if (need[13])
           run(b, net.b5lc(), b.adj[15], 15, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.adj[13], 13,
               1.0, b0 == 0 ? 0.0 : 1.0, s);
         if (need[14])
           run(b, net.b5rc(), b.val[13], 13, b.adj[15], 15, offp(b, b.adj[14], b0 * net.b_stride_n4()), 14,
-              1.0, 0.0, s);
+              1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr);
       }
       continue;
     }

@@ -104,9 +104,25 @@ struct Exec {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* err = nullptr;  // device flag set by an expired bounded wait
+  // two slots for packed operands that stay the same over a loop of products
+  // (the loop-invariant factor of the sliced chain): packed once, reused
+  void* keep[2] = {nullptr, nullptr};
+  size_t keep_bytes[2] = {0, 0};
 };
-void contract(const GettCall& g, const Exec& ex, cudaStream_t s);
+// An operand of a tensor-core product that is the same as in the previous
+// call of the same loop: side 1 = A, 2 = B; valid = the slot already holds
+// its planes (skip packing).
+struct Keep {
+  int side = 0;
+  int slot = 0;
+  bool valid = false;
+};
+void contract(const GettCall& g, const Exec& ex, cudaStream_t s, const Keep* keep = nullptr);
 size_t tc_workspace_bytes(const GettCall& g, int prec);
+// Bytes of the packed planes of one operand (side 1 = A, 2 = B) of g.
+size_t tc_keep_bytes(const GettCall& g, int prec, int side);
+// Keep-slot sizes the sliced chain of a SideNet needs (slot 0: N3, slot 1: N6).
+void keep_need(const class SideNet& net, int prec, size_t need[2]);
 
 // Buffers bound to a SideNet for one evaluation.  Leaves, root output,
 // operator adjoint and u/w adjoints are double; internal node values and
