@@ -181,6 +181,8 @@ void extract_complex(const double* e, int64_t n, double* z, cudaStream_t s);
 // Scratch of the eigensolver, kept by its owner so that no call allocates.
 struct EigWork {
   DevBuf small, cs, red;
+  DevBuf bar;           // grid-barrier words of the cooperative sweep (zeroed once)
+  int coop_blocks = 0;  // resident blocks of the sweep kernel (0: not queried)
   std::map<int, DevBuf> sched;  // round-robin schedule per matrix size
 };
 void sym_eig(double* A, double* V, double* evals, int n, EigWork& w, cudaStream_t s);

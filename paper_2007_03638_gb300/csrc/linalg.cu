@@ -1,9 +1,11 @@
 // Small dense FP64 linear algebra for the geometry: symmetric
 // eigendecomposition by cyclic Jacobi with the parallel (round-robin)
-// ordering, in one CTA.  Used for the preconditioner's density matrices
+// ordering, in one CTA up to order 64 and as one cooperative multi-CTA
+// launch per sweep above.  Used for the preconditioner's density matrices
 // (n = chi^2 for disentanglers, chi for isometries) and for the thin SVD of
 // Grassmann tangents (eigen-decomposition of X^dag X, n = chi).
 #include "common.h"
+#include <algorithm>
 #include <cmath>
 
 namespace mera {
@@ -125,13 +127,14 @@ namespace {
 // ----------------------------------------------- multi-CTA Jacobi rounds ---
 // One round applies n/2 disjoint rotations J: A <- J^T A J, V <- V J.  Every
 // 2x2 block (pair a rows, pair b columns) of the result depends only on the
-// same block of A and on the rotations of pairs a and b, so a round is one
-// fully parallel kernel after a small kernel that computes the rotations.
-__global__ void jac_rot_k(const double* __restrict__ A, int n, const int2* __restrict__ pairs, int h,
-                          double2* __restrict__ cs) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= h) return;
-  const int p = pairs[k].x, q = pairs[k].y;
+// same block of A and on the rotations of pairs a and b, so a round is a
+// fully parallel step after a small step that computes the rotations.  A
+// whole sweep (all rounds) runs in one cooperative launch with a grid
+// barrier between the steps.
+
+// Rotation (Golub-Van Loan symmetric Schur 2x2) of pair (p, q); q >= n: none.
+__device__ __forceinline__ double2 jac_rotation(const double* A, int n, int2 pq) {
+  const int p = pq.x, q = pq.y;
   double c = 1.0, sn = 0.0;
   if (q < n) {
     const double apq = A[(int64_t)p * n + q];
@@ -143,15 +146,16 @@ __global__ void jac_rot_k(const double* __restrict__ A, int n, const int2* __res
       sn = t * c;
     }
   }
-  cs[k] = make_double2(c, sn);
+  return make_double2(c, sn);
 }
 
-__global__ void jac_apply_k(double* __restrict__ A, double* __restrict__ V, int n,
-                            const int2* __restrict__ pairs, int h, const double2* __restrict__ cs) {
+// Work item i of a round's apply step: i < h*h a 2x2 block of A, else one
+// row entry pair of V.
+__device__ __forceinline__ void jac_apply_item(double* A, double* V, int n, const int2* pairs, int h,
+                                               const double2* cs, int64_t i) {
   const int64_t nblk = (int64_t)h * h;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid < nblk) {
-    const int a = (int)(tid / h), b = (int)(tid % h);
+  if (i < nblk) {
+    const int a = (int)(i / h), b = (int)(i % h);
     const int pa = pairs[a].x, qa = pairs[a].y, pb = pairs[b].x, qb = pairs[b].y;
     const double ca = cs[a].x, sa = cs[a].y, cb = cs[b].x, sb = cs[b].y;
     const bool ra = qa < n, rb = qb < n;
@@ -167,15 +171,70 @@ __global__ void jac_apply_k(double* __restrict__ A, double* __restrict__ V, int 
     if (rb) A[(int64_t)pa * n + qb] = sb * y00 + cb * y01;
     if (ra) A[(int64_t)qa * n + pb] = cb * y10 - sb * y11;
     if (ra && rb) A[(int64_t)qa * n + qb] = sb * y10 + cb * y11;
-  } else if (tid < nblk + (int64_t)n * h) {
-    const int64_t t = tid - nblk;
-    const int i = (int)(t / h), b = (int)(t % h);
+  } else if (i < nblk + (int64_t)n * h) {
+    const int64_t t = i - nblk;
+    const int r = (int)(t / h), b = (int)(t % h);
     const int pb = pairs[b].x, qb = pairs[b].y;
     if (qb >= n) return;
     const double cb = cs[b].x, sb = cs[b].y;
-    const double vp = V[(int64_t)i * n + pb], vq = V[(int64_t)i * n + qb];
-    V[(int64_t)i * n + pb] = cb * vp - sb * vq;
-    V[(int64_t)i * n + qb] = sb * vp + cb * vq;
+    const double vp = V[(int64_t)r * n + pb], vq = V[(int64_t)r * n + qb];
+    V[(int64_t)r * n + pb] = cb * vp - sb * vq;
+    V[(int64_t)r * n + qb] = sb * vp + cb * vq;
+  }
+}
+
+__device__ __forceinline__ uint64_t jac_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier of a cooperative launch (every block resident).  bar[0]
+// counts arrivals, bar[1] is the generation, bar[2] the error flag.  The wait
+// is bounded (2 s) and also ends when another block has given up; false then.
+// gen (thread 0 only) is this block's copy of the generation.
+__device__ bool jac_grid_barrier(unsigned* bar, unsigned& gen) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+    } else {
+      const uint64_t t0 = jac_timer();
+      for (uint32_t it = 1; *(volatile unsigned*)&bar[1] == gen; ++it) {
+        if (*(volatile unsigned*)&bar[2]) { ok = 0; break; }
+        if ((it & 255u) == 0 && jac_timer() - t0 > 2000000000ull) {
+          atomicExch(&bar[2], 1u);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ++gen;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// One cyclic Jacobi sweep: all m-1 rounds of the round-robin schedule.
+__global__ __launch_bounds__(1024) void jac_sweep_k(double* A, double* V, int n, const int2* sched, int h,
+                                                    int rounds, double2* cs, unsigned* bar) {
+  unsigned gen = 0;
+  if (threadIdx.x == 0) gen = *(volatile unsigned*)&bar[1];
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t work = (int64_t)h * h + (int64_t)n * h;
+  for (int r = 0; r < rounds; ++r) {
+    const int2* pairs = sched + (int64_t)r * h;
+    for (int64_t k = tid; k < h; k += nthr) cs[k] = jac_rotation(A, n, pairs[k]);
+    if (!jac_grid_barrier(bar, gen)) return;
+    for (int64_t i = tid; i < work; i += nthr) jac_apply_item(A, V, n, pairs, h, cs, i);
+    if (!jac_grid_barrier(bar, gen)) return;
   }
 }
 
@@ -261,6 +320,10 @@ void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, EigWork
   }
   if (w.cs.bytes < sizeof(double2) * h) w.cs.alloc(sizeof(double2) * h);
   if (w.red.bytes < 2 * sizeof(double)) w.red.alloc(2 * sizeof(double));
+  if (!w.bar.p) {
+    w.bar.alloc(4 * sizeof(unsigned));
+    MERA_CUDA(cudaMemsetAsync(w.bar.p, 0, 4 * sizeof(unsigned), s));
+  }
   DevBuf& dpairs = w.sched.at(n);
   DevBuf& dcs = w.cs;
   DevBuf& dred = w.red;
@@ -268,25 +331,51 @@ void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, EigWork
     eye_k<<<(unsigned)(((int64_t)n * n + 255) / 256), 256, 0, s>>>(V, n);
     count_launch();
   }
+  // one block per SM at most (the grid barrier's cost grows with the block count)
   const int64_t work = (int64_t)h * h + (int64_t)n * h;
-  const unsigned nb = (unsigned)((work + 255) / 256);
+  if (!w.coop_blocks) {
+    int dev = 0, nsm = 0, occ = 0;
+    MERA_CUDA(cudaGetDevice(&dev));
+    MERA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    MERA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jac_sweep_k, 1024, 0));
+    if (occ < 1) throw Error(MERA_ERR_UNSUPPORTED, "sym_eig: sweep kernel cannot be resident");
+    w.coop_blocks = nsm;
+  }
+  const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(w.coop_blocks, (work + 1023) / 1024));
+  double* pA = A;
+  double* pV = V;
+  int nn = n, hh = h, rounds = m - 1;
+  int2* psched = dpairs.as<int2>();
+  double2* pcs = dcs.as<double2>();
+  unsigned* pbar = w.bar.as<unsigned>();
+  void* args[] = {&pA, &pV, &nn, &psched, &hh, &rounds, &pcs, &pbar};
   double red[2] = {0, 0};
+  unsigned flag[4] = {0, 0, 0, 0};
   double scale = 0.0;
   for (int sweep = 0; sweep < 40; ++sweep) {
     MERA_CUDA(cudaMemsetAsync(dred.p, 0, 2 * sizeof(double), s));
     jac_offdiag_k<<<152, 256, 0, s>>>(A, n, dred.as<double>());
     count_launch();
     MERA_CUDA(cudaMemcpyAsync(red, dred.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MERA_CUDA(cudaMemcpyAsync(flag, w.bar.p, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     MERA_CUDA(cudaStreamSynchronize(s));
+    if (flag[2]) {
+      MERA_CUDA(cudaMemsetAsync(w.bar.p, 0, 4 * sizeof(unsigned), s));
+      MERA_CUDA(cudaStreamSynchronize(s));
+      throw Error(MERA_ERR_DEVICE_TIMEOUT, "sym_eig: a bounded grid barrier wait expired");
+    }
     if (sweep == 0) scale = std::max(red[0], red[1]);
     if (red[0] <= 1e-15 * (scale > 0 ? scale : 1.0)) break;
-    for (int r = 0; r < m - 1; ++r) {
-      const int2* pr = dpairs.as<int2>() + (int64_t)r * h;
-      jac_rot_k<<<(unsigned)((h + 127) / 128), 128, 0, s>>>(A, n, pr, h, dcs.as<double2>());
-      jac_apply_k<<<nb, 256, 0, s>>>(A, V, n, pr, h, dcs.as<double2>());
-      count_launch(2);
-    }
+    MERA_CUDA(cudaLaunchCooperativeKernel((const void*)jac_sweep_k, dim3(nb), dim3(1024), args, 0, s));
+    count_launch();
     MERA_CHECK_LAUNCH();
+  }
+  MERA_CUDA(cudaMemcpyAsync(flag, w.bar.p, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+  if (flag[2]) {
+    MERA_CUDA(cudaMemsetAsync(w.bar.p, 0, 4 * sizeof(unsigned), s));
+    MERA_CUDA(cudaStreamSynchronize(s));
+    throw Error(MERA_ERR_DEVICE_TIMEOUT, "sym_eig: a bounded grid barrier wait expired");
   }
   diag_k<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A, n, evals);
   count_launch();
