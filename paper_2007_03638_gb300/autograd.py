@@ -7,10 +7,14 @@ conjugated-leaf adjoints are the u/w environments; the forward
 intermediates are recomputed there (warm-started from the forward's fixed
 point) instead of being kept by autograd.
 
-Gradient convention: for real tensors the library's partial derivative
-D_v = 2 dC/d conj(v) (Sec. 2.3) equals the ordinary gradient dC/dv, which is
-what torch expects, so backward returns grad_output * D_v (unprojected; the
-Riemannian gradient is its tangent projection, ``Mera.project``).
+Gradient convention: the library's partial derivative is
+D_v = 2 dC/d conj(v) (Sec. 2.3).  For real tensors that is the ordinary
+gradient dC/dv.  For complex tensors torch's gradient of a real function is
+also 2 dC/d conj(v) (it returns 2 z for |z|^2), so in both cases backward
+returns grad_output * D_v, unscaled and unprojected (the Riemannian
+gradient is its tangent projection, ``Mera.project``).  Complex tensors need
+a problem created with dtype MERA_C128; their first-order change is
+dC = Re sum conj(grad) dW.
 """
 from __future__ import annotations
 
@@ -22,7 +26,8 @@ from . import mera as gm
 class MeraEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, problem: "gm.Mera", *tensors):
-        pts = [t.detach().to(torch.float64).contiguous() for t in tensors]
+        pts = [t.detach().to(torch.complex128 if t.is_complex() else torch.float64).contiguous()
+               for t in tensors]
         problem.set_tensors(pts)
         e = problem.energy_only()
         ctx.problem = problem
