@@ -53,7 +53,7 @@ DEFAULT_WORKLOAD = "xxz_chi32_L3_bf16"
 # them inside L-BFGS steps (measured by this script's own GPU runs); used only
 # to express the reference arm's bounded sample in gradient evaluations.
 FLOPS_PER_GRAD = {
-    "xxz_chi32_L3_bf16": 3.3e15, "xxz_chi32_L3_3xtf32": 3.3e15,
+    "xxz_chi32_L3_bf16": 4.1e15, "xxz_chi32_L3_3xtf32": 4.1e15,
     "xxz_chi24_L3_3xtf32": 4.7e14, "xxz_chi24_L3_bf16": 4.7e14,
     "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13,
     "ising_chi12_L3_fp64": 1.6e12, "ising_chi12_L3_3xtf32": 1.13e12, "ising_chi12_L3_bf16": 1.13e12,
