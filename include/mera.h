@@ -179,6 +179,19 @@ int mera_lbfgs_step(mera_t m, mera_iter_info* info);
 /* One nonlinear conjugate-gradient iteration (Hager-Zhang beta, Sec. 3). */
 int mera_cg_step(mera_t m, mera_iter_info* info);
 
+/* One Evenbly-Vidal sweep, the comparator of the paper's optimisers (Sec. 4
+ * and App. ev_steplimit): for every tensor in the order u_0, w_0, ..., u_S,
+ * w_S, the environment D of the cost with the shifted 3-site term
+ * h3 - gamma 1 is computed at the current point (one full evaluation) and the
+ * tensor is replaced by -Q, Q the isometric polar factor of D = Q P (the sign
+ * leaves the state and its energy unchanged; -Q keeps the tensor's sign near a
+ * fixed point).  gamma should make h3 - gamma 1 negative definite (its largest
+ * eigenvalue plus a margin); it acts as an inverse step size.  Clears the
+ * L-BFGS/CG history.  info: energy (unshifted) and |G| at the new point from
+ * one more evaluation, n_evals = number of tensors + 1, alpha = 0.
+ * MERA_ERR_ARG for a non-finite gamma. */
+int mera_ev_sweep(mera_t m, double gamma, mera_iter_info* info);
+
 typedef struct {
     int method;       /* 0 = L-BFGS, 1 = CG                  */
     int maxiter;

@@ -72,8 +72,10 @@ __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, doubl
     }
   } else if (kind == 3) {
     r = 1.0 / sqrt(l * l + d * d);
-  } else {
+  } else if (kind == 4) {
     r = sqrt(l * l + d * d);
+  } else {
+    r = 1.0 / sqrt(fmax(l, d));  // inverse square root of a positive semidefinite matrix (floor d)
   }
   out[i] = r;
 }
@@ -117,6 +119,7 @@ struct mera_ctx {
   mera_config cfg{};
   cudaStream_t s = nullptr;
   bool cplx = false;                      // interleaved complex128 data
+  double hshift = 0.0;                    // evaluations use h3 - hshift 1 (Evenbly-Vidal sweeps)
   int rs = 1;                             // reals per element (1 or 2)
   int L = 0, nt = 0;
   std::vector<int64_t> dims;
@@ -447,6 +450,7 @@ double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
   const int L = c.L;
   // up-sweep
   copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6) * c.rs, s);
+  if (c.hshift != 0.0) add_id(c, -c.hshift, P(c.h[0]), ipow(c.dims[0], 3), s);
   for (int l = 0; l <= L; ++l) prepare_layer(c, l, W, s);
   for (int l = 0; l < L; ++l) {
     const int64_t n3 = ipow(c.dims[l + 1], 3);
@@ -941,6 +945,71 @@ LsResult hager_zhang(Ctx& c, double f0, double df0, double a0, cudaStream_t s) {
   return res;
 }
 
+// ------------------------------------------------------- Evenbly-Vidal ----
+// W <- -Q with D = Q P the polar decomposition, Q = D (D^dag D)^(-1/2): the
+// update of one tensor from its environment D (App. ev_steplimit), then two
+// Newton-Schulz steps so that W is isometric to rounding.
+void ev_replace(Ctx& c, int i, const double* D, double* W, cudaStream_t s) {
+  const int64_t n = c.rows[i], p = c.cols[i], q = p * c.rs;
+  double* Z = P(c.gtmp[0]);   // D^dag D, then (complex) its real embedding
+  double* V = P(c.gtmp[1]);   // eigenvectors (q x q)
+  double* R = P(c.gtmp[2]);   // (D^dag D)^(-1/2), p x p
+  double* F = P(c.gtmp[4]);   // q x q scratch
+  double* f = P(c.gtmp[5]);   // eigenvalues, then their inverse square roots
+  mm(c, 'C', 'N', p, p, n, 1.0, D, p, D, p, 0.0, Z, p, s);
+  herm(c, Z, p, s);
+  if (c.cplx) {
+    embed_complex(Z, p, F, s);
+    copy(Z, F, q * q, s);
+  }
+  sym_eig(Z, V, f, (int)q, c.eigw, s);
+  spectral_k<<<blocks(q), 256, 0, s>>>(f, (int)q, 5, 0.0, 1e-300, f);
+  vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, f, (int)q, c.cplx ? F : R);
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  if (c.cplx) extract_complex(F, p, R, s);
+  mm(c, 'N', 'N', n, p, p, -1.0, D, p, R, p, 0.0, W, p, s);
+  polar_ns(c, W, n, p, s);
+}
+
+void ensure_current(Ctx& c, cudaStream_t s);
+void clear_history(Ctx& c);
+
+// One sweep over u_0, w_0, ..., u_S, w_S: environment of the cost with the
+// shifted term h3 - gamma 1 at the current point, then the tensor's update.
+// Ends with one unshifted evaluation at the new point.
+void ev_sweep(Ctx& c, double gamma, mera_iter_info* info, cudaStream_t s) {
+  Eval& E = c.ev[c.cur];
+  const int64_t mv0 = c.matvecs;
+  int evals = 0;
+  c.hshift = gamma;
+  try {
+    for (int i = 0; i < c.nt; ++i) {
+      energy_grad(c, P(c.Wcur), E, s);
+      ++evals;
+      ev_replace(c, i, P(E.D) + c.offs[i], P(c.Wcur) + c.offs[i], s);
+    }
+  } catch (...) {
+    c.hshift = 0.0;
+    c.ev[0].valid = c.ev[1].valid = false;
+    c.geom.valid = false;
+    throw;
+  }
+  c.hshift = 0.0;
+  c.ev[0].valid = c.ev[1].valid = false;
+  c.geom.valid = false;
+  clear_history(c);
+  energy_grad(c, P(c.Wcur), E, s);
+  ++evals;
+  info->iter = ++c.iters;
+  info->energy = E.e;
+  info->gnorm = std::sqrt(inner(c, P(E.G), P(E.G), s));
+  info->alpha = 0.0;
+  info->n_evals = evals;
+  info->ls_ok = 1;
+  info->krylov_matvecs = (int)(c.matvecs - mv0);
+}
+
 void ensure_current(Ctx& c, cudaStream_t s) {
   if (!c.ev[c.cur].valid) energy_grad(c, P(c.Wcur), c.ev[c.cur], s);
 }
@@ -1413,6 +1482,14 @@ int mera_lbfgs_step(mera_t m, mera_iter_info* info) {
 int mera_cg_step(mera_t m, mera_iter_info* info) {
   if (!m || !info) return MERA_ERR_ARG;
   return wrap(m, [&] { mera::cg_step(*m, info, m->s); });
+}
+
+int mera_ev_sweep(mera_t m, double gamma, mera_iter_info* info) {
+  if (!m || !info || !std::isfinite(gamma)) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    std::memset(info, 0, sizeof(*info));
+    mera::ev_sweep(*m, gamma, info, m->s);
+  });
 }
 
 int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
