@@ -16,6 +16,8 @@ import json
 import math
 import time
 
+import numpy as np
+
 from . import inputs as inp
 from . import mera as gm
 
@@ -31,7 +33,10 @@ def exact_energy(model, par):
 
 
 def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, gtol=1e-6, seed=0,
-        lbfgs_m=8, krylov_dim=20, out=print):
+        lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None):
+    """method: 0 L-BFGS, 1 CG, 2 Evenbly-Vidal sweeps (one record per sweep;
+    ev_gamma = the Hamiltonian shift, default the largest eigenvalue of the
+    3-site term plus 0.5)."""
     bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
     h3 = inp.three_site_blocked(bond)
     cfg = gm.default_config(4, chi, n_trans, prec=prec, lbfgs_m=lbfgs_m, krylov_dim=krylov_dim)
@@ -39,11 +44,13 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
     us, ws = inp.random_mera(4, chi, n_trans, seed=seed)
     m.set_tensors([t for p in zip(us, ws) for t in p])
     ex = exact_energy(model, par)
+    if method == 2 and ev_gamma is None:
+        ev_gamma = float(np.linalg.eigvalsh(h3).max()) + 0.5
     t0 = time.perf_counter()
     rec = None
     evals = 0
     for it in range(iters):
-        info = m.cg_step() if method == 1 else m.lbfgs_step()
+        info = m.cg_step() if method == 1 else m.ev_sweep(ev_gamma) if method == 2 else m.lbfgs_step()
         evals += info["n_evals"]
         e_spin = info["energy"] / 2
         rec = {"iter": it + 1, "energy_per_spin": e_spin,
@@ -54,7 +61,7 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
         if info["gnorm"] < gtol:
             break
     summary = {"summary": True, "model": model, "param": par, "chi": chi, "n_trans": n_trans,
-               "prec": ["fp64", "3xtf32", "split_bf16"][prec], "method": ["lbfgs", "cg"][method],
+               "prec": ["fp64", "3xtf32", "split_bf16"][prec], "method": ["lbfgs", "cg", "ev"][method],
                "iters": rec["iter"], "energy_per_spin": rec["energy_per_spin"], "exact": ex,
                "error": rec["error"], "gnorm": rec["gnorm"], "evals": evals, "time_s": rec["time_s"]}
     out(json.dumps(summary))
@@ -70,7 +77,9 @@ def main():
     ap.add_argument("--chi", type=int, default=4)
     ap.add_argument("--n-trans", type=int, default=2)
     ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16")
-    ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg"])
+    ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev"])
+    ap.add_argument("--ev-gamma", type=float, default=None,
+                    help="Evenbly-Vidal Hamiltonian shift (default: largest eigenvalue of the 3-site term + 0.5)")
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--gtol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
@@ -78,8 +87,9 @@ def main():
     ap.add_argument("--krylov-dim", type=int, default=20)
     a = ap.parse_args()
     par = a.field if a.model == "ising" else a.delta
-    run(a.model, par, a.chi, a.n_trans, a.prec, 1 if a.method == "cg" else 0, a.iters, a.gtol, a.seed,
-        a.m, a.krylov_dim)
+    method = {"lbfgs": 0, "cg": 1, "ev": 2}[a.method]
+    run(a.model, par, a.chi, a.n_trans, a.prec, method, a.iters, a.gtol, a.seed, a.m, a.krylov_dim,
+        ev_gamma=a.ev_gamma)
 
 
 if __name__ == "__main__":
