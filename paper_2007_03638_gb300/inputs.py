@@ -132,3 +132,41 @@ def exact_ising_energy_per_spin(h: float = 1.0, n: int = 200000) -> float:
 
 EXACT_ISING_CRITICAL = -4.0 / np.pi
 EXACT_XXZ_DELTA1 = 1.0 - 4.0 * np.log(2.0)
+
+
+def ternary_layer_dims(d: int, chi: int, n_trans: int) -> list[int]:
+    """Ternary MERA bond dimensions chi_0 = d, chi_{l+1} = min(chi, chi_l**3);
+    the last entry (index n_trans) is the scale-invariant layer's, forced to chi."""
+    dims = [d]
+    for _ in range(n_trans):
+        dims.append(min(chi, dims[-1] ** 3))
+    if dims[-1] != chi:
+        raise ValueError(f"transition layers cannot reach chi={chi} from d={d}")
+    return dims
+
+
+def random_ternary_mera(d: int, chi: int, n_trans: int, seed: int, dtype=np.float64):
+    """Seeded ternary starting point: per layer a unitary u (c^2 x c^2) and an
+    isometry w (c^3 x c'), QR of Gaussians with columns sign-fixed by diag(R)."""
+    rng = np.random.default_rng(seed)
+    dims = ternary_layer_dims(d, chi, n_trans)
+    us, ws = [], []
+    for l in range(n_trans + 1):
+        c = dims[l]
+        cp = dims[l + 1] if l < n_trans else dims[n_trans]
+        us.append(_haar_like(rng, c * c, c * c, dtype))
+        ws.append(_haar_like(rng, c**3, cp, dtype))
+    return us, ws
+
+
+def product_state_ternary_mera(d: int, chi: int, n_trans: int):
+    """u = 1 and w|k> = the k-th basis vector of the fine triple (so
+    w|0> = |000>): the scale-invariant product state |00...0>."""
+    dims = ternary_layer_dims(d, chi, n_trans)
+    us, ws = [], []
+    for l in range(n_trans + 1):
+        c = dims[l]
+        cp = dims[l + 1] if l < n_trans else dims[n_trans]
+        us.append(np.eye(c * c))
+        ws.append(np.eye(c**3, cp))
+    return us, ws

@@ -86,3 +86,46 @@ def dense_descend(rho, u, w, side):
     perm = keep + rest + [6 + k for k in keep] + [6 + k for k in rest]
     big = np.transpose(big, perm).reshape(c**3, c**3, c**3, c**3)
     return np.einsum("aibi->ab", big)
+
+
+# ------------------------------------------------------------- ternary ----
+# |fine> = U W |coarse> with w mapping coarse site k to the fine triple
+# (3k, 3k+1, 3k+2) and u acting on the fine pairs (3k+2, 3k+3), periodic.
+
+def apply_ternary_isometry_layer(psi, w):
+    """Each site k of psi (dim c') becomes the triple (3k, 3k+1, 3k+2) via w (c**3, c')."""
+    n = psi.ndim
+    c = int(round(w.shape[0] ** (1.0 / 3.0)))
+    w4 = w.reshape(c, c, c, w.shape[1])
+    for k in reversed(range(n)):
+        psi = np.tensordot(psi, w4, axes=([k], [3]))  # three new legs appended at the end
+        psi = np.moveaxis(psi, [psi.ndim - 3, psi.ndim - 2, psi.ndim - 1], [k, k + 1, k + 2])
+    return psi
+
+
+def apply_ternary_disentangler_layer(psi, u):
+    """u on every pair (3k+2, 3k+3), periodic."""
+    n = psi.ndim
+    for k in range(n // 3):
+        psi = apply_two_site(psi, u, (3 * k + 2) % n, (3 * k + 3) % n)
+    return psi
+
+
+def finite_ternary_state(top, layers):
+    """top: state tensor on the top sites; layers: [(u, w), ...] from the top down."""
+    psi = top
+    for u, w in layers:
+        psi = apply_ternary_isometry_layer(psi, w)
+        psi = apply_ternary_disentangler_layer(psi, u)
+    return psi
+
+
+def averaged_rdm2(psi):
+    """Average over positions of the 2-site reduced density matrix (periodic)."""
+    n = psi.ndim
+    d = psi.shape[0]
+    acc = np.zeros((d**2, d**2), dtype=np.result_type(psi, 1.0))
+    for i in range(n):
+        p = np.moveaxis(psi, [i % n, (i + 1) % n], [0, 1]).reshape(d**2, -1)
+        acc += p @ p.conj().T
+    return acc / n / np.vdot(psi, psi).real
