@@ -102,11 +102,23 @@ typedef struct {
                           contraction chain (must divide the coarse bond
                           dimension; 0 = automatic: no slicing while the
                           7-leg intermediate has at most 2^30 entries)        */
+    int network;       /* mera_network: MERA_BINARY (default) or MERA_TERNARY */
 } mera_config;
 
-/* Fill *cfg with defaults for (d_b, chi, n_trans): F64, FP64 contractions,
- * Grassmann isometries, preconditioner on, Krylov dim 20, 2000 products,
- * tol 1e-14, no recomputation, m = 8. */
+/* Network of the MERA (Sec. 4).  MERA_BINARY: the binary MERA described
+ * above, three-site operators.  MERA_TERNARY: the ternary MERA of the
+ * paper's benchmark: w_l is (chi_l^3) x (chi_{l+1}) (w[x_a x_b x_c, k], the
+ * coarse site to a fine triple), u_l is (chi_l^2) x (chi_l^2) on the pairs
+ * that straddle two triples, chi_{l+1} = min(chi, chi_l^3), and operators
+ * (h3 of mera_create, the level operators) are two-site: (d_b^2) x (d_b^2)
+ * terms whose translates sum to H, energy per site.  The ternary network
+ * runs every entry point except the preconditioner (create it with
+ * precond = 0; MERA_ERR_UNSUPPORTED otherwise). */
+typedef enum { MERA_BINARY = 0, MERA_TERNARY = 1 } mera_network;
+
+/* Fill *cfg with defaults for (d_b, chi, n_trans): binary network, F64,
+ * FP64 contractions, Grassmann isometries, preconditioner on, Krylov dim 20,
+ * 2000 products, tol 1e-14, no recomputation, m = 8. */
 void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
 
 /* Create a problem.  h3 is the 3-site Hamiltonian term on bottom sites,

@@ -18,6 +18,7 @@
 #include "common.h"
 #include "tn.h"
 #include "tc_gemm.h"
+#include "tnet.h"
 
 #include <algorithm>
 #include <cmath>
@@ -90,6 +91,10 @@ struct Layer {
   std::unique_ptr<SideNet> net[2];
   SideBufs buf[2];
   std::vector<DevBuf> own[2];
+  // ternary network: sides L, C, R
+  std::unique_ptr<Net> tnet[3];
+  NetBufs tbuf[3];
+  std::vector<DevBuf> town[3];
 };
 
 // Per-evaluation results at one point.
@@ -120,6 +125,8 @@ struct mera_ctx {
   cudaStream_t s = nullptr;
   bool cplx = false;                      // interleaved complex128 data
   double hshift = 0.0;                    // evaluations use h3 - hshift 1 (Evenbly-Vidal sweeps)
+  bool tern = false;                      // ternary network
+  int ns = 3;                             // sites of a level operator (3 binary, 2 ternary)
   int rs = 1;                             // reals per element (1 or 2)
   int L = 0, nt = 0;
   std::vector<int64_t> dims;
@@ -170,6 +177,8 @@ int64_t ipow(int64_t b, int e) {
   while (e-- > 0) r *= b;
   return r;
 }
+// order of a level operator (matrix of ns sites of dimension c)
+int64_t opn(const Ctx& c, int64_t dim) { return ipow(dim, c.ns); }
 
 // element-type helpers: x = (x + x^dag)/2, x += a 1, matrix products whose
 // 'C' operands are conjugate-transposed (plain transposes for real data)
@@ -203,8 +212,64 @@ int64_t choose_chunk(int64_t cf, int64_t cc) {
   return nb;
 }
 
+// Ternary network: three networks per layer, every internal node value and
+// adjoint in its own buffer (no intermediate above chi^6).
+void build_layers_ternary(Ctx& c) {
+  const bool mixed = c.cfg.prec != MERA_PREC_FP64;
+  const size_t es = (mixed ? sizeof(float) : sizeof(double)) * c.rs;
+  size_t ws_need = 0;
+  for (int l = 0; l <= c.L; ++l) {
+    Layer& ly = c.layers[l];
+    ly.cf = c.dims[l];
+    ly.cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    for (int sd = 0; sd < 3; ++sd) {
+      ly.tnet[sd] = std::make_unique<Net>(ternary_netdef("LCR"[sd]), ly.cf, ly.cc, c.pool);
+      Net& net = *ly.tnet[sd];
+      NetBufs& b = ly.tbuf[sd];
+      b.leaf.assign(net.nleaf(), nullptr);
+      b.val.assign(net.nnode(), nullptr);
+      b.adj.assign(net.nnode(), nullptr);
+      for (int node = net.nleaf(); node < net.nnode(); ++node) {
+        if (node != net.root()) {
+          ly.town[sd].emplace_back(es * net.size(node));
+          b.val[node] = P(ly.town[sd].back());
+        }
+        ly.town[sd].emplace_back(es * net.size(node));
+        b.adj[node] = P(ly.town[sd].back());
+      }
+      b.f32 = mixed;
+      b.cplx = c.cplx;
+      b.ex = &c.ex;
+      for (const GemmPlan* p : net.plans()) ws_need = std::max(ws_need, tc_workspace_bytes(p->proto, c.cfg.prec));
+    }
+  }
+  c.ex.prec = c.cfg.prec;
+  if (mixed) {
+    c.tc_ws.alloc(ws_need);
+    c.tc_err.alloc(sizeof(int));
+    MERA_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), c.s));
+    MERA_CUDA(cudaStreamSynchronize(c.s));
+    c.ex.ws = c.tc_ws.p;
+    c.ex.ws_bytes = ws_need;
+    c.ex.err = c.tc_err.as<int>();
+  }
+}
+
+void bind_ternary(Layer& ly, int sd, const double* op, const double* u, const double* w) {
+  NetBufs& b = ly.tbuf[sd];
+  const Net& net = *ly.tnet[sd];
+  for (int i = 0; i < net.nleaf(); ++i) {
+    const int r = net.role(i);
+    b.leaf[i] = r == ROLE_OP ? op : (r == ROLE_U || r == ROLE_UB) ? u : w;
+  }
+}
+
 void build_layers(Ctx& c) {
   c.layers.resize(c.L + 1);
+  if (c.tern) {
+    build_layers_ternary(c);
+    return;
+  }
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
   const size_t es = (mixed ? sizeof(float) : sizeof(double)) * c.rs;
   size_t scratch_need = 0, ws_need = 0, kneed[2] = {0, 0};
@@ -290,6 +355,13 @@ void ascend(Ctx& c, int l, const double* W, const double* op, double* out, doubl
   Layer& ly = c.layers[l];
   const double* u = W + c.offs[2 * l];
   const double* w = W + c.offs[2 * l + 1];
+  if (c.tern) {  // Abar = (A_L + A_C + A_R) / 3
+    for (int sd = 0; sd < 3; ++sd) {
+      bind_ternary(ly, sd, op, u, w);
+      net_forward(*ly.tnet[sd], ly.tbuf[sd], out, af / 3.0, 1.0, s);
+    }
+    return;
+  }
   for (int sd = 0; sd < 2; ++sd) {
     bind_leaves(ly, sd, op, u, w);
     side_forward(*ly.net[sd], ly.buf[sd], out, 0.5 * af, 1.0, s);
@@ -300,6 +372,13 @@ void prepare_layer(Ctx& c, int l, const double* W, cudaStream_t s) {
   Layer& ly = c.layers[l];
   const double* u = W + c.offs[2 * l];
   const double* w = W + c.offs[2 * l + 1];
+  if (c.tern) {
+    for (int sd = 0; sd < 3; ++sd) {
+      bind_ternary(ly, sd, nullptr, u, w);
+      net_prepare(*ly.tnet[sd], ly.tbuf[sd], s);
+    }
+    return;
+  }
   for (int sd = 0; sd < 2; ++sd) {
     bind_leaves(ly, sd, nullptr, u, w);
     side_prepare(*ly.net[sd], ly.buf[sd], s);
@@ -309,6 +388,11 @@ void prepare_layer(Ctx& c, int l, const double* W, cudaStream_t s) {
 // out += af * Dbar(r) (both sides); operator-path reverse pass only.
 void descend(Ctx& c, int l, const double* r, double* out, double af, cudaStream_t s) {
   Layer& ly = c.layers[l];
+  if (c.tern) {  // Dbar = (D_L + D_C + D_R) / 3; needs only the prepared values
+    for (int sd = 0; sd < 3; ++sd)
+      net_backward(*ly.tnet[sd], ly.tbuf[sd], r, true, out, af / 3.0, false, nullptr, nullptr, 0.0, s);
+    return;
+  }
   for (int sd = 0; sd < 2; ++sd) {
     ly.buf[sd].adj[SideNet::ROOT] = const_cast<double*>(r);
     side_backward(*ly.net[sd], ly.buf[sd], true, out, 0.5 * af, false, nullptr, nullptr, 0.0, s);
@@ -419,7 +503,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   const int L = c.L;
   c.prof.energy_grad_calls++;
   E.e = forward_energy(c, W, s);
-  const int64_t cS = c.dims[L], n3 = ipow(cS, 3), n = n3 * n3;
+  const int64_t cS = c.dims[L], n3 = opn(c, cS), n = n3 * n3;
   const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
   const double tol = std::max(c.cfg.krylov_tol, floor_tol);
   double* rhoS = P(c.rho[L]);
@@ -449,17 +533,17 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
 double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
   const int L = c.L;
   // up-sweep
-  copy(P(c.h[0]), P(c.h0), ipow(c.dims[0], 6) * c.rs, s);
-  if (c.hshift != 0.0) add_id(c, -c.hshift, P(c.h[0]), ipow(c.dims[0], 3), s);
+  copy(P(c.h[0]), P(c.h0), opn(c, c.dims[0]) * opn(c, c.dims[0]) * c.rs, s);
+  if (c.hshift != 0.0) add_id(c, -c.hshift, P(c.h[0]), opn(c, c.dims[0]), s);
   for (int l = 0; l <= L; ++l) prepare_layer(c, l, W, s);
   for (int l = 0; l < L; ++l) {
-    const int64_t n3 = ipow(c.dims[l + 1], 3);
+    const int64_t n3 = opn(c, c.dims[l + 1]);
     fill(0.0, P(c.h[l + 1]), n3 * n3 * c.rs, s);
     ascend(c, l, W, P(c.h[l]), P(c.h[l + 1]), 1.0, s);
     herm(c, P(c.h[l + 1]), n3, s);
   }
   // scale-invariant layer
-  const int64_t cS = c.dims[L], n3 = ipow(cS, 3), n = n3 * n3, nr = n * c.rs;
+  const int64_t cS = c.dims[L], n3 = opn(c, cS), n = n3 * n3, nr = n * c.rs;
   double* rhoS = P(c.rho[L]);
   if (!c.have_rho) {
     fill(0.0, rhoS, nr, s);
@@ -515,8 +599,15 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
     const double* op = l < L ? P(c.h[l]) : xs;
     const double* r = l < L ? P(c.rho[l + 1]) : rhoS;
     const bool need_op = l < L;
-    if (need_op) fill(0.0, P(c.rho[l]), ipow(ly.cf, 6) * c.rs, s);
-    for (int sd = 0; sd < 2; ++sd) {
+    if (need_op) fill(0.0, P(c.rho[l]), opn(c, ly.cf) * opn(c, ly.cf) * c.rs, s);
+    for (int sd = 0; c.tern && sd < 3; ++sd) {
+      // D_v = 2 dC/d conj(v) with C = Tr(Abar(h) rho), Abar the average of three maps
+      bind_ternary(ly, sd, op, u, w);
+      if (l == L || c.cfg.recompute_env) net_forward(*ly.tnet[sd], ly.tbuf[sd], nullptr, 0.0, 0.0, s);
+      net_backward(*ly.tnet[sd], ly.tbuf[sd], r, need_op, need_op ? P(c.rho[l]) : nullptr, 1.0 / 3.0, true,
+                   D + c.offs[2 * l], D + c.offs[2 * l + 1], 2.0 / 3.0, s);
+    }
+    for (int sd = 0; !c.tern && sd < 2; ++sd) {
       SideBufs& b = ly.buf[sd];
       bind_leaves(ly, sd, op, u, w);
       // the reverse pass needs N3, N7, N8 for this layer's operator: the
@@ -527,7 +618,7 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
       side_backward(*ly.net[sd], b, need_op, need_op ? P(c.rho[l]) : nullptr, 0.5, true,
                     D + c.offs[2 * l], D + c.offs[2 * l + 1], 1.0, s);
     }
-    if (need_op) herm(c, P(c.rho[l]), ipow(ly.cf, 3), s);
+    if (need_op) herm(c, P(c.rho[l]), opn(c, ly.cf), s);
   }
   // projection
   for (int i = 0; i < c.nt; ++i)
@@ -541,7 +632,7 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   }
   check_device_flag(c, s);
   if (!finite) throw Error(MERA_ERR_NONFINITE, "non-finite energy or gradient");
-  compute_rho_v(c, E, W, s);
+  if (!c.tern) compute_rho_v(c, E, W, s);  // the ternary preconditioner is not built
   E.eig_ready = false;
   E.valid = true;
 }
@@ -1205,30 +1296,40 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     throw Error(MERA_ERR_UNSUPPORTED, "complex tensors run in the FP64 path only");
   if (cfg.prec != MERA_PREC_FP64 && cfg.prec != MERA_PREC_3XTF32 && cfg.prec != MERA_PREC_SPLIT_BF16)
     throw Error(MERA_ERR_ARG, "unknown precision mode");
+  if (cfg.network != MERA_BINARY && cfg.network != MERA_TERNARY) throw Error(MERA_ERR_ARG, "unknown network");
+  c.tern = cfg.network == MERA_TERNARY;
+  c.ns = c.tern ? 2 : 3;
+  if (c.tern && cfg.precond)
+    throw Error(MERA_ERR_UNSUPPORTED, "the ternary network's preconditioner is not built: set precond = 0");
   c.pool.set_stream(s);
   c.L = cfg.n_trans;
   c.dims.push_back(cfg.d_b);
-  for (int l = 0; l < c.L; ++l) c.dims.push_back(std::min<int64_t>(cfg.chi, c.dims.back() * c.dims.back()));
+  // a coarse site holds two (binary) or three (ternary) fine sites
+  for (int l = 0; l < c.L; ++l) {
+    const int64_t d = c.dims.back();
+    c.dims.push_back(std::min<int64_t>(cfg.chi, c.tern ? d * d * d : d * d));
+  }
   if (c.dims.back() != cfg.chi) throw Error(MERA_ERR_ARG, "transition layers do not reach chi");
   c.nt = 2 * (c.L + 1);
   int64_t off = 0;
   for (int l = 0; l <= c.L; ++l) {
     const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    const int64_t wr = c.tern ? cf * cf * cf : cf * cf;  // rows of w: the fine pair or triple
     c.rows.push_back(cf * cf); c.cols.push_back(cf * cf); c.offs.push_back(off); off += cf * cf * cf * cf * c.rs;
-    c.rows.push_back(cf * cf); c.cols.push_back(cc);      c.offs.push_back(off); off += cf * cf * cc * c.rs;
+    c.rows.push_back(wr);      c.cols.push_back(cc);      c.offs.push_back(off); off += wr * cc * c.rs;
   }
   c.total = off;
   build_layers(c);
   const size_t tb = sizeof(double) * c.total;
   c.Wcur.alloc(tb);
   c.Wtry.alloc(tb);
-  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 6) * c.rs);
+  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 2 * c.ns) * c.rs);
   MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
   for (int l = 0; l <= c.L; ++l) {
-    c.h.emplace_back(sizeof(double) * ipow(c.dims[l], 6) * c.rs);
-    c.rho.emplace_back(sizeof(double) * ipow(c.dims[l], 6) * c.rs);
+    c.h.emplace_back(sizeof(double) * ipow(c.dims[l], 2 * c.ns) * c.rs);
+    c.rho.emplace_back(sizeof(double) * ipow(c.dims[l], 2 * c.ns) * c.rs);
   }
-  const int64_t nS = ipow(cfg.chi, 6) * c.rs;  // reals of one chi^6 operator
+  const int64_t nS = ipow(cfg.chi, 2 * c.ns) * c.rs;  // reals of one level operator (chi^6 binary)
   c.x.alloc(sizeof(double) * nS);
   c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));
   c.ktmp.alloc(sizeof(double) * nS);
@@ -1241,6 +1342,7 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
     gmax = std::max({gmax, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
                      cf * cc * cc * cf, cf * cc * cf * cf * cf});
+    if (c.tern) gmax = std::max(gmax, cf * cf * cf * cc);  // ternary w
   }
   gmax *= c.cplx ? 4 : 1;  // complex data and 2p x 2p real embeddings
   for (auto& b : c.gtmp) b.alloc(sizeof(double) * gmax);
@@ -1348,6 +1450,7 @@ void mera_config_default(mera_config* c, int d_b, int chi, int n_trans) {
   c->recompute_env = 0;
   c->lbfgs_m = 8;
   c->b_chunk = 0;
+  c->network = MERA_BINARY;
 }
 
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out) {
@@ -1513,8 +1616,53 @@ int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
   });
 }
 
+namespace {
+// mera_footprint_bytes for the ternary network
+size_t footprint_ternary(const mera_config* cfg) {
+  std::vector<int64_t> dims{cfg->d_b};
+  for (int l = 0; l < cfg->n_trans; ++l) {
+    const int64_t d = dims.back();
+    dims.push_back(std::min<int64_t>(cfg->chi, d * d * d));
+  }
+  if (dims.back() != cfg->chi) return 0;
+  const bool mixed = cfg->prec != MERA_PREC_FP64;
+  const size_t rs = cfg->dtype == MERA_C128 ? 2 : 1;
+  const size_t es = (mixed ? 4 : 8) * rs;
+  mera::TablePool pool(true);
+  size_t bytes = 0, ws = 0, total = 0, gmax = 1;
+  for (size_t l = 0; l < dims.size(); ++l) {
+    const int64_t cf = dims[l], cc = l + 1 < dims.size() ? dims[l + 1] : dims[l];
+    total += (cf * cf * cf * cf + cf * cf * cf * cc) * rs;
+    bytes += 2 * 8 * rs * (size_t)mera::ipow(cf, 4);  // h_l, rho_l
+    gmax = std::max<size_t>({gmax, (size_t)(cf * cf * cf * cf), (size_t)(cc * cc * cc * cc),
+                             (size_t)(cf * cf * cc * cc * cc), (size_t)(cf * cc * cc * cf),
+                             (size_t)(cf * cc * cf * cf * cf), (size_t)(cf * cf * cf * cc)});
+    for (char sd : {'L', 'C', 'R'}) {
+      mera::Net net(mera::ternary_netdef(sd), cf, cc, pool);
+      for (int node = net.nleaf(); node < net.nnode(); ++node)
+        bytes += es * (size_t)net.size(node) * (node == net.root() ? 1 : 2);
+      for (const mera::GemmPlan* p : net.plans()) ws = std::max(ws, mera::tc_workspace_bytes(p->proto, cfg->prec));
+    }
+  }
+  const size_t nS = (size_t)mera::ipow(cfg->chi, 4) * rs;
+  bytes += ws + pool.bytes();
+  bytes += 8 * nS * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);  // basis, tmp, x, bvec
+  bytes += 8 * gmax * 6 * rs * rs;
+  bytes += 8 * (size_t)total * (size_t)(2 * std::max(1, cfg->lbfgs_m) + 2 + 4 + 4);
+  return bytes;
+}
+}  // namespace
+
 size_t mera_footprint_bytes(const mera_config* cfg) {
   if (!cfg || cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
+  if (cfg->network == MERA_TERNARY) {
+    try {
+      return footprint_ternary(cfg);
+    } catch (...) {
+      return 0;
+    }
+  }
+  if (cfg->network != MERA_BINARY) return 0;
   try {
     // mirror of the allocations made by mera_create, with plans built dry
     std::vector<int64_t> dims{cfg->d_b};

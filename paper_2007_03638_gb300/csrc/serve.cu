@@ -180,14 +180,19 @@ int mera_server_submit(mera_server_t sv, const mera_config* cfg, const void* h3,
   r->bytes = mera_footprint_bytes(cfg);
   if (r->bytes == 0) return MERA_ERR_ARG;
   if (r->bytes > sv->budget) return MERA_ERR_OOM;
-  const int64_t n3 = (int64_t)cfg->d_b * cfg->d_b * cfg->d_b;
+  const bool tern = cfg->network == MERA_TERNARY;
+  // operator order: three (binary) or two (ternary) sites
+  const int64_t n3 = tern ? (int64_t)cfg->d_b * cfg->d_b : (int64_t)cfg->d_b * cfg->d_b * cfg->d_b;
   const size_t es = sizeof(double) * (cfg->dtype == MERA_C128 ? 2 : 1);
   r->h3.assign(static_cast<const char*>(h3), static_cast<const char*>(h3) + es * n3 * n3);
   std::vector<int64_t> dims{cfg->d_b};
-  for (int l = 0; l < cfg->n_trans; ++l) dims.push_back(std::min<int64_t>(cfg->chi, dims.back() * dims.back()));
+  for (int l = 0; l < cfg->n_trans; ++l) {
+    const int64_t d = dims.back();
+    dims.push_back(std::min<int64_t>(cfg->chi, tern ? d * d * d : d * d));
+  }
   for (int l = 0; l <= cfg->n_trans; ++l) {
     const int64_t cf = dims[l], cc = l < cfg->n_trans ? dims[l + 1] : dims[l];
-    const int64_t sz[2] = {cf * cf * cf * cf, cf * cf * cc};
+    const int64_t sz[2] = {cf * cf * cf * cf, (tern ? cf * cf * cf : cf * cf) * cc};
     for (int k = 0; k < 2; ++k) {
       const char* p = static_cast<const char*>(tensors[2 * l + k]);
       if (!p) return MERA_ERR_ARG;

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmera.so")
 
 MERA_F64, MERA_C128 = 0, 1
+MERA_BINARY, MERA_TERNARY = 0, 1
 PREC_FP64, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
 
 ERRORS = {
@@ -36,7 +37,7 @@ class Config(C.Structure):
     _fields_ = [("d_b", C.c_int), ("chi", C.c_int), ("n_trans", C.c_int), ("dtype", C.c_int),
                 ("prec", C.c_int), ("w_stiefel", C.c_int), ("precond", C.c_int),
                 ("krylov_dim", C.c_int), ("krylov_maxiter", C.c_int), ("krylov_tol", C.c_double),
-                ("recompute_env", C.c_int), ("lbfgs_m", C.c_int), ("b_chunk", C.c_int)]
+                ("recompute_env", C.c_int), ("lbfgs_m", C.c_int), ("b_chunk", C.c_int), ("network", C.c_int)]
 
 
 class IterInfo(C.Structure):
