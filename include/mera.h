@@ -111,9 +111,10 @@ typedef struct {
  * coarse site to a fine triple), u_l is (chi_l^2) x (chi_l^2) on the pairs
  * that straddle two triples, chi_{l+1} = min(chi, chi_l^3), and operators
  * (h3 of mera_create, the level operators) are two-site: (d_b^2) x (d_b^2)
- * terms whose translates sum to H, energy per site.  The ternary network
- * runs every entry point except the preconditioner (create it with
- * precond = 0; MERA_ERR_UNSUPPORTED otherwise). */
+ * terms whose translates sum to H, energy per site.  For the ternary
+ * network the preconditioner's rho_w is the one-site marginal of the level
+ * density matrix and rho_u the state on the two isometry outputs a u acts
+ * on; every entry point serves both networks. */
 typedef enum { MERA_BINARY = 0, MERA_TERNARY = 1 } mera_network;
 
 /* Fill *cfg with defaults for (d_b, chi, n_trans): binary network, F64,

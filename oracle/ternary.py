@@ -27,7 +27,8 @@ the conjugated (plain) isometries.
 Pins (tests/test_oracle_ternary.py): dense periodic ternary MERA states of 6
 and 18 sites; the product-state closed form; unitality, trace preservation
 and adjointness; dense superoperator fixed point and series at chi = 2;
-central finite differences of the energy in every tensor.
+central finite differences of the energy in every tensor; the tensors'
+density matrices against reduced density matrices of a dense state.
 """
 from __future__ import annotations
 
@@ -182,3 +183,28 @@ def energy(h0, us, ws, tol=1e-14):
         h = ascend(h, us[l], ws[l])
     rho_s = si_fixed_point(us[L], ws[L], tol=tol)
     return float(np.real(np.trace(h @ rho_s)))
+
+
+def tensor_density_matrices(rhos, ws):
+    """Reduced density matrices on the top legs of every tensor (Sec. 4) for
+    the ternary network: rho_w of layer l is the one-site marginal of the
+    two-site rho_{l+1} (average of its left and right sites, equal for a
+    translation-averaged state); rho_u is the two-site state on the isometry
+    outputs that u acts on, the third leg of w_j and the first of w_{j+1}:
+    W rho_{l+1} W^dag with the other four isometry legs traced.  ``rhos[l]``
+    is the two-site density matrix at level l (rhos[L] = rho_S)."""
+    L = len(ws) - 1
+    out = []
+    for l in range(L + 1):
+        r = rhos[l + 1] if l < L else rhos[L]
+        w = ws[l]
+        cp = w.shape[1]
+        c = int(round(w.shape[0] ** (1.0 / 3.0)))
+        r4 = r.reshape(cp, cp, cp, cp)
+        rw = 0.5 * (_contract([(r4, "a b A b")], "a A") + _contract([(r4, "b a b A")], "a A"))
+        w4 = w.reshape(c, c, c, cp)
+        ru = _contract([(w4, "p0 p1 x2 a"), (w4, "x3 p4 p5 b"), (r4, "a b A B"),
+                        (w4.conj(), "p0 p1 X2 A"), (w4.conj(), "X3 p4 p5 B")],
+                       "x2 x3 X2 X3").reshape(c * c, c * c)
+        out += [ru, rw]
+    return out

@@ -81,6 +81,29 @@ __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, doubl
   out[i] = r;
 }
 
+// rho_w of the ternary network: the one-site marginal (Tr_right + Tr_left) / 2
+// of a two-site operator r (c states per site, row-major (c^2 x c^2)).
+__global__ void marg_tern_k(const double* __restrict__ r, int64_t c, double* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c * c) return;
+  const int64_t a = idx / c, A = idx % c, n = c * c;
+  double s = 0.0;
+  for (int64_t b = 0; b < c; ++b) s += r[(a * c + b) * n + A * c + b] + r[(b * c + a) * n + b * c + A];
+  out[idx] = 0.5 * s;
+}
+__global__ void marg_tern_c_k(const double2* __restrict__ r, int64_t c, double2* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c * c) return;
+  const int64_t a = idx / c, A = idx % c, n = c * c;
+  double sx = 0.0, sy = 0.0;
+  for (int64_t b = 0; b < c; ++b) {
+    const double2 u = r[(a * c + b) * n + A * c + b], v = r[(b * c + a) * n + b * c + A];
+    sx += u.x + v.x;
+    sy += u.y + v.y;
+  }
+  out[idx] = make_double2(0.5 * sx, 0.5 * sy);
+}
+
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -632,14 +655,77 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   }
   check_device_flag(c, s);
   if (!finite) throw Error(MERA_ERR_NONFINITE, "non-finite energy or gradient");
-  if (!c.tern) compute_rho_v(c, E, W, s);  // the ternary preconditioner is not built
+  compute_rho_v(c, E, W, s);
   E.eig_ready = false;
   E.valid = true;
 }
 
 // rho_w: one-site marginal of the density matrix above the layer; rho_u:
 // W rho2 W^T on the pair of isometry outputs that u acts on (Sec. 4).
+// Ternary network: rho_w the one-site marginal of rho_{l+1}; rho_u the state
+// on the isometry outputs a u acts on (third leg of w_j, first of w_{j+1}):
+//   T1[p0 p1 x2 b A B]    = w[p0 p1 x2 a] rho[a b A B]
+//   T2[x2 b B X2]         = T1 x conj w[p0 p1 X2 A]
+//   T3[x2 B X2 x3 p4 p5]  = T2 x w[x3 p4 p5 b]
+//   rho_u[x2 x3 X2 X3]    = T3 x conj w[X3 p4 p5 B]
+void compute_rho_v_ternary(Ctx& c, Eval& E, const double* W, cudaStream_t s) {
+  auto D = [](std::vector<int> legs, std::vector<int64_t> ext) {
+    TDesc d;
+    d.legs = legs;
+    d.ext = ext;
+    d.stride.assign(legs.size(), 1);
+    for (size_t j = legs.size(); j-- > 1;) d.stride[j - 1] = d.stride[j] * ext[j];
+    return d;
+  };
+  for (int l = 0; l <= c.L; ++l) {
+    const int64_t cf = c.layers[l].cf, cc = c.layers[l].cc;
+    const double* r = l < c.L ? P(c.rho[l + 1]) : P(c.rho[c.L]);
+    const double* w = W + c.offs[2 * l + 1];
+    double* rw = P(E.rho_v[2 * l + 1]);
+    double* ru = P(E.rho_v[2 * l]);
+    if (c.cplx)
+      marg_tern_c_k<<<blocks(cc * cc), 256, 0, s>>>(reinterpret_cast<const double2*>(r), cc,
+                                                     reinterpret_cast<double2*>(rw));
+    else
+      marg_tern_k<<<blocks(cc * cc), 256, 0, s>>>(r, cc, rw);
+    count_launch();
+    MERA_CHECK_LAUNCH();
+    enum { p0, p1, x2, x3, X2, X3, p4, p5, a, b, A, B };
+    const TDesc wa = D({p0, p1, x2, a}, {cf, cf, cf, cc}), R = D({a, b, A, B}, {cc, cc, cc, cc});
+    const TDesc T1 = D({p0, p1, x2, b, A, B}, {cf, cf, cf, cc, cc, cc});
+    const TDesc wA = D({p0, p1, X2, A}, {cf, cf, cf, cc});
+    const TDesc T2 = D({x2, b, B, X2}, {cf, cc, cc, cf});
+    const TDesc wb = D({x3, p4, p5, b}, {cf, cf, cf, cc});
+    const TDesc T3 = D({x2, B, X2, x3, p4, p5}, {cf, cc, cf, cf, cf, cf});
+    const TDesc wB = D({X3, p4, p5, B}, {cf, cf, cf, cc});
+    const TDesc RU = D({x2, x3, X2, X3}, {cf, cf, cf, cf});
+    double* t1 = P(c.gtmp[2]);
+    double* t2 = P(c.gtmp[3]);
+    double* t3 = P(c.gtmp[4]);
+    auto run = [&](const TDesc& A_, const TDesc& B_, const TDesc& C_, const double* pa, const double* pb, double* pc,
+                   bool conj_b) {
+      GettCall g = make_plan(A_, B_, C_, c.pool).proto;
+      g.A = pa;
+      g.B = pb;
+      g.C = pc;
+      g.cplx = c.cplx;
+      g.b_conj = c.cplx && conj_b;
+      gett_f64(g, s);
+    };
+    run(wa, R, T1, w, r, t1, false);
+    run(T1, wA, T2, t1, w, t2, true);
+    run(T2, wb, T3, t2, w, t3, false);
+    run(T3, wB, RU, t3, w, ru, true);
+    herm(c, ru, cf * cf, s);
+    herm(c, rw, cc, s);
+  }
+}
+
 void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s) {
+  if (c.tern) {
+    compute_rho_v_ternary(c, E, W, s);
+    return;
+  }
   for (int l = 0; l <= c.L; ++l) {
     const int64_t cf = c.layers[l].cf, cc = c.layers[l].cc;
     const double* r = l < c.L ? P(c.rho[l + 1]) : P(c.rho[c.L]);
@@ -1299,8 +1385,6 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   if (cfg.network != MERA_BINARY && cfg.network != MERA_TERNARY) throw Error(MERA_ERR_ARG, "unknown network");
   c.tern = cfg.network == MERA_TERNARY;
   c.ns = c.tern ? 2 : 3;
-  if (c.tern && cfg.precond)
-    throw Error(MERA_ERR_UNSUPPORTED, "the ternary network's preconditioner is not built: set precond = 0");
   c.pool.set_stream(s);
   c.L = cfg.n_trans;
   c.dims.push_back(cfg.d_b);
@@ -1342,7 +1426,8 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
     gmax = std::max({gmax, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
                      cf * cc * cc * cf, cf * cc * cf * cf * cf});
-    if (c.tern) gmax = std::max(gmax, cf * cf * cf * cc);  // ternary w
+    // ternary: w, and the rho_u builder's T1 (cf^3 cc^3) and T3 (cf^5 cc)
+    if (c.tern) gmax = std::max({gmax, cf * cf * cf * cc, cf * cf * cf * cc * cc * cc, cf * cf * cf * cf * cf * cc});
   }
   gmax *= c.cplx ? 4 : 1;  // complex data and 2p x 2p real embeddings
   for (auto& b : c.gtmp) b.alloc(sizeof(double) * gmax);
@@ -1636,7 +1721,8 @@ size_t footprint_ternary(const mera_config* cfg) {
     bytes += 2 * 8 * rs * (size_t)mera::ipow(cf, 4);  // h_l, rho_l
     gmax = std::max<size_t>({gmax, (size_t)(cf * cf * cf * cf), (size_t)(cc * cc * cc * cc),
                              (size_t)(cf * cf * cc * cc * cc), (size_t)(cf * cc * cc * cf),
-                             (size_t)(cf * cc * cf * cf * cf), (size_t)(cf * cf * cf * cc)});
+                             (size_t)(cf * cc * cf * cf * cf), (size_t)(cf * cf * cf * cc),
+                             (size_t)(cf * cf * cf * cc * cc * cc), (size_t)(cf * cf * cf * cf * cf * cc)});
     for (char sd : {'L', 'C', 'R'}) {
       mera::Net net(mera::ternary_netdef(sd), cf, cc, pool);
       for (int node = net.nleaf(); node < net.nnode(); ++node)

@@ -1,8 +1,8 @@
 """Ternary MERA (mera_config.network = MERA_TERNARY) on the GPU against the
 ternary oracle (oracle/ternary.py), through the C ABI: energy per site and
 every partial derivative D_v = 2 dC/d conj(v) at 1e-12 (FP64, real and
-complex), within the mixed-precision bound for 3xTF32; L-BFGS and
-Evenbly-Vidal sweeps descend; the preconditioner is refused."""
+complex), within the mixed-precision bound for 3xTF32; the preconditioner
+with the ternary density matrices; L-BFGS and Evenbly-Vidal sweeps descend."""
 import numpy as np
 import pytest
 
@@ -34,7 +34,6 @@ def _rel(a, b):
 
 
 def _cfg(gm, chi, L, **kw):
-    kw.setdefault("precond", 0)
     return gm.default_config(2, chi, L, network=gm.MERA_TERNARY, **kw)
 
 
@@ -97,7 +96,33 @@ def test_ternary_lbfgs_and_ev_descend(gm):
         assert np.abs(t.T @ t - np.eye(t.shape[1])).max() < 1e-12
 
 
-def test_ternary_preconditioner_refused(gm):
-    with pytest.raises(gm.MeraError) as ex:
-        gm.Mera(_cfg(gm, 4, 1, precond=1), inp.ising_bond(1.0))
-    assert ex.value.code == -8  # MERA_ERR_UNSUPPORTED
+@pytest.mark.parametrize("dt", [np.float64, np.complex128])
+def test_ternary_preconditioner_parity(gm, dt):
+    """Eq. preconditioner with the ternary density matrices (rho_w the
+    one-site marginal, rho_u the state on a u's isometry outputs) against the
+    oracle's, delta_v = |G_v|."""
+    if dt == np.complex128:
+        X, Y = inp.PAULI_X, inp.PAULI_Y
+        h = inp.xxz_bond(0.5).astype(np.complex128) + 0.7 * (np.kron(X, Y) - np.kron(Y, X))
+        m = gm.Mera(_cfg(gm, 4, 1, dtype=gm.MERA_C128), h)
+    else:
+        h = inp.ising_bond(1.0)
+        m = gm.Mera(_cfg(gm, 4, 1), h)
+    us, ws = inp.random_ternary_mera(2, 4, 1, seed=7, dtype=dt)
+    pt = _flat(us, ws)
+    m.set_tensors(pt)
+    m.energy_grad()
+    e_ref, ds, info = ot.energy_grad(h, us, ws)
+    rv = ot.tensor_density_matrices(info["rho"], ws)
+    kinds = [geo.STIEFEL if i % 2 == 0 else geo.GRASSMANN for i in range(len(pt))]
+    Gr = [geo.project(W, d, k) for W, d, k in zip(pt, ds, kinds)]
+    deltas = [float(np.linalg.norm(g)) for g in Gr]
+    rng = np.random.default_rng(3)
+    Xs = []
+    for W, k in zip(pt, kinds):
+        Z = rng.standard_normal(W.shape) + (1j * rng.standard_normal(W.shape) if dt == np.complex128 else 0)
+        Xs.append(geo.project(W, Z, k))
+    Xt = m.precondition(Xs)
+    for W, x, r, dl, k, xt in zip(pt, Xs, rv, deltas, kinds, Xt):
+        ref = geo.precondition(W, x, r, dl, k)
+        assert np.abs(xt - ref).max() < 1e-11 * max(1, np.abs(ref).max())

@@ -136,3 +136,28 @@ def test_gradient_finite_differences(which):
     fd = (C(eps) - C(-eps)) / (2 * eps)
     an = sum(float(np.sum(d * x)) for d, x in zip(ds, X))
     assert abs(fd - an) < 1e-7 * max(1.0, abs(an)), (which, fd, an)
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.complex128])
+def test_tensor_density_matrices_vs_dense(dt):
+    """rho_u is the two-site density matrix of the isometry outputs that a u
+    acts on: on a dense 6-site state before the disentanglers, the average
+    over the two pairs (2, 3) and (5, 0) of their reduced density matrix;
+    rho_w is the one-site marginal.  Both have unit trace."""
+    rng = np.random.default_rng(12)
+    w = inp._haar_like(rng, 8, 3, dt)
+    top = rng.standard_normal((3, 3)) + (1j * rng.standard_normal((3, 3)) if dt == np.complex128 else 0)
+    top /= np.linalg.norm(top)
+    rho_top = _top_rdm(top)
+    ru, rw = ot.tensor_density_matrices([rho_top], [w])
+    psi = bf.apply_ternary_isometry_layer(top, w)   # W level: 6 sites, no u yet
+    def rdm(i, j):
+        p = np.moveaxis(psi, [i, j], [0, 1]).reshape(4, -1)
+        return p @ p.conj().T
+    dense = 0.5 * (rdm(2, 3) + rdm(5, 0))
+    assert np.abs(ru - dense).max() < 1e-13
+    t = top.reshape(9, 1) @ top.reshape(9, 1).conj().T
+    t4 = t.reshape(3, 3, 3, 3)
+    one = 0.5 * (np.einsum("abAb->aA", t4) + np.einsum("babA->aA", t4))
+    assert np.abs(rw - one).max() < 1e-14
+    assert abs(np.trace(ru) - 1) < 1e-13 and abs(np.trace(rw) - 1) < 1e-13
