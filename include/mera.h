@@ -1,6 +1,6 @@
 /*
  * mera.h -- C ABI of libmera: energy/gradient and Riemannian optimisation of
- * a scale-invariant binary MERA on one GB300 (sm_103a).
+ * a scale-invariant binary (default) or ternary MERA on one GB300 (sm_103a).
  *
  * Method: Hauru, Van Damme, Haegeman, "Riemannian optimization of isometric
  * tensor networks" (arXiv:2007.03638).  Section numbers and equation labels
@@ -25,6 +25,9 @@
  *         outputs it acts on; left leg most significant);
  *   w_l : (chi_l^2) x (chi_{l+1}) isometry, row-major, w[x_a x_b, k],
  *         w^dag w = 1 (w_L is chi^2 x chi).
+ * (The ternary network, mera_config.network = MERA_TERNARY, has
+ * chi_{l+1} = min(chi, chi_l^3) and w_l of (chi_l^3) x (chi_{l+1}); see
+ * mera_network.)
  * Tangent vectors, partial derivatives and gradients use the same shapes.
  * mera_tensor_shape() reports them.  Element type: double (MERA_F64) or
  * interleaved complex double (MERA_C128: real part first, the layout of C99
@@ -125,7 +128,8 @@ void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
 /* Create a problem.  h3 is the 3-site Hamiltonian term on bottom sites,
  * a (d_b^3) x (d_b^3) row-major matrix h[f0 f1 f2, g0 g1 g2] of the config's
  * element type whose translates sum to H (the cost is the energy per bottom
- * site, C = Tr(h rho), Sec. 4).  stream: a cudaStream_t (NULL = default
+ * site, C = Tr(h rho), Sec. 4); for the ternary network a two-site term,
+ * (d_b^2) x (d_b^2).  stream: a cudaStream_t (NULL = default
  * stream).  The tensors start as the identity-disentangler / first-columns
  * isometry point until mera_set_tensors is called. */
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
@@ -194,7 +198,7 @@ int mera_cg_step(mera_t m, mera_iter_info* info);
 
 /* One Evenbly-Vidal sweep, the comparator of the paper's optimisers (Sec. 4
  * and App. ev_steplimit): for every tensor in the order u_0, w_0, ..., u_S,
- * w_S, the environment D of the cost with the shifted 3-site term
+ * w_S, the environment D of the cost with the shifted term
  * h3 - gamma 1 is computed at the current point (one full evaluation) and the
  * tensor is replaced by -Q, Q the isometric polar factor of D = Q P (the sign
  * leaves the state and its energy unchanged; -Q keeps the tensor's sign near a
