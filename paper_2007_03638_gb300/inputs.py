@@ -170,3 +170,10 @@ def product_state_ternary_mera(d: int, chi: int, n_trans: int):
         us.append(np.eye(c * c))
         ws.append(np.eye(c**3, cp))
     return us, ws
+
+
+def random_mps(D: int, d: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Seeded left-canonical uniform-MPS tensor A (D, d, D): thin QR of a
+    Gaussian (D d) x D matrix, columns sign-fixed by diag(R)."""
+    rng = np.random.default_rng(seed)
+    return _haar_like(rng, D * d, D, dtype).reshape(D, d, D)
