@@ -288,3 +288,17 @@ def cg(problem, point, maxiter=100, gtol=1e-6, eta=0.01, callback=None, maxeval=
         d = lin(-1.0, Pg2, beta, d2)
         point, e, G, aux, Pg, alpha_prev = p2, e2, G2, aux2, Pg2, alpha
     return point, e, hist
+
+
+class TernaryProblem(MeraProblem):
+    """The ternary-MERA energy (oracle/ternary.py) on the same product manifold:
+    u's Stiefel (unitary), w's Grassmann, the ternary density matrices in the
+    preconditioner."""
+
+    def fg(self, point):
+        from . import ternary as ot
+        us, ws = point[0::2], point[1::2]
+        e, ds, info = ot.energy_grad(self.h0, us, ws, tol=self.tol)
+        G = [geo.project(W, D, k) for W, D, k in zip(point, ds, self.kinds(point))]
+        rv = ot.tensor_density_matrices(info["rho"], ws)
+        return e, G, {"rho_v": rv, "delta": [float(np.linalg.norm(g)) for g in G]}
