@@ -177,3 +177,45 @@ def random_mps(D: int, d: int, seed: int, dtype=np.float64) -> np.ndarray:
     Gaussian (D d) x D matrix, columns sign-fixed by diag(R)."""
     rng = np.random.default_rng(seed)
     return _haar_like(rng, D * d, D, dtype).reshape(D, d, D)
+
+
+def z2_parities(dim: int) -> np.ndarray:
+    """Z2 charges of the basis of a leg of dimension dim: the first ceil(dim/2)
+    states even (0), the rest odd (1).  For a spin-1/2 leg (dim 2) this is the
+    eigenbasis of Z: |0> even, |1> odd, the parity of the Ising chain."""
+    return np.array([0] * ((dim + 1) // 2) + [1] * (dim // 2), dtype=np.int64)
+
+
+def fused_parities(*dims: int) -> np.ndarray:
+    """Charges of the product basis of several legs (last leg fastest)."""
+    p = np.zeros(1, dtype=np.int64)
+    for d in dims:
+        p = (p[:, None] + z2_parities(d)[None, :]).ravel() % 2
+    return p
+
+
+def _z2_block_isometry(rng, row_par, col_par, dtype):
+    """Isometry (rows x cols) mapping each column charge into the rows of the
+    same charge only (block diagonal in the charge basis)."""
+    W = np.zeros((row_par.size, col_par.size), dtype=dtype)
+    for q in (0, 1):
+        r, c = np.flatnonzero(row_par == q), np.flatnonzero(col_par == q)
+        if c.size:
+            W[np.ix_(r, c)] = _haar_like(rng, r.size, c.size, dtype)
+    return W
+
+
+def random_z2_ternary_mera(chi: int, n_trans: int, seed: int, dtype=np.float64):
+    """Seeded Z2-symmetric ternary MERA on spins (d = 2): every u and w maps
+    each charge sector into the same sector (parities of fine legs fused, coarse
+    legs charged by z2_parities)."""
+    rng = np.random.default_rng(seed)
+    dims = ternary_layer_dims(2, chi, n_trans)
+    us, ws = [], []
+    for l in range(n_trans + 1):
+        c = dims[l]
+        cp = dims[l + 1] if l < n_trans else dims[n_trans]
+        pair = fused_parities(c, c)
+        us.append(_z2_block_isometry(rng, pair, pair, dtype))
+        ws.append(_z2_block_isometry(rng, fused_parities(c, c, c), z2_parities(cp), dtype))
+    return us, ws
