@@ -2,6 +2,7 @@
 
     python -m paper_2007_03638_gb300.solve --model ising --chi 4 --n-trans 2 --iters 300
     python -m paper_2007_03638_gb300.solve --model xxz --delta 1 --chi 8 --prec 1 --method cg
+    python -m paper_2007_03638_gb300.solve --network ternary --z2 --chi 8 --n-trans 2 --method ev
 
 Each iteration prints one JSON record: energy per spin, its distance to the
 exact value (critical Ising -4/pi or Ising at field h by quadrature, XXZ at
@@ -32,17 +33,31 @@ def exact_energy(model, par):
     return None
 
 
+def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
+    """(h, d_b, tensors, spins per bottom site) of a run: the binary network on
+    blocked sites (two spins, three-site term), the ternary one on spins
+    (two-site term); z2: Z2-symmetric ternary starting point."""
+    bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
+    if network == "ternary":
+        us, ws = (inp.random_z2_ternary_mera(chi, n_trans, seed=seed) if z2
+                  else inp.random_ternary_mera(2, chi, n_trans, seed=seed))
+        return bond, 2, [t for p in zip(us, ws) for t in p], 1
+    if z2:
+        raise ValueError("Z2-symmetric starting points are built for the ternary network")
+    us, ws = inp.random_mera(4, chi, n_trans, seed=seed)
+    return inp.three_site_blocked(bond), 4, [t for p in zip(us, ws) for t in p], 2
+
+
 def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, gtol=1e-6, seed=0,
-        lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None):
+        lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None, network="binary", z2=False):
     """method: 0 L-BFGS, 1 CG, 2 Evenbly-Vidal sweeps (one record per sweep;
     ev_gamma = the Hamiltonian shift, default the largest eigenvalue of the
-    3-site term plus 0.5)."""
-    bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
-    h3 = inp.three_site_blocked(bond)
-    cfg = gm.default_config(4, chi, n_trans, prec=prec, lbfgs_m=lbfgs_m, krylov_dim=krylov_dim)
+    Hamiltonian term plus 0.5).  network: "binary" or "ternary"."""
+    h3, d_b, tensors, spins = problem(model, par, chi, n_trans, network, z2, seed)
+    cfg = gm.default_config(d_b, chi, n_trans, prec=prec, lbfgs_m=lbfgs_m, krylov_dim=krylov_dim,
+                            network=gm.MERA_TERNARY if network == "ternary" else gm.MERA_BINARY)
     m = gm.Mera(cfg, h3)
-    us, ws = inp.random_mera(4, chi, n_trans, seed=seed)
-    m.set_tensors([t for p in zip(us, ws) for t in p])
+    m.set_tensors(tensors)
     ex = exact_energy(model, par)
     if method == 2 and ev_gamma is None:
         ev_gamma = float(np.linalg.eigvalsh(h3).max()) + 0.5
@@ -52,7 +67,7 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
     for it in range(iters):
         info = m.cg_step() if method == 1 else m.ev_sweep(ev_gamma) if method == 2 else m.lbfgs_step()
         evals += info["n_evals"]
-        e_spin = info["energy"] / 2
+        e_spin = info["energy"] / spins
         rec = {"iter": it + 1, "energy_per_spin": e_spin,
                "error": (e_spin - ex) if ex is not None else None, "gnorm": info["gnorm"],
                "alpha": info["alpha"], "n_evals": info["n_evals"], "krylov_matvecs": info["krylov_matvecs"],
@@ -60,7 +75,8 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
         out(json.dumps(rec))
         if info["gnorm"] < gtol:
             break
-    summary = {"summary": True, "model": model, "param": par, "chi": chi, "n_trans": n_trans,
+    summary = {"summary": True, "model": model, "param": par, "network": network, "z2": z2, "chi": chi,
+               "n_trans": n_trans,
                "prec": ["fp64", "3xtf32", "split_bf16"][prec], "method": ["lbfgs", "cg", "ev"][method],
                "iters": rec["iter"], "energy_per_spin": rec["energy_per_spin"], "exact": ex,
                "error": rec["error"], "gnorm": rec["gnorm"], "evals": evals, "time_s": rec["time_s"]}
@@ -78,6 +94,8 @@ def main():
     ap.add_argument("--n-trans", type=int, default=2)
     ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16")
     ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev"])
+    ap.add_argument("--network", default="binary", choices=["binary", "ternary"])
+    ap.add_argument("--z2", action="store_true", help="Z2-symmetric starting point (ternary network)")
     ap.add_argument("--ev-gamma", type=float, default=None,
                     help="Evenbly-Vidal Hamiltonian shift (default: largest eigenvalue of the 3-site term + 0.5)")
     ap.add_argument("--iters", type=int, default=300)
@@ -89,7 +107,7 @@ def main():
     par = a.field if a.model == "ising" else a.delta
     method = {"lbfgs": 0, "cg": 1, "ev": 2}[a.method]
     run(a.model, par, a.chi, a.n_trans, a.prec, method, a.iters, a.gtol, a.seed, a.m, a.krylov_dim,
-        ev_gamma=a.ev_gamma)
+        ev_gamma=a.ev_gamma, network=a.network, z2=a.z2)
 
 
 if __name__ == "__main__":

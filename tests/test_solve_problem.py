@@ -1,0 +1,29 @@
+"""Host-side set-up of the optimisation driver (no GPU): the binary network on
+blocked sites with a three-site term, the ternary network on spins with a
+two-site term, Z2-symmetric ternary starting points."""
+import numpy as np
+import pytest
+
+from oracle import z2
+from paper_2007_03638_gb300 import inputs as inp
+from paper_2007_03638_gb300 import solve
+
+
+def test_binary_problem():
+    h, d_b, tensors, spins = solve.problem("ising", 1.0, 8, 3)
+    assert (h.shape, d_b, spins, len(tensors)) == ((64, 64), 4, 2, 8)
+
+
+def test_ternary_z2_problem_is_the_figure_2_setting():
+    h, d_b, tensors, spins = solve.problem("ising", 1.0, 8, 2, network="ternary", z2=True)
+    assert (h.shape, d_b, spins, len(tensors)) == ((4, 4), 2, 1, 6)
+    assert [t.shape for t in tensors] == [(4, 4), (8, 8), (64, 64), (512, 8), (64, 64), (512, 8)]
+    p = inp.fused_parities(2, 2)
+    assert z2.violation(h, p, p) == 0.0
+    w0 = tensors[1]
+    assert z2.violation(w0, inp.fused_parities(2, 2, 2), inp.z2_parities(8)) == 0.0
+
+
+def test_z2_needs_the_ternary_network():
+    with pytest.raises(ValueError):
+        solve.problem("ising", 1.0, 8, 3, z2=True)
