@@ -1,4 +1,4 @@
-"""Host-side set-up of the optimisation driver (no GPU): the binary network on
+"""Host-side set-up of the optimisation program solve.py (no GPU): the binary network on
 blocked sites with a three-site term, the ternary network on spins with a
 two-site term, Z2-symmetric ternary starting points."""
 import numpy as np
