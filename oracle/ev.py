@@ -43,21 +43,26 @@ def ev_update(D):
     return -polar_factor(D)
 
 
-def ev_sweep(h3, us, ws, gamma, tol=1e-14):
+def ev_sweep(h3, us, ws, gamma, tol=1e-14, network="binary"):
     """One sweep: for i = 0..2L+1 (u_0, w_0, ..., u_S, w_S), recompute the
     environments of the shifted cost at the current point and replace tensor
     i by -polar(D_i).  Returns (us, ws, energies) with energies[i] the energy
-    per bottom site (unshifted) after update i."""
+    per bottom site (unshifted) after update i.  network: "binary" (h3 a
+    three-site term) or "ternary" (a two-site term, oracle/ternary.py)."""
+    if network == "ternary":
+        from . import ternary as net
+    else:
+        net = om
     us = [u.copy() for u in us]
     ws = [w.copy() for w in ws]
     hs = np.asarray(h3) - gamma * np.eye(np.asarray(h3).shape[0])
     energies = []
     for i in range(2 * len(us)):
-        _, ds, _ = om.energy_grad(hs, us, ws, tol=tol)
+        _, ds, _ = net.energy_grad(hs, us, ws, tol=tol)
         l, k = divmod(i, 2)
         if k == 0:
             us[l] = ev_update(ds[i])
         else:
             ws[l] = ev_update(ds[i])
-        energies.append(om.energy(h3, us, ws, tol=tol))
+        energies.append(net.energy(h3, us, ws, tol=tol))
     return us, ws, energies

@@ -64,3 +64,15 @@ def test_sweeps_lower_the_energy():
     # still a MERA: every tensor isometric
     for t in us + ws:
         assert np.abs(t.conj().T @ t - np.eye(t.shape[1])).max() < 1e-12
+
+
+def test_sweeps_lower_the_ternary_energy():
+    h = inp.ising_bond(1.0)
+    gamma = float(np.linalg.eigvalsh(h).max()) + 0.5
+    us, ws = inp.random_ternary_mera(2, 4, 1, seed=5)
+    from oracle import ternary as ot
+    e = [ot.energy(h, us, ws)]
+    for _ in range(3):
+        us, ws, es = ev.ev_sweep(h, us, ws, gamma, network="ternary")
+        e.append(es[-1])
+    assert all(b < a for a, b in zip(e, e[1:])), e
