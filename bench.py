@@ -80,8 +80,9 @@ def tensor_peaks():
     return {2: (bf16, src), 1: (bf16 * 1.1 / 2.25, src + " x nominal tf32/bf16 ratio 1.1/2.25")}
 
 
-# DRAM traffic per launch of the contraction kernel, from the ncu capture
-# summarised in profiles/gett_f64_ising_chi12.md (null once the kernel changes).
+# DRAM traffic per launch of the dominant kernel from an ncu capture of the
+# same workload, kept only while the kernel is unchanged since the capture
+# (none is: the roofline's traffic is reported as null).
 GETT_TRAFFIC_BYTES = {}
 
 
@@ -239,7 +240,7 @@ def run_reference(args, wl):
 
 
 def run_serve(args):
-    """Reduced serving stream (see DESIGN.md): Poisson arrivals at 50/s, Ising
+    """Reduced serving stream: Poisson arrivals at 50/s, Ising
     h ~ U[0.5,1.5] or XXZ Delta ~ U[0,2], chi from --serve-chis, 3xTF32, stop
     at |G| < 1e-6 or --serve-maxiter iterations."""
     import torch
