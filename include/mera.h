@@ -74,7 +74,7 @@ enum {
     MERA_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired       */
     MERA_ERR_NOT_ISOMETRIC = -6,  /* input tensor violates W^dag W = 1        */
     MERA_ERR_CUDA = -7,           /* CUDA runtime error                       */
-    MERA_ERR_UNSUPPORTED = -8     /* valid request this build cannot serve    */
+    MERA_ERR_UNSUPPORTED = -8     /* valid request the library does not serve */
 };
 
 typedef enum { MERA_F64 = 0, MERA_C128 = 1 } mera_dtype;
