@@ -32,19 +32,20 @@ from . import mera as om
 
 
 def polar_factor(D):
-    """Q of the polar decomposition D = Q P (Q isometric, P = Q^dag D Hermitian
+    """(App. ev_steplimit) Q of the polar decomposition D = Q P (Q isometric, P = Q^dag D Hermitian
     positive semidefinite): Q = U V^dag from the thin SVD D = U S V^dag."""
     u, _, vh = np.linalg.svd(D, full_matrices=False)
     return u @ vh
 
 
 def ev_update(D):
-    """The new tensor for environment D: -Q (see the module docstring)."""
+    """The new tensor for environment D: -Q (App. ev_steplimit; the sign is
+    discussed in the module docstring)."""
     return -polar_factor(D)
 
 
 def ev_sweep(h3, us, ws, gamma, tol=1e-14, network="binary"):
-    """One sweep: for i = 0..2L+1 (u_0, w_0, ..., u_S, w_S), recompute the
+    """One Evenbly-Vidal sweep (Sec. 4, App. ev_steplimit): for i = 0..2L+1 (u_0, w_0, ..., u_S, w_S), recompute the
     environments of the shifted cost at the current point and replace tensor
     i by -polar(D_i).  Returns (us, ws, energies) with energies[i] the energy
     per bottom site (unshifted) after update i.  network: "binary" (h3 a

@@ -51,10 +51,12 @@ def as_tensor(M, d):
 
 
 def transfer_right(A, y):
+    """E_R(y) = sum_s A^s y A^s^dag, the map of Eq. mps_right_transfermatrix."""
     return np.einsum("asb,bc,dsc->ad", A, y, A.conj())
 
 
 def transfer_left(A, x):
+    """E_L(x) = sum_s A^s^dag x A^s (E_L(1) = 1: Eq. mps_isometricity)."""
     return np.einsum("asb,ac,csd->bd", A.conj(), x, A)
 
 
@@ -99,18 +101,20 @@ def _t_h(A, h, y):
 
 
 def energy(A, h):
-    """Energy per site of the normalised infinite MPS (valid off the manifold)."""
+    """Energy per site of the normalised infinite MPS of Eq. mps (valid off the
+    manifold), Sec. 5."""
     l, r, lam = fixed_points(A)
     return float(np.real(np.trace(l @ _t_h(A, h, r)) / (lam**2 * np.trace(l @ r))))
 
 
 def right_fixed_point(A):
-    """rho = E_R(rho), Tr rho = 1 (left-canonical A)."""
+    """rho = E_R(rho), Tr rho = 1 (left-canonical A): Eq. mps_right_transfermatrix."""
     return fixed_points(A)[1]
 
 
 def energy_grad(A, h):
-    """(e, D, rho) at a left-canonical A: D = 2 de/d conj(A), shape (D, d, D)."""
+    """(e, D, rho) at a left-canonical A: D = 2 de/d conj(A), shape (D, d, D),
+    with the energy environments of Eq. mps_derivative (Sec. 5)."""
     Dd, d, _ = A.shape
     rho = right_fixed_point(A)
     one = np.eye(Dd)
@@ -144,7 +148,9 @@ def gradient(A, D):
 
 
 def precondition(X, rho, delta):
-    """X -> X (rho + delta 1)^{-1} (matrix form, right virtual index)."""
+    """X -> X (rho + delta 1)^{-1} (matrix form, right virtual index):
+    Eq. mps_preconditioning with the regularisation of Sec. 5; it inverts the
+    metric of Eq. mps_inner."""
     d = X.shape[1]
     M = as_matrix(X)
     return as_tensor(M @ np.linalg.inv(rho + delta * np.eye(rho.shape[0])), d)

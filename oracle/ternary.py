@@ -74,29 +74,32 @@ OP_LEGS, OUT_LEGS, RHO_LEGS = "f0 f1 g0 g1", "a b A B", "A B a b"
 
 
 def ascend_side(o, u, w, side):
-    """A_side(o): two-site fine operator -> two-site coarse operator."""
+    """A_side(o): two-site fine operator -> two-site coarse operator (Sec. 4)."""
     c, cp = _dims(u, w)
     pairs = [(o.reshape((c,) * 4), OP_LEGS)] + [(a, l) for a, l, _ in _network(side, u, w)]
     return _contract(pairs, OUT_LEGS).reshape(cp**2, cp**2)
 
 
 def descend_side(r, u, w, side):
-    """D_side(r), the adjoint of A_side."""
+    """D_side(r), the adjoint of A_side (Sec. 4)."""
     c, cp = _dims(u, w)
     pairs = [(a, l) for a, l, _ in _network(side, u, w)] + [(r.reshape((cp,) * 4), RHO_LEGS)]
     return _contract(pairs, "g0 g1 f0 f1").reshape(c**2, c**2)
 
 
 def ascend(o, u, w):
+    """Abar(o) = (A_L + A_C + A_R)(o) / 3 (Sec. 4)."""
     return sum(ascend_side(o, u, w, s) for s in SIDES) / 3.0
 
 
 def descend(r, u, w):
+    """Dbar(r) = (D_L + D_C + D_R)(r) / 3 (Sec. 4)."""
     return sum(descend_side(r, u, w, s) for s in SIDES) / 3.0
 
 
 def layer_derivatives(h, r, u, w):
-    """D_u, D_w of C = Tr(Abar(h) r) for one layer (D_v = 2 dC/d conj(v))."""
+    """D_u, D_w of C = Tr(Abar(h) r) for one layer (D_v = 2 dC/d conj(v),
+    Sec. 2.3 and Sec. 4)."""
     c, cp = _dims(u, w)
     dt = np.result_type(h, r, u, w)
     du = np.zeros((c,) * 4, dtype=dt)
@@ -117,7 +120,7 @@ def layer_derivatives(h, r, u, w):
 
 
 def si_fixed_point(u, w, tol=1e-14):
-    """rho_S = Dbar_S(rho_S), unit trace, hermitised (Krylov eigensolver)."""
+    """rho_S = Dbar_S(rho_S), unit trace, hermitised (Krylov eigensolver, App. B)."""
     c, cp = _dims(u, w)
     n = c**4
     dt = np.result_type(u, w)
@@ -137,7 +140,8 @@ def si_fixed_point(u, w, tol=1e-14):
 
 
 def si_env_series(h, rho, u, w, tol=1e-14):
-    """x with x - Abar_S(x) + Tr(x rho) 1 = h (the series of App. B)."""
+    """x with x - Abar_S(x) + Tr(x rho) 1 = h (the series of App. B,
+    Eq. scale_invariant_partial)."""
     c, _ = _dims(u, w)
     n = c**4
     dt = np.result_type(h, rho, u, w)
@@ -177,6 +181,7 @@ def energy_grad(h0, us, ws, tol=1e-14):
 
 
 def energy(h0, us, ws, tol=1e-14):
+    """Energy per site only: ascending sweep and scale-invariant fixed point (Sec. 4, App. B)."""
     L = len(us) - 1
     h = np.asarray(h0)
     for l in range(L):

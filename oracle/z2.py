@@ -1,6 +1,7 @@
-"""Z2 symmetry of isometric tensors, FP64 (Sec. 4: symmetric tensors are block
+"""Z2 symmetry of isometric tensors, FP64 (Sec. 6: symmetric tensors are block
 diagonal in the charge basis, and the isometry condition, the projection, the
-retraction and the transport act on the individual blocks).
+retraction and the transport act on the individual blocks; the benchmark of
+Sec. 4, Fig. 2, enforces Z2).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
@@ -26,7 +27,8 @@ from . import geometry as geo
 
 
 def violation(W, row_par, col_par):
-    """Largest entry of W that connects different charges."""
+    """Largest entry of W that connects different charges (zero for a
+    symmetric tensor, Sec. 6)."""
     bad = row_par[:, None] != col_par[None, :]
     return float(np.abs(W[bad]).max()) if bad.any() else 0.0
 
@@ -58,12 +60,15 @@ def _blockwise(fn, row_par, col_par, *mats):
 
 
 def project_blockwise(W, D, kind, row_par, col_par):
+    """Eqs. stiefel_gradient / grassmann_gradient on each charge block (Sec. 6)."""
     return _blockwise(lambda w, d: geo.project(w, d, kind), row_par, col_par, W, D)
 
 
 def retract_blockwise(W, X, alpha, row_par, col_par):
+    """The retraction of Sec. 2.3 on each charge block (Sec. 6)."""
     return _blockwise(lambda w, x: geo.retract(w, x, alpha), row_par, col_par, W, X)
 
 
 def transport_blockwise(W, X, alpha, Y, row_par, col_par):
+    """The vector transport of Sec. 2.3 on each charge block (Sec. 6)."""
     return _blockwise(lambda w, x, y: geo.transport(w, x, alpha, y), row_par, col_par, W, X, Y)

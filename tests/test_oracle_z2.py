@@ -1,6 +1,6 @@
 """Pins of the Z2 utilities (oracle/z2.py): the Ising chain's parity, symmetry
 of a symmetric MERA's derivatives and level operators, and the blockwise
-geometry of Sec. 4 (projection, retraction and transport per charge block)
+geometry of Sec. 6 (projection, retraction and transport per charge block)
 against the dense geometry."""
 import numpy as np
 import pytest
