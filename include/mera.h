@@ -88,7 +88,7 @@ typedef enum { MERA_PREC_FP64 = 0, MERA_PREC_3XTF32 = 1, MERA_PREC_SPLIT_BF16 = 
 typedef struct {
     int d_b;           /* bottom site dimension (4: two spins blocked)        */
     int chi;           /* bond dimension of the scale-invariant layer          */
-    int n_trans;       /* number of transition layers (>= 1)                   */
+    int n_trans;       /* number of transition layers (>= 1; 0 for an MPS)    */
     int dtype;         /* mera_dtype                                           */
     int prec;          /* mera_prec                                            */
     int w_stiefel;     /* 0: isometries on the Grassmann manifold (Sec. 4),
@@ -105,7 +105,8 @@ typedef struct {
                           contraction chain (must divide the coarse bond
                           dimension; 0 = automatic: no slicing while the
                           7-leg intermediate has at most 2^30 entries)        */
-    int network;       /* mera_network: MERA_BINARY (default) or MERA_TERNARY */
+    int network;       /* mera_network: MERA_BINARY (default), MERA_TERNARY
+                          or MERA_MPS                                          */
 } mera_config;
 
 /* Network of the MERA (Sec. 4).  MERA_BINARY: the binary MERA described
@@ -118,7 +119,29 @@ typedef struct {
  * network the preconditioner's rho_w is the one-site marginal of the level
  * density matrix and rho_u the state on the two isometry outputs a u acts
  * on; every entry point serves both networks. */
-typedef enum { MERA_BINARY = 0, MERA_TERNARY = 1 } mera_network;
+typedef enum { MERA_BINARY = 0, MERA_TERNARY = 1, MERA_MPS = 2 } mera_network;
+
+/* MERA_MPS: the uniform (one-site translation-invariant) infinite MPS of
+ * Sec. 5 on the same geometry and optimisers.  Config: d_b = physical
+ * dimension d, chi = bond dimension D (>= 1), n_trans = 0, prec =
+ * MERA_PREC_FP64, w_stiefel = 0 (b_chunk and recompute_env are unused).
+ * The point is one tensor A, (D d) x D row-major, A[a s, b] (rows: left
+ * virtual leg then physical leg; column: right virtual leg), left-canonical:
+ * A^dag A = 1 (Eq. mps_isometricity), a point of the Grassmann manifold
+ * (right unitary rotations are gauge).  h3 of mera_create is a two-site
+ * term, (d^2) x (d^2), h[s t, s' t'] (rows the bra pair); the cost is the
+ * energy per site of the normalised state, e = Tr(T_h(rho)) with rho the
+ * unit-trace fixed point of E_R(y) = sum_s A^s y A^s^dag
+ * (Eq. mps_right_transfermatrix).  mera_energy_grad gives the partial
+ * derivative of Eq. mps_derivative (D = 2 de/d conj(A); the left and right
+ * energy environments solve (1 - E_L + |1)(rho|) H_l = h_l and
+ * (1 - E_R + |rho)(1|) H_r = h_r by GMRES, h_l and h_r being the
+ * left- and right-contracted term h - e 1) and its Grassmann projection;
+ * the preconditioner is X -> X (rho + delta 1)^(-1), delta = |G|^2
+ * (Eq. mps_preconditioning with the regularisation of Sec. 5).  Other
+ * configurations return MERA_ERR_ARG (shape) or MERA_ERR_UNSUPPORTED
+ * (mixed precision, Stiefel); mera_ev_sweep and the server return
+ * MERA_ERR_UNSUPPORTED for an MPS. */
 
 /* Fill *cfg with defaults for (d_b, chi, n_trans): binary network, F64,
  * FP64 contractions, Grassmann isometries, preconditioner on, Krylov dim 20,
@@ -128,14 +151,14 @@ void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
 /* Create a problem.  h3 is the 3-site Hamiltonian term on bottom sites,
  * a (d_b^3) x (d_b^3) row-major matrix h[f0 f1 f2, g0 g1 g2] of the config's
  * element type whose translates sum to H (the cost is the energy per bottom
- * site, C = Tr(h rho), Sec. 4); for the ternary network a two-site term,
- * (d_b^2) x (d_b^2).  stream: a cudaStream_t (NULL = default
+ * site, C = Tr(h rho), Sec. 4); for the ternary network and the MPS a
+ * two-site term, (d_b^2) x (d_b^2).  stream: a cudaStream_t (NULL = default
  * stream).  The tensors start as the identity-disentangler / first-columns
  * isometry point until mera_set_tensors is called. */
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
 int mera_destroy(mera_t m);
 
-/* Number of tensors (2*(n_trans+1)) and the shape of tensor i. */
+/* Number of tensors (2*(n_trans+1); 1 for an MPS) and the shape of tensor i. */
 int mera_num_tensors(mera_t m);
 int mera_tensor_shape(mera_t m, int i, int64_t* rows, int64_t* cols);
 

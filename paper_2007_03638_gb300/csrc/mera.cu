@@ -53,7 +53,8 @@ __global__ void sylvester_scale_k(double* a, const double* __restrict__ lt, int 
 
 // evals -> function values used by the Grassmann retraction/transport and
 // the preconditioner (kind: 0 cos(a s), 1 sin(a s)/s, 2 (1-cos(a s))/s^2,
-// 3 1/sqrt(l^2+d^2), 4 sqrt(l^2+d^2)); for kinds 0-2 the input is s^2.
+// 3 1/sqrt(l^2+d^2), 4 sqrt(l^2+d^2), 5 1/sqrt(max(l, d)), 6 1/(l + d));
+// for kinds 0-2 the input is s^2.
 __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, double a, double d,
                            double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,8 +76,10 @@ __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, doubl
     r = 1.0 / sqrt(l * l + d * d);
   } else if (kind == 4) {
     r = sqrt(l * l + d * d);
-  } else {
+  } else if (kind == 5) {
     r = 1.0 / sqrt(fmax(l, d));  // inverse square root of a positive semidefinite matrix (floor d)
+  } else {
+    r = 1.0 / (l + d);           // (rho + d 1)^(-1), the MPS preconditioner
   }
   out[i] = r;
 }
@@ -102,6 +105,17 @@ __global__ void marg_tern_c_k(const double2* __restrict__ r, int64_t c, double2*
     sy += u.y + v.y;
   }
   out[idx] = make_double2(0.5 * sx, 0.5 * sy);
+}
+
+// y += (re + i im) x, n interleaved complex elements
+__global__ void axpy_c_k(double re, double im, const double2* __restrict__ x, double2* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 a = x[i];
+  double2 b = y[i];
+  b.x += re * a.x - im * a.y;
+  b.y += re * a.y + im * a.x;
+  y[i] = b;
 }
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -149,6 +163,7 @@ struct mera_ctx {
   bool cplx = false;                      // interleaved complex128 data
   double hshift = 0.0;                    // evaluations use h3 - hshift 1 (Evenbly-Vidal sweeps)
   bool tern = false;                      // ternary network
+  bool mps = false;                       // uniform MPS (one Grassmann tensor, two-site term)
   int ns = 3;                             // sites of a level operator (3 binary, 2 ternary)
   int rs = 1;                             // reals per element (1 or 2)
   int L = 0, nt = 0;
@@ -168,6 +183,11 @@ struct mera_ctx {
   mera::Exec ex;                          // contraction arithmetic
   mera::DevBuf tc_ws, tc_err;             // tensor-core operand planes, wait-expiry flag
   mera::DevBuf tc_keep[2];                // packed planes of loop-invariant operands (sliced chain)
+  // uniform MPS: two-site tensor B = A A, (h - e 1) B, its product with rho,
+  // a (D d) x D scratch, the contracted terms h_l, h_r and the left
+  // environment H_l (the right one lives in x, rho in rho[0])
+  mera::DevBuf mB, mHB, mT, mA1, mhl, mhr, mHl;
+  mera::GemmPlan mps_hplan;               // h on the physical pair of B
   mera::DevBuf gtmp[6];                   // geometry temporaries
   mera::Reducer red;
   mera::Eval ev[2];
@@ -202,6 +222,11 @@ int64_t ipow(int64_t b, int e) {
 }
 // order of a level operator (matrix of ns sites of dimension c)
 int64_t opn(const Ctx& c, int64_t dim) { return ipow(dim, c.ns); }
+
+// Tensor i is a Grassmann point (an MPS tensor, or an isometry unless the
+// config asks for Stiefel); the others (disentanglers, Stiefel isometries)
+// use the Stiefel forms.
+bool grass(const Ctx& c, int i) { return c.mps || (i % 2 == 1 && !c.cfg.w_stiefel); }
 
 // element-type helpers: x = (x + x^dag)/2, x += a 1, matrix products whose
 // 'C' operands are conjugate-transposed (plain transposes for real data)
@@ -509,10 +534,154 @@ void project_tensor(Ctx& c, int i, const double* W, const double* D, double* G, 
   const int64_t n = c.rows[i], p = c.cols[i];
   double* S = P(c.gtmp[0]);
   mm(c, 'C', 'N', p, p, n, 1.0, W, p, D, p, 0.0, S, p, s);     // S = W^dag D
-  const bool stiefel = (i % 2 == 0) || c.cfg.w_stiefel;
+  const bool stiefel = !grass(c, i);
   if (stiefel) herm(c, S, p, s);                                // (S + S^dag)/2
   if (G != D) copy(G, D, n * p * c.rs, s);
   mm(c, 'N', 'N', n, p, p, -1.0, W, p, S, p, 1.0, G, p, s);    // G = D - W S
+}
+
+// ------------------------------------------------------------ uniform MPS --
+// Sec. 5: one left-canonical tensor A ((D d) x D, rows (a s), column b; A^s
+// the D x D matrix at fixed physical index s) on the Grassmann manifold and a
+// two-site term h.  With the transfer maps
+//   E_R(y) = sum_s A^s y A^s^dag,   E_L(x) = sum_s A^s^dag x A^s  (E_L(1) = 1),
+// rho the unit-trace fixed point of E_R (Eq. mps_right_transfermatrix),
+// B = A A the two-site tensor [a][s][t][c] and HB = h applied to its
+// physical pair, the energy per site is e = Re <B, HB rho>.  The partial
+// derivative of Eq. mps_derivative, D = 2 de/d conj(A), takes the shifted
+// term h - e 1 (which makes the environment sums converge):
+//   T   = (h - e) B rho,  h_l = B^dag (h - e) B,  h_r = T B^dag,
+//   (1 - E_L + |1)(rho|) H_l = h_l,  (1 - E_R + |rho)(1|) H_r = h_r,
+//   D/2 = T A^dag (bra copy on the left site of the term)
+//       + A^dag T (bra copy on the right site) + H_l A rho + A H_r,
+// the products read with the reshapes of the row-major arrays named below.
+
+// out = beta out + alpha E_R(y)   (D x D; scratch mA1)
+void mps_right(Ctx& c, const double* A, const double* y, double* out, double alpha, double beta, cudaStream_t s) {
+  const int64_t D = c.cols[0], d = c.cfg.d_b;
+  double* T = P(c.mA1);
+  mm(c, 'N', 'N', D * d, D, D, 1.0, A, D, y, D, 0.0, T, D, s);                 // T[(a s), c] = (A^s y)[a, c]
+  mm(c, 'N', 'C', D, D, d * D, alpha, T, d * D, A, d * D, beta, out, D, s);     // T[a, (s c)] A[e, (s c)]^*
+}
+
+// out = beta out + alpha E_L(x)   (D x D; scratch mA1)
+void mps_left(Ctx& c, const double* A, const double* x, double* out, double alpha, double beta, cudaStream_t s) {
+  const int64_t D = c.cols[0], d = c.cfg.d_b;
+  double* T = P(c.mA1);
+  mm(c, 'N', 'N', D, d * D, D, 1.0, x, D, A, d * D, 0.0, T, d * D, s);         // T[a, (s c)] = (x A^s)[a, c]
+  mm(c, 'C', 'N', D, D, D * d, alpha, A, D, T, D, beta, out, D, s);             // A[(a s), b]^* T[(a s), c]
+}
+
+// Energy per site at A: rho (GMRES, warm-started), B, HB and mT = HB rho.
+double mps_energy(Ctx& c, const double* A, cudaStream_t s) {
+  const int64_t D = c.cols[0], d = c.cfg.d_b, n = D * D, nr = n * c.rs, nb = D * d * d * D * c.rs;
+  double* rho = P(c.rho[0]);
+  double* bvec = P(c.bvec);
+  fill(0.0, bvec, nr, s);
+  add_id(c, 1.0 / (double)D, bvec, D, s);
+  if (!c.have_rho) copy(rho, bvec, nr, s);
+  // (1 - E_R + |b)(1|) rho = b, b = 1/D: the fixed point with Tr rho = 1
+  auto op_rho = [&](const double* v, double* out) {
+    copy(out, v, nr, s);
+    mps_right(c, A, v, out, -1.0, 1.0, s);
+    if (c.cplx) {
+      double tr, ti;
+      c.red.trace_c(v, D, s, &tr, &ti);
+      add_identity_c(tr / (double)D, ti / (double)D, out, D, s);
+    } else {
+      axpy(c.red.trace(v, D, s), bvec, out, n, s);
+    }
+    ++c.matvecs;
+  };
+  gmres(c, op_rho, bvec, rho, nr, c.cfg.krylov_tol, s);
+  double tr = 0.0, ti = 0.0;
+  if (c.cplx) c.red.trace_c(rho, D, s, &tr, &ti); else tr = c.red.trace(rho, D, s);
+  if (!(std::fabs(tr) > 0)) throw Error(MERA_ERR_NONFINITE, "MPS fixed point has zero trace");
+  scal(1.0 / tr, rho, nr, s);
+  herm(c, rho, D, s);
+  c.have_rho = true;
+  // B[(a s), (t c)] = A[(a s), b] A[b, (t c)]
+  mm(c, 'N', 'N', D * d, d * D, D, 1.0, A, D, A, d * D, 0.0, P(c.mB), d * D, s);
+  // HB[a, (s t), c] = h[(s t), (u v)] B[a, (u v), c]
+  GettCall g = c.mps_hplan.proto;
+  g.A = P(c.h0);
+  g.B = P(c.mB);
+  g.C = P(c.mHB);
+  g.cplx = c.cplx;
+  gett_f64(g, s);
+  mm(c, 'N', 'N', D * d * d, D, D, 1.0, P(c.mHB), D, rho, D, 0.0, P(c.mT), D, s);  // HB rho
+  // Tr T_h(rho) = sum conj(B) (HB rho): the real dot product of the arrays
+  const double e = c.red.dot(P(c.mB), P(c.mT), nb, s);
+  if (!std::isfinite(e)) throw Error(MERA_ERR_NONFINITE, "non-finite MPS energy");
+  return e;
+}
+
+// Full MPS evaluation at A into E (energy, D, G, delta, rho for the preconditioner).
+void mps_energy_grad(Ctx& c, const double* A, Eval& E, cudaStream_t s) {
+  E.e = mps_energy(c, A, s);
+  const int64_t D = c.cols[0], d = c.cfg.d_b, n = D * D, nr = n * c.rs, nb = D * d * d * D * c.rs;
+  const double* rho = P(c.rho[0]);
+  const double* B = P(c.mB);
+  double* HB = P(c.mHB);
+  double* T = P(c.mT);
+  double* hl = P(c.mhl);
+  double* hr = P(c.mhr);
+  double* Hl = P(c.mHl);
+  double* Hr = P(c.x);
+  axpy(-E.e, B, HB, nb, s);                                                      // (h - e 1) B
+  mm(c, 'N', 'N', D * d * d, D, D, 1.0, HB, D, rho, D, 0.0, T, D, s);           // T = (h - e) B rho
+  mm(c, 'C', 'N', D, D, D * d * d, 1.0, B, D, HB, D, 0.0, hl, D, s);            // h_l = B^dag (h - e) B
+  mm(c, 'N', 'C', D, D, d * d * D, 1.0, T, d * d * D, B, d * d * D, 0.0, hr, D, s);  // h_r = T B^dag
+  if (!c.have_x) {
+    copy(Hl, hl, nr, s);
+    copy(Hr, hr, nr, s);
+  }
+  // (1 - E_L + |1)(rho|) H_l = h_l: the added term is Tr(rho v) 1
+  auto op_l = [&](const double* v, double* out) {
+    copy(out, v, nr, s);
+    mps_left(c, A, v, out, -1.0, 1.0, s);
+    if (c.cplx) {
+      double tr, ti;
+      c.red.dot_c(rho, v, n, s, &tr, &ti);  // sum conj(rho_ij) v_ij = Tr(rho v), rho hermitian
+      add_identity_c(tr, ti, out, D, s);
+    } else {
+      add_identity(c.red.dot(v, rho, n, s), out, D, s);
+    }
+    ++c.matvecs;
+  };
+  // (1 - E_R + |rho)(1|) H_r = h_r: the added term is Tr(v) rho
+  auto op_r = [&](const double* v, double* out) {
+    copy(out, v, nr, s);
+    mps_right(c, A, v, out, -1.0, 1.0, s);
+    if (c.cplx) {
+      double tr, ti;
+      c.red.trace_c(v, D, s, &tr, &ti);
+      axpy_c_k<<<blocks(n), 256, 0, s>>>(tr, ti, reinterpret_cast<const double2*>(rho),
+                                         reinterpret_cast<double2*>(out), n);
+      count_launch();
+      MERA_CHECK_LAUNCH();
+    } else {
+      axpy(c.red.trace(v, D, s), rho, out, n, s);
+    }
+    ++c.matvecs;
+  };
+  gmres(c, op_l, hl, Hl, nr, c.cfg.krylov_tol, s);
+  gmres(c, op_r, hr, Hr, nr, c.cfg.krylov_tol, s);
+  c.have_x = true;
+  double* Dv = P(E.D);
+  double* Arho = P(c.mA1);
+  mm(c, 'N', 'C', D * d, D, d * D, 2.0, T, d * D, A, d * D, 0.0, Dv, D, s);      // T[(a s), (t c)] A[e, (t c)]^*
+  mm(c, 'C', 'N', D, d * D, D * d, 2.0, A, D, T, d * D, 1.0, Dv, d * D, s);      // A[(e t), c]^* T[(e t), (s f)]
+  mm(c, 'N', 'N', D * d, D, D, 1.0, A, D, rho, D, 0.0, Arho, D, s);             // A rho
+  mm(c, 'N', 'N', D, d * D, D, 2.0, Hl, D, Arho, d * D, 1.0, Dv, d * D, s);     // H_l A rho
+  mm(c, 'N', 'N', D * d, D, D, 2.0, A, D, Hr, D, 1.0, Dv, D, s);                // A H_r
+  project_tensor(c, 0, A, Dv, P(E.G), s);
+  const double* g = P(E.G);
+  E.delta.assign(1, std::sqrt(c.red.dot(g, g, c.rows[0] * c.cols[0] * c.rs, s)));
+  if (!std::isfinite(E.delta[0])) throw Error(MERA_ERR_NONFINITE, "non-finite MPS gradient");
+  copy(P(E.rho_v[0]), rho, nr, s);
+  E.eig_ready = false;
+  E.valid = true;
 }
 
 void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
@@ -525,6 +694,10 @@ double forward_energy(Ctx& c, const double* W, cudaStream_t s);
 void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   const int L = c.L;
   c.prof.energy_grad_calls++;
+  if (c.mps) {
+    mps_energy_grad(c, W, E, s);
+    return;
+  }
   E.e = forward_energy(c, W, s);
   const int64_t cS = c.dims[L], n3 = opn(c, cS), n = n3 * n3;
   const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
@@ -554,6 +727,7 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
 }
 
 double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
+  if (c.mps) return mps_energy(c, W, s);
   const int L = c.L;
   // up-sweep
   copy(P(c.h[0]), P(c.h0), opn(c, c.dims[0]) * opn(c, c.dims[0]) * c.rs, s);
@@ -834,14 +1008,18 @@ void precondition(Ctx& c, Eval& E, const double* W, const double* X, double* Xt,
     double* Yi = Xt + c.offs[i];
     const double* V = P(E.evec[i]);
     double* lt = P(c.gtmp[5]);
-    const bool stiefel = (i % 2 == 0) || c.cfg.w_stiefel;
+    const bool stiefel = !grass(c, i);
     double* A = P(c.gtmp[0]);
     double* T = P(c.gtmp[1]);
     double* Rinv = P(c.gtmp[2]);
     double* Z = P(c.gtmp[3]);
     double* Em = P(c.gtmp[4]);
-    // regularised inverse (rho^2 + delta^2)^(-1/2) = V diag(1/lt) V^T
-    spectral_k<<<blocks(q), 256, 0, s>>>(P(E.eval[i]), (int)q, 3, 0.0, E.delta[i], lt);
+    // regularised inverse (rho^2 + delta^2)^(-1/2) = V diag(lt) V^T; for an
+    // MPS (rho + delta^2 1)^(-1) (Sec. 5, delta = |G|)
+    if (c.mps)
+      spectral_k<<<blocks(q), 256, 0, s>>>(P(E.eval[i]), (int)q, 6, 0.0, E.delta[i] * E.delta[i], lt);
+    else
+      spectral_k<<<blocks(q), 256, 0, s>>>(P(E.eval[i]), (int)q, 3, 0.0, E.delta[i], lt);
     vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, lt, (int)q, c.cplx ? Em : Rinv);
     count_launch(2);
     if (c.cplx) extract_complex(Em, p, Rinv, s);
@@ -928,7 +1106,7 @@ void make_geom(Ctx& c, const double* W, const double* X, double alpha, cudaStrea
     if (n == p) {
       mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, P(g.Amat[i]), p, s);
       expm_skew(c, P(g.Amat[i]), alpha, p, P(g.E[i]), P(c.gtmp[2]), P(c.gtmp[3]), s);
-    } else if (i % 2 == 1 && !c.cfg.w_stiefel) {
+    } else if (grass(c, i)) {
       // Grassmann: X^dag X = V S^2 V^dag (through the real embedding for complex data)
       double* Z = P(c.gtmp[0]);
       double* ev = P(c.gtmp[5]);
@@ -1131,8 +1309,9 @@ void ev_replace(Ctx& c, int i, const double* D, double* W, cudaStream_t s) {
   double* Z = P(c.gtmp[0]);   // D^dag D, then (complex) its real embedding
   double* V = P(c.gtmp[1]);   // eigenvectors (q x q)
   double* R = P(c.gtmp[2]);   // (D^dag D)^(-1/2), p x p
+  double* fr = P(c.gtmp[3]);  // inverse square roots of the eigenvalues
   double* F = P(c.gtmp[4]);   // q x q scratch
-  double* f = P(c.gtmp[5]);   // eigenvalues, then their inverse square roots
+  double* f = P(c.gtmp[5]);   // eigenvalues
   mm(c, 'C', 'N', p, p, n, 1.0, D, p, D, p, 0.0, Z, p, s);
   herm(c, Z, p, s);
   if (c.cplx) {
@@ -1140,8 +1319,8 @@ void ev_replace(Ctx& c, int i, const double* D, double* W, cudaStream_t s) {
     copy(Z, F, q * q, s);
   }
   sym_eig(Z, V, f, (int)q, c.eigw, s);
-  spectral_k<<<blocks(q), 256, 0, s>>>(f, (int)q, 5, 0.0, 1e-300, f);
-  vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, f, (int)q, c.cplx ? F : R);
+  spectral_k<<<blocks(q), 256, 0, s>>>(f, (int)q, 5, 0.0, 1e-300, fr);
+  vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, fr, (int)q, c.cplx ? F : R);
   count_launch(2);
   MERA_CHECK_LAUNCH();
   if (c.cplx) extract_complex(F, p, R, s);
@@ -1156,6 +1335,7 @@ void clear_history(Ctx& c);
 // shifted term h3 - gamma 1 at the current point, then the tensor's update.
 // Ends with one unshifted evaluation at the new point.
 void ev_sweep(Ctx& c, double gamma, mera_iter_info* info, cudaStream_t s) {
+  if (c.mps) throw Error(MERA_ERR_UNSUPPORTED, "Evenbly-Vidal sweeps are defined for the MERA networks");
   Eval& E = c.ev[c.cur];
   const int64_t mv0 = c.matvecs;
   int evals = 0;
@@ -1197,8 +1377,9 @@ void clear_history(Ctx& c) {
   c.alpha_prev = 1.0;
 }
 
-// Accept the last trial: transport history, move point.
-void accept(Ctx& c, cudaStream_t s) {
+// Accept the last trial: its point and evaluation become the current ones
+// (the caller has transported the history).
+void accept(Ctx& c, cudaStream_t) {
   std::swap(c.Wcur, c.Wtry);
   c.cur = 1 - c.cur;
 }
@@ -1371,21 +1552,86 @@ void check_isometric(Ctx& c, const double* W, cudaStream_t s) {
   }
 }
 
+// Shapes and buffers of a uniform MPS (Sec. 5): one (D d) x D tensor, the
+// Krylov vectors and scratch of its D x D transfer-map solves.
+void create_mps(Ctx& c, int64_t* nS, int64_t* gmax) {
+  const mera_config& cfg = c.cfg;
+  if (cfg.d_b < 2 || cfg.chi < 1 || cfg.n_trans != 0) throw Error(MERA_ERR_ARG, "MPS: d_b >= 2, chi >= 1, n_trans = 0");
+  if (cfg.prec != MERA_PREC_FP64) throw Error(MERA_ERR_UNSUPPORTED, "the MPS runs in the FP64 path only");
+  if (cfg.w_stiefel) throw Error(MERA_ERR_UNSUPPORTED, "non-square Stiefel retraction not built");
+  const int64_t D = cfg.chi, d = cfg.d_b, es = sizeof(double) * c.rs;
+  c.L = 0;
+  c.dims.assign(1, D);
+  c.nt = 1;
+  c.rows.assign(1, D * d);
+  c.cols.assign(1, D);
+  c.offs.assign(1, 0);
+  c.total = D * d * D * c.rs;
+  c.rho.emplace_back(es * D * D);
+  for (DevBuf* b : {&c.mB, &c.mHB, &c.mT}) b->alloc(es * D * d * d * D);
+  c.mA1.alloc(es * D * d * D);
+  for (DevBuf* b : {&c.mhl, &c.mhr, &c.mHl}) b->alloc(es * D * D);
+  auto desc = [](std::vector<int> legs, std::vector<int64_t> ext) {
+    TDesc t;
+    t.legs = legs;
+    t.ext = ext;
+    t.stride.assign(legs.size(), 1);
+    for (size_t j = legs.size(); j-- > 1;) t.stride[j - 1] = t.stride[j] * ext[j];
+    return t;
+  };
+  enum { ls, lt, lu, lv, la, lc };
+  // HB[a s t c] = h[s t u v] B[a u v c]
+  c.mps_hplan = make_plan(desc({ls, lt, lu, lv}, {d, d, d, d}), desc({la, lu, lv, lc}, {D, d, d, D}),
+                          desc({la, ls, lt, lc}, {D, d, d, D}), c.pool);
+  *nS = D * D * c.rs;
+  *gmax = D * d * D;  // the tensor (polar scratch); D x D matrices and 2D x 2D embeddings fit after the x4 below
+}
+
+void create_mera(Ctx& c, int64_t* nS, int64_t* gmax);
+void finish_create(Ctx& c, cudaStream_t s);
+
 void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.cfg = cfg;
   c.s = s;
-  if (cfg.d_b < 2 || cfg.chi < 2 || cfg.n_trans < 1) throw Error(MERA_ERR_ARG, "bad d_b/chi/n_trans");
   if (cfg.dtype != MERA_F64 && cfg.dtype != MERA_C128) throw Error(MERA_ERR_ARG, "unknown dtype");
   c.cplx = cfg.dtype == MERA_C128;
   c.rs = c.cplx ? 2 : 1;
-  if (c.cplx && cfg.prec != MERA_PREC_FP64)
-    throw Error(MERA_ERR_UNSUPPORTED, "complex tensors run in the FP64 path only");
   if (cfg.prec != MERA_PREC_FP64 && cfg.prec != MERA_PREC_3XTF32 && cfg.prec != MERA_PREC_SPLIT_BF16)
     throw Error(MERA_ERR_ARG, "unknown precision mode");
-  if (cfg.network != MERA_BINARY && cfg.network != MERA_TERNARY) throw Error(MERA_ERR_ARG, "unknown network");
+  if (cfg.network != MERA_BINARY && cfg.network != MERA_TERNARY && cfg.network != MERA_MPS)
+    throw Error(MERA_ERR_ARG, "unknown network");
   c.tern = cfg.network == MERA_TERNARY;
-  c.ns = c.tern ? 2 : 3;
+  c.mps = cfg.network == MERA_MPS;
+  c.ns = c.tern || c.mps ? 2 : 3;
   c.pool.set_stream(s);
+  int64_t nS = 0, gmax = 1;  // reals of one Krylov vector; elements of a geometry temporary
+  if (c.mps) {
+    create_mps(c, &nS, &gmax);
+  } else {
+    create_mera(c, &nS, &gmax);
+  }
+  const size_t tb = sizeof(double) * c.total;
+  c.Wcur.alloc(tb);
+  c.Wtry.alloc(tb);
+  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 2 * c.ns) * c.rs);
+  MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
+  c.x.alloc(sizeof(double) * nS);
+  c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));
+  c.ktmp.alloc(sizeof(double) * nS);
+  c.kcoef.alloc(sizeof(double) * (cfg.krylov_dim + 2));
+  c.red.init(std::max(8, cfg.krylov_dim + 2));
+  c.bvec.alloc(sizeof(double) * nS);
+  gmax *= c.cplx ? 4 : 1;  // complex data and 2p x 2p real embeddings
+  for (auto& b : c.gtmp) b.alloc(sizeof(double) * gmax);
+  finish_create(c, s);
+}
+
+// Shapes, networks and level buffers of a binary or ternary MERA.
+void create_mera(Ctx& c, int64_t* nS, int64_t* gmax) {
+  const mera_config& cfg = c.cfg;
+  if (cfg.d_b < 2 || cfg.chi < 2 || cfg.n_trans < 1) throw Error(MERA_ERR_ARG, "bad d_b/chi/n_trans");
+  if (c.cplx && cfg.prec != MERA_PREC_FP64)
+    throw Error(MERA_ERR_UNSUPPORTED, "complex tensors run in the FP64 path only");
   c.L = cfg.n_trans;
   c.dims.push_back(cfg.d_b);
   // a coarse site holds two (binary) or three (ternary) fine sites
@@ -1404,33 +1650,28 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   }
   c.total = off;
   build_layers(c);
-  const size_t tb = sizeof(double) * c.total;
-  c.Wcur.alloc(tb);
-  c.Wtry.alloc(tb);
-  c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 2 * c.ns) * c.rs);
-  MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
   for (int l = 0; l <= c.L; ++l) {
     c.h.emplace_back(sizeof(double) * ipow(c.dims[l], 2 * c.ns) * c.rs);
     c.rho.emplace_back(sizeof(double) * ipow(c.dims[l], 2 * c.ns) * c.rs);
   }
-  const int64_t nS = ipow(cfg.chi, 2 * c.ns) * c.rs;  // reals of one level operator (chi^6 binary)
-  c.x.alloc(sizeof(double) * nS);
-  c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));
-  c.ktmp.alloc(sizeof(double) * nS);
-  c.kcoef.alloc(sizeof(double) * (cfg.krylov_dim + 2));
-  c.red.init(std::max(8, cfg.krylov_dim + 2));
+  *nS = ipow(cfg.chi, 2 * c.ns) * c.rs;  // reals of one level operator (chi^6 binary)
   // geometry temporaries: max over tensors / rho_u builders
-  c.bvec.alloc(sizeof(double) * nS);
-  int64_t gmax = 1;
+  int64_t g = 1;
   for (int l = 0; l <= c.L; ++l) {
     const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
-    gmax = std::max({gmax, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
-                     cf * cc * cc * cf, cf * cc * cf * cf * cf});
+    g = std::max({g, cf * cf * cf * cf, cc * cc * cc * cc, cf * cf * cc * cc * cc,
+                  cf * cc * cc * cf, cf * cc * cf * cf * cf});
     // ternary: w, and the rho_u builder's T1 (cf^3 cc^3) and T3 (cf^5 cc)
-    if (c.tern) gmax = std::max({gmax, cf * cf * cf * cc, cf * cf * cf * cc * cc * cc, cf * cf * cf * cf * cf * cc});
+    if (c.tern) g = std::max({g, cf * cf * cf * cc, cf * cf * cf * cc * cc * cc, cf * cf * cf * cf * cf * cc});
   }
-  gmax *= c.cplx ? 4 : 1;  // complex data and 2p x 2p real embeddings
-  for (auto& b : c.gtmp) b.alloc(sizeof(double) * gmax);
+  *gmax = g;
+}
+
+// Buffers every problem has: evaluations, step geometry, optimiser memory,
+// and the default point (u = 1, w = first columns).
+void finish_create(Ctx& c, cudaStream_t s) {
+  const mera_config& cfg = c.cfg;
+  const size_t tb = sizeof(double) * c.total;
   for (auto& E : c.ev) {
     E.G.alloc(tb);
     E.D.alloc(tb);
@@ -1461,7 +1702,6 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.dir2.alloc(tb);
   c.tmpv.alloc(tb);
   c.tmpv2.alloc(tb);
-  // default point: u = 1, w = first columns
   std::vector<double> host(c.total, 0.0);
   for (int i = 0; i < c.nt; ++i)
     for (int64_t k = 0; k < std::min(c.rows[i], c.cols[i]); ++k)
@@ -1702,6 +1942,22 @@ int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
 }
 
 namespace {
+// mera_footprint_bytes for a uniform MPS (mirror of create_mps and the shared buffers)
+size_t footprint_mps(const mera_config* cfg) {
+  if (cfg->d_b < 2 || cfg->chi < 1 || cfg->n_trans != 0 || cfg->prec != MERA_PREC_FP64 || cfg->w_stiefel) return 0;
+  const size_t rs = cfg->dtype == MERA_C128 ? 2 : 1, D = cfg->chi, d = cfg->d_b;
+  const size_t n = D * D * rs;                  // reals of a D x D matrix
+  const size_t total = D * d * D * rs;          // reals of the tensor
+  const size_t q = D * rs;                      // order of the (embedded) eigenproblems
+  size_t bytes = n + 3 * D * d * d * D * rs + total + 3 * n;             // rho, B, HB, T, scratch, h_l, h_r, H_l
+  bytes += d * d * d * d * rs;                                           // h
+  bytes += n * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);           // Krylov basis, tmp, x, bvec
+  bytes += 6 * D * d * D * rs * rs;                                      // geometry temporaries
+  bytes += 2 * (n + q * q + q) + 2 * q * q + 4 * n;                      // evaluations' rho/eig, step geometry
+  bytes += total * (size_t)(2 * std::max(1, cfg->lbfgs_m) + 2 + 4 + 4);  // memory, points, directions, G/D
+  return 8 * bytes;
+}
+
 // mera_footprint_bytes for the ternary network
 size_t footprint_ternary(const mera_config* cfg) {
   std::vector<int64_t> dims{cfg->d_b};
@@ -1740,7 +1996,9 @@ size_t footprint_ternary(const mera_config* cfg) {
 }  // namespace
 
 size_t mera_footprint_bytes(const mera_config* cfg) {
-  if (!cfg || cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
+  if (!cfg) return 0;
+  if (cfg->network == MERA_MPS) return footprint_mps(cfg);
+  if (cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
   if (cfg->network == MERA_TERNARY) {
     try {
       return footprint_ternary(cfg);

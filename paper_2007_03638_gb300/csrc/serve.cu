@@ -175,6 +175,7 @@ int mera_server_create(size_t mem_budget_bytes, int n_workers, mera_server_t* ou
 int mera_server_submit(mera_server_t sv, const mera_config* cfg, const void* h3, const void* const* tensors,
                        int method, double gtol, int maxiter, int64_t* id) {
   if (!sv || !cfg || !h3 || !tensors || !id || maxiter < 1) return MERA_ERR_ARG;
+  if (cfg->network == MERA_MPS) return MERA_ERR_UNSUPPORTED;  // the request stream holds MERA problems
   auto r = std::make_unique<Request>();
   r->cfg = *cfg;
   r->bytes = mera_footprint_bytes(cfg);

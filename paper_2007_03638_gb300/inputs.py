@@ -179,6 +179,23 @@ def random_mps(D: int, d: int, seed: int, dtype=np.float64) -> np.ndarray:
     return _haar_like(rng, D * d, D, dtype).reshape(D, d, D)
 
 
+def aklt_mps():
+    """The AKLT state (spin 1, D = 2) as a left-canonical uniform-MPS tensor
+    A (2, 3, 2) (physical basis m = +1, 0, -1) and its bond term
+    S.S + (S.S)^2 / 3, whose exact ground state it is (energy -2/3 per bond)."""
+    sp = np.array([[0.0, 1.0], [0.0, 0.0]])
+    A = np.zeros((2, 3, 2))
+    A[:, 0, :] = np.sqrt(2.0 / 3.0) * sp
+    A[:, 1, :] = -np.sqrt(1.0 / 3.0) * np.diag([1.0, -1.0])
+    A[:, 2, :] = -np.sqrt(2.0 / 3.0) * sp.T
+    s = 1.0 / np.sqrt(2.0)
+    Sx = s * np.array([[0, 1, 0], [1, 0, 1], [0, 1, 0]], dtype=complex)
+    Sy = s * np.array([[0, -1j, 0], [1j, 0, -1j], [0, 1j, 0]])
+    Sz = np.diag([1.0, 0.0, -1.0]).astype(complex)
+    SS = np.real(np.kron(Sx, Sx) + np.kron(Sy, Sy) + np.kron(Sz, Sz))
+    return A, SS + SS @ SS / 3.0
+
+
 def z2_parities(dim: int) -> np.ndarray:
     """Z2 charges of the basis of a leg of dimension dim: the first ceil(dim/2)
     states even (0), the rest odd (1).  For a spin-1/2 leg (dim 2) this is the

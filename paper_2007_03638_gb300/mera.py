@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libmera.so")
 
 MERA_F64, MERA_C128 = 0, 1
-MERA_BINARY, MERA_TERNARY = 0, 1
+MERA_BINARY, MERA_TERNARY, MERA_MPS = 0, 1, 2
 PREC_FP64, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
 
 ERRORS = {

@@ -1,8 +1,9 @@
-"""Run a MERA ground-state optimisation and log every iteration.
+"""Run a MERA (or uniform-MPS) ground-state optimisation and log every iteration.
 
     python -m paper_2007_03638_gb300.solve --model ising --chi 4 --n-trans 2 --iters 300
     python -m paper_2007_03638_gb300.solve --model xxz --delta 1 --chi 8 --prec 1 --method cg
     python -m paper_2007_03638_gb300.solve --network ternary --z2 --chi 8 --n-trans 2 --method ev
+    python -m paper_2007_03638_gb300.solve --network mps --model ising --field 1.5 --chi 16
 
 Each iteration prints one JSON record: energy per spin, its distance to the
 exact value (critical Ising -4/pi or Ising at field h by quadrature, XXZ at
@@ -35,9 +36,15 @@ def exact_energy(model, par):
 
 def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
     """(h, d_b, tensors, spins per bottom site) of a run: the binary network on
-    blocked sites (two spins, three-site term), the ternary one on spins
-    (two-site term); z2: Z2-symmetric ternary starting point."""
+    blocked sites (two spins, three-site term), the ternary one and the uniform
+    MPS (bond dimension chi, n_trans unused) on spins (two-site term); z2:
+    Z2-symmetric ternary starting point."""
     bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
+    if network == "mps":
+        if z2:
+            raise ValueError("Z2-symmetric starting points are built for the ternary network")
+        A = inp.random_mps(chi, 2, seed=seed)
+        return bond, 2, [A.reshape(chi * 2, chi)], 1
     if network == "ternary":
         us, ws = (inp.random_z2_ternary_mera(chi, n_trans, seed=seed) if z2
                   else inp.random_ternary_mera(2, chi, n_trans, seed=seed))
@@ -52,10 +59,11 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
         lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None, network="binary", z2=False):
     """method: 0 L-BFGS, 1 CG, 2 Evenbly-Vidal sweeps (one record per sweep;
     ev_gamma = the Hamiltonian shift, default the largest eigenvalue of the
-    Hamiltonian term plus 0.5).  network: "binary" or "ternary"."""
+    Hamiltonian term plus 0.5).  network: "binary", "ternary" or "mps"."""
     h3, d_b, tensors, spins = problem(model, par, chi, n_trans, network, z2, seed)
-    cfg = gm.default_config(d_b, chi, n_trans, prec=prec, lbfgs_m=lbfgs_m, krylov_dim=krylov_dim,
-                            network=gm.MERA_TERNARY if network == "ternary" else gm.MERA_BINARY)
+    net = {"binary": gm.MERA_BINARY, "ternary": gm.MERA_TERNARY, "mps": gm.MERA_MPS}[network]
+    cfg = gm.default_config(d_b, chi, 0 if network == "mps" else n_trans, prec=prec, lbfgs_m=lbfgs_m,
+                            krylov_dim=krylov_dim, network=net)
     m = gm.Mera(cfg, h3)
     m.set_tensors(tensors)
     ex = exact_energy(model, par)
@@ -94,7 +102,7 @@ def main():
     ap.add_argument("--n-trans", type=int, default=2)
     ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16")
     ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev"])
-    ap.add_argument("--network", default="binary", choices=["binary", "ternary"])
+    ap.add_argument("--network", default="binary", choices=["binary", "ternary", "mps"])
     ap.add_argument("--z2", action="store_true", help="Z2-symmetric starting point (ternary network)")
     ap.add_argument("--ev-gamma", type=float, default=None,
                     help="Evenbly-Vidal Hamiltonian shift (default: largest eigenvalue of the 3-site term + 0.5)")

@@ -70,3 +70,40 @@ def test_footprint_accounts_for_element_type_and_precision(lib):
     # invalid: no transition layer; chi = 64 unreachable from d_b = 4 in one layer (4 -> 16)
     assert gm.footprint_bytes(gm.default_config(4, 3, 0)) == 0
     assert gm.footprint_bytes(gm.default_config(4, 64, 1)) == 0
+
+
+def test_enums_match_header():
+    """The binding's enum values are the header's."""
+    from paper_2007_03638_gb300 import mera as gm
+    src = open(os.path.join(ROOT, "include", "mera.h")).read()
+    for name in ("MERA_F64", "MERA_C128", "MERA_BINARY", "MERA_TERNARY", "MERA_MPS",
+                 "MERA_PREC_FP64", "MERA_PREC_3XTF32", "MERA_PREC_SPLIT_BF16"):
+        val = int(re.search(rf"\b{name}\s*=\s*(\d+)", src).group(1))
+        py = {"MERA_PREC_FP64": "PREC_FP64", "MERA_PREC_3XTF32": "PREC_3XTF32",
+              "MERA_PREC_SPLIT_BF16": "PREC_SPLIT_BF16"}.get(name, name)
+        assert getattr(gm, py) == val, name
+
+
+def test_mps_footprint(lib):
+    """mera_footprint_bytes for a uniform MPS (network = MERA_MPS): positive,
+    growing like the D^2 d^2 two-site buffers and the tangent lists, doubled by
+    complex data, and 0 for what the MPS path does not serve (transition
+    layers, mixed precision, Stiefel, a one-dimensional site)."""
+    from paper_2007_03638_gb300 import mera as gm
+
+    def fp(d, D, n_trans=0, **kw):
+        return gm.footprint_bytes(gm.default_config(d, D, n_trans, network=gm.MERA_MPS, **kw))
+
+    small, big = fp(2, 8), fp(2, 64)
+    assert 0 < small < big
+    # at D = 64, d = 2 the (D d d D) buffers, the Krylov vectors and 2m + 10
+    # tensors of D d D reals dominate: within a factor 2 of that count
+    D, d, k, m = 64, 2, 20, 8
+    est = 8 * (3 * D * d * d * D + (k + 4) * D * D + (2 * m + 10) * D * d * D)
+    assert est < big < 2 * est
+    assert 1.8 * big < fp(2, 64, dtype=gm.MERA_C128) < 4.2 * big
+    assert fp(3, 1) > 0
+    assert fp(2, 8, n_trans=1) == 0
+    assert fp(2, 8, prec=gm.PREC_SPLIT_BF16) == 0
+    assert fp(2, 8, w_stiefel=1) == 0
+    assert fp(1, 8) == 0

@@ -10,24 +10,8 @@ from oracle import optim as oo
 from paper_2007_03638_gb300 import inputs as inp
 
 
-def _aklt():
-    """AKLT (spin 1, D = 2) in left-canonical form and its bond term
-    S.S + (S.S)^2/3 (= 2 P_2 - 2/3, P_2 the projector on total spin 2)."""
-    sp = np.array([[0.0, 1.0], [0.0, 0.0]])
-    A = np.zeros((2, 3, 2))
-    A[:, 0, :] = np.sqrt(2.0 / 3.0) * sp            # m = +1
-    A[:, 1, :] = -np.sqrt(1.0 / 3.0) * np.diag([1.0, -1.0])
-    A[:, 2, :] = -np.sqrt(2.0 / 3.0) * sp.T         # m = -1
-    s = 1.0 / np.sqrt(2.0)
-    Sx = s * np.array([[0, 1, 0], [1, 0, 1], [0, 1, 0]], dtype=complex)
-    Sy = s * np.array([[0, -1j, 0], [1j, 0, -1j], [0, 1j, 0]])
-    Sz = np.diag([1.0, 0.0, -1.0]).astype(complex)
-    SS = np.real(np.kron(Sx, Sx) + np.kron(Sy, Sy) + np.kron(Sz, Sz))
-    return A, SS + SS @ SS / 3.0
-
-
 def test_aklt_is_an_exact_ground_state():
-    A, h = _aklt()
+    A, h = inp.aklt_mps()
     M = mps.as_matrix(A)
     assert np.abs(M.T @ M - np.eye(2)).max() < 1e-14          # left-canonical
     e, D, rho = mps.energy_grad(A, h)

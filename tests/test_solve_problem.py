@@ -1,6 +1,6 @@
 """Host-side set-up of the optimisation program solve.py (no GPU): the binary network on
-blocked sites with a three-site term, the ternary network on spins with a
-two-site term, Z2-symmetric ternary starting points."""
+blocked sites with a three-site term, the ternary network and the uniform MPS
+on spins with a two-site term, Z2-symmetric ternary starting points."""
 import numpy as np
 import pytest
 
@@ -27,3 +27,13 @@ def test_ternary_z2_problem_is_the_figure_2_setting():
 def test_z2_needs_the_ternary_network():
     with pytest.raises(ValueError):
         solve.problem("ising", 1.0, 8, 3, z2=True)
+
+
+def test_mps_problem():
+    h, d_b, tensors, spins = solve.problem("xxz", 1.0, 12, 0, network="mps")
+    assert (h.shape, d_b, spins, len(tensors)) == ((4, 4), 2, 1, 1)
+    A = tensors[0]
+    assert A.shape == (24, 12)
+    assert np.abs(A.T @ A - np.eye(12)).max() < 1e-13
+    with pytest.raises(ValueError):
+        solve.problem("ising", 1.0, 8, 0, network="mps", z2=True)
