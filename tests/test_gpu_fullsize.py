@@ -1,0 +1,73 @@
+"""The benchmark workload at full size on the GPU (XXZ Delta = 1, chi = 32, three
+transition layers, split-BF16, the launch configuration bench.py times), checked
+through properties that hold at any size, since the oracle cannot evaluate a
+chi = 32 network:
+
+* repeatability: two evaluations at the same point give bit-identical energy and
+  gradient (every reduction runs in a fixed order; split-K slices and cluster
+  products must not race);
+* tangency: W^dag G = 0 for the Grassmann isometries, W^dag G skew for the
+  disentanglers (Eqs. stiefel_gradient, grassmann_gradient);
+* the variational bound: the energy per spin lies above the exact ground-state
+  energy 1 - 4 ln 2 of the Heisenberg chain (Pauli convention);
+* the gradient is the derivative of the energy: a central difference of the
+  energy along the retraction in the direction -G/|G| matches -|G| within the
+  mixed-precision noise;
+* the retracted point is isometric to rounding.
+"""
+import numpy as np
+import pytest
+
+from paper_2007_03638_gb300 import inputs as inp
+
+pytestmark = [pytest.mark.gpu_pending, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def problem():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03638_gb300 import build as b
+    b.build()
+    from paper_2007_03638_gb300 import mera as gm
+    chi, L = 32, 3
+    h3 = inp.three_site_blocked(inp.xxz_bond(1.0))
+    cfg = gm.default_config(4, chi, L, prec=gm.PREC_SPLIT_BF16, lbfgs_m=16, krylov_dim=4)
+    m = gm.Mera(cfg, h3)
+    us, ws = inp.random_mera(4, chi, L, seed=0)
+    point = [t for p in zip(us, ws) for t in p]
+    m.set_tensors(point)
+    yield m, point
+    m.close()
+
+
+def test_fullsize_properties(problem):
+    m, point = problem
+    e0, G = m.energy_grad()
+    e1, G1 = m.energy_grad()
+    assert e0 == e1
+    for a, b in zip(G, G1):
+        assert np.array_equal(a, b)
+    gn = np.sqrt(sum(float(np.sum(g * g)) for g in G))
+    assert np.isfinite(gn) and gn > 0
+    for i, (W, g) in enumerate(zip(point, G)):
+        S = W.T @ g
+        if i % 2 == 0:
+            assert np.abs(S + S.T).max() < 1e-10 * gn, i
+        else:
+            assert np.abs(S).max() < 1e-10 * gn, i
+    assert e0 / 2 > inp.EXACT_XXZ_DELTA1
+    X = [-g / gn for g in G]
+    alpha = 0.02
+    e = {}
+    for a in (alpha, -alpha):
+        m.set_tensors(point)
+        m.retract(X, a)
+        e[a] = m.energy_only()
+        if a > 0:
+            for W in m.get_tensors():
+                assert np.abs(W.T @ W - np.eye(W.shape[1])).max() < 1e-12
+    fd = (e[alpha] - e[-alpha]) / (2 * alpha)
+    assert abs(fd + gn) < 0.05 * gn + 1e-3, (fd, -gn)
+    m.set_tensors(point)
