@@ -164,6 +164,7 @@ struct mera_ctx {
   double hshift = 0.0;                    // evaluations use h3 - hshift 1 (Evenbly-Vidal sweeps)
   bool tern = false;                      // ternary network
   bool mps = false;                       // uniform MPS (one Grassmann tensor, two-site term)
+  bool z2 = false;                        // Z2-symmetric ternary problem: networks run by charge sector
   int ns = 3;                             // sites of a level operator (3 binary, 2 ternary)
   int rs = 1;                             // reals per element (1 or 2)
   int L = 0, nt = 0;
@@ -271,7 +272,7 @@ void build_layers_ternary(Ctx& c) {
     ly.cf = c.dims[l];
     ly.cc = l < c.L ? c.dims[l + 1] : c.dims[l];
     for (int sd = 0; sd < 3; ++sd) {
-      ly.tnet[sd] = std::make_unique<Net>(ternary_netdef("LCR"[sd]), ly.cf, ly.cc, c.pool);
+      ly.tnet[sd] = std::make_unique<Net>(ternary_netdef("LCR"[sd]), ly.cf, ly.cc, c.pool, c.z2);
       Net& net = *ly.tnet[sd];
       NetBufs& b = ly.tbuf[sd];
       b.leaf.assign(net.nleaf(), nullptr);
@@ -285,6 +286,10 @@ void build_layers_ternary(Ctx& c) {
         ly.town[sd].emplace_back(es * net.size(node));
         b.adj[node] = P(ly.town[sd].back());
       }
+      // charge sectors leave the odd-charge entries of node buffers untouched
+      // (and never read them): keep those at zero
+      if (c.z2)
+        for (DevBuf& db : ly.town[sd]) MERA_CUDA(cudaMemsetAsync(db.p, 0, db.bytes, c.s));
       b.f32 = mixed;
       b.cplx = c.cplx;
       b.ex = &c.ex;
@@ -1590,6 +1595,54 @@ void create_mps(Ctx& c, int64_t* nS, int64_t* gmax) {
 void create_mera(Ctx& c, int64_t* nS, int64_t* gmax);
 void finish_create(Ctx& c, cudaStream_t s);
 
+// Z2 symmetry of a (rows x cols) matrix on the device whose rows (columns)
+// are index tuples of legs with dimensions rdims (cdims), row-major: every
+// entry between a row and a column of different total charge (the legs'
+// gradings summed, first half of each leg even) must be below 1e-12 of the
+// largest entry (Sec. 6); MERA_ERR_ARG otherwise.
+void check_z2(Ctx& c, const double* dev, const std::vector<int64_t>& rdims, const std::vector<int64_t>& cdims,
+              const std::string& what, cudaStream_t s) {
+  auto charges = [](const std::vector<int64_t>& dims) {
+    int64_t n = 1;
+    for (int64_t e : dims) n *= e;
+    std::vector<int> ch(n, 0);
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t r = i;
+      for (size_t j = dims.size(); j-- > 0;) {
+        ch[i] ^= z2_charge(r % dims[j], dims[j]);
+        r /= dims[j];
+      }
+    }
+    return ch;
+  };
+  const std::vector<int> cr = charges(rdims), cc = charges(cdims);
+  const int64_t R = (int64_t)cr.size(), C = (int64_t)cc.size();
+  std::vector<double> h((size_t)(R * C * c.rs));
+  MERA_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+  double big = 0.0, bad = 0.0;
+  for (int64_t r = 0; r < R; ++r)
+    for (int64_t k = 0; k < C; ++k) {
+      const double* e = h.data() + (r * C + k) * c.rs;
+      const double mag = c.cplx ? std::hypot(e[0], e[1]) : std::fabs(e[0]);
+      big = std::max(big, mag);
+      if (cr[r] != cc[k]) bad = std::max(bad, mag);
+    }
+  if (!(bad <= 1e-12 * big))
+    throw Error(MERA_ERR_ARG, what + " is not Z2-symmetric (entry " + std::to_string(bad) +
+                                  " between different charges)");
+}
+
+// Z2 symmetry of every tensor of a ternary point: u_l (cf cf) x (cf cf),
+// w_l (cf cf cf) x (cc).
+void check_z2_point(Ctx& c, const double* W, cudaStream_t s) {
+  for (int l = 0; l <= c.L; ++l) {
+    const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    check_z2(c, W + c.offs[2 * l], {cf, cf}, {cf, cf}, "u_" + std::to_string(l), s);
+    check_z2(c, W + c.offs[2 * l + 1], {cf, cf, cf}, {cc}, "w_" + std::to_string(l), s);
+  }
+}
+
 void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.cfg = cfg;
   c.s = s;
@@ -1602,6 +1655,9 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     throw Error(MERA_ERR_ARG, "unknown network");
   c.tern = cfg.network == MERA_TERNARY;
   c.mps = cfg.network == MERA_MPS;
+  if (cfg.z2 != 0 && cfg.z2 != 1) throw Error(MERA_ERR_ARG, "z2 must be 0 or 1");
+  c.z2 = cfg.z2 == 1;
+  if (c.z2 && !c.tern) throw Error(MERA_ERR_UNSUPPORTED, "Z2 charge sectors are built for the ternary network");
   c.ns = c.tern || c.mps ? 2 : 3;
   c.pool.set_stream(s);
   int64_t nS = 0, gmax = 1;  // reals of one Krylov vector; elements of a geometry temporary
@@ -1615,6 +1671,10 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.Wtry.alloc(tb);
   c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 2 * c.ns) * c.rs);
   MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
+  if (c.z2) {
+    const std::vector<int64_t> pair{cfg.d_b, cfg.d_b};
+    check_z2(c, P(c.h0), pair, pair, "the Hamiltonian term", s);
+  }
   c.x.alloc(sizeof(double) * nS);
   c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));
   c.ktmp.alloc(sizeof(double) * nS);
@@ -1776,6 +1836,7 @@ void mera_config_default(mera_config* c, int d_b, int chi, int n_trans) {
   c->lbfgs_m = 8;
   c->b_chunk = 0;
   c->network = MERA_BINARY;
+  c->z2 = 0;
 }
 
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out) {
@@ -1813,6 +1874,7 @@ int mera_set_tensors(mera_t m, const void* const* t) {
   return wrap(m, [&] {
     copy_in(m, t, mera::P(m->Wtry));
     mera::check_isometric(*m, mera::P(m->Wtry), m->s);
+    if (m->z2) mera::check_z2_point(*m, mera::P(m->Wtry), m->s);
     std::swap(m->Wcur, m->Wtry);
     m->ev[0].valid = m->ev[1].valid = false;
     mera::clear_history(*m);
@@ -1997,6 +2059,7 @@ size_t footprint_ternary(const mera_config* cfg) {
 
 size_t mera_footprint_bytes(const mera_config* cfg) {
   if (!cfg) return 0;
+  if (cfg->z2 != 0 && (cfg->z2 != 1 || cfg->network != MERA_TERNARY)) return 0;
   if (cfg->network == MERA_MPS) return footprint_mps(cfg);
   if (cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
   if (cfg->network == MERA_TERNARY) {

@@ -66,52 +66,6 @@ bool group_offsets(const std::vector<int64_t>& ext, const std::vector<int64_t>& 
   return true;
 }
 
-void set_group(const TDesc& t, const std::vector<int>& legs, TablePool& pool, const int64_t** tab,
-               int64_t* stride, int64_t* count) {
-  std::vector<int64_t> ext, str;
-  int64_t n = 1;
-  for (int l : legs) {
-    int j = t.find(l);
-    ext.push_back(t.ext[j]);
-    str.push_back(t.stride[j]);
-    n *= t.ext[j];
-  }
-  std::vector<int64_t> offs;
-  int64_t s = 0;
-  if (group_offsets(ext, str, offs, &s)) {
-    *tab = pool.get(offs);
-    *stride = 0;
-  } else {
-    *tab = nullptr;
-    *stride = s;
-  }
-  *count = n;
-}
-
-// Offsets of every index of a leg group (odometer over the group's legs, last fastest).
-std::vector<int64_t> all_offsets(const TDesc& t, const std::vector<int>& legs) {
-  std::vector<int64_t> ext, str;
-  int64_t n = 1;
-  for (int l : legs) {
-    const int j = t.find(l);
-    ext.push_back(t.ext[j]);
-    str.push_back(t.stride[j]);
-    n *= t.ext[j];
-  }
-  std::vector<int64_t> out(n);
-  std::vector<int64_t> idx(ext.size(), 0);
-  int64_t o = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    out[i] = o;
-    for (size_t j = ext.size(); j-- > 0;) {
-      if (++idx[j] < ext[j]) { o += str[j]; break; }
-      o -= str[j] * (ext[j] - 1);
-      idx[j] = 0;
-    }
-  }
-  return out;
-}
-
 // off(i) = off(i - i % r) + i % r for every i
 bool runs_of(const std::vector<int64_t>& off, int64_t r) {
   for (size_t i = 0; i < off.size(); ++i)
@@ -129,7 +83,72 @@ TDesc make_desc(const std::vector<int>& legs, const std::vector<int64_t>& ext) {
 }
 }  // namespace
 
-GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool) {
+std::vector<int64_t> sector_offsets(const TDesc& t, const std::vector<int>& legs, int q) {
+  std::vector<int64_t> ext, str;
+  int64_t n = 1;
+  for (int l : legs) {
+    const int j = t.find(l);
+    if (j < 0) throw Error(MERA_ERR_ARG, "sector_offsets: leg not in the tensor");
+    ext.push_back(t.ext[j]);
+    str.push_back(t.stride[j]);
+    n *= t.ext[j];
+  }
+  std::vector<int64_t> out;
+  out.reserve(q < 0 ? n : n / 2 + 1);
+  std::vector<int64_t> idx(ext.size(), 0);
+  int64_t o = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int ch = 0;
+    for (size_t j = 0; j < ext.size(); ++j) ch ^= z2_charge(idx[j], ext[j]);
+    if (q < 0 || ch == q) out.push_back(o);
+    for (size_t j = ext.size(); j-- > 0;) {
+      if (++idx[j] < ext[j]) { o += str[j]; break; }
+      o -= str[j] * (ext[j] - 1);
+      idx[j] = 0;
+    }
+  }
+  return out;
+}
+
+namespace {
+// Dense group: a table, or an affine stride (the tables the dense path has
+// always used).
+HostGroup dense_group(const TDesc& t, const std::vector<int>& legs) {
+  std::vector<int64_t> ext, str;
+  HostGroup g;
+  g.count = 1;
+  for (int l : legs) {
+    const int j = t.find(l);
+    ext.push_back(t.ext[j]);
+    str.push_back(t.stride[j]);
+    g.count *= t.ext[j];
+  }
+  int64_t s = 0;
+  if (!group_offsets(ext, str, g.table, &s)) {
+    g.table.clear();
+    g.stride = s;
+  }
+  return g;
+}
+
+HostGroup sector_group(const TDesc& t, const std::vector<int>& legs, int q) {
+  HostGroup g;
+  g.table = sector_offsets(t, legs, q);
+  g.count = (int64_t)g.table.size();
+  return g;
+}
+
+const int64_t* upload(const HostGroup& g, TablePool& pool, int64_t* stride) {
+  if (g.table.empty()) {
+    *stride = g.stride;
+    return nullptr;
+  }
+  *stride = 0;
+  return pool.get(g.table);
+}
+}  // namespace
+
+HostPlan host_plan(const TDesc& A, const TDesc& B, const TDesc& C, int q) {
   std::vector<int> M, N, K;
   for (int l : C.legs) {
     const bool inA = A.find(l) >= 0, inB = B.find(l) >= 0;
@@ -143,19 +162,23 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
     }
   for (int l : A.legs)
     if (C.find(l) < 0 && B.find(l) < 0) throw Error(MERA_ERR_ARG, "make_plan: dangling leg in A");
-  GemmPlan p;
-  GettCall& g = p.proto;
-  int64_t m, n, k, m2, n2, k2;
-  set_group(A, M, pool, &g.a.t0, &g.a.s0, &m);
-  set_group(A, K, pool, &g.a.t1, &g.a.s1, &k);
-  set_group(B, K, pool, &g.b.t0, &g.b.s0, &k2);
-  set_group(B, N, pool, &g.b.t1, &g.b.s1, &n);
-  set_group(C, M, pool, &g.c.t0, &g.c.s0, &m2);
-  set_group(C, N, pool, &g.c.t1, &g.c.s1, &n2);
-  if (m != m2 || n != n2 || k != k2) throw Error(MERA_ERR_ARG, "make_plan: extent mismatch");
-  g.M = m;
-  g.N = n;
-  g.K = k;
+  HostPlan h;
+  auto grp = [&](const TDesc& t, const std::vector<int>& legs) {
+    return q < 0 ? dense_group(t, legs) : sector_group(t, legs, q);
+  };
+  h.am = grp(A, M);
+  h.ak = grp(A, K);
+  h.bk = grp(B, K);
+  h.bn = grp(B, N);
+  h.cm = grp(C, M);
+  h.cn = grp(C, N);
+  if (h.am.count != h.cm.count || h.bn.count != h.cn.count || h.ak.count != h.bk.count)
+    throw Error(MERA_ERR_ARG, "make_plan: extent mismatch");
+  h.M = h.am.count;
+  h.N = h.bn.count;
+  h.K = h.ak.count;
+  if (q >= 0 && h.M > 0 && h.N > 0 && h.K == 0)
+    throw Error(MERA_ERR_UNSUPPORTED, "make_plan: a charge sector with outputs but no summed index");
   // orientation hints for operand packing: where is each operand's stride-1 leg?
   auto fast_leg = [](const TDesc& t) {
     int best = -1;
@@ -164,10 +187,10 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
     return best < 0 ? -1 : t.legs[best];
   };
   const int fa = fast_leg(A), fb = fast_leg(B);
-  g.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
-  g.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
+  h.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
+  h.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
   // output layout hints (see GettCall), for C = A B and for C^T = B^T A^T
-  const std::vector<int64_t> om = all_offsets(C, M), on = all_offsets(C, N);
+  const std::vector<int64_t> om = sector_offsets(C, M, q), on = sector_offsets(C, N, q);
   auto vec_of = [](const std::vector<int64_t>& rows, const std::vector<int64_t>& cols) {
     for (int64_t v : {8, 4}) {
       if ((int64_t)cols.size() % v || !runs_of(cols, v)) continue;
@@ -178,11 +201,36 @@ GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& po
     }
     return 1;
   };
-  g.c_rows = runs_of(om, 32);
-  g.c_vec = vec_of(om, on);
-  g.c_rows_t = runs_of(on, 32);
-  g.c_vec_t = vec_of(on, om);
+  h.c_rows = runs_of(om, 32);
+  h.c_vec = vec_of(om, on);
+  h.c_rows_t = runs_of(on, 32);
+  h.c_vec_t = vec_of(on, om);
+  return h;
+}
+
+GemmPlan upload_plan(const HostPlan& h, TablePool& pool) {
+  GemmPlan p;
+  GettCall& g = p.proto;
+  g.a.t0 = upload(h.am, pool, &g.a.s0);
+  g.a.t1 = upload(h.ak, pool, &g.a.s1);
+  g.b.t0 = upload(h.bk, pool, &g.b.s0);
+  g.b.t1 = upload(h.bn, pool, &g.b.s1);
+  g.c.t0 = upload(h.cm, pool, &g.c.s0);
+  g.c.t1 = upload(h.cn, pool, &g.c.s1);
+  g.M = h.M;
+  g.N = h.N;
+  g.K = h.K;
+  g.a_rfast = h.a_rfast;
+  g.b_rfast = h.b_rfast;
+  g.c_rows = h.c_rows;
+  g.c_vec = h.c_vec;
+  g.c_rows_t = h.c_rows_t;
+  g.c_vec_t = h.c_vec_t;
   return p;
+}
+
+GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool, int q) {
+  return upload_plan(host_plan(A, B, C, q), pool);
 }
 
 // N1..N10 children (node ids).

@@ -46,7 +46,41 @@ struct GemmPlan {
   GettCall proto;  // tables/strides/sizes; data pointers filled at run time
   double flops() const { return 2.0 * proto.M * proto.N * proto.K; }
 };
-GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool);
+
+// Z2 grading of a leg of extent e: index i has charge 1 iff i >= ceil(e/2)
+// (the first half of a leg's basis even); a tuple of indices has the sum of
+// its legs' charges mod 2.
+inline int z2_charge(int64_t i, int64_t e) { return i >= (e + 1) / 2 ? 1 : 0; }
+
+// Offsets in t's storage of the index tuples of the leg group `legs`
+// (odometer order, last leg fastest); q >= 0 keeps only the tuples of Z2
+// charge q, q < 0 keeps all.
+std::vector<int64_t> sector_offsets(const TDesc& t, const std::vector<int>& legs, int q);
+
+// The index bookkeeping of one contraction on the host, before upload.
+// Groups: M = legs of C from A, N = legs of C from B (in C's order), K = legs
+// shared by A and B (in B's order).  A group is addressed by a table of
+// offsets, or (affine) by index * stride.  q < 0: the dense contraction
+// (affine groups detected); q = 0 or 1: the Z2 charge sector q, in which every
+// group keeps its tuples of charge q (always tables).  For Z2-symmetric A and
+// B (every entry of total charge 1 zero), C = A B is the sum of the two
+// sectors, each writing only C's entries whose M and N tuples have charge q;
+// the sectors hold a quarter of the dense multiply-adds.
+struct HostGroup {
+  std::vector<int64_t> table;  // empty when affine
+  int64_t stride = 0;
+  int64_t count = 0;
+};
+struct HostPlan {
+  int64_t M = 0, N = 0, K = 0;
+  HostGroup am, ak, bk, bn, cm, cn;
+  int a_rfast = 0, b_rfast = 0;
+  int c_rows = 0, c_vec = 1, c_rows_t = 0, c_vec_t = 1;  // output layout hints of GettCall
+};
+HostPlan host_plan(const TDesc& A, const TDesc& B, const TDesc& C, int q = -1);
+GemmPlan upload_plan(const HostPlan& h, TablePool& pool);
+// host_plan + upload_plan
+GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool, int q = -1);
 
 // Ascending network of one side (A_L or A_R) of one layer.  Node numbering:
 // 0..10 leaves (0 = operator; 1,3 = conj u; 2,5 = u; 4,7,9 = conj w;

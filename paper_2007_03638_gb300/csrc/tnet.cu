@@ -54,9 +54,24 @@ TDesc desc_of(const std::vector<int>& legs, const std::vector<int64_t>& ext) {
   for (size_t j = legs.size(); j-- > 1;) d.stride[j - 1] = d.stride[j] * ext[j];
   return d;
 }
+
+// The dense plan of a product, or its nonempty Z2 charge sectors.
+PlanSet plans_of(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool, bool z2) {
+  PlanSet ps;
+  if (!z2) {
+    ps.p[0] = make_plan(A, B, C, pool);
+    ps.n = 1;
+    return ps;
+  }
+  for (int q = 0; q < 2; ++q) {
+    const HostPlan h = host_plan(A, B, C, q);
+    if (h.M > 0 && h.N > 0) ps.p[ps.n++] = upload_plan(h, pool);
+  }
+  return ps;
+}
 }  // namespace
 
-Net::Net(const NetDef& d, int64_t cf, int64_t cc, TablePool& pool) {
+Net::Net(const NetDef& d, int64_t cf, int64_t cc, TablePool& pool, bool z2) {
   nleaf_ = (int)d.legs.size();
   nnode_ = nleaf_ + (int)d.kids.size();
   kids_ = d.kids;
@@ -112,47 +127,48 @@ Net::Net(const NetDef& d, int64_t cf, int64_t cc, TablePool& pool) {
   const TDesc opadj = desc_of(legs_of(d.op_adj, e2), e2);
   for (int k = 0; k < (int)kids_.size(); ++k) {
     const int node = nleaf_ + k, l = kids_[k][0], r = kids_[k][1];
-    fwd_.push_back(make_plan(desc_[l], desc_[r], desc_[node], pool));
+    fwd_.push_back(plans_of(desc_[l], desc_[r], desc_[node], pool, z2));
     const TDesc& dn = node == root() ? seed : desc_[node];
-    bwdl_.push_back(make_plan(dn, desc_[r], l == 0 ? opadj : desc_[l], pool));
-    bwdr_.push_back(make_plan(desc_[l], dn, r == 0 ? opadj : desc_[r], pool));
+    bwdl_.push_back(plans_of(dn, desc_[r], l == 0 ? opadj : desc_[l], pool, z2));
+    bwdr_.push_back(plans_of(desc_[l], dn, r == 0 ? opadj : desc_[r], pool, z2));
   }
 }
 
 std::vector<const GemmPlan*> Net::plans() const {
   std::vector<const GemmPlan*> out;
-  for (size_t k = 0; k < fwd_.size(); ++k) {
-    out.push_back(&fwd_[k]);
-    out.push_back(&bwdl_[k]);
-    out.push_back(&bwdr_[k]);
-  }
+  for (size_t k = 0; k < fwd_.size(); ++k)
+    for (const PlanSet* ps : {&fwd_[k], &bwdl_[k], &bwdr_[k]})
+      for (int i = 0; i < ps->n; ++i) out.push_back(&ps->p[i]);
   return out;
 }
 
 namespace {
 constexpr int EXT = -1;  // operator input/output, seed, root output, environment accumulators: double
 
-// One plan: node operands (internal nodes float in mixed mode, conjugated
-// u/w leaves read conjugated for complex data).
-void nrun(const Net& net, const NetBufs& b, const GemmPlan& p, const double* A, int an, const double* B, int bn,
+// One product (its dense plan or each charge sector): node operands (internal
+// nodes float in mixed mode, conjugated u/w leaves read conjugated for
+// complex data).
+void nrun(const Net& net, const NetBufs& b, const PlanSet& ps, const double* A, int an, const double* B, int bn,
           double* C, int cn, double alpha, double beta, cudaStream_t s) {
   auto internal = [&](int n) { return n >= net.nleaf() && n != EXT; };
   auto conj = [&](int n) {
     return n >= 0 && n < net.nleaf() && (net.role(n) == ROLE_UB || net.role(n) == ROLE_WB);
   };
-  GettCall g = p.proto;
-  g.A = A;
-  g.B = B;
-  g.C = C;
-  g.alpha = alpha;
-  g.beta = beta;
-  g.a32 = b.f32 && internal(an);
-  g.b32 = b.f32 && internal(bn);
-  g.c32 = b.f32 && internal(cn);
-  g.cplx = b.cplx;
-  g.a_conj = b.cplx && conj(an);
-  g.b_conj = b.cplx && conj(bn);
-  contract(g, *b.ex, s);
+  for (int i = 0; i < ps.n; ++i) {
+    GettCall g = ps.p[i].proto;
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.a32 = b.f32 && internal(an);
+    g.b32 = b.f32 && internal(bn);
+    g.c32 = b.f32 && internal(cn);
+    g.cplx = b.cplx;
+    g.a_conj = b.cplx && conj(an);
+    g.b_conj = b.cplx && conj(bn);
+    contract(g, *b.ex, s);
+  }
 }
 
 const double* value(const Net& net, const NetBufs& b, int node) {

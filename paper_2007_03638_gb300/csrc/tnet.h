@@ -1,5 +1,8 @@
 // A tensor network given as data: leaves with named legs and roles, and a
-// pairwise contraction tree.  Used for the ternary MERA's three ascending
+// pairwise contraction tree.  With z2 set, every leg carries the Z2 grading of
+// tn.h (first half of its basis even) and every pairwise product runs as its
+// two charge sectors (a quarter of the dense work), which is exact when the
+// leaves and the seed are Z2-symmetric.  Used for the ternary MERA's three ascending
 // networks (the binary network has its own sliced executor, tn.h).  One
 // forward pass evaluates the ascended operator; one reverse pass seeded with
 // the density matrix gives the descended operator (the adjoint of the
@@ -28,10 +31,17 @@ struct NetDef {
 // The ternary MERA's networks A_L, A_C, A_R (side 'L', 'C', 'R').
 NetDef ternary_netdef(char side);
 
+// The plans of one pairwise product: the dense plan, or its nonempty Z2
+// charge sectors.
+struct PlanSet {
+  GemmPlan p[2];
+  int n = 0;
+};
+
 class Net {
  public:
   // Coarse legs (a b c A B C) have extent cc, all others cf.
-  Net(const NetDef& d, int64_t cf, int64_t cc, TablePool& pool);
+  Net(const NetDef& d, int64_t cf, int64_t cc, TablePool& pool, bool z2 = false);
   int nleaf() const { return nleaf_; }
   int nnode() const { return nnode_; }
   int root() const { return nnode_ - 1; }
@@ -41,9 +51,9 @@ class Net {
   // true: the node's value does not involve the operator leaf (computed once per point)
   bool fixed(int node) const { return fixed_[node]; }
   int64_t size(int node) const { return desc_[node].size(); }
-  const GemmPlan& fwd(int node) const { return fwd_[node - nleaf_]; }
-  const GemmPlan& bwd_left(int node) const { return bwdl_[node - nleaf_]; }
-  const GemmPlan& bwd_right(int node) const { return bwdr_[node - nleaf_]; }
+  const PlanSet& fwd(int node) const { return fwd_[node - nleaf_]; }
+  const PlanSet& bwd_left(int node) const { return bwdl_[node - nleaf_]; }
+  const PlanSet& bwd_right(int node) const { return bwdr_[node - nleaf_]; }
   std::vector<const GemmPlan*> plans() const;
 
  private:
@@ -52,7 +62,7 @@ class Net {
   std::vector<int> role_;
   std::vector<bool> fixed_;
   std::vector<TDesc> desc_;
-  std::vector<GemmPlan> fwd_, bwdl_, bwdr_;
+  std::vector<PlanSet> fwd_, bwdl_, bwdr_;
 };
 
 // Buffers of one network for one layer: leaves (double), internal node

@@ -37,7 +37,8 @@ class Config(C.Structure):
     _fields_ = [("d_b", C.c_int), ("chi", C.c_int), ("n_trans", C.c_int), ("dtype", C.c_int),
                 ("prec", C.c_int), ("w_stiefel", C.c_int), ("precond", C.c_int),
                 ("krylov_dim", C.c_int), ("krylov_maxiter", C.c_int), ("krylov_tol", C.c_double),
-                ("recompute_env", C.c_int), ("lbfgs_m", C.c_int), ("b_chunk", C.c_int), ("network", C.c_int)]
+                ("recompute_env", C.c_int), ("lbfgs_m", C.c_int), ("b_chunk", C.c_int), ("network", C.c_int),
+                ("z2", C.c_int)]
 
 
 class IterInfo(C.Structure):

@@ -38,7 +38,8 @@ def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
     """(h, d_b, tensors, spins per bottom site) of a run: the binary network on
     blocked sites (two spins, three-site term), the ternary one and the uniform
     MPS (bond dimension chi, n_trans unused) on spins (two-site term); z2:
-    Z2-symmetric ternary starting point."""
+    Z2-symmetric ternary starting point (run() then sets the library's Z2
+    mode, which contracts by charge sector)."""
     bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
     if network == "mps":
         if z2:
@@ -63,7 +64,7 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
     h3, d_b, tensors, spins = problem(model, par, chi, n_trans, network, z2, seed)
     net = {"binary": gm.MERA_BINARY, "ternary": gm.MERA_TERNARY, "mps": gm.MERA_MPS}[network]
     cfg = gm.default_config(d_b, chi, 0 if network == "mps" else n_trans, prec=prec, lbfgs_m=lbfgs_m,
-                            krylov_dim=krylov_dim, network=net)
+                            krylov_dim=krylov_dim, network=net, z2=int(z2))
     m = gm.Mera(cfg, h3)
     m.set_tensors(tensors)
     ex = exact_energy(model, par)
@@ -103,7 +104,8 @@ def main():
     ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16")
     ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev"])
     ap.add_argument("--network", default="binary", choices=["binary", "ternary", "mps"])
-    ap.add_argument("--z2", action="store_true", help="Z2-symmetric starting point (ternary network)")
+    ap.add_argument("--z2", action="store_true",
+                    help="Z2-symmetric problem (ternary network): symmetric starting point, contractions by charge sector")
     ap.add_argument("--ev-gamma", type=float, default=None,
                     help="Evenbly-Vidal Hamiltonian shift (default: largest eigenvalue of the 3-site term + 0.5)")
     ap.add_argument("--iters", type=int, default=300)
