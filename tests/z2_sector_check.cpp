@@ -8,6 +8,8 @@
 // host loop of the GETT definition
 //   C[cm[m] + cn[n]] = sum_k A[am[m] + ak[k]] B[bk[k] + bn[n]]  (+ beta C)
 // and checks that
+//   * the dense plan reproduces the definition (a sum over every assignment of
+//     the legs);
 //   * the two sector plans together reproduce the dense result entry by entry,
 //     and the dense result is itself symmetric;
 //   * the sectors write disjoint entries, exactly the entries of even charge;
@@ -138,6 +140,31 @@ int main() {
     std::vector<double> cd(C.size(), NAN), cs(C.size(), 0.0);
     std::vector<int> touched(C.size(), 0);
     apply(hd, a, b, cd, nullptr);
+    // the dense plan against the definition: a sum over every assignment of the legs
+    {
+      const int nl = nm + nk + nn;
+      std::vector<double> cref(C.size(), 0.0);
+      std::vector<int64_t> idx(nl, 0);
+      int64_t total = 1;
+      for (int64_t e : ext) total *= e;
+      auto at = [&](const TDesc& t) {
+        int64_t o = 0;
+        for (size_t j = 0; j < t.legs.size(); ++j) o += idx[t.legs[j]] * t.stride[j];
+        return o;
+      };
+      for (int64_t i = 0; i < total; ++i) {
+        cref[at(C)] += a[at(A)] * b[at(B)];
+        for (int j = nl; j-- > 0;) {
+          if (++idx[j] < ext[j]) break;
+          idx[j] = 0;
+        }
+      }
+      for (int64_t x = 0; x < C.size(); ++x)
+        if (std::fabs(cref[x] - cd[x]) > 1e-13 * (1.0 + std::fabs(cref[x]))) {
+          std::printf("trial %d: dense plan differs from the definition at %lld\n", trial, (long long)x);
+          return 1;
+        }
+    }
     const HostPlan h0 = mera::host_plan(A, B, C, 0), h1 = mera::host_plan(A, B, C, 1);
     apply(h0, a, b, cs, &touched);
     apply(h1, a, b, cs, &touched);
