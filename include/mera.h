@@ -31,9 +31,11 @@
  * Tangent vectors, partial derivatives and gradients use the same shapes.
  * mera_tensor_shape() reports them.  Element type: double (MERA_F64) or
  * interleaved complex double (MERA_C128: real part first, the layout of C99
- * double _Complex).  Complex problems (a Hamiltonian or tensors with
- * imaginary parts) run with prec = MERA_PREC_FP64 only; mera_create returns
- * MERA_ERR_UNSUPPORTED for a complex problem in a mixed-precision mode.  For
+ * double _Complex).  In a mixed-precision mode every complex contraction
+ * of the MERA networks runs as four real tensor-core products of the real
+ * and imaginary parts (Re C = Re A Re B - Im A Im B, Im C = Re A Im B +
+ * Im A Re B; conjugated operands by sign), the rest in FP64 as for real
+ * data (the MPS serves FP64 only, see MERA_MPS).  For
  * complex data the inner product of the tangent space is Re Tr(X^dag Y) and
  * the projections, retractions and preconditioner use conjugate transposes
  * where the real case has transposes (Sec. 2.3, Sec. 3).

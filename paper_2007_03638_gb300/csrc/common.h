@@ -123,6 +123,12 @@ struct GettCall {
   // the same hints for the transposed product C^T = B^T A^T (roles of the
   // M and N groups exchanged)
   int c_rows_t = 0, c_vec_t = 1;
+  // Real view of complex operands, for the tensor-core path: the same groups
+  // addressed in reals (the real part of element e at 2e, the imaginary part
+  // at 2e + 1) and that view's output hints; has_rv = 0 when the plan has none.
+  GettOperand ar, br, cr;
+  int cr_rows = 0, cr_vec = 1, cr_rows_t = 0, cr_vec_t = 1;
+  int has_rv = 0;
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 

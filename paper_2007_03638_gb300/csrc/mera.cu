@@ -1690,8 +1690,9 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
 void create_mera(Ctx& c, int64_t* nS, int64_t* gmax) {
   const mera_config& cfg = c.cfg;
   if (cfg.d_b < 2 || cfg.chi < 2 || cfg.n_trans < 1) throw Error(MERA_ERR_ARG, "bad d_b/chi/n_trans");
-  if (c.cplx && cfg.prec != MERA_PREC_FP64)
-    throw Error(MERA_ERR_UNSUPPORTED, "complex tensors run in the FP64 path only");
+  // complex data on the tensor cores: every product as four real products of
+  // the real views, whose tables the plans then carry
+  c.pool.set_real_view(c.cplx && cfg.prec != MERA_PREC_FP64);
   c.L = cfg.n_trans;
   c.dims.push_back(cfg.d_b);
   // a coarse site holds two (binary) or three (ternary) fine sites

@@ -138,6 +138,39 @@ HostGroup sector_group(const TDesc& t, const std::vector<int>& legs, int q) {
   return g;
 }
 
+std::vector<int64_t> offsets_of(const HostGroup& g) {
+  if (!g.table.empty()) return g.table;
+  std::vector<int64_t> o(g.count);
+  for (int64_t i = 0; i < g.count; ++i) o[i] = i * g.stride;
+  return o;
+}
+
+HostGroup doubled(const HostGroup& g) {
+  HostGroup r = g;
+  for (int64_t& o : r.table) o *= 2;
+  r.stride *= 2;
+  return r;
+}
+
+// Output layout hints (see GettCall) of the M-group and N-group offsets of C,
+// for C = A B and for C^T = B^T A^T.
+void set_hints(HostPlan& h, const std::vector<int64_t>& om, const std::vector<int64_t>& on) {
+  auto vec_of = [](const std::vector<int64_t>& rows, const std::vector<int64_t>& cols) {
+    for (int64_t v : {8, 4}) {
+      if ((int64_t)cols.size() % v || !runs_of(cols, v)) continue;
+      bool ok = true;
+      for (int64_t o : rows) ok = ok && o % v == 0;
+      for (size_t i = 0; i < cols.size() && ok; i += v) ok = cols[i] % v == 0;
+      if (ok) return (int)v;
+    }
+    return 1;
+  };
+  h.c_rows = runs_of(om, 32);
+  h.c_vec = vec_of(om, on);
+  h.c_rows_t = runs_of(on, 32);
+  h.c_vec_t = vec_of(on, om);
+}
+
 const int64_t* upload(const HostGroup& g, TablePool& pool, int64_t* stride) {
   if (g.table.empty()) {
     *stride = g.stride;
@@ -189,23 +222,28 @@ HostPlan host_plan(const TDesc& A, const TDesc& B, const TDesc& C, int q) {
   const int fa = fast_leg(A), fb = fast_leg(B);
   h.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
   h.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
-  // output layout hints (see GettCall), for C = A B and for C^T = B^T A^T
-  const std::vector<int64_t> om = sector_offsets(C, M, q), on = sector_offsets(C, N, q);
-  auto vec_of = [](const std::vector<int64_t>& rows, const std::vector<int64_t>& cols) {
-    for (int64_t v : {8, 4}) {
-      if ((int64_t)cols.size() % v || !runs_of(cols, v)) continue;
-      bool ok = true;
-      for (int64_t o : rows) ok = ok && o % v == 0;
-      for (size_t i = 0; i < cols.size() && ok; i += v) ok = cols[i] % v == 0;
-      if (ok) return (int)v;
-    }
-    return 1;
-  };
-  h.c_rows = runs_of(om, 32);
-  h.c_vec = vec_of(om, on);
-  h.c_rows_t = runs_of(on, 32);
-  h.c_vec_t = vec_of(on, om);
+  set_hints(h, offsets_of(h.cm), offsets_of(h.cn));
   return h;
+}
+
+HostPlan real_view(const HostPlan& h) {
+  HostPlan r = h;
+  for (HostGroup* g : {&r.am, &r.ak, &r.bk, &r.bn, &r.cm, &r.cn}) *g = doubled(*g);
+  set_hints(r, offsets_of(r.cm), offsets_of(r.cn));
+  return r;
+}
+
+std::array<ComplexPart, 4> complex_parts(bool a_conj, bool b_conj) {
+  auto sign = [&](int ca, int cb) {
+    double sg = ca && cb ? -1.0 : 1.0;  // i * i = -1
+    if (ca && a_conj) sg = -sg;
+    if (cb && b_conj) sg = -sg;
+    return sg;
+  };
+  return {{{0, 0, 0, sign(0, 0), true},
+           {1, 1, 0, sign(1, 1), false},
+           {0, 1, 1, sign(0, 1), true},
+           {1, 0, 1, sign(1, 0), false}}};
 }
 
 GemmPlan upload_plan(const HostPlan& h, TablePool& pool) {
@@ -226,6 +264,20 @@ GemmPlan upload_plan(const HostPlan& h, TablePool& pool) {
   g.c_vec = h.c_vec;
   g.c_rows_t = h.c_rows_t;
   g.c_vec_t = h.c_vec_t;
+  if (pool.real_view()) {
+    const HostPlan r = real_view(h);
+    g.ar.t0 = upload(r.am, pool, &g.ar.s0);
+    g.ar.t1 = upload(r.ak, pool, &g.ar.s1);
+    g.br.t0 = upload(r.bk, pool, &g.br.s0);
+    g.br.t1 = upload(r.bn, pool, &g.br.s1);
+    g.cr.t0 = upload(r.cm, pool, &g.cr.s0);
+    g.cr.t1 = upload(r.cn, pool, &g.cr.s1);
+    g.cr_rows = r.c_rows;
+    g.cr_vec = r.c_vec;
+    g.cr_rows_t = r.c_rows_t;
+    g.cr_vec_t = r.c_vec_t;
+    g.has_rv = 1;
+  }
   return p;
 }
 
@@ -441,6 +493,32 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   if (ex.prec == MERA_PREC_FP64) {
     if (g0.a32 || g0.b32 || g0.c32) throw Error(MERA_ERR_ARG, "contract: float operand in the FP64 path");
     gett_f64(g0, s);
+    return;
+  }
+  if (g0.cplx) {
+    // complex operands: four real products of the real views (no keep slot:
+    // every part packs its own components)
+    if (!g0.has_rv) throw Error(MERA_ERR_UNSUPPORTED, "contract: complex tensor-core product without a real view");
+    auto part_ptr = [](const double* p, bool f32, int comp) {
+      return f32 ? reinterpret_cast<const double*>(reinterpret_cast<const float*>(p) + comp) : p + comp;
+    };
+    for (const ComplexPart& pt : complex_parts(g0.a_conj != 0, g0.b_conj != 0)) {
+      GettCall h = g0;
+      h.cplx = h.a_conj = h.b_conj = h.has_rv = 0;
+      h.a = g0.ar;
+      h.b = g0.br;
+      h.c = g0.cr;
+      h.c_rows = g0.cr_rows;
+      h.c_vec = g0.cr_vec;
+      h.c_rows_t = g0.cr_rows_t;
+      h.c_vec_t = g0.cr_vec_t;
+      h.A = part_ptr(g0.A, g0.a32, pt.ca);
+      h.B = part_ptr(g0.B, g0.b32, pt.cb);
+      h.C = const_cast<double*>(part_ptr(g0.C, g0.c32, pt.cc));
+      h.alpha = pt.sign * g0.alpha;
+      h.beta = pt.first ? g0.beta : 1.0;
+      contract(h, ex, s, nullptr);
+    }
     return;
   }
   // tensor cores: take the orientation whose output columns run contiguously

@@ -31,11 +31,16 @@ class TablePool {
   explicit TablePool(bool dry = false) : dry_(dry) {}
   // uploads are issued on this stream (ordered with the owner's kernels)
   void set_stream(cudaStream_t s) { stream_ = s; }
+  // plans made with this pool also carry the real view of complex operands
+  // (complex problems in a mixed-precision mode)
+  void set_real_view(bool v) { real_view_ = v; }
+  bool real_view() const { return real_view_; }
   const int64_t* get(const std::vector<int64_t>& host);
   size_t bytes() const { return bytes_; }
 
  private:
   bool dry_ = false;
+  bool real_view_ = false;
   cudaStream_t stream_ = nullptr;
   std::map<std::vector<int64_t>, DevBuf> tables_;
   size_t bytes_ = 0;
@@ -78,7 +83,27 @@ struct HostPlan {
   int c_rows = 0, c_vec = 1, c_rows_t = 0, c_vec_t = 1;  // output layout hints of GettCall
 };
 HostPlan host_plan(const TDesc& A, const TDesc& B, const TDesc& C, int q = -1);
+// The same plan addressed in reals, for interleaved complex data: every
+// offset and stride doubled (the real part of element e at 2e; the imaginary
+// part is reached by offsetting the base pointer by one real), and the output
+// hints of that view.
+HostPlan real_view(const HostPlan& h);
+// Uploads h's tables; with pool.real_view() also those of real_view(h).
 GemmPlan upload_plan(const HostPlan& h, TablePool& pool);
+
+// A complex product C = op(A) op(B) (op: conjugation or not) as four real
+// products of the real views: Re C = Re A Re B - Im A Im B and
+// Im C = Re A Im B + Im A Re B, the imaginary part of a conjugated operand
+// entering with the opposite sign.  Part i multiplies component ca of A by
+// component cb of B into component cc of C with the given sign; `first` marks
+// the first write of a component (it takes the caller's beta, the second
+// accumulates with beta = 1).
+struct ComplexPart {
+  int ca, cb, cc;
+  double sign;
+  bool first;
+};
+std::array<ComplexPart, 4> complex_parts(bool a_conj, bool b_conj);
 // host_plan + upload_plan
 GemmPlan make_plan(const TDesc& A, const TDesc& B, const TDesc& C, TablePool& pool, int q = -1);
 

@@ -1,6 +1,6 @@
-// Host check of the Z2 charge-sector contraction plans (mera::host_plan with
-// q = 0, 1) against the dense plan (q = -1), built by tests/test_z2_sectors.py
-// and linked against libmera.so; needs no GPU.
+// Host check of the contraction plans (mera::host_plan): the dense plan, its
+// Z2 charge sectors and the real view of complex operands.  Built by
+// tests/test_plan_host.py and linked against libmera.so; needs no GPU.
 //
 // For random pairwise contractions (2 to 4 legs per operand, extents 2 to 5,
 // shared legs and output order drawn at random) of random Z2-symmetric
@@ -20,8 +20,12 @@
 //     divisible by v, the N offsets run contiguously through aligned groups of
 //     v, every M offset and every group-start N offset a multiple of v; and
 //     the same for the transposed product).
-// Prints "ok <cases>" and the grading of extents 1..6 on success, else the
-// first failure, and exits non-zero.
+// Then, for random complex contractions (interleaved storage, either operand
+// conjugated, beta 0 or not), the four real products of mera::complex_parts on
+// the real view (mera::real_view) reproduce alpha op(A) op(B) + beta C computed
+// from the definition, and the real view's output hints hold.
+// Prints "ok <cases>", "complex ok <cases>" and the grading of extents 1..6 on
+// success, else the first failure, and exits non-zero.
 #include "tn.h"
 
 #include <algorithm>
@@ -202,6 +206,86 @@ int main() {
     ++cases;
   }
   std::printf("ok %d\n", cases);
+  // complex products through the real view
+  int ccases = 0;
+  for (int trial = 0; trial < 200; ++trial) {
+    std::uniform_int_distribution<int> nlegs(1, 2), ext_d(1, 4), bit(0, 1);
+    std::normal_distribution<double> nd;
+    const int nm = nlegs(rng), nk = nlegs(rng), nn = nlegs(rng), nl = nm + nk + nn;
+    std::vector<int64_t> ext(nl);
+    for (auto& e : ext) e = ext_d(rng);
+    std::vector<int> la, lb, lc;
+    for (int i = 0; i < nm; ++i) { la.push_back(i); lc.push_back(i); }
+    for (int i = nm; i < nm + nk; ++i) { la.push_back(i); lb.push_back(i); }
+    for (int i = nm + nk; i < nl; ++i) { lb.push_back(i); lc.push_back(i); }
+    std::shuffle(la.begin(), la.end(), rng);
+    std::shuffle(lb.begin(), lb.end(), rng);
+    std::shuffle(lc.begin(), lc.end(), rng);
+    auto exts = [&](const std::vector<int>& legs) {
+      std::vector<int64_t> e;
+      for (int l : legs) e.push_back(ext[l]);
+      return e;
+    };
+    const TDesc A = desc(la, exts(la)), B = desc(lb, exts(lb)), C = desc(lc, exts(lc));
+    auto rnd = [&](int64_t n) {
+      std::vector<double> v(2 * n);
+      for (double& x : v) x = nd(rng);
+      return v;
+    };
+    const std::vector<double> a = rnd(A.size()), b = rnd(B.size()), c0 = rnd(C.size());
+    const bool ac = bit(rng), bc = bit(rng);
+    const double alpha = nd(rng), beta = bit(rng) ? 0.0 : nd(rng);
+    // definition: complex sum over every assignment of the legs
+    std::vector<double> cref(2 * C.size(), 0.0);
+    {
+      std::vector<int64_t> idx(nl, 0);
+      int64_t total = 1;
+      for (int64_t e : ext) total *= e;
+      auto at = [&](const TDesc& t) {
+        int64_t o = 0;
+        for (size_t j = 0; j < t.legs.size(); ++j) o += idx[t.legs[j]] * t.stride[j];
+        return o;
+      };
+      for (int64_t i = 0; i < total; ++i) {
+        const int64_t ia = at(A), ib = at(B), ic = at(C);
+        const double ar = a[2 * ia], ai = ac ? -a[2 * ia + 1] : a[2 * ia + 1];
+        const double br = b[2 * ib], bi = bc ? -b[2 * ib + 1] : b[2 * ib + 1];
+        cref[2 * ic] += ar * br - ai * bi;
+        cref[2 * ic + 1] += ar * bi + ai * br;
+        for (int j = nl; j-- > 0;) {
+          if (++idx[j] < ext[j]) break;
+          idx[j] = 0;
+        }
+      }
+      for (int64_t x = 0; x < 2 * C.size(); ++x) cref[x] = alpha * cref[x] + beta * c0[x];
+    }
+    // the four real products on the real view, with the GETT's alpha/beta rule
+    const HostPlan r = mera::real_view(mera::host_plan(A, B, C, -1));
+    std::vector<double> cs = c0;
+    for (const mera::ComplexPart& pt : mera::complex_parts(ac, bc)) {
+      const double al = pt.sign * alpha, be = pt.first ? beta : 1.0;
+      for (int64_t m = 0; m < r.M; ++m)
+        for (int64_t n = 0; n < r.N; ++n) {
+          double sum = 0.0;
+          for (int64_t k = 0; k < r.K; ++k)
+            sum += a[pt.ca + off(r.am, m) + off(r.ak, k)] * b[pt.cb + off(r.bk, k) + off(r.bn, n)];
+          double& dst = cs[pt.cc + off(r.cm, m) + off(r.cn, n)];
+          dst = be != 0.0 ? be * dst + al * sum : al * sum;
+        }
+    }
+    for (int64_t x = 0; x < 2 * C.size(); ++x)
+      if (std::fabs(cs[x] - cref[x]) > 1e-12 * (1.0 + std::fabs(cref[x]))) {
+        std::printf("complex trial %d: entry %lld real view %.17g definition %.17g\n", trial, (long long)x, cs[x],
+                    cref[x]);
+        return 1;
+      }
+    if (!hints_hold(r)) {
+      std::printf("complex trial %d: an output layout hint of the real view does not hold\n", trial);
+      return 1;
+    }
+    ++ccases;
+  }
+  std::printf("complex ok %d\n", ccases);
   // the grading, for comparison with the input generators
   for (int64_t e = 1; e <= 6; ++e) {
     std::printf("grading %lld:", (long long)e);

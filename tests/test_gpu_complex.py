@@ -151,10 +151,3 @@ def test_lbfgs_complex_descends(gm):
     assert all(b <= a + 1e-12 for a, b in zip(es, es[1:]))
     for t in m.get_tensors():
         assert np.abs(t.conj().T @ t - np.eye(t.shape[1])).max() < 1e-13
-
-
-def test_complex_mixed_precision_refused(gm):
-    cfg = gm.default_config(4, 4, 2, dtype=gm.MERA_C128, prec=1)
-    with pytest.raises(gm.MeraError) as ex:
-        gm.Mera(cfg, _ham(4, "dm", 0))
-    assert ex.value.code == -8  # MERA_ERR_UNSUPPORTED
