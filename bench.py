@@ -4,16 +4,18 @@
 A step is one full Riemannian L-BFGS iteration of the scale-invariant binary
 MERA (two-loop direction with the preconditioner, Hager-Zhang line search
 with as many energy/gradient evaluations as it needs, retraction, transport
-of the history).  The reported value is energy/gradient evaluations per
+of the history); other workloads take the same step for the ternary MERA
+(with or without Z2 charge sectors), the uniform MPS or complex tensors.  The reported value is energy/gradient evaluations per
 second over the timed steps, summed over ranks (independent replicas: the
 optimisation does not shard across GPUs, so N GPUs run N problems).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU FP64 oracle, same metric
 
-Inputs are synthetic and seeded (QR-of-Gaussian tensors, critical Ising or
-XXZ Hamiltonian on blocked spin pairs).  L2 is flushed (256 MiB write)
-between timed steps.
+Inputs are synthetic and seeded (QR-of-Gaussian tensors, Z2-symmetric blocks
+for the z2 workloads; critical Ising, Ising with a longitudinal field or the
+Heisenberg chain, on blocked spin pairs for the binary MERA and on spins
+otherwise).  L2 is flushed (256 MiB write) between timed steps.
 """
 from __future__ import annotations
 
@@ -47,7 +49,20 @@ WORKLOADS = {
     "xxz_chi24_L3_bf16": ("xxz", 4, 24, 3, 2, {"lbfgs_m": 16}),
     "xxz_chi32_L3_3xtf32": ("xxz", 4, 32, 3, 1, {"lbfgs_m": 16, "krylov_dim": 4}),
     "xxz_chi32_L3_bf16": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4}),
+    # extra config fields: network 1 = ternary, 2 = uniform MPS (chi = bond
+    # dimension D); z2 = 1: Z2 charge sectors; dtype 1 = complex128
+    "ternary_ising_chi8_L2_fp64": ("ising", 2, 8, 2, 0, {"network": 1}),
+    "ternary_ising_chi8_L2_fp64_z2": ("ising", 2, 8, 2, 0, {"network": 1, "z2": 1}),
+    "ternary_xxz_chi16_L2_3xtf32": ("xxz", 2, 16, 2, 1, {"network": 1}),
+    "ternary_xxz_chi16_L2_3xtf32_z2": ("xxz", 2, 16, 2, 1, {"network": 1, "z2": 1}),
+    "mps_xxz_D32_fp64": ("xxz", 2, 32, 0, 0, {"network": 2}),
+    "ising_hz_chi8_L3_c128_fp64": ("ising_hz", 4, 8, 3, 0, {"dtype": 1}),
+    "ising_hz_chi16_L3_c128_3xtf32": ("ising_hz", 4, 16, 3, 1, {"dtype": 1, "lbfgs_m": 16}),
 }
+# Workloads whose CPU baseline times whole oracle energy/gradient evaluations
+# (seconds each); the others time one layer's ascending map.
+WHOLE_EVAL = {"ternary_ising_chi8_L2_fp64", "ternary_ising_chi8_L2_fp64_z2", "ternary_xxz_chi16_L2_3xtf32",
+              "ternary_xxz_chi16_L2_3xtf32_z2", "mps_xxz_D32_fp64"}
 DEFAULT_WORKLOAD = "xxz_chi32_L3_bf16"
 # Algorithmic flops of one energy/gradient evaluation as the GPU path counts
 # them inside L-BFGS steps (measured by this script's own GPU runs); used only
@@ -58,6 +73,9 @@ FLOPS_PER_GRAD = {
     "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13,
     "ising_chi12_L3_fp64": 1.6e12, "ising_chi12_L3_3xtf32": 1.13e12, "ising_chi12_L3_bf16": 1.13e12,
     "ising_chi8_L3_fp64": 5e10, "ising_chi4_L2_fp64": 1.2e8,
+    # complex workloads: 4 x the real workload's (8 real flops per complex
+    # multiply-add), an estimate until measured
+    "ising_hz_chi8_L3_c128_fp64": 2e11, "ising_hz_chi16_L3_c128_3xtf32": 5.8e13,
 }
 METRIC = "MERA grad evals/s"
 UNIT = "grad_evals/s"
@@ -86,9 +104,31 @@ def tensor_peaks():
 GETT_TRAFFIC_BYTES = {}
 
 
-def hamiltonian(kind, d_b):
-    bond = inp.ising_bond(1.0) if kind == "ising" else inp.xxz_bond(1.0)
+def hamiltonian(kind, d_b, network=0):
+    """The workload's Hamiltonian term: critical Ising, Ising with a
+    longitudinal field h_z = 0.13 (-h_z X per spin) or the Heisenberg chain;
+    three-site (blocked spin pairs when d_b = 4) for the binary MERA, the
+    two-site bond for the ternary MERA and the MPS."""
+    bond = (inp.ising_bond(1.0) if kind == "ising" else inp.ising_bond(1.0, 0.13) if kind == "ising_hz"
+            else inp.xxz_bond(1.0))
+    if network in (1, 2):
+        return bond
     return inp.three_site_blocked(bond) if d_b == 4 else inp.three_site_unblocked(bond)
+
+
+def initial_point(d_b, chi, L, extra, seed):
+    """Seeded starting tensors of a workload (QR of Gaussian matrices; Z2-symmetric
+    blocks when z2 is set; complex when dtype = 1)."""
+    net = extra.get("network", 0)
+    dt = np.complex128 if extra.get("dtype", 0) == 1 else np.float64
+    if net == 2:
+        return [inp.random_mps(chi, d_b, seed=seed, dtype=dt).reshape(chi * d_b, chi)]
+    if net == 1:
+        us, ws = (inp.random_z2_ternary_mera(chi, L, seed=seed, dtype=dt) if extra.get("z2")
+                  else inp.random_ternary_mera(d_b, chi, L, seed=seed, dtype=dt))
+    else:
+        us, ws = inp.random_mera(d_b, chi, L, seed=seed, dtype=dt)
+    return [t for p in zip(us, ws) for t in p]
 
 
 def ascend_flops(cf, cc=None):
@@ -161,18 +201,18 @@ def sample_layer(d_b, chi, L):
     return 1, dims[1], dims[2]
 
 
-def oracle_sample(d_b, chi, L, seconds=10.0, seed=0):
+def oracle_sample(d_b, chi, L, seconds=10.0, seed=0, cplx=False):
     """Time the oracle's ascending map of one layer of the workload (seeded
-    tensors of that layer, random symmetric operator) on the host cores: both
+    tensors of that layer, random Hermitian operator) on the host cores: both
     sides up to chi=16, the left side A_L alone above (half the flops)."""
     from oracle import mera as om
     layer, cf, cc = sample_layer(d_b, chi, L)
     one_side = chi > 16
-    us, ws = inp.random_mera(d_b, chi, L, seed=seed)
+    us, ws = inp.random_mera(d_b, chi, L, seed=seed, dtype=np.complex128 if cplx else np.float64)
     u, w = us[layer], ws[layer]
     rng = np.random.default_rng(seed)
-    h = rng.standard_normal((cf**3, cf**3))
-    h = 0.5 * (h + h.T)
+    h = rng.standard_normal((cf**3, cf**3)) + (1j * rng.standard_normal((cf**3, cf**3)) if cplx else 0)
+    h = 0.5 * (h + h.conj().T)
     n, t0 = 0, time.perf_counter()
     while True:
         if one_side:
@@ -184,6 +224,32 @@ def oracle_sample(d_b, chi, L, seconds=10.0, seed=0):
         if dt >= seconds:
             break
     return dt / n, n, layer, cf, cc, (0.5 if one_side else 1.0)
+
+
+def oracle_eval_sample(wl, seconds=10.0, seed=0):
+    """Time whole oracle energy/gradient evaluations of the workload (the
+    ternary oracle, or the MPS oracle) at its seeded point on the host cores,
+    at least one and until `seconds` have passed.  Returns (seconds per
+    evaluation, evaluations)."""
+    kind, d_b, chi, L, prec, extra = wl
+    net = extra.get("network", 0)
+    h = hamiltonian(kind, d_b, net)
+    point = initial_point(d_b, chi, L, extra, seed)
+    if net == 2:
+        from oracle import mps
+        A = point[0].reshape(chi, d_b, chi)
+        run = lambda: mps.energy_grad(A, h)  # noqa: E731
+    else:
+        from oracle import ternary as ot
+        run = lambda: ot.energy_grad(h, point[0::2], point[1::2])  # noqa: E731
+    n, t0 = 0, time.perf_counter()
+    while True:
+        run()
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    return dt / n, n
 
 
 def host_cores():
@@ -218,20 +284,31 @@ def run_reference(args, wl):
     if rank != 0:
         return
     kind, d_b, chi, L, prec, extra = wl
-    flops_grad = args.ref_flops_per_grad or FLOPS_PER_GRAD[args.workload]
+    cplx = extra.get("dtype", 0) == 1
     per = []
-    for i in range(args.warmup + args.steps):
-        t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.ref_seconds, seed=i)
-        if i >= args.warmup:
-            per.append(t)
-    frac = part * ascend_flops(cf, cc) / flops_grad
-    t = sum(per) / len(per)
-    value = frac / t
-    sample = (f"oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}ascending map of layer {layer} (chi {cf}->{cc}), "
-              f"{t:.2f} s each = {frac:.3g} of one gradient evaluation's algorithmic flops ({flops_grad:.3g})")
+    if args.workload in WHOLE_EVAL:
+        for i in range(args.warmup + args.steps):
+            t, n = oracle_eval_sample(wl, seconds=args.ref_seconds)
+            if i >= args.warmup:
+                per.append(t)
+        t = sum(per) / len(per)
+        value = 1.0 / t
+        sample = f"oracle (NumPy FP64) energy/gradient evaluations of the workload at its seeded point, {t:.2f} s each"
+    else:
+        flops_grad = args.ref_flops_per_grad or FLOPS_PER_GRAD[args.workload]
+        for i in range(args.warmup + args.steps):
+            t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.ref_seconds, seed=i, cplx=cplx)
+            if i >= args.warmup:
+                per.append(t)
+        frac = part * ascend_flops(cf, cc) * (4 if cplx else 1) / flops_grad
+        t = sum(per) / len(per)
+        value = frac / t
+        sample = (f"oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}ascending map of layer {layer} "
+                  f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient evaluation's algorithmic flops "
+                  f"({flops_grad:.3g})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64",
             "data": "synthetic", "config": {"workload": args.workload, "chi": chi, "n_trans": L},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                              "sample": sample},
@@ -314,11 +391,11 @@ def main():
     from paper_2007_03638_gb300 import mera as gm
 
     kind, d_b, chi, L, prec, extra = wl
-    h3 = hamiltonian(kind, d_b)
+    net, cplx = extra.get("network", 0), extra.get("dtype", 0) == 1
+    h3 = hamiltonian(kind, d_b, net)
     stream = torch.cuda.current_stream()
     m = gm.Mera(gm.default_config(d_b, chi, L, prec=prec, **extra), h3, stream=stream.cuda_stream)
-    us, ws = inp.random_mera(d_b, chi, L, seed=args.seed + rank)
-    point = [t for p in zip(us, ws) for t in p]
+    point = initial_point(d_b, chi, L, extra, args.seed + rank)
     m.set_tensors(point)
     if args.energy_once:
         print(json.dumps({"workload": args.workload, "energy": m.energy(), "launches": m.launch_count()}))
@@ -358,9 +435,9 @@ def main():
 
     # end to end: host (pinned) tensors in, host gradient out, per evaluation
     pinned = [torch.from_numpy(np.ascontiguousarray(t)).pin_memory() for t in m.get_tensors()]
-    gout = [torch.empty(s, dtype=torch.float64).pin_memory() for s in m.shapes]
-    h2d = sum(t.numel() * 8 for t in pinned)
-    d2h = sum(t.numel() * 8 for t in gout) + 8
+    gout = [torch.empty(s, dtype=torch.complex128 if cplx else torch.float64).pin_memory() for s in m.shapes]
+    h2d = sum(t.numel() * t.element_size() for t in pinned)
+    d2h = sum(t.numel() * t.element_size() for t in gout) + 8
     big = chi >= 24
     for _ in range(1 if big else 2):
         m.set_tensors(pinned)
@@ -381,7 +458,7 @@ def main():
     achieved = st["gett_flops"] / (st["gett_ms"] / 1e3) if st["gett_ms"] > 0 else None
     if prec == 0:
         peak, psrc, kname, bound = FP64_PEAK_FLOPS, "derived FP64 FMA rate (152 SMs x 2 FMA/clk x 2070 MHz)", \
-            "gett_f64_kernel", "alu"
+            "gett_c128_kernel" if cplx else "gett_f64_kernel", "alu"
     else:
         peak, psrc = tensor_peaks()[prec]
         kname, bound = "tc_gemm_kernel (%s)" % ("3xTF32" if prec == 1 else "split-BF16"), "tensor"
@@ -396,9 +473,13 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": ["f64", "tf32x3+f32acc (f64 Krylov/geometry)", "bf16x3+f32acc (f64 Krylov/geometry)"][prec], "data": "synthetic",
+            "dtype": ("complex " if cplx else "") + ["f64", "tf32x3+f32acc (f64 Krylov/geometry)",
+                                                     "bf16x3+f32acc (f64 Krylov/geometry)"][prec],
+            "data": "synthetic",
             "config": {"workload": args.workload, "hamiltonian": kind, "d_b": d_b, "chi": chi,
                        "n_trans": L, "prec": ["fp64", "3xtf32", "split_bf16"][prec],
+                       "network": ["binary", "ternary", "mps"][net], "z2": bool(extra.get("z2", 0)),
+                       "element": "complex128" if cplx else "float64",
                        "step": "one L-BFGS iteration (m=%d)" % extra.get("lbfgs_m", 8), "l2": "flushed (256 MiB write) between steps",
                        "parallelism": f"replicas x{world}"},
             "lbfgs_iters_per_s": world * args.steps / (t_ms / 1e3),
@@ -412,13 +493,19 @@ def main():
             "gpu_launches": st["launches"],
             "clocks": clocks.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds)
-        frac = part * ascend_flops(cf, cc) / gett_flops_per_grad
-        line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                                "sample": f"{n} x oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}"
-                                          f"ascending map of layer {layer} "
-                                          f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient "
-                                          f"evaluation's algorithmic flops"}
+        if args.workload in WHOLE_EVAL:
+            t, n = oracle_eval_sample(wl, seconds=args.cpu_seconds)
+            line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                                    "sample": f"{n} x oracle (NumPy FP64) energy/gradient evaluation of the "
+                                              f"workload at its seeded point, {t:.2f} s each"}
+        else:
+            t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds, cplx=cplx)
+            frac = part * ascend_flops(cf, cc) * (4 if cplx else 1) / gett_flops_per_grad
+            line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                                    "sample": f"{n} x oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}"
+                                              f"ascending map of layer {layer} "
+                                              f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient "
+                                              f"evaluation's algorithmic flops"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
