@@ -24,11 +24,15 @@
 // conjugated, beta 0 or not), the four real products of mera::complex_parts on
 // the real view (mera::real_view) reproduce alpha op(A) op(B) + beta C computed
 // from the definition, and the real view's output hints hold.
-// Prints "ok <cases>", "complex ok <cases>" and the grading of extents 1..6 on
-// success, else the first failure, and exits non-zero.
+// Finally the library's ternary networks build with charge-sector plans, and
+// both networks with real views, on a dry table pool.
+// Prints "ok <cases>", "complex ok <cases>", "networks ok <n>" and the grading
+// of extents 1..6 on success, else the first failure, and exits non-zero.
 #include "tn.h"
+#include "tnet.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -286,6 +290,34 @@ int main() {
     ++ccases;
   }
   std::printf("complex ok %d\n", ccases);
+  // the library's own networks build in every mode (dry table pool: no device)
+  int nets = 0;
+  try {
+    for (const std::array<int64_t, 2> dims :
+         {std::array<int64_t, 2>{2, 8}, std::array<int64_t, 2>{8, 8}, std::array<int64_t, 2>{4, 16}}) {
+      for (int mode = 0; mode < 3; ++mode) {  // 0 dense, 1 Z2 sectors, 2 real views (complex, mixed)
+        mera::TablePool pool(true);
+        pool.set_real_view(mode == 2);
+        for (char side : {'L', 'C', 'R'}) {
+          mera::Net net(mera::ternary_netdef(side), dims[0], dims[1], pool, mode == 1);
+          for (const mera::GemmPlan* p : net.plans())
+            if (mode == 2 && !p->proto.has_rv) throw std::runtime_error("a ternary plan without its real view");
+          ++nets;
+        }
+        if (mode != 1)
+          for (char side : {'L', 'R'}) {
+            mera::SideNet net(side, dims[0], dims[1], pool, dims[1] / 2);
+            for (const mera::GemmPlan* p : net.executed_plans())
+              if (mode == 2 && !p->proto.has_rv) throw std::runtime_error("a binary plan without its real view");
+            ++nets;
+          }
+      }
+    }
+  } catch (const std::exception& e) {
+    std::printf("networks: %s\n", e.what());
+    return 1;
+  }
+  std::printf("networks ok %d\n", nets);
   // the grading, for comparison with the input generators
   for (int64_t e = 1; e <= 6; ++e) {
     std::printf("grading %lld:", (long long)e);

@@ -4,8 +4,9 @@ Z2 charge-sector plans of random symmetric contractions reproduce the dense
 ones entry by entry, write exactly the even-charge entries, hold a quarter of
 the work and keep the output-layout hints the tensor-core epilogue relies on;
 the four real products of the real view of complex operands reproduce complex
-contractions (conjugated operands, beta); the library's leg grading equals the
-input generators'."""
+contractions (conjugated operands, beta); the library's networks build with
+sector plans and real views; the library's leg grading equals the input
+generators'."""
 import os
 import shutil
 import subprocess
@@ -34,9 +35,10 @@ def test_plans_match_definitions(tmp_path):
     lines = r.stdout.splitlines()
     assert lines[0] == "ok 300"
     assert lines[1] == "complex ok 200"
+    assert lines[2] == "networks ok 39"
     # the library grades legs as the input generators do (first half even)
     from paper_2007_03638_gb300 import inputs as inp
-    for line in lines[2:]:
+    for line in lines[3:]:
         head, vals = line.split(":")
         e = int(head.split()[1])
         assert [int(v) for v in vals.split()] == inp.z2_parities(e).tolist(), line
