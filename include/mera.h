@@ -167,7 +167,7 @@ void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
  * site, C = Tr(h rho), Sec. 4); for the ternary network and the MPS a
  * two-site term, (d_b^2) x (d_b^2).  stream: a cudaStream_t (NULL = default
  * stream).  The tensors start as the identity-disentangler / first-columns
- * isometry point until mera_set_tensors is called. */
+ * isometry point until mera_set_tensors or mera_init_random is called. */
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
 int mera_destroy(mera_t m);
 
@@ -180,6 +180,25 @@ int mera_tensor_shape(mera_t m, int i, int64_t* rows, int64_t* cols);
  * clears the optimiser history. */
 int mera_set_tensors(mera_t m, const void* const* tensors);
 int mera_get_tensors(mera_t m, void* const* tensors);
+
+/* Fill the point with seeded random isometries: the sign-fixed
+ * QR-of-Gaussian initialisation (the thin QR factor of a Gaussian matrix,
+ * R's diagonal real and positive), tensor by tensor in the order of the
+ * tensor list.  The Gaussian matrix of tensor i is row-major (interleaved
+ * real and imaginary parts, each N(0,1), for MERA_C128), and its entries are
+ * g_0, g_1, ... of stream i: with SplitMix64 (Steele, Lea, Flood, OOPSLA
+ * 2014) written x_k(s) = mix(s + k * 0x9E3779B97F4A7C15) for k >= 1 and
+ * mix(z) = z3 of z1 = (z ^ z >> 30) * 0xBF58476D1CE4E5B9,
+ * z2 = (z1 ^ z1 >> 27) * 0x94D049BB133111EB, z3 = z2 ^ z2 >> 31 (64-bit),
+ * base_i = x_{i+1}(seed), u_k = ((x_k(base_i) >> 11) + 0.5) * 2^-53, and for
+ * every pair j = 0, 2, 4, ...: r = sqrt(-2 ln u_{j+1}),
+ * t = 2 pi u_{j+2}, g_j = r cos t, g_{j+1} = r sin t (Box-Muller).  With
+ * z2 = 1 each charge block (rows and columns of charge q in ascending order)
+ * is factored on its own and the entries between charges are zero.  Host
+ * computation (once per problem), then a copy to the device; resets the
+ * optimiser history like mera_set_tensors.  MERA_ERR_ARG if a charge block
+ * has fewer rows than columns. */
+int mera_init_random(mera_t m, uint64_t seed);
 
 /* Energy per bottom site C = Tr(h rho) and the Riemannian gradient G at the
  * current point (Sec. 4 with App. B; G_v is the tangent projection of the

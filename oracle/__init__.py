@@ -16,4 +16,12 @@ Modules
               metric, Hilbert-space preconditioner (Sec. 2, Sec. 3).
 ``optim``     Hager-Zhang line search, L-BFGS two-loop and nonlinear CG on the
               product manifold (Sec. 3).
+``ternary``   the ternary MERA's three ascending maps of two-site operators,
+              its scale-invariant layer and derivatives (Sec. 4, App. B).
+``ev``        Evenbly-Vidal updates and sweeps (App. ev_steplimit).
+``mps``       the uniform MPS: transfer maps, energy, derivative and
+              preconditioner (Sec. 5).
+``z2``        Z2 symmetry: charge violation, blockwise geometry (Sec. 6).
+``rng``       the seeded generator and sign-fixed QR-of-Gaussian isometries of
+              the library's random initialisation.
 """

@@ -196,4 +196,16 @@ void sym_eig(double* A, double* V, double* evals, int n, EigWork& w, cudaStream_
 // A was already rotated into, and the result accumulates onto it.
 void sym_eig_from(double* A, double* V, double* evals, int n, bool warm, EigWork& w, cudaStream_t s);
 
+// ---------------------------------------------------------- seeded init ----
+// k-th output (k >= 1) of SplitMix64 started at `state`.
+uint64_t splitmix64_output(uint64_t state, uint64_t k);
+// `count` standard normals of stream `stream` under `seed` (Box-Muller on
+// pairs of uniforms from the SplitMix64 outputs; see mera_init_random).
+void seeded_gaussians(uint64_t seed, uint64_t stream, int64_t count, double* out);
+// out (n x p row-major, interleaved complex if cplx) = the sign-fixed thin QR
+// factor of the seeded Gaussian matrix of stream `stream`; with row/column
+// charges (Z2, may be null) the same per charge block, zero between charges.
+void random_isometry(uint64_t seed, uint64_t stream, int64_t n, int64_t p, bool cplx, const int* row_charge,
+                     const int* col_charge, double* out);
+
 }  // namespace mera

@@ -1600,22 +1600,24 @@ void finish_create(Ctx& c, cudaStream_t s);
 // entry between a row and a column of different total charge (the legs'
 // gradings summed, first half of each leg even) must be below 1e-12 of the
 // largest entry (Sec. 6); MERA_ERR_ARG otherwise.
+// Z2 charge of every index tuple of legs with dimensions dims (row-major).
+std::vector<int> fused_charges(const std::vector<int64_t>& dims) {
+  int64_t n = 1;
+  for (int64_t e : dims) n *= e;
+  std::vector<int> ch(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t r = i;
+    for (size_t j = dims.size(); j-- > 0;) {
+      ch[i] ^= z2_charge(r % dims[j], dims[j]);
+      r /= dims[j];
+    }
+  }
+  return ch;
+}
+
 void check_z2(Ctx& c, const double* dev, const std::vector<int64_t>& rdims, const std::vector<int64_t>& cdims,
               const std::string& what, cudaStream_t s) {
-  auto charges = [](const std::vector<int64_t>& dims) {
-    int64_t n = 1;
-    for (int64_t e : dims) n *= e;
-    std::vector<int> ch(n, 0);
-    for (int64_t i = 0; i < n; ++i) {
-      int64_t r = i;
-      for (size_t j = dims.size(); j-- > 0;) {
-        ch[i] ^= z2_charge(r % dims[j], dims[j]);
-        r /= dims[j];
-      }
-    }
-    return ch;
-  };
-  const std::vector<int> cr = charges(rdims), cc = charges(cdims);
+  const std::vector<int> cr = fused_charges(rdims), cc = fused_charges(cdims);
   const int64_t R = (int64_t)cr.size(), C = (int64_t)cc.size();
   std::vector<double> h((size_t)(R * C * c.rs));
   MERA_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
@@ -1877,6 +1879,29 @@ int mera_set_tensors(mera_t m, const void* const* t) {
     mera::check_isometric(*m, mera::P(m->Wtry), m->s);
     if (m->z2) mera::check_z2_point(*m, mera::P(m->Wtry), m->s);
     std::swap(m->Wcur, m->Wtry);
+    m->ev[0].valid = m->ev[1].valid = false;
+    mera::clear_history(*m);
+    m->iters = 0;
+  });
+}
+
+int mera_init_random(mera_t m, uint64_t seed) {
+  if (!m) return MERA_ERR_ARG;
+  return wrap(m, [&] {
+    std::vector<double> host(m->total);
+    for (int i = 0; i < m->nt; ++i) {
+      std::vector<int> rq, cq;
+      if (m->z2) {  // ternary: u_l (cf cf) x (cf cf), w_l (cf cf cf) x (cc)
+        const int l = i / 2;
+        const int64_t cf = m->dims[l], cc = l < m->L ? m->dims[l + 1] : m->dims[l];
+        rq = mera::fused_charges(i % 2 == 0 ? std::vector<int64_t>{cf, cf} : std::vector<int64_t>{cf, cf, cf});
+        cq = mera::fused_charges(i % 2 == 0 ? std::vector<int64_t>{cf, cf} : std::vector<int64_t>{cc});
+      }
+      mera::random_isometry(seed, (uint64_t)i, m->rows[i], m->cols[i], m->cplx, m->z2 ? rq.data() : nullptr,
+                            m->z2 ? cq.data() : nullptr, host.data() + m->offs[i]);
+    }
+    MERA_CUDA(cudaMemcpyAsync(m->Wcur.p, host.data(), sizeof(double) * m->total, cudaMemcpyHostToDevice, m->s));
+    MERA_CUDA(cudaStreamSynchronize(m->s));
     m->ev[0].valid = m->ev[1].valid = false;
     mera::clear_history(*m);
     m->iters = 0;

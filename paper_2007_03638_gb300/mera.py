@@ -70,7 +70,7 @@ class SolveResult(C.Structure):
 
 
 EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tensors", "mera_energy",
-           "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_energy_grad",
+           "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_init_random", "mera_energy_grad",
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_ev_sweep", "mera_solve", "mera_footprint_bytes",
            "mera_launch_count", "mera_get_stats", "mera_profile", "mera_profile_dump", "mera_dots_noalloc",
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "mera_tensor_shape": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "mera_set_tensors": (C.c_int, [C.c_void_p, vpp]),
         "mera_get_tensors": (C.c_int, [C.c_void_p, vpp]),
+        "mera_init_random": (C.c_int, [C.c_void_p, C.c_uint64]),
         "mera_energy_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), vpp, vpp]),
         "mera_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
         "mera_project": (C.c_int, [C.c_void_p, vpp, vpp]),
@@ -256,6 +257,10 @@ class Mera:
     def set_tensors(self, tensors):
         keep = []
         self._check(self.L.mera_set_tensors(self.h, _ptrs(tensors, keep, self.dtype)))
+
+    def init_random(self, seed):
+        """Seeded sign-fixed QR-of-Gaussian point (see mera_init_random in mera.h)."""
+        self._check(self.L.mera_init_random(self.h, int(seed)))
 
     def get_tensors(self, device=False):
         out = self._alloc(device)
