@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -410,8 +411,10 @@ def main():
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    # nvidia-smi samples of the timed region: $MERA_BENCH_CLOCKS_DIR (kept) or a temporary directory
+    clk_dir = os.environ.get("MERA_BENCH_CLOCKS_DIR") or tempfile.mkdtemp(prefix="mera_bench_clocks_")
+    clk_path = os.path.join(clk_dir, f"clocks_rank{rank}.csv")
+    os.makedirs(clk_dir, exist_ok=True)
     infos = []
     with Clocks(clk_path, local) as clocks:
         # named range: a profiler can select exactly the timed launches
