@@ -1,6 +1,7 @@
 /*
  * mera.h -- C ABI of libmera: energy/gradient and Riemannian optimisation of
- * a scale-invariant binary (default) or ternary MERA on one GB300 (sm_103a).
+ * a scale-invariant binary (default) or ternary MERA, or of a uniform MPS, on
+ * one GB300 (sm_103a).
  *
  * Method: Hauru, Van Damme, Haegeman, "Riemannian optimization of isometric
  * tensor networks" (arXiv:2007.03638).  Section numbers and equation labels
@@ -261,7 +262,7 @@ int mera_cg_step(mera_t m, mera_iter_info* info);
  * eigenvalue plus a margin); it acts as an inverse step size.  Clears the
  * L-BFGS/CG history.  info: energy (unshifted) and |G| at the new point from
  * one more evaluation, n_evals = number of tensors + 1, alpha = 0.
- * MERA_ERR_ARG for a non-finite gamma. */
+ * MERA_ERR_ARG for a non-finite gamma; MERA_ERR_UNSUPPORTED for an MPS. */
 int mera_ev_sweep(mera_t m, double gamma, mera_iter_info* info);
 
 typedef struct {
