@@ -53,8 +53,8 @@ __global__ void sylvester_scale_k(double* a, const double* __restrict__ lt, int 
 
 // evals -> function values used by the Grassmann retraction/transport and
 // the preconditioner (kind: 0 cos(a s), 1 sin(a s)/s, 2 (1-cos(a s))/s^2,
-// 3 1/sqrt(l^2+d^2), 4 sqrt(l^2+d^2), 5 1/sqrt(max(l, d)), 6 1/(l + d));
-// for kinds 0-2 the input is s^2.
+// 3 1/sqrt(l^2+d^2), 4 sqrt(l^2+d^2), 5 1/sqrt(max(l, d)), 6 1/(l + d),
+// 7 1/sqrt(l) for l > d else 0, 8 sqrt(max(l, 0))); for kinds 0-2 the input is s^2.
 __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, double a, double d,
                            double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,8 +78,12 @@ __global__ void spectral_k(const double* __restrict__ ev, int n, int kind, doubl
     r = sqrt(l * l + d * d);
   } else if (kind == 5) {
     r = 1.0 / sqrt(fmax(l, d));  // inverse square root of a positive semidefinite matrix (floor d)
-  } else {
+  } else if (kind == 6) {
     r = 1.0 / (l + d);           // (rho + d 1)^(-1), the MPS preconditioner
+  } else if (kind == 7) {
+    r = l > d ? 1.0 / sqrt(l) : 0.0;  // pseudo-inverse square root
+  } else {
+    r = sqrt(fmax(l, 0.0));
   }
   out[i] = r;
 }
@@ -105,6 +109,16 @@ __global__ void marg_tern_c_k(const double2* __restrict__ r, int64_t c, double2*
     sy += u.y + v.y;
   }
   out[idx] = make_double2(0.5 * sx, 0.5 * sy);
+}
+
+// dst[i * ldd + j] = alpha src[i * lds + j] for i < rows, j < cols; rs reals
+// per element (1 real, 2 interleaved complex)
+__global__ void copy_block_k(double* __restrict__ dst, int64_t ldd, const double* __restrict__ src, int64_t lds,
+                             int64_t rows, int64_t cols, double alpha, int rs) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols * rs) return;
+  const int64_t e = idx / rs, part = idx % rs, i = e / cols, j = e % cols;
+  dst[(i * ldd + j) * rs + part] = alpha * src[(i * lds + j) * rs + part];
 }
 
 // y += (re + i im) x, n interleaved complex elements
@@ -151,7 +165,8 @@ struct StepGeom {
   bool valid = false;
   double alpha = 0.0;
   std::vector<DevBuf> Amat;   // u: A = W^T X ; w: V (evecs of X^T X)
-  std::vector<DevBuf> E;      // u: exp(alpha A) ; w: unused
+  std::vector<DevBuf> E;      // u: exp(alpha A); Stiefel w: exp(alpha [[A, -P], [P, 0]]) (2p x 2p); else unused
+  std::vector<DevBuf> Q2;     // Stiefel w: orthonormal basis of the range of (1 - W W^dag) X (n x p)
   std::vector<DevBuf> P1, P2, Pc;  // w: spectral matrices
 };
 
@@ -1100,6 +1115,62 @@ void polar_ns(Ctx& c, double* X, int64_t n, int64_t p, cudaStream_t s) {
   }
 }
 
+// Non-square Stiefel point (an isometry with w_stiefel): Eq. retraction on
+// the span of W and Q2, an orthonormal basis of the range of
+// Z = (1 - W W^dag) X = W_perp B.  With A = W^dag X, Z^dag Z = V S^2 V^dag,
+// Q2 = Z V S^-1 V^dag (directions with S = 0 dropped: they do not enter) and
+// P = V S V^dag (so Z = Q2 P), e^{alpha Q_X} acts on [W Q2] as
+// E = exp(alpha [[A, -P], [P, 0]]) and as the identity on the complement:
+// R = W E11 + Q2 E21 and T(Y) = Y + [W Q2] (E - 1) [W Q2]^dag Y.  Leaves A in
+// Amat, Q2 and E in the step geometry.
+void stiefel_geom(Ctx& c, int i, const double* Wi, const double* Xi, double alpha, cudaStream_t s) {
+  StepGeom& g = c.geom;
+  const int64_t n = c.rows[i], p = c.cols[i], q = p * c.rs, p2 = 2 * p;
+  double* A = P(g.Amat[i]);
+  double* Q2 = P(g.Q2[i]);
+  double* Z = P(c.gtmp[3]);
+  double* ZZ = P(c.gtmp[0]);
+  double* V = P(c.gtmp[1]);
+  double* Pm = P(c.gtmp[2]);
+  double* F = P(c.gtmp[4]);
+  double* ev = P(c.gtmp[5]);
+  mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Xi, p, 0.0, A, p, s);   // A = W^dag X
+  copy(Z, Xi, n * p * c.rs, s);
+  mm(c, 'N', 'N', n, p, p, -1.0, Wi, p, A, p, 1.0, Z, p, s);   // Z = X - W A
+  const double zn = c.red.dot(Z, Z, n * p * c.rs, s);
+  mm(c, 'C', 'N', p, p, n, 1.0, Z, p, Z, p, 0.0, ZZ, p, s);    // Z^dag Z
+  herm(c, ZZ, p, s);
+  if (c.cplx) {
+    embed_complex(ZZ, p, F, s);
+    copy(ZZ, F, q * q, s);
+  }
+  sym_eig(ZZ, V, ev, (int)q, c.eigw, s);
+  // Q2 = Z V S^-1 V^dag (eigenvalues below 1e-24 |Z|^2 dropped), P = V S V^dag
+  double* f = P(c.gtmp[2]);
+  spectral_k<<<blocks(q), 256, 0, s>>>(ev, (int)q, 7, 0.0, 1e-24 * zn, f);
+  vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, f, (int)q, F);
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  double* Sinv = P(c.gtmp[0]);  // Z^dag Z is no longer needed
+  if (c.cplx) extract_complex(F, p, Sinv, s); else copy(Sinv, F, q * q, s);
+  mm(c, 'N', 'N', n, p, p, 1.0, Z, p, Sinv, p, 0.0, Q2, p, s);
+  spectral_k<<<blocks(q), 256, 0, s>>>(ev, (int)q, 8, 0.0, 0.0, f);
+  vfvt_k<<<blocks(q * q), 256, 0, s>>>(V, f, (int)q, F);
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  if (c.cplx) extract_complex(F, p, Pm, s); else copy(Pm, F, q * q, s);
+  // M = [[A, -P], [P, 0]] (2p x 2p) in V's buffer, E = exp(alpha M)
+  double* M = V;
+  fill(0.0, M, p2 * p2 * c.rs, s);
+  const unsigned nb = blocks(p * p * c.rs);
+  copy_block_k<<<nb, 256, 0, s>>>(M, p2, A, p, p, p, 1.0, c.rs);
+  copy_block_k<<<nb, 256, 0, s>>>(M + p * c.rs, p2, Pm, p, p, p, -1.0, c.rs);
+  copy_block_k<<<nb, 256, 0, s>>>(M + p * p2 * c.rs, p2, Pm, p, p, p, 1.0, c.rs);
+  count_launch(3);
+  MERA_CHECK_LAUNCH();
+  expm_skew(c, M, alpha, p2, P(g.E[i]), P(c.gtmp[4]), P(c.gtmp[5]), s);
+}
+
 // Fill c.geom for direction X at point W and step alpha.
 void make_geom(Ctx& c, const double* W, const double* X, double alpha, cudaStream_t s) {
   StepGeom& g = c.geom;
@@ -1132,7 +1203,7 @@ void make_geom(Ctx& c, const double* W, const double* X, double alpha, cudaStrea
       }
       MERA_CHECK_LAUNCH();
     } else {
-      throw Error(MERA_ERR_UNSUPPORTED, "non-square Stiefel retraction not built");
+      stiefel_geom(c, i, Wi, Xi, alpha, s);
     }
   }
   g.valid = true;
@@ -1148,9 +1219,14 @@ void apply_retract(Ctx& c, const double* W, const double* X, double* Wout, cudaS
     double* Ri = Wout + c.offs[i];
     if (n == p) {
       mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, P(g.E[i]), p, 0.0, Ri, p, s);
-    } else {
+    } else if (grass(c, i)) {
       mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, P(g.Pc[i]), p, 0.0, Ri, p, s);
       mm(c, 'N', 'N', n, p, p, 1.0, Xi, p, P(g.P1[i]), p, 1.0, Ri, p, s);
+    } else {
+      // R = W E11 + Q2 E21 (E is 2p x 2p)
+      const double* E = P(g.E[i]);
+      mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, E, 2 * p, 0.0, Ri, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, P(g.Q2[i]), p, E + 2 * p * p * c.rs, 2 * p, 1.0, Ri, p, s);
     }
     polar_ns(c, Ri, n, p, s);
   }
@@ -1171,13 +1247,30 @@ void apply_transport(Ctx& c, const double* W, const double* X, double* Y, cudaSt
       mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Yi, p, 0.0, Z, p, s);
       mm(c, 'N', 'N', p, p, p, 1.0, P(g.E[i]), p, Z, p, 0.0, Z2, p, s);
       mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, Z2, p, 0.0, Yi, p, s);
-    } else {
+    } else if (grass(c, i)) {
       // Y - W P1 (X^dag Y) - X P2 (X^dag Y)
       mm(c, 'C', 'N', p, p, n, 1.0, Xi, p, Yi, p, 0.0, Z, p, s);
       mm(c, 'N', 'N', p, p, p, 1.0, P(g.P1[i]), p, Z, p, 0.0, Z2, p, s);
       mm(c, 'N', 'N', n, p, p, -1.0, Wi, p, Z2, p, 1.0, Yi, p, s);
       mm(c, 'N', 'N', p, p, p, 1.0, P(g.P2[i]), p, Z, p, 0.0, Z2, p, s);
       mm(c, 'N', 'N', n, p, p, -1.0, Xi, p, Z2, p, 1.0, Yi, p, s);
+    } else {
+      // Y + W ((E11 - 1) C1 + E12 C2) + Q2 (E21 C1 + (E22 - 1) C2), C1 = W^dag Y, C2 = Q2^dag Y
+      const double* E = P(g.E[i]);
+      const double* Q2 = P(g.Q2[i]);
+      const int64_t r = c.rs, ld = 2 * p;
+      double* K1 = P(c.gtmp[2]);
+      double* K2 = P(c.gtmp[3]);
+      mm(c, 'C', 'N', p, p, n, 1.0, Wi, p, Yi, p, 0.0, Z, p, s);
+      mm(c, 'C', 'N', p, p, n, 1.0, Q2, p, Yi, p, 0.0, Z2, p, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, E, ld, Z, p, 0.0, K1, p, s);
+      axpy(-1.0, Z, K1, p * p * r, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, E + p * r, ld, Z2, p, 1.0, K1, p, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, E + p * ld * r, ld, Z, p, 0.0, K2, p, s);
+      mm(c, 'N', 'N', p, p, p, 1.0, E + (p * ld + p) * r, ld, Z2, p, 1.0, K2, p, s);
+      axpy(-1.0, Z2, K2, p * p * r, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Wi, p, K1, p, 1.0, Yi, p, s);
+      mm(c, 'N', 'N', n, p, p, 1.0, Q2, p, K2, p, 1.0, Yi, p, s);
     }
   }
 }
@@ -1563,7 +1656,7 @@ void create_mps(Ctx& c, int64_t* nS, int64_t* gmax) {
   const mera_config& cfg = c.cfg;
   if (cfg.d_b < 2 || cfg.chi < 1 || cfg.n_trans != 0) throw Error(MERA_ERR_ARG, "MPS: d_b >= 2, chi >= 1, n_trans = 0");
   if (cfg.prec != MERA_PREC_FP64) throw Error(MERA_ERR_UNSUPPORTED, "the MPS runs in the FP64 path only");
-  if (cfg.w_stiefel) throw Error(MERA_ERR_UNSUPPORTED, "non-square Stiefel retraction not built");
+  if (cfg.w_stiefel) throw Error(MERA_ERR_UNSUPPORTED, "the MPS tensor is a Grassmann point (right rotations are gauge)");
   const int64_t D = cfg.chi, d = cfg.d_b, es = sizeof(double) * c.rs;
   c.L = 0;
   c.dims.assign(1, D);
@@ -1751,7 +1844,10 @@ void finish_create(Ctx& c, cudaStream_t s) {
     const int64_t p = c.cols[i], q = p * c.rs;
     c.eig_cache.emplace_back(sizeof(double) * q * q);
     g.Amat.emplace_back(sizeof(double) * q * q);
-    g.E.emplace_back(sizeof(double) * p * p * c.rs);
+    // a non-square Stiefel point's exponential lives on 2p dimensions
+    const bool st2 = !grass(c, i) && c.rows[i] != p;
+    g.E.emplace_back(sizeof(double) * (st2 ? 4 : 1) * p * p * c.rs);
+    g.Q2.emplace_back(st2 ? sizeof(double) * c.rows[i] * p * c.rs : 0);
     g.P1.emplace_back(sizeof(double) * p * p * c.rs);
     g.P2.emplace_back(sizeof(double) * p * p * c.rs);
     g.Pc.emplace_back(sizeof(double) * p * p * c.rs);
