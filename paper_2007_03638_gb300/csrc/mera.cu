@@ -196,6 +196,7 @@ struct mera_ctx {
   bool have_rho = false, have_x = false;
   mera::DevBuf kbasis, ktmp, kcoef;       // Krylov workspace
   mera::DevBuf scratch;                   // transient contraction buffers
+  mera::DevBuf recomp;                    // N3, N7, N8 of every layer and side when recomputed (recompute_env)
   mera::Exec ex;                          // contraction arithmetic
   mera::DevBuf tc_ws, tc_err;             // tensor-core operand planes, wait-expiry flag
   mera::DevBuf tc_keep[2];                // packed planes of loop-invariant operands (sliced chain)
@@ -341,6 +342,12 @@ void build_layers(Ctx& c) {
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
   const size_t es = (mixed ? sizeof(float) : sizeof(double)) * c.rs;
   size_t scratch_need = 0, ws_need = 0, kneed[2] = {0, 0};
+  // With recomputation, the operator-dependent nodes N3, N7, N8 are rebuilt
+  // by each side's forward pass right before they are read (the sides and
+  // layers run one after another on the stream): one set serves all.
+  const bool share = c.cfg.recompute_env != 0;
+  const int dep[3] = {13, 17, 18};
+  int64_t dep_max[3] = {0, 0, 0};
   for (int l = 0; l <= c.L; ++l) {
     Layer& ly = c.layers[l];
     ly.cf = c.dims[l];
@@ -353,8 +360,13 @@ void build_layers(Ctx& c) {
     for (int sd = 0; sd < 2; ++sd) {
       ly.net[sd] = std::make_unique<SideNet>(sd == 0 ? 'L' : 'R', ly.cf, ly.cc, c.pool, chunk);
       SideNet& net = *ly.net[sd];
-      // persistent node values: N1 N3 N4 N6 N7 N8 N9
+      // persistent node values: N1 N3 N4 N6 N7 N8 N9 (N3 N7 N8 shared when recomputed)
       for (int node : {11, 13, 14, 16, 17, 18, 19}) {
+        if (share && (node == 13 || node == 17 || node == 18)) {
+          const int k = node == 13 ? 0 : node == 17 ? 1 : 2;
+          dep_max[k] = std::max(dep_max[k], net.alloc_size(node));
+          continue;
+        }
         ly.own[sd].emplace_back(es * net.alloc_size(node));
         ly.buf[sd].val[node] = P(ly.own[sd].back());
       }
@@ -374,6 +386,20 @@ void build_layers(Ctx& c) {
     }
   }
   c.scratch.alloc(es * scratch_need);
+  if (share) {
+    // each part aligned like a separate allocation (the tensor-core epilogue
+    // picks its store path, and with it its rounding, from the alignment)
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    c.recomp.alloc(al(es * dep_max[0]) + al(es * dep_max[1]) + al(es * dep_max[2]));
+    for (int l = 0; l <= c.L; ++l)
+      for (int sd = 0; sd < 2; ++sd) {
+        char* p = static_cast<char*>(c.recomp.p);
+        for (int k = 0; k < 3; ++k) {
+          c.layers[l].buf[sd].val[dep[k]] = reinterpret_cast<double*>(p);
+          p += al(es * dep_max[k]);
+        }
+      }
+  }
   c.ex.prec = c.cfg.prec;
   if (mixed) {
     c.tc_ws.alloc(ws_need);
@@ -2201,7 +2227,7 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
     const size_t rs = cfg->dtype == MERA_C128 ? 2 : 1;
     const size_t es = (mixed ? 4 : 8) * rs;
     mera::TablePool pool(true);
-    size_t bytes = 0, scratch = 0, ws = 0, total = 0, gmax = 1, keep[2] = {0, 0};
+    size_t bytes = 0, scratch = 0, ws = 0, total = 0, gmax = 1, keep[2] = {0, 0}, dep_max[3] = {0, 0, 0};
     for (size_t l = 0; l < dims.size(); ++l) {
       const int64_t cf = dims[l], cc = l + 1 < dims.size() ? dims[l + 1] : dims[l];
       int64_t chunk = mera::choose_chunk(cf, cc);
@@ -2213,7 +2239,14 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
                                (size_t)(cf * cc * cf * cf * cf)});
       for (char sd : {'L', 'R'}) {
         mera::SideNet net(sd, cf, cc, pool, chunk);
-        for (int node : {11, 13, 14, 16, 17, 18, 19}) bytes += es * net.alloc_size(node);
+        for (int node : {11, 13, 14, 16, 17, 18, 19}) {
+          if (cfg->recompute_env && (node == 13 || node == 17 || node == 18)) {
+            const int k = node == 13 ? 0 : node == 17 ? 1 : 2;
+            dep_max[k] = std::max<size_t>(dep_max[k], net.alloc_size(node));
+            continue;
+          }
+          bytes += es * net.alloc_size(node);
+        }
         size_t need = 0;
         for (int node : {12, 15}) need += net.alloc_size(node);
         for (int node = 11; node < 20; ++node) need += net.alloc_size(node);
@@ -2227,6 +2260,7 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
       }
     }
     const size_t nS = (size_t)mera::ipow(cfg->chi, 6) * rs;
+    bytes += es * (dep_max[0] + dep_max[1] + dep_max[2]);  // shared N3, N7, N8 (recomputation)
     bytes += scratch + ws + keep[0] + keep[1] + pool.bytes();
     bytes += 8 * nS * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);  // basis, tmp, x, bvec
     bytes += 8 * gmax * 6 * rs * rs;

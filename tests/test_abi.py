@@ -119,3 +119,17 @@ def test_z2_flag_footprint(lib):
     assert gm.footprint_bytes(gm.default_config(4, 8, 3, z2=1)) == 0
     assert gm.footprint_bytes(gm.default_config(2, 8, 0, network=gm.MERA_MPS, z2=1)) == 0
     assert gm.default_config(4, 8, 3).z2 == 0
+
+
+def test_recompute_env_shares_the_operator_nodes(lib):
+    """With recompute_env = 1 the binary network keeps one set of its
+    operator-dependent intermediates (N3, N7, N8) for all layers and sides:
+    at chi = 32 split-BF16 about 41 GB less (two transition layers' worth and
+    one side's, 4 x 4.3 GB per layer and side, float)."""
+    from paper_2007_03638_gb300 import mera as gm
+    kw = dict(prec=gm.PREC_SPLIT_BF16, lbfgs_m=16, krylov_dim=4)
+    keep = gm.footprint_bytes(gm.default_config(4, 32, 3, **kw))
+    share = gm.footprint_bytes(gm.default_config(4, 32, 3, recompute_env=1, **kw))
+    assert 40e9 < keep - share < 43e9
+    assert gm.footprint_bytes(gm.default_config(4, 8, 3, recompute_env=1)) < gm.footprint_bytes(
+        gm.default_config(4, 8, 3))
