@@ -50,6 +50,8 @@ WORKLOADS = {
     "xxz_chi24_L3_bf16": ("xxz", 4, 24, 3, 2, {"lbfgs_m": 16}),
     "xxz_chi32_L3_3xtf32": ("xxz", 4, 32, 3, 1, {"lbfgs_m": 16, "krylov_dim": 4}),
     "xxz_chi32_L3_bf16": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4}),
+    # the same with environment recomputation (one set of intermediates for all layers)
+    "xxz_chi32_L3_bf16_recompute": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4, "recompute_env": 1}),
     # extra config fields: network 1 = ternary, 2 = uniform MPS (chi = bond
     # dimension D); z2 = 1: Z2 charge sectors; dtype 1 = complex128
     "ternary_ising_chi8_L2_fp64": ("ising", 2, 8, 2, 0, {"network": 1}),
@@ -69,7 +71,7 @@ DEFAULT_WORKLOAD = "xxz_chi32_L3_bf16"
 # them inside L-BFGS steps (measured by this script's own GPU runs); used only
 # to express the reference arm's bounded sample in gradient evaluations.
 FLOPS_PER_GRAD = {
-    "xxz_chi32_L3_bf16": 4.1e15, "xxz_chi32_L3_3xtf32": 4.1e15,
+    "xxz_chi32_L3_bf16": 4.1e15, "xxz_chi32_L3_3xtf32": 4.1e15, "xxz_chi32_L3_bf16_recompute": 4.1e15,
     "xxz_chi24_L3_3xtf32": 4.7e14, "xxz_chi24_L3_bf16": 4.7e14,
     "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13,
     "ising_chi12_L3_fp64": 1.6e12, "ising_chi12_L3_3xtf32": 1.13e12, "ising_chi12_L3_bf16": 1.13e12,
@@ -395,9 +397,13 @@ def main():
     net, cplx = extra.get("network", 0), extra.get("dtype", 0) == 1
     h3 = hamiltonian(kind, d_b, net)
     stream = torch.cuda.current_stream()
-    m = gm.Mera(gm.default_config(d_b, chi, L, prec=prec, **extra), h3, stream=stream.cuda_stream)
+    cfg = gm.default_config(d_b, chi, L, prec=prec, **extra)
+    free0, _ = torch.cuda.mem_get_info()
+    m = gm.Mera(cfg, h3, stream=stream.cuda_stream)
     point = initial_point(d_b, chi, L, extra, args.seed + rank)
     m.set_tensors(point)
+    free1, _ = torch.cuda.mem_get_info()
+    memory = {"device_bytes": int(free0 - free1), "footprint_bytes": gm.footprint_bytes(cfg)}
     if args.energy_once:
         print(json.dumps({"workload": args.workload, "energy": m.energy(), "launches": m.launch_count()}))
         return
@@ -494,6 +500,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "call": "mera_set_tensors(host) + mera_energy_grad(grad -> host)"},
             "gpu_launches": st["launches"],
+            "memory": memory,
             "clocks": clocks.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if args.workload in WHOLE_EVAL:

@@ -87,6 +87,8 @@ def fake_device(monkeypatch):
     monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
     monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: _Stream())
+    free = iter([10 * 2**30, 7 * 2**30] * 4)
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (next(free), 16 * 2**30))
     monkeypatch.setattr(torch.cuda.nvtx, "range_push", lambda *a: None)
     monkeypatch.setattr(torch.cuda.nvtx, "range_pop", lambda *a: None)
     monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
@@ -125,3 +127,4 @@ def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
     assert line["e2e"]["h2d_bytes_per_step"] > 0
     for k in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert k in line["clocks"], k
+    assert line["memory"]["device_bytes"] == 3 * 2**30 and line["memory"]["footprint_bytes"] > 0
