@@ -11,12 +11,8 @@
 //                 rho_l and the environments; the scale-invariant layer uses
 //                 Tr(Abar_S(x) rho_S)
 //     projection  Eqs. (stiefel_gradient), (grassmann_gradient)
-//   geometry      retraction / transport (Eqs. retraction, transport) with the
-//                 low-rank forms: W exp(alpha W^dag X) for unitaries, sines and
-//                 cosines of the singular values of X for Grassmann tangents;
-//                 polar re-isometrisation by Newton-Schulz
-//   preconditioner Eq. (preconditioner_solution) in the eigenbasis of rho_v
-//   optimiser     L-BFGS two-loop / Hager-Zhang CG, Hager-Zhang line search
+//     rho_v       the density matrices of the preconditioner (Sec. 4)
+//   creation      shapes, networks and buffers; input checks (isometry, Z2)
 #include "ctx.h"
 
 #include <algorithm>
