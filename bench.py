@@ -59,6 +59,7 @@ WORKLOADS = {
     "ternary_xxz_chi16_L2_3xtf32": ("xxz", 2, 16, 2, 1, {"network": 1}),
     "ternary_xxz_chi16_L2_3xtf32_z2": ("xxz", 2, 16, 2, 1, {"network": 1, "z2": 1}),
     "mps_xxz_D32_fp64": ("xxz", 2, 32, 0, 0, {"network": 2}),
+    "ising_chi16_L3_3xtf32_z2": ("ising", 4, 16, 3, 1, {"z2": 1, "lbfgs_m": 16}),
     "ising_hz_chi8_L3_c128_fp64": ("ising_hz", 4, 8, 3, 0, {"dtype": 1}),
     "ising_hz_chi16_L3_c128_3xtf32": ("ising_hz", 4, 16, 3, 1, {"dtype": 1, "lbfgs_m": 16}),
 }
@@ -79,6 +80,8 @@ FLOPS_PER_GRAD = {
     # complex workloads: 4 x the real workload's (8 real flops per complex
     # multiply-add), an estimate until measured
     "ising_hz_chi8_L3_c128_fp64": 2e11, "ising_hz_chi16_L3_c128_3xtf32": 5.8e13,
+    # Z2 workloads: the dense evaluation's count (the oracle contracts densely)
+    "ising_chi16_L3_3xtf32_z2": 1.45e13,
 }
 METRIC = "MERA grad evals/s"
 UNIT = "grad_evals/s"
@@ -107,16 +110,18 @@ def tensor_peaks():
 GETT_TRAFFIC_BYTES = {}
 
 
-def hamiltonian(kind, d_b, network=0):
+def hamiltonian(kind, d_b, network=0, z2=False):
     """The workload's Hamiltonian term: critical Ising, Ising with a
     longitudinal field h_z = 0.13 (-h_z X per spin) or the Heisenberg chain;
     three-site (blocked spin pairs when d_b = 4) for the binary MERA, the
-    two-site bond for the ternary MERA and the MPS."""
+    two-site bond for the ternary MERA and the MPS; blocked pairs in the
+    parity-ordered basis for Z2-symmetric binary problems."""
     bond = (inp.ising_bond(1.0) if kind == "ising" else inp.ising_bond(1.0, 0.13) if kind == "ising_hz"
             else inp.xxz_bond(1.0))
     if network in (1, 2):
         return bond
-    return inp.three_site_blocked(bond) if d_b == 4 else inp.three_site_unblocked(bond)
+    h3 = inp.three_site_blocked(bond) if d_b == 4 else inp.three_site_unblocked(bond)
+    return inp.parity_ordered_three_site(h3) if (z2 and d_b == 4) else h3
 
 
 def initial_point(d_b, chi, L, extra, seed):
@@ -129,6 +134,8 @@ def initial_point(d_b, chi, L, extra, seed):
     if net == 1:
         us, ws = (inp.random_z2_ternary_mera(chi, L, seed=seed, dtype=dt) if extra.get("z2")
                   else inp.random_ternary_mera(d_b, chi, L, seed=seed, dtype=dt))
+    elif extra.get("z2"):
+        us, ws = inp.random_z2_mera(d_b, chi, L, seed=seed, dtype=dt)
     else:
         us, ws = inp.random_mera(d_b, chi, L, seed=seed, dtype=dt)
     return [t for p in zip(us, ws) for t in p]
@@ -236,7 +243,7 @@ def oracle_eval_sample(wl, seconds=10.0, seed=0):
     evaluation, evaluations)."""
     kind, d_b, chi, L, prec, extra = wl
     net = extra.get("network", 0)
-    h = hamiltonian(kind, d_b, net)
+    h = hamiltonian(kind, d_b, net, bool(extra.get("z2", 0)))
     point = initial_point(d_b, chi, L, extra, seed)
     if net == 2:
         from oracle import mps
@@ -395,7 +402,7 @@ def main():
 
     kind, d_b, chi, L, prec, extra = wl
     net, cplx = extra.get("network", 0), extra.get("dtype", 0) == 1
-    h3 = hamiltonian(kind, d_b, net)
+    h3 = hamiltonian(kind, d_b, net, bool(extra.get("z2", 0)))
     stream = torch.cuda.current_stream()
     cfg = gm.default_config(d_b, chi, L, prec=prec, **extra)
     free0, _ = torch.cuda.mem_get_info()
@@ -510,7 +517,9 @@ def main():
                                               f"workload at its seeded point, {t:.2f} s each"}
         else:
             t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds, cplx=cplx)
-            frac = part * ascend_flops(cf, cc) * (4 if cplx else 1) / gett_flops_per_grad
+            # the oracle contracts densely: a Z2 workload's fraction is of the dense count
+            per_grad = FLOPS_PER_GRAD[args.workload] if extra.get("z2") else gett_flops_per_grad
+            frac = part * ascend_flops(cf, cc) * (4 if cplx else 1) / per_grad
             line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                     "sample": f"{n} x oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}"
                                               f"ascending map of layer {layer} "

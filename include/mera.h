@@ -113,17 +113,21 @@ typedef struct {
                           7-leg intermediate has at most 2^30 entries)        */
     int network;       /* mera_network: MERA_BINARY (default), MERA_TERNARY
                           or MERA_MPS                                          */
-    int z2;            /* 1: Z2-symmetric problem (ternary network only):
-                          every leg is graded (the first half of its basis
-                          even, the rest odd), the Hamiltonian term and the
-                          tensors must be symmetric (an entry between index
-                          tuples of different total charge is zero, Sec. 6;
-                          mera_create / mera_set_tensors return MERA_ERR_ARG
-                          when one exceeds 1e-12 of the largest entry), and
-                          every contraction of the networks runs as its two
-                          charge sectors, a quarter of the dense work.  The
-                          results are those of the dense path.  Binary
-                          network or MPS with z2 = 1: MERA_ERR_UNSUPPORTED.  */
+    int z2;            /* 1: Z2-symmetric problem: every leg is graded (the
+                          first half of its basis even, the rest odd), the
+                          Hamiltonian term and the tensors must be symmetric
+                          (an entry between index tuples of different total
+                          charge is zero, Sec. 6; mera_create /
+                          mera_set_tensors return MERA_ERR_ARG when one
+                          exceeds 1e-12 of the largest entry), and every
+                          contraction of the networks runs as its two charge
+                          sectors, a quarter of the dense work; the results
+                          are those of the dense path.  Ternary network; the
+                          binary one where its chi^9 chain needs no slicing
+                          (chi_l^6 chi_{l+1} <= 2^30 on every layer, chi <= 16
+                          from d_b = 4: blocked spin pairs must then be in a
+                          basis whose first half is even); otherwise, and for
+                          an MPS, MERA_ERR_UNSUPPORTED.                      */
 } mera_config;
 
 /* Network of the MERA (Sec. 4).  MERA_BINARY: the binary MERA described

@@ -120,11 +120,11 @@ int mera_init_random(mera_t m, uint64_t seed) {
     std::vector<double> host(m->total);
     for (int i = 0; i < m->nt; ++i) {
       std::vector<int> rq, cq;
-      if (m->z2) {  // ternary: u_l (cf cf) x (cf cf), w_l (cf cf cf) x (cc)
-        const int l = i / 2;
-        const int64_t cf = m->dims[l], cc = l < m->L ? m->dims[l + 1] : m->dims[l];
-        rq = mera::fused_charges(i % 2 == 0 ? std::vector<int64_t>{cf, cf} : std::vector<int64_t>{cf, cf, cf});
-        cq = mera::fused_charges(i % 2 == 0 ? std::vector<int64_t>{cf, cf} : std::vector<int64_t>{cc});
+      if (m->z2) {
+        std::vector<int64_t> rows, cols;
+        mera::tensor_legs(*m, i, rows, cols);
+        rq = mera::fused_charges(rows);
+        cq = mera::fused_charges(cols);
       }
       mera::random_isometry(seed, (uint64_t)i, m->rows[i], m->cols[i], m->cplx, m->z2 ? rq.data() : nullptr,
                             m->z2 ? cq.data() : nullptr, host.data() + m->offs[i]);
@@ -276,11 +276,15 @@ size_t footprint_mps(const mera_config* cfg) {
 }
 
 // mera_footprint_bytes for the ternary network
-size_t footprint_ternary(const mera_config* cfg) {
+// mera_footprint_bytes for the data-defined networks: the ternary MERA, or
+// the binary one with Z2 charge sectors (0 where its chain would be sliced)
+size_t footprint_net(const mera_config* cfg) {
+  const bool tern = cfg->network == MERA_TERNARY;
+  const int ns = tern ? 2 : 3;  // sites of a level operator
   std::vector<int64_t> dims{cfg->d_b};
   for (int l = 0; l < cfg->n_trans; ++l) {
     const int64_t d = dims.back();
-    dims.push_back(std::min<int64_t>(cfg->chi, d * d * d));
+    dims.push_back(std::min<int64_t>(cfg->chi, tern ? d * d * d : d * d));
   }
   if (dims.back() != cfg->chi) return 0;
   const bool mixed = cfg->prec != MERA_PREC_FP64;
@@ -290,20 +294,24 @@ size_t footprint_ternary(const mera_config* cfg) {
   size_t bytes = 0, ws = 0, total = 0, gmax = 1;
   for (size_t l = 0; l < dims.size(); ++l) {
     const int64_t cf = dims[l], cc = l + 1 < dims.size() ? dims[l + 1] : dims[l];
-    total += (cf * cf * cf * cf + cf * cf * cf * cc) * rs;
-    bytes += 2 * 8 * rs * (size_t)mera::ipow(cf, 4);  // h_l, rho_l
+    if (!tern && (mera::choose_chunk(cf, cc) != 0 || (cfg->b_chunk > 0 && cfg->b_chunk < cc))) return 0;
+    const int64_t wr = tern ? cf * cf * cf : cf * cf;
+    total += (cf * cf * cf * cf + wr * cc) * rs;
+    bytes += 2 * 8 * rs * (size_t)mera::ipow(cf, 2 * ns);  // h_l, rho_l
     gmax = std::max<size_t>({gmax, (size_t)(cf * cf * cf * cf), (size_t)(cc * cc * cc * cc),
                              (size_t)(cf * cf * cc * cc * cc), (size_t)(cf * cc * cc * cf),
-                             (size_t)(cf * cc * cf * cf * cf), (size_t)(cf * cf * cf * cc),
-                             (size_t)(cf * cf * cf * cc * cc * cc), (size_t)(cf * cf * cf * cf * cf * cc)});
-    for (char sd : {'L', 'C', 'R'}) {
-      mera::Net net(mera::ternary_netdef(sd), cf, cc, pool);
+                             (size_t)(cf * cc * cf * cf * cf)});
+    if (tern)
+      gmax = std::max<size_t>({gmax, (size_t)(cf * cf * cf * cc), (size_t)(cf * cf * cf * cc * cc * cc),
+                               (size_t)(cf * cf * cf * cf * cf * cc)});
+    for (char sd : std::string(tern ? "LCR" : "LR")) {
+      mera::Net net(tern ? mera::ternary_netdef(sd) : mera::binary_netdef(sd), cf, cc, pool, cfg->z2 == 1);
       for (int node = net.nleaf(); node < net.nnode(); ++node)
         bytes += es * (size_t)net.size(node) * (node == net.root() ? 1 : 2);
       for (const mera::GemmPlan* p : net.plans()) ws = std::max(ws, mera::tc_workspace_bytes(p->proto, cfg->prec));
     }
   }
-  const size_t nS = (size_t)mera::ipow(cfg->chi, 4) * rs;
+  const size_t nS = (size_t)mera::ipow(cfg->chi, 2 * ns) * rs;
   bytes += ws + pool.bytes();
   bytes += 8 * nS * (size_t)(std::max(2, cfg->krylov_dim) + 1 + 3);  // basis, tmp, x, bvec
   bytes += 8 * gmax * 6 * rs * rs;
@@ -314,12 +322,12 @@ size_t footprint_ternary(const mera_config* cfg) {
 
 size_t mera_footprint_bytes(const mera_config* cfg) {
   if (!cfg) return 0;
-  if (cfg->z2 != 0 && (cfg->z2 != 1 || cfg->network != MERA_TERNARY)) return 0;
+  if (cfg->z2 != 0 && (cfg->z2 != 1 || cfg->network == MERA_MPS)) return 0;
   if (cfg->network == MERA_MPS) return footprint_mps(cfg);
   if (cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
-  if (cfg->network == MERA_TERNARY) {
+  if (cfg->network == MERA_TERNARY || (cfg->network == MERA_BINARY && cfg->z2 == 1)) {
     try {
-      return footprint_ternary(cfg);
+      return footprint_net(cfg);
     } catch (...) {
       return 0;
     }

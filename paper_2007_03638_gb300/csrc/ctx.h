@@ -59,7 +59,9 @@ struct mera_ctx {
   double hshift = 0.0;                    // evaluations use h3 - hshift 1 (Evenbly-Vidal sweeps)
   bool tern = false;                      // ternary network
   bool mps = false;                       // uniform MPS (one Grassmann tensor, two-site term)
-  bool z2 = false;                        // Z2-symmetric ternary problem: networks run by charge sector
+  bool z2 = false;                        // Z2-symmetric problem: networks run by charge sector
+  bool gnet = false;                      // networks on the data-defined executor (ternary; Z2 binary)
+  int nsides = 2;                         // ascending maps per layer (3 ternary, 2 binary)
   int ns = 3;                             // sites of a level operator (3 binary, 2 ternary)
   int rs = 1;                             // reals per element (1 or 2)
   int L = 0, nt = 0;
@@ -154,6 +156,8 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s);
 double forward_energy(Ctx& c, const double* W, cudaStream_t s);
 void check_isometric(Ctx& c, const double* W, cudaStream_t s);
 std::vector<int> fused_charges(const std::vector<int64_t>& dims);
+// legs (dimensions) of the rows and columns of tensor i of a MERA point
+void tensor_legs(const Ctx& c, int i, std::vector<int64_t>& rows, std::vector<int64_t>& cols);
 void check_z2_point(Ctx& c, const double* W, cudaStream_t s);
 void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s);
 

@@ -69,18 +69,26 @@ int64_t choose_chunk(int64_t cf, int64_t cc) {
   return nb;
 }
 
-// Ternary network: three networks per layer, every internal node value and
-// adjoint in its own buffer (no intermediate above chi^6).
-void build_layers_ternary(Ctx& c) {
+// Data-defined networks (tnet.h): the ternary network's three per layer (no
+// intermediate above chi^6), or the binary network's two for Z2-symmetric
+// problems (unsliced chains only); every internal node value and adjoint in
+// its own buffer.
+void build_layers_net(Ctx& c) {
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
   const size_t es = (mixed ? sizeof(float) : sizeof(double)) * c.rs;
   size_t ws_need = 0;
+  for (int l = 0; l <= c.L && !c.tern; ++l) {
+    const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+    if (choose_chunk(cf, cc) != 0 || (c.cfg.b_chunk > 0 && c.cfg.b_chunk < cc))
+      throw Error(MERA_ERR_UNSUPPORTED, "Z2 charge sectors of the binary network need an unsliced chain (chi <= 16)");
+  }
   for (int l = 0; l <= c.L; ++l) {
     Layer& ly = c.layers[l];
     ly.cf = c.dims[l];
     ly.cc = l < c.L ? c.dims[l + 1] : c.dims[l];
-    for (int sd = 0; sd < 3; ++sd) {
-      ly.tnet[sd] = std::make_unique<Net>(ternary_netdef("LCR"[sd]), ly.cf, ly.cc, c.pool, c.z2);
+    for (int sd = 0; sd < c.nsides; ++sd) {
+      ly.tnet[sd] = std::make_unique<Net>(c.tern ? ternary_netdef("LCR"[sd]) : binary_netdef("LR"[sd]), ly.cf, ly.cc,
+                                          c.pool, c.z2);
       Net& net = *ly.tnet[sd];
       NetBufs& b = ly.tbuf[sd];
       b.leaf.assign(net.nleaf(), nullptr);
@@ -116,7 +124,7 @@ void build_layers_ternary(Ctx& c) {
   }
 }
 
-void bind_ternary(Layer& ly, int sd, const double* op, const double* u, const double* w) {
+void bind_net(Layer& ly, int sd, const double* op, const double* u, const double* w) {
   NetBufs& b = ly.tbuf[sd];
   const Net& net = *ly.tnet[sd];
   for (int i = 0; i < net.nleaf(); ++i) {
@@ -127,8 +135,8 @@ void bind_ternary(Layer& ly, int sd, const double* op, const double* u, const do
 
 void build_layers(Ctx& c) {
   c.layers.resize(c.L + 1);
-  if (c.tern) {
-    build_layers_ternary(c);
+  if (c.gnet) {
+    build_layers_net(c);
     return;
   }
   const bool mixed = c.cfg.prec != MERA_PREC_FP64;
@@ -241,10 +249,10 @@ void ascend(Ctx& c, int l, const double* W, const double* op, double* out, doubl
   Layer& ly = c.layers[l];
   const double* u = W + c.offs[2 * l];
   const double* w = W + c.offs[2 * l + 1];
-  if (c.tern) {  // Abar = (A_L + A_C + A_R) / 3
-    for (int sd = 0; sd < 3; ++sd) {
-      bind_ternary(ly, sd, op, u, w);
-      net_forward(*ly.tnet[sd], ly.tbuf[sd], out, af / 3.0, 1.0, s);
+  if (c.gnet) {  // Abar = the average of the nsides maps
+    for (int sd = 0; sd < c.nsides; ++sd) {
+      bind_net(ly, sd, op, u, w);
+      net_forward(*ly.tnet[sd], ly.tbuf[sd], out, af / c.nsides, 1.0, s);
     }
     return;
   }
@@ -258,9 +266,9 @@ void prepare_layer(Ctx& c, int l, const double* W, cudaStream_t s) {
   Layer& ly = c.layers[l];
   const double* u = W + c.offs[2 * l];
   const double* w = W + c.offs[2 * l + 1];
-  if (c.tern) {
-    for (int sd = 0; sd < 3; ++sd) {
-      bind_ternary(ly, sd, nullptr, u, w);
+  if (c.gnet) {
+    for (int sd = 0; sd < c.nsides; ++sd) {
+      bind_net(ly, sd, nullptr, u, w);
       net_prepare(*ly.tnet[sd], ly.tbuf[sd], s);
     }
     return;
@@ -274,9 +282,9 @@ void prepare_layer(Ctx& c, int l, const double* W, cudaStream_t s) {
 // out += af * Dbar(r) (both sides); operator-path reverse pass only.
 void descend(Ctx& c, int l, const double* r, double* out, double af, cudaStream_t s) {
   Layer& ly = c.layers[l];
-  if (c.tern) {  // Dbar = (D_L + D_C + D_R) / 3; needs only the prepared values
-    for (int sd = 0; sd < 3; ++sd)
-      net_backward(*ly.tnet[sd], ly.tbuf[sd], r, true, out, af / 3.0, false, nullptr, nullptr, 0.0, s);
+  if (c.gnet) {  // Dbar = the average of the nsides adjoint maps; needs only the prepared values
+    for (int sd = 0; sd < c.nsides; ++sd)
+      net_backward(*ly.tnet[sd], ly.tbuf[sd], r, true, out, af / c.nsides, false, nullptr, nullptr, 0.0, s);
     return;
   }
   for (int sd = 0; sd < 2; ++sd) {
@@ -491,14 +499,14 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
     const double* r = l < L ? P(c.rho[l + 1]) : rhoS;
     const bool need_op = l < L;
     if (need_op) fill(0.0, P(c.rho[l]), opn(c, ly.cf) * opn(c, ly.cf) * c.rs, s);
-    for (int sd = 0; c.tern && sd < 3; ++sd) {
-      // D_v = 2 dC/d conj(v) with C = Tr(Abar(h) rho), Abar the average of three maps
-      bind_ternary(ly, sd, op, u, w);
+    for (int sd = 0; c.gnet && sd < c.nsides; ++sd) {
+      // D_v = 2 dC/d conj(v) with C = Tr(Abar(h) rho), Abar the average of the nsides maps
+      bind_net(ly, sd, op, u, w);
       if (l == L || c.cfg.recompute_env) net_forward(*ly.tnet[sd], ly.tbuf[sd], nullptr, 0.0, 0.0, s);
-      net_backward(*ly.tnet[sd], ly.tbuf[sd], r, need_op, need_op ? P(c.rho[l]) : nullptr, 1.0 / 3.0, true,
-                   D + c.offs[2 * l], D + c.offs[2 * l + 1], 2.0 / 3.0, s);
+      net_backward(*ly.tnet[sd], ly.tbuf[sd], r, need_op, need_op ? P(c.rho[l]) : nullptr, 1.0 / c.nsides, true,
+                   D + c.offs[2 * l], D + c.offs[2 * l + 1], 2.0 / c.nsides, s);
     }
-    for (int sd = 0; !c.tern && sd < 2; ++sd) {
+    for (int sd = 0; !c.gnet && sd < 2; ++sd) {
       SideBufs& b = ly.buf[sd];
       bind_leaves(ly, sd, op, u, w);
       // the reverse pass needs N3, N7, N8 for this layer's operator: the
@@ -707,13 +715,25 @@ void check_z2(Ctx& c, const double* dev, const std::vector<int64_t>& rdims, cons
                                   " between different charges)");
 }
 
-// Z2 symmetry of every tensor of a ternary point: u_l (cf cf) x (cf cf),
-// w_l (cf cf cf) x (cc).
+// Legs of the rows and columns of tensor i of a MERA point: u_l (cf cf) x
+// (cf cf), w_l (cf cf) x (cc) binary or (cf cf cf) x (cc) ternary.
+void tensor_legs(const Ctx& c, int i, std::vector<int64_t>& rows, std::vector<int64_t>& cols) {
+  const int l = i / 2;
+  const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
+  if (i % 2 == 0) {
+    rows = cols = {cf, cf};
+  } else {
+    rows.assign(c.tern ? 3 : 2, cf);
+    cols = {cc};
+  }
+}
+
+// Z2 symmetry of every tensor of a MERA point.
 void check_z2_point(Ctx& c, const double* W, cudaStream_t s) {
-  for (int l = 0; l <= c.L; ++l) {
-    const int64_t cf = c.dims[l], cc = l < c.L ? c.dims[l + 1] : c.dims[l];
-    check_z2(c, W + c.offs[2 * l], {cf, cf}, {cf, cf}, "u_" + std::to_string(l), s);
-    check_z2(c, W + c.offs[2 * l + 1], {cf, cf, cf}, {cc}, "w_" + std::to_string(l), s);
+  for (int i = 0; i < c.nt; ++i) {
+    std::vector<int64_t> rows, cols;
+    tensor_legs(c, i, rows, cols);
+    check_z2(c, W + c.offs[i], rows, cols, (i % 2 == 0 ? "u_" : "w_") + std::to_string(i / 2), s);
   }
 }
 
@@ -731,7 +751,9 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.mps = cfg.network == MERA_MPS;
   if (cfg.z2 != 0 && cfg.z2 != 1) throw Error(MERA_ERR_ARG, "z2 must be 0 or 1");
   c.z2 = cfg.z2 == 1;
-  if (c.z2 && !c.tern) throw Error(MERA_ERR_UNSUPPORTED, "Z2 charge sectors are built for the ternary network");
+  if (c.z2 && c.mps) throw Error(MERA_ERR_UNSUPPORTED, "Z2 charge sectors are built for the MERA networks");
+  c.gnet = c.tern || c.z2;
+  c.nsides = c.tern ? 3 : 2;
   c.ns = c.tern || c.mps ? 2 : 3;
   c.pool.set_stream(s);
   int64_t nS = 0, gmax = 1;  // reals of one Krylov vector; elements of a geometry temporary
@@ -746,8 +768,8 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 2 * c.ns) * c.rs);
   MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
   if (c.z2) {
-    const std::vector<int64_t> pair{cfg.d_b, cfg.d_b};
-    check_z2(c, P(c.h0), pair, pair, "the Hamiltonian term", s);
+    const std::vector<int64_t> sites(c.ns, cfg.d_b);
+    check_z2(c, P(c.h0), sites, sites, "the Hamiltonian term", s);
   }
   c.x.alloc(sizeof(double) * nS);
   c.kbasis.alloc(sizeof(double) * nS * (std::max(2, cfg.krylov_dim) + 1));

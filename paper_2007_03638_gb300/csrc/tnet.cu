@@ -37,6 +37,29 @@ NetDef ternary_netdef(char side) {
   return d;
 }
 
+NetDef binary_netdef(char side) {
+  // The binary MERA's A_L (o on fine 0,1,2) and A_R (o on fine 1,2,3): the
+  // same leaves, legs and pairwise tree as the sliced executor of tn.cu
+  // (2.13 chi^9 per side, one 7-leg intermediate), given as data.
+  NetDef d;
+  d.out = "a b c A B C";
+  d.rho = "A B C a b c";
+  if (side == 'L') {
+    d.legs = {"f0 f1 f2 g0 g1 g2", "f1 f2 x1 x2", "g1 g2 y1 y2", "fm f0 xm x0", "x0 x1 b", "fm g0 ym y0",
+              "y0 y1 B", "xl xm a", "xl ym A", "x2 x3 c", "y2 x3 C"};
+    d.op_adj = "g0 g1 g2 f0 f1 f2";
+  } else if (side == 'R') {
+    d.legs = {"f1 f2 f3 g1 g2 g3", "f1 f2 x1 x2", "g1 g2 y1 y2", "f3 f4 x3 x4", "x2 x3 b", "g3 f4 y3 y4",
+              "y2 y3 B", "x4 x5 c", "y4 x5 C", "x0 x1 a", "x0 y1 A"};
+    d.op_adj = "g1 g2 g3 f1 f2 f3";
+  } else {
+    throw Error(MERA_ERR_ARG, "binary_netdef: side must be L or R");
+  }
+  d.role = {ROLE_OP, ROLE_UB, ROLE_U, ROLE_UB, ROLE_WB, ROLE_U, ROLE_W, ROLE_WB, ROLE_W, ROLE_WB, ROLE_W};
+  d.kids = {{7, 8}, {0, 1}, {12, 2}, {3, 4}, {13, 14}, {5, 6}, {15, 16}, {11, 17}, {9, 10}, {18, 19}};
+  return d;
+}
+
 namespace {
 std::vector<std::string> words(const std::string& s) {
   std::istringstream is(s);

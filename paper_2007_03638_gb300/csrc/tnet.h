@@ -2,8 +2,9 @@
 // pairwise contraction tree.  With z2 set, every leg carries the Z2 grading of
 // tn.h (first half of its basis even) and every pairwise product runs as its
 // two charge sectors (a quarter of the dense work), which is exact when the
-// leaves and the seed are Z2-symmetric.  Used for the ternary MERA's three ascending
-// networks (the binary network has its own sliced executor, tn.h).  One
+// leaves and the seed are Z2-symmetric.  Used for the ternary MERA's three
+// ascending networks and for Z2-symmetric binary problems (the binary
+// network's default executor, which slices its chi^9 chain, is in tn.h).  One
 // forward pass evaluates the ascended operator; one reverse pass seeded with
 // the density matrix gives the descended operator (the adjoint of the
 // operator leaf) and the environments (adjoints of the conjugated u and w
@@ -30,6 +31,9 @@ struct NetDef {
 
 // The ternary MERA's networks A_L, A_C, A_R (side 'L', 'C', 'R').
 NetDef ternary_netdef(char side);
+// The binary MERA's networks A_L, A_R (side 'L', 'R'), for the executor below
+// (unsliced chains: the Z2 charge sectors of binary problems).
+NetDef binary_netdef(char side);
 
 // The plans of one pairwise product: the dense plan, or its nonempty Z2
 // charge sectors.

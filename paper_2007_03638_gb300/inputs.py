@@ -236,3 +236,34 @@ def random_z2_ternary_mera(chi: int, n_trans: int, seed: int, dtype=np.float64):
         us.append(_z2_block_isometry(rng, pair, pair, dtype))
         ws.append(_z2_block_isometry(rng, fused_parities(c, c, c), z2_parities(cp), dtype))
     return us, ws
+
+
+# Basis of a blocked spin pair (s1 s2) ordered by parity: the even states
+# |00>, |11> first, then the odd |01>, |10>, so that the first half of the
+# site's basis is even (the grading of the library's Z2 mode).
+PAIR_PARITY_ORDER = np.array([0, 3, 1, 2])
+
+
+def parity_ordered_three_site(h3: np.ndarray) -> np.ndarray:
+    """A three-site term on blocked spin pairs (three_site_blocked) in the
+    parity-ordered site basis: P h3 P^T with P the permutation
+    PAIR_PARITY_ORDER on each of the three sites."""
+    perm = np.array([(a * 16 + b * 4 + c) for a in PAIR_PARITY_ORDER for b in PAIR_PARITY_ORDER
+                     for c in PAIR_PARITY_ORDER])
+    return h3[np.ix_(perm, perm)]
+
+
+def random_z2_mera(d_b: int, chi: int, n_trans: int, seed: int, dtype=np.float64):
+    """Seeded Z2-symmetric binary MERA: every u and w maps each charge sector
+    into the same sector (parities of fine legs fused, every leg graded with
+    the first half of its basis even)."""
+    rng = np.random.default_rng(seed)
+    dims = layer_dims(d_b, chi, n_trans)
+    us, ws = [], []
+    for l in range(n_trans + 1):
+        c = dims[l]
+        cp = dims[l + 1] if l < n_trans else dims[n_trans]
+        pair = fused_parities(c, c)
+        us.append(_z2_block_isometry(rng, pair, pair, dtype))
+        ws.append(_z2_block_isometry(rng, pair, z2_parities(cp), dtype))
+    return us, ws

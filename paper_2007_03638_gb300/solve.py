@@ -38,8 +38,9 @@ def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
     """(h, d_b, tensors, spins per bottom site) of a run: the binary network on
     blocked sites (two spins, three-site term), the ternary one and the uniform
     MPS (bond dimension chi, n_trans unused) on spins (two-site term); z2:
-    Z2-symmetric ternary starting point (run() then sets the library's Z2
-    mode, which contracts by charge sector)."""
+    Z2-symmetric starting point (binary: blocked pairs in the parity-ordered
+    basis), and run() sets the library's Z2 mode, which contracts by charge
+    sector."""
     bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
     if network == "mps":
         if z2:
@@ -50,8 +51,10 @@ def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
         us, ws = (inp.random_z2_ternary_mera(chi, n_trans, seed=seed) if z2
                   else inp.random_ternary_mera(2, chi, n_trans, seed=seed))
         return bond, 2, [t for p in zip(us, ws) for t in p], 1
-    if z2:
-        raise ValueError("Z2-symmetric starting points are built for the ternary network")
+    if z2:  # blocked spin pairs in the parity-ordered basis, symmetric tensors
+        us, ws = inp.random_z2_mera(4, chi, n_trans, seed=seed)
+        return (inp.parity_ordered_three_site(inp.three_site_blocked(bond)), 4,
+                [t for p in zip(us, ws) for t in p], 2)
     us, ws = inp.random_mera(4, chi, n_trans, seed=seed)
     return inp.three_site_blocked(bond), 4, [t for p in zip(us, ws) for t in p], 2
 
@@ -105,7 +108,7 @@ def main():
     ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev"])
     ap.add_argument("--network", default="binary", choices=["binary", "ternary", "mps"])
     ap.add_argument("--z2", action="store_true",
-                    help="Z2-symmetric problem (ternary network): symmetric starting point, contractions by charge sector")
+                    help="Z2-symmetric problem (ternary, or binary up to chi = 16): contractions by charge sector")
     ap.add_argument("--ev-gamma", type=float, default=None,
                     help="Evenbly-Vidal Hamiltonian shift (default: largest eigenvalue of the 3-site term + 0.5)")
     ap.add_argument("--iters", type=int, default=300)

@@ -24,8 +24,9 @@
 // conjugated, beta 0 or not), the four real products of mera::complex_parts on
 // the real view (mera::real_view) reproduce alpha op(A) op(B) + beta C computed
 // from the definition, and the real view's output hints hold.
-// Finally the library's ternary networks build with charge-sector plans, and
-// both networks with real views, on a dry table pool.
+// Finally the library's networks build on a dry table pool: the data-defined
+// ternary and binary ones with charge-sector plans and real views, the sliced
+// binary executor with real views.
 // Prints "ok <cases>", "complex ok <cases>", "networks ok <n>" and the grading
 // of extents 1..6 on success, else the first failure, and exits non-zero.
 #include "tn.h"
@@ -302,6 +303,12 @@ int main() {
           mera::Net net(mera::ternary_netdef(side), dims[0], dims[1], pool, mode == 1);
           for (const mera::GemmPlan* p : net.plans())
             if (mode == 2 && !p->proto.has_rv) throw std::runtime_error("a ternary plan without its real view");
+          ++nets;
+        }
+        for (char side : {'L', 'R'}) {  // the binary network as data (Z2 binary problems)
+          mera::Net net(mera::binary_netdef(side), dims[0], dims[1], pool, mode == 1);
+          for (const mera::GemmPlan* p : net.plans())
+            if (mode == 2 && !p->proto.has_rv) throw std::runtime_error("a binary plan without its real view");
           ++nets;
         }
         if (mode != 1)

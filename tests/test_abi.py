@@ -110,13 +110,15 @@ def test_mps_footprint(lib):
 
 
 def test_z2_flag_footprint(lib):
-    """mera_config.z2: served for the ternary network only (the footprint, a
-    dry run of the allocations, is 0 for what mera_create refuses)."""
+    """mera_config.z2: served for the ternary network, and for the binary one
+    where its chi^9 chain runs unsliced (the footprint, a dry run of the
+    allocations, is 0 for what mera_create refuses)."""
     from paper_2007_03638_gb300 import mera as gm
     tern = gm.footprint_bytes(gm.default_config(2, 8, 2, network=gm.MERA_TERNARY, z2=1))
     assert tern > 0
     assert gm.footprint_bytes(gm.default_config(2, 8, 2, network=gm.MERA_TERNARY, z2=2)) == 0
-    assert gm.footprint_bytes(gm.default_config(4, 8, 3, z2=1)) == 0
+    assert gm.footprint_bytes(gm.default_config(4, 8, 3, z2=1)) > 0
+    assert gm.footprint_bytes(gm.default_config(4, 32, 3, z2=1)) == 0  # sliced chain
     assert gm.footprint_bytes(gm.default_config(2, 8, 0, network=gm.MERA_MPS, z2=1)) == 0
     assert gm.default_config(4, 8, 3).z2 == 0
 

@@ -102,7 +102,8 @@ CONTRACT = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step
 
 
 @pytest.mark.parametrize("workload", ["ising_chi4_L2_fp64", "ising_chi12_L3_bf16", "ternary_ising_chi8_L2_fp64_z2",
-                                      "mps_xxz_D32_fp64", "ising_hz_chi8_L3_c128_fp64"])
+                                      "mps_xxz_D32_fp64", "ising_hz_chi8_L3_c128_fp64",
+                                      "ising_chi16_L3_3xtf32_z2"])
 def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", workload, "--steps", "2", "--warmup", "3",
                                       "--cpu-seconds", "0.1"])

@@ -1,10 +1,12 @@
-"""Z2-symmetric ternary MERA on the GPU (mera_config.z2 = 1, Sec. 6; the
-setting of Fig. 2: Ising chain, chi = 8, two transition layers): every network
-contraction runs as its two charge sectors.  Against the ternary oracle and the
-dense GPU path on the same symmetric point: energy and every partial derivative
-at 1e-12 in FP64, within the mixed-precision bound for 3xTF32, derivatives
-exactly symmetric; L-BFGS keeps the tensors symmetric and follows the dense
-path; non-symmetric tensors or Hamiltonians are refused."""
+"""Z2-symmetric MERA on the GPU (mera_config.z2 = 1, Sec. 6): the ternary
+network in the setting of Fig. 2 (Ising chain, chi = 8, two transition
+layers) and the binary network where its chain runs unsliced (blocked spin
+pairs in the parity-ordered basis); every network contraction runs as its two
+charge sectors.  Against the oracles and the dense GPU path on the same
+symmetric point: energy and every partial derivative at 1e-12 in FP64, within
+the mixed-precision bound for 3xTF32, derivatives exactly symmetric; L-BFGS
+keeps the tensors symmetric and follows the dense path; non-symmetric tensors
+or Hamiltonians, and the sliced chain, are refused."""
 import numpy as np
 import pytest
 
@@ -109,5 +111,43 @@ def test_z2_refusals(gm):
         m.set_tensors(_flat(us, ws))
     assert ei.value.code == -1
     with pytest.raises(gm.MeraError) as ei:
-        gm.Mera(gm.default_config(4, 8, 3, z2=1), inp.three_site_blocked(h))
+        gm.Mera(gm.default_config(2, 8, 0, network=gm.MERA_MPS, z2=1), h)
     assert ei.value.code == -8
+
+
+@pytest.mark.parametrize("chi,L,seed,prec,tol", [(4, 2, 0, 0, TOL), (8, 3, 1, 0, TOL), (8, 3, 2, 1, 2e-6)])
+def test_z2_binary_matches_dense_and_oracle(gm, chi, L, seed, prec, tol):
+    from oracle import mera as om
+    h3 = inp.parity_ordered_three_site(inp.three_site_blocked(inp.ising_bond(1.0)))
+    us, ws = inp.random_z2_mera(4, chi, L, seed=seed)
+    pt = _flat(us, ws)
+    sym = gm.Mera(gm.default_config(4, chi, L, z2=1, prec=prec), h3)
+    sym.set_tensors(pt)
+    e, G, D = sym.energy_grad(deriv=True)
+    e_ref, ds, _ = om.energy_grad(h3, us, ws)
+    assert abs(e - e_ref) <= tol * max(1.0, abs(e_ref)), (e, e_ref)
+    dims = inp.layer_dims(4, chi, L)
+    for i, d_ref in enumerate(ds):
+        assert _rel(D[i], d_ref) < 10 * tol, (i, _rel(D[i], d_ref))
+        c = dims[i // 2]
+        cp = dims[min(i // 2 + 1, L)]
+        pair = inp.fused_parities(c, c)
+        cols = pair if i % 2 == 0 else inp.z2_parities(cp)
+        assert z2.violation(D[i], pair, cols) == 0.0, i
+    if prec == 0:
+        dense = gm.Mera(gm.default_config(4, chi, L), h3)
+        dense.set_tensors(pt)
+        e0, G0 = dense.energy_grad()
+        assert abs(e - e0) <= TOL * max(1.0, abs(e0))
+        for a, b in zip(G, G0):
+            assert np.abs(a - b).max() < TOL * max(1.0, np.abs(b).max())
+
+
+def test_z2_binary_refusals(gm):
+    h3 = inp.parity_ordered_three_site(inp.three_site_blocked(inp.ising_bond(1.0)))
+    with pytest.raises(gm.MeraError) as ei:  # the chi^9 chain of chi = 32 is sliced
+        gm.Mera(gm.default_config(4, 32, 3, z2=1, prec=2), h3)
+    assert ei.value.code == -8
+    with pytest.raises(gm.MeraError) as ei:  # the product basis of a blocked pair is not graded first-half-even
+        gm.Mera(gm.default_config(4, 8, 3, z2=1), inp.three_site_blocked(inp.ising_bond(1.0)))
+    assert ei.value.code == -1

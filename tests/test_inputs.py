@@ -51,3 +51,25 @@ def test_poisson_stream_recipe():
     again = serve.poisson_stream(5, rate=rate, chis=(4, 8), seed=7)
     assert [(a["t"], a["model"], a["param"], a["chi"]) for a in again] == \
         [(a["t"], a["model"], a["param"], a["chi"]) for a in reqs[:5]]
+
+
+def test_z2_inputs_of_the_binary_network():
+    """Blocked spin pairs in the parity-ordered basis: the Ising and Heisenberg
+    three-site terms commute with the parity under the first-half-even grading
+    (they do not in the plain product basis) and keep their spectrum; the
+    seeded symmetric binary MERA is made of symmetric isometries."""
+    from oracle import z2
+    p3 = inp.fused_parities(4, 4, 4)
+    for bond in (inp.ising_bond(1.0), inp.xxz_bond(1.0)):
+        h = inp.three_site_blocked(bond)
+        ho = inp.parity_ordered_three_site(h)
+        assert z2.violation(ho, p3, p3) == 0.0
+        assert np.allclose(np.linalg.eigvalsh(ho), np.linalg.eigvalsh(h), atol=1e-12)
+    assert z2.violation(inp.three_site_blocked(inp.ising_bond(1.0)), p3, p3) > 0.1
+    us, ws = inp.random_z2_mera(4, 8, 3, seed=2)
+    dims = inp.layer_dims(4, 8, 3)
+    for l, (u, w) in enumerate(zip(us, ws)):
+        c, cp = dims[l], dims[min(l + 1, 3)]
+        pair = inp.fused_parities(c, c)
+        assert z2.violation(u, pair, pair) == 0.0 and z2.violation(w, pair, inp.z2_parities(cp)) == 0.0
+        assert np.abs(w.T @ w - np.eye(cp)).max() < 1e-13

@@ -35,7 +35,7 @@ def test_plans_match_definitions(tmp_path):
     lines = r.stdout.splitlines()
     assert lines[0] == "ok 300"
     assert lines[1] == "complex ok 200"
-    assert lines[2] == "networks ok 39"
+    assert lines[2] == "networks ok 57"
     # the library grades legs as the input generators do (first half even)
     from paper_2007_03638_gb300 import inputs as inp
     for line in lines[3:]:

@@ -24,9 +24,13 @@ def test_ternary_z2_problem_is_the_figure_2_setting():
     assert z2.violation(w0, inp.fused_parities(2, 2, 2), inp.z2_parities(8)) == 0.0
 
 
-def test_z2_needs_the_ternary_network():
-    with pytest.raises(ValueError):
-        solve.problem("ising", 1.0, 8, 3, z2=True)
+def test_binary_z2_problem_is_parity_ordered():
+    h, d_b, tensors, spins = solve.problem("ising", 1.0, 8, 3, z2=True)
+    p3 = inp.fused_parities(4, 4, 4)
+    assert (h.shape, d_b, spins, len(tensors)) == ((64, 64), 4, 2, 8)
+    assert z2.violation(h, p3, p3) == 0.0
+    pair = inp.fused_parities(4, 4)
+    assert z2.violation(tensors[0], pair, pair) == 0.0
 
 
 def test_mps_problem():
