@@ -259,6 +259,11 @@ int mera_lbfgs_step(mera_t m, mera_iter_info* info);
 /* One nonlinear conjugate-gradient iteration (Hager-Zhang beta, Sec. 3). */
 int mera_cg_step(mera_t m, mera_iter_info* info);
 
+/* One Riemannian gradient-descent iteration (Sec. 3): retraction along the
+ * negative preconditioned gradient, the Hager-Zhang step started at the
+ * previous accepted step.  Clears the L-BFGS/CG history. */
+int mera_gd_step(mera_t m, mera_iter_info* info);
+
 /* One Evenbly-Vidal sweep, the comparator of the paper's optimisers (Sec. 4
  * and App. ev_steplimit): for every tensor in the order u_0, w_0, ..., u_S,
  * w_S, the environment D of the cost with the shifted term
@@ -273,7 +278,7 @@ int mera_cg_step(mera_t m, mera_iter_info* info);
 int mera_ev_sweep(mera_t m, double gamma, mera_iter_info* info);
 
 typedef struct {
-    int method;       /* 0 = L-BFGS, 1 = CG                  */
+    int method;       /* 0 = L-BFGS, 1 = CG, 2 = gradient descent */
     int maxiter;
     double gtol;      /* stop when |G| < gtol                 */
 } mera_solve_opts;

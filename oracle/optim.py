@@ -290,6 +290,39 @@ def cg(problem, point, maxiter=100, gtol=1e-6, eta=0.01, callback=None, maxeval=
     return point, e, hist
 
 
+def gd(problem, point, maxiter=100, gtol=1e-6, callback=None, maxeval=20):
+    """Riemannian gradient descent (Sec. 3): retract along the negative
+    preconditioned gradient -P(G), the step from the Hager-Zhang line search
+    started at the previous accepted step."""
+    inner = geo.inner
+    e, G, aux = problem.fg(point)
+    alpha_prev = 1.0
+    hist = []
+    for it in range(maxiter):
+        gnorm = math.sqrt(inner(G, G))
+        hist.append({"iter": it, "energy": e, "gnorm": gnorm})
+        if callback:
+            callback(it, e, gnorm, point)
+        if gnorm < gtol:
+            break
+        d = lin(-1.0, problem.precondition(point, aux, G))
+        df0 = inner(G, d)
+
+        def phi(a, _p=point, _d=d):
+            p2 = problem.retract(_p, _d, a)
+            e2, G2, aux2 = problem.fg(p2)
+            d2 = problem.transport(_p, _d, a, _d)
+            return e2, inner(G2, d2), (p2, G2, aux2)
+
+        alpha, e2, _, pay, nev, ok = hager_zhang(phi, e, df0, alpha_prev, maxeval=maxeval)
+        hist[-1].update(alpha=alpha, nev=nev, ls_ok=ok)
+        if alpha is None or (not ok and e2 >= e):
+            break
+        point, G, aux = pay
+        e, alpha_prev = e2, alpha
+    return point, e, hist
+
+
 class TernaryProblem(MeraProblem):
     """The ternary-MERA energy (oracle/ternary.py) on the same product manifold:
     u's Stiefel (unitary), w's Grassmann, the ternary density matrices in the

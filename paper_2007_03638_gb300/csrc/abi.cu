@@ -229,6 +229,11 @@ int mera_cg_step(mera_t m, mera_iter_info* info) {
   return wrap(m, [&] { mera::cg_step(*m, info, m->s); });
 }
 
+int mera_gd_step(mera_t m, mera_iter_info* info) {
+  if (!m || !info) return MERA_ERR_ARG;
+  return wrap(m, [&] { mera::gd_step(*m, info, m->s); });
+}
+
 int mera_ev_sweep(mera_t m, double gamma, mera_iter_info* info) {
   if (!m || !info || !std::isfinite(gamma)) return MERA_ERR_ARG;
   return wrap(m, [&] {
@@ -247,6 +252,7 @@ int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
     r->n_evals = 1;
     for (int it = 0; it < o->maxiter && !(gn < o->gtol); ++it) {
       if (o->method == 1) mera::cg_step(*m, &info, m->s);
+      else if (o->method == 2) mera::gd_step(*m, &info, m->s);
       else mera::lbfgs_step(*m, &info, m->s);
       gn = info.gnorm;
       r->iters++;

@@ -184,6 +184,7 @@ void ensure_current(Ctx& c, cudaStream_t s);
 void clear_history(Ctx& c);
 void lbfgs_step(Ctx& c, mera_iter_info* info, cudaStream_t s);
 void cg_step(Ctx& c, mera_iter_info* info, cudaStream_t s);
+void gd_step(Ctx& c, mera_iter_info* info, cudaStream_t s);
 void ev_sweep(Ctx& c, double gamma, mera_iter_info* info, cudaStream_t s);
 
 }  // namespace mera

@@ -301,6 +301,43 @@ void lbfgs_step(Ctx& c, mera_iter_info* info, cudaStream_t s) {
   info->krylov_matvecs = (int)(c.matvecs - mv0);
 }
 
+// Riemannian gradient descent (Sec. 3): the direction -P(G), the
+// Hager-Zhang step started at the previous accepted step.
+void gd_step(Ctx& c, mera_iter_info* info, cudaStream_t s) {
+  ensure_current(c, s);
+  const int64_t mv0 = c.matvecs;
+  Eval& E = c.ev[c.cur];
+  const double* W = P(c.Wcur);
+  double* G = P(E.G);
+  double* d = P(c.dir);
+  // the L-BFGS pairs and the CG direction are not transported by this step
+  c.mem_n = 0;
+  c.mem_rho.clear();
+  precondition(c, E, W, G, d, s);
+  scal(-1.0, d, c.total, s);
+  const double df0 = inner(c, G, d, s);
+  const double f0 = E.e;
+  LsResult ls = hager_zhang(c, f0, df0, c.alpha_prev, s);
+  info->n_evals = ls.nev;
+  info->ls_ok = ls.ok;
+  if (!ls.found || (!ls.ok && ls.f >= f0)) {
+    info->alpha = 0.0;
+    info->energy = f0;
+    info->gnorm = std::sqrt(inner(c, G, G, s));
+    info->iter = ++c.iters;
+    info->krylov_matvecs = (int)(c.matvecs - mv0);
+    return;
+  }
+  c.alpha_prev = ls.alpha;
+  accept(c, s);
+  Eval& En = c.ev[c.cur];
+  info->alpha = ls.alpha;
+  info->energy = En.e;
+  info->gnorm = std::sqrt(inner(c, P(En.G), P(En.G), s));
+  info->iter = ++c.iters;
+  info->krylov_matvecs = (int)(c.matvecs - mv0);
+}
+
 void cg_step(Ctx& c, mera_iter_info* info, cudaStream_t s) {
   ensure_current(c, s);
   const int64_t mv0 = c.matvecs;

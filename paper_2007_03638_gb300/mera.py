@@ -72,7 +72,7 @@ class SolveResult(C.Structure):
 EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tensors", "mera_energy",
            "mera_tensor_shape", "mera_set_tensors", "mera_get_tensors", "mera_init_random", "mera_energy_grad",
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
-           "mera_lbfgs_step", "mera_cg_step", "mera_ev_sweep", "mera_solve", "mera_footprint_bytes",
+           "mera_lbfgs_step", "mera_cg_step", "mera_gd_step", "mera_ev_sweep", "mera_solve", "mera_footprint_bytes",
            "mera_launch_count", "mera_get_stats", "mera_profile", "mera_profile_dump", "mera_dots_noalloc",
            "mera_gemm", "mera_strerror", "mera_last_error", "mera_server_create",
            "mera_server_submit", "mera_server_poll", "mera_server_wait", "mera_server_destroy"]
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "mera_precondition": (C.c_int, [C.c_void_p, vpp, vpp]),
         "mera_lbfgs_step": (C.c_int, [C.c_void_p, C.POINTER(IterInfo)]),
         "mera_cg_step": (C.c_int, [C.c_void_p, C.POINTER(IterInfo)]),
+        "mera_gd_step": (C.c_int, [C.c_void_p, C.POINTER(IterInfo)]),
         "mera_ev_sweep": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(IterInfo)]),
         "mera_solve": (C.c_int, [C.c_void_p, C.POINTER(SolveOpts), C.POINTER(SolveResult)]),
         "mera_footprint_bytes": (C.c_size_t, [C.POINTER(Config)]),
@@ -338,6 +339,12 @@ class Mera:
     def cg_step(self):
         info = IterInfo()
         self._check(self.L.mera_cg_step(self.h, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in IterInfo._fields_}
+
+    def gd_step(self):
+        """One Riemannian gradient-descent iteration (negative preconditioned gradient)."""
+        info = IterInfo()
+        self._check(self.L.mera_gd_step(self.h, C.byref(info)))
         return {f: getattr(info, f) for f, _ in IterInfo._fields_}
 
     def ev_sweep(self, gamma):

@@ -63,7 +63,7 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
         lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None, network="binary", z2=False):
     """method: 0 L-BFGS, 1 CG, 2 Evenbly-Vidal sweeps (one record per sweep;
     ev_gamma = the Hamiltonian shift, default the largest eigenvalue of the
-    Hamiltonian term plus 0.5).  network: "binary", "ternary" or "mps"."""
+    Hamiltonian term plus 0.5), 3 gradient descent.  network: "binary", "ternary" or "mps"."""
     h3, d_b, tensors, spins = problem(model, par, chi, n_trans, network, z2, seed)
     net = {"binary": gm.MERA_BINARY, "ternary": gm.MERA_TERNARY, "mps": gm.MERA_MPS}[network]
     cfg = gm.default_config(d_b, chi, 0 if network == "mps" else n_trans, prec=prec, lbfgs_m=lbfgs_m,
@@ -77,7 +77,8 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
     rec = None
     evals = 0
     for it in range(iters):
-        info = m.cg_step() if method == 1 else m.ev_sweep(ev_gamma) if method == 2 else m.lbfgs_step()
+        info = (m.cg_step() if method == 1 else m.ev_sweep(ev_gamma) if method == 2 else m.gd_step() if method == 3
+                else m.lbfgs_step())
         evals += info["n_evals"]
         e_spin = info["energy"] / spins
         rec = {"iter": it + 1, "energy_per_spin": e_spin,
@@ -89,7 +90,7 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
             break
     summary = {"summary": True, "model": model, "param": par, "network": network, "z2": z2, "chi": chi,
                "n_trans": n_trans,
-               "prec": ["fp64", "3xtf32", "split_bf16"][prec], "method": ["lbfgs", "cg", "ev"][method],
+               "prec": ["fp64", "3xtf32", "split_bf16"][prec], "method": ["lbfgs", "cg", "ev", "gd"][method],
                "iters": rec["iter"], "energy_per_spin": rec["energy_per_spin"], "exact": ex,
                "error": rec["error"], "gnorm": rec["gnorm"], "evals": evals, "time_s": rec["time_s"]}
     out(json.dumps(summary))
@@ -105,7 +106,7 @@ def main():
     ap.add_argument("--chi", type=int, default=4)
     ap.add_argument("--n-trans", type=int, default=2)
     ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16")
-    ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev"])
+    ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev", "gd"])
     ap.add_argument("--network", default="binary", choices=["binary", "ternary", "mps"])
     ap.add_argument("--z2", action="store_true",
                     help="Z2-symmetric problem (ternary, or binary up to chi = 16): contractions by charge sector")
@@ -118,7 +119,7 @@ def main():
     ap.add_argument("--krylov-dim", type=int, default=20)
     a = ap.parse_args()
     par = a.field if a.model == "ising" else a.delta
-    method = {"lbfgs": 0, "cg": 1, "ev": 2}[a.method]
+    method = {"lbfgs": 0, "cg": 1, "ev": 2, "gd": 3}[a.method]
     run(a.model, par, a.chi, a.n_trans, a.prec, method, a.iters, a.gtol, a.seed, a.m, a.krylov_dim,
         ev_gamma=a.ev_gamma, network=a.network, z2=a.z2)
 

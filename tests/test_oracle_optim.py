@@ -98,3 +98,42 @@ def test_mera_lbfgs_short_run():
     assert e / 2 < -1.1
     for t in p:
         assert np.abs(t.T @ t - np.eye(t.shape[1])).max() < 1e-13
+
+
+class _NewtonPreconditioned(_Quadratic):
+    """The quadratic with the exact inverse Hessian as preconditioner."""
+
+    def precondition(self, p, aux, X):
+        return [np.linalg.solve(self.A, x) for x in X]
+
+
+def test_gd_with_the_inverse_hessian_is_one_newton_step():
+    """Preconditioned by A^-1, the descent direction is the Newton step and the
+    line search's first trial (alpha = 1) is the exact minimiser."""
+    prob = _NewtonPreconditioned(20, 3)
+    p, e, hist = oo.gd(prob, [np.zeros(20)], maxiter=3, gtol=1e-10)
+    x = np.linalg.solve(prob.A, prob.b)
+    assert hist[0]["alpha"] == 1.0
+    assert np.abs(p[0] - x).max() < 1e-10
+    assert len(hist) <= 2
+
+
+def test_gd_descends_and_converges_on_a_quadratic():
+    """Identity preconditioner, condition number 10: the energy never rises by
+    more than the approximate-Wolfe allowance (1e-6 |f|) and the iterates reach
+    the minimiser."""
+    prob = _Quadratic(20, 4)
+    prob.A = np.diag(np.linspace(1.0, 10.0, 20))
+    p, e, hist = oo.gd(prob, [np.zeros(20)], maxiter=500, gtol=1e-9)
+    es = [h["energy"] for h in hist]
+    assert all(b <= a + 1e-6 * abs(a) for a, b in zip(es, es[1:]))
+    assert np.abs(p[0] - np.linalg.solve(prob.A, prob.b)).max() < 1e-8
+
+
+def test_mera_gd_short_run():
+    us, ws = inp.random_mera(4, 4, 2, seed=0)
+    h3 = inp.three_site_blocked(inp.ising_bond(1.0))
+    p, e, hist = oo.gd(oo.MeraProblem(h3), [t for pair in zip(us, ws) for t in pair], maxiter=10)
+    es = [h["energy"] for h in hist]
+    assert all(b <= a + 1e-14 for a, b in zip(es, es[1:]))
+    assert e / 2 > inp.EXACT_ISING_CRITICAL
