@@ -175,7 +175,11 @@ void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
  * site, C = Tr(h rho), Sec. 4); for the ternary network and the MPS a
  * two-site term, (d_b^2) x (d_b^2).  stream: a cudaStream_t (NULL = default
  * stream).  The tensors start as the identity-disentangler / first-columns
- * isometry point until mera_set_tensors or mera_init_random is called. */
+ * isometry point until mera_set_tensors or mera_init_random is called.
+ * MERA_ERR_ARG (before any device work) for a config outside its ranges:
+ * unknown dtype, prec or network; w_stiefel, precond, recompute_env or z2
+ * not 0 or 1; krylov_tol not in (0, 1); krylov_maxiter, krylov_dim or lbfgs_m
+ * below 1; a negative b_chunk. */
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
 int mera_destroy(mera_t m);
 

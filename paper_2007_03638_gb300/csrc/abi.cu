@@ -180,7 +180,7 @@ int mera_inner(mera_t m, const void* const* X, const void* const* Y, double* out
 }
 
 int mera_transport(mera_t m, const void* const* X, double alpha, void* const* Y) {
-  if (!m || !X || !Y) return MERA_ERR_ARG;
+  if (!m || !X || !Y || !std::isfinite(alpha)) return MERA_ERR_ARG;
   return wrap(m, [&] {
     copy_in(m, X, mera::P(m->dir2));
     copy_in(m, (const void* const*)Y, mera::P(m->tmpv));
@@ -191,7 +191,7 @@ int mera_transport(mera_t m, const void* const* X, double alpha, void* const* Y)
 }
 
 int mera_retract(mera_t m, const void* const* X, double alpha, void* const* Xprime) {
-  if (!m || !X) return MERA_ERR_ARG;
+  if (!m || !X || !std::isfinite(alpha)) return MERA_ERR_ARG;
   return wrap(m, [&] {
     copy_in(m, X, mera::P(m->dir2));
     mera::make_geom(*m, mera::P(m->Wcur), mera::P(m->dir2), alpha, m->s);
@@ -243,7 +243,7 @@ int mera_ev_sweep(mera_t m, double gamma, mera_iter_info* info) {
 }
 
 int mera_solve(mera_t m, const mera_solve_opts* o, mera_solve_result* r) {
-  if (!m || !o || !r) return MERA_ERR_ARG;
+  if (!m || !o || !r || o->method < 0 || o->method > 2 || o->maxiter < 0) return MERA_ERR_ARG;
   return wrap(m, [&] {
     std::memset(r, 0, sizeof(*r));
     mera::ensure_current(*m, m->s);
@@ -327,7 +327,9 @@ size_t footprint_net(const mera_config* cfg) {
 }  // namespace
 
 size_t mera_footprint_bytes(const mera_config* cfg) {
-  if (!cfg) return 0;
+  if (!cfg || !mera::config_range_error(*cfg).empty()) return 0;
+  if (cfg->dtype != MERA_F64 && cfg->dtype != MERA_C128) return 0;
+  if (cfg->prec != MERA_PREC_FP64 && cfg->prec != MERA_PREC_3XTF32 && cfg->prec != MERA_PREC_SPLIT_BF16) return 0;
   if (cfg->z2 != 0 && (cfg->z2 != 1 || cfg->network == MERA_MPS)) return 0;
   if (cfg->network == MERA_MPS) return footprint_mps(cfg);
   if (cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;

@@ -160,6 +160,8 @@ std::vector<int> fused_charges(const std::vector<int64_t>& dims);
 void tensor_legs(const Ctx& c, int i, std::vector<int64_t>& rows, std::vector<int64_t>& cols);
 void check_z2_point(Ctx& c, const double* W, cudaStream_t s);
 void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s);
+// why cfg's flags, tolerances or counts are out of range ("" if they are not)
+std::string config_range_error(const mera_config& cfg);
 
 // ---- mps.cu ----
 double mps_energy(Ctx& c, const double* A, cudaStream_t s);

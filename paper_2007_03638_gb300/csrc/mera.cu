@@ -675,6 +675,16 @@ void check_isometric(Ctx& c, const double* W, cudaStream_t s) {
 void create_mera(Ctx& c, int64_t* nS, int64_t* gmax);
 void finish_create(Ctx& c, cudaStream_t s);
 
+std::string config_range_error(const mera_config& cfg) {
+  auto flag = [](int v) { return v == 0 || v == 1; };
+  if (!flag(cfg.w_stiefel) || !flag(cfg.precond) || !flag(cfg.recompute_env) || !flag(cfg.z2))
+    return "w_stiefel, precond, recompute_env and z2 must be 0 or 1";
+  if (!(cfg.krylov_tol > 0.0 && cfg.krylov_tol < 1.0)) return "need 0 < krylov_tol < 1";
+  if (cfg.krylov_maxiter < 1 || cfg.krylov_dim < 1 || cfg.lbfgs_m < 1) return "need krylov_maxiter, krylov_dim, lbfgs_m >= 1";
+  if (cfg.b_chunk < 0) return "need b_chunk >= 0";
+  return "";
+}
+
 // Z2 charge of every index tuple of legs with dimensions dims (row-major).
 std::vector<int> fused_charges(const std::vector<int64_t>& dims) {
   int64_t n = 1;
@@ -747,6 +757,8 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
     throw Error(MERA_ERR_ARG, "unknown precision mode");
   if (cfg.network != MERA_BINARY && cfg.network != MERA_TERNARY && cfg.network != MERA_MPS)
     throw Error(MERA_ERR_ARG, "unknown network");
+  const std::string bad = config_range_error(cfg);
+  if (!bad.empty()) throw Error(MERA_ERR_ARG, bad);
   c.tern = cfg.network == MERA_TERNARY;
   c.mps = cfg.network == MERA_MPS;
   if (cfg.z2 != 0 && cfg.z2 != 1) throw Error(MERA_ERR_ARG, "z2 must be 0 or 1");

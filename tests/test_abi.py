@@ -135,3 +135,25 @@ def test_recompute_env_shares_the_operator_nodes(lib):
     assert 40e9 < keep - share < 43e9
     assert gm.footprint_bytes(gm.default_config(4, 8, 3, recompute_env=1)) < gm.footprint_bytes(
         gm.default_config(4, 8, 3))
+
+
+
+def test_create_refuses_configs_out_of_range(lib):
+    """mera_create checks the config before any device work, so invalid ones
+    are refused with MERA_ERR_ARG on a machine without a GPU too."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2007_03638_gb300 import mera as gm
+    h = np.zeros((64, 64))
+    bad = [dict(precond=2), dict(krylov_tol=0.0), dict(krylov_tol=float("nan")), dict(krylov_tol=1.5),
+           dict(krylov_maxiter=0), dict(krylov_dim=0), dict(lbfgs_m=0), dict(b_chunk=-1), dict(w_stiefel=3),
+           dict(recompute_env=-1), dict(network=7), dict(dtype=5), dict(prec=9), dict(z2=3)]
+    for kw in bad:
+        cfg = gm.default_config(4, 8, 3, **kw)
+        handle = C.c_void_p()
+        rc = lib.mera_create(C.byref(cfg), C.c_void_p(h.ctypes.data), None, C.byref(handle))
+        assert rc == -1 and not handle.value, kw
+        if "network" not in kw:
+            assert gm.footprint_bytes(cfg) == 0, kw
