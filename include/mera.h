@@ -179,7 +179,8 @@ void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
  * MERA_ERR_ARG (before any device work) for a config outside its ranges:
  * unknown dtype, prec or network; w_stiefel, precond, recompute_env or z2
  * not 0 or 1; krylov_tol not in (0, 1); krylov_maxiter, krylov_dim or lbfgs_m
- * below 1; a negative b_chunk. */
+ * below 1; a negative b_chunk; a Hamiltonian term that is not Hermitian
+ * (|h - h^dag| above 1e-10 of its largest entry) or not finite. */
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
 int mera_destroy(mera_t m);
 

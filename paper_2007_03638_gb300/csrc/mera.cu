@@ -685,6 +685,27 @@ std::string config_range_error(const mera_config& cfg) {
   return "";
 }
 
+// The Hamiltonian term (n x n on the device) must be Hermitian: |h - h^dag|
+// at most 1e-10 of its largest entry, else MERA_ERR_ARG.
+void check_hermitian(Ctx& c, const double* dev, int64_t n, cudaStream_t s) {
+  std::vector<double> h((size_t)(n * n * c.rs));
+  MERA_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  MERA_CUDA(cudaStreamSynchronize(s));
+  double big = 0.0, bad = 0.0;
+  for (const double x : h)
+    if (!std::isfinite(x)) throw Error(MERA_ERR_ARG, "the Hamiltonian term is not finite");
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      const double* a = h.data() + (i * n + j) * c.rs;
+      const double* b = h.data() + (j * n + i) * c.rs;
+      const double dr = a[0] - b[0], di = c.cplx ? a[1] + b[1] : 0.0;  // h_ij - conj(h_ji)
+      big = std::max(big, c.cplx ? std::hypot(a[0], a[1]) : std::fabs(a[0]));
+      bad = std::max(bad, std::hypot(dr, di));
+    }
+  if (bad > 1e-10 * big)
+    throw Error(MERA_ERR_ARG, "the Hamiltonian term is not Hermitian (|h - h^dag| = " + std::to_string(bad) + ")");
+}
+
 // Z2 charge of every index tuple of legs with dimensions dims (row-major).
 std::vector<int> fused_charges(const std::vector<int64_t>& dims) {
   int64_t n = 1;
@@ -779,6 +800,7 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   c.Wtry.alloc(tb);
   c.h0.alloc(sizeof(double) * ipow(cfg.d_b, 2 * c.ns) * c.rs);
   MERA_CUDA(cudaMemcpyAsync(c.h0.p, h3, c.h0.bytes, cudaMemcpyDefault, s));
+  check_hermitian(c, P(c.h0), ipow(cfg.d_b, c.ns), s);
   if (c.z2) {
     const std::vector<int64_t> sites(c.ns, cfg.d_b);
     check_z2(c, P(c.h0), sites, sites, "the Hamiltonian term", s);

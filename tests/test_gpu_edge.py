@@ -3,7 +3,8 @@
 whose Riemannian gradient vanishes while its partial derivative does not) in a
 transition layer, and the smallest network (one transition layer), through
 the FP64 and 3xTF32 paths; an L-BFGS step leaves the square isometry's
-subspace unchanged."""
+subspace unchanged.  Hamiltonian terms that are not Hermitian or not finite are
+refused at creation."""
 import numpy as np
 import pytest
 
@@ -47,3 +48,21 @@ def test_square_isometry(gm, prec, tol):
     w1 = m.get_tensors()[1]
     # the span of a square isometry is the whole space: W^T W = 1 and W W^T = 1 before and after
     assert np.abs(w1 @ w1.T - np.eye(4)).max() < 1e-12 and np.abs(w0 @ w0.T - np.eye(4)).max() < 1e-12
+
+
+def test_hamiltonian_checks(gm):
+    h3 = inp.three_site_blocked(inp.ising_bond(1.0))
+    bad = h3.copy()
+    bad[0, 1] += 1e-3
+    with pytest.raises(gm.MeraError) as ei:
+        gm.Mera(gm.default_config(4, 4, 2), bad)
+    assert ei.value.code == -1
+    bad = h3.copy()
+    bad[3, 3] = np.nan
+    with pytest.raises(gm.MeraError) as ei:
+        gm.Mera(gm.default_config(4, 4, 2), bad)
+    assert ei.value.code == -1
+    hc = h3.astype(np.complex128)
+    hc[0, 1] += 1e-3j
+    hc[1, 0] -= 1e-3j  # still Hermitian
+    gm.Mera(gm.default_config(4, 4, 2, dtype=gm.MERA_C128), hc).close()
