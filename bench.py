@@ -11,6 +11,7 @@ optimisation does not shard across GPUs, so N GPUs run N problems).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...   # the CPU FP64 oracle, same metric
+    python bench.py --shapes-out shapes.csv  # per-shape device time of one L-BFGS iteration
 
 Inputs are synthetic and seeded (QR-of-Gaussian tensors, Z2-symmetric blocks
 for the z2 workloads; critical Ising, Ising with a longitudinal field or the
@@ -64,9 +65,11 @@ WORKLOADS = {
     "ising_hz_chi16_L3_c128_3xtf32": ("ising_hz", 4, 16, 3, 1, {"dtype": 1, "lbfgs_m": 16}),
 }
 # Workloads whose CPU baseline times whole oracle energy/gradient evaluations
-# (seconds each); the others time one layer's ascending map.
-WHOLE_EVAL = {"ternary_ising_chi8_L2_fp64", "ternary_ising_chi8_L2_fp64_z2", "ternary_xxz_chi16_L2_3xtf32",
-              "ternary_xxz_chi16_L2_3xtf32_z2", "mps_xxz_D32_fp64"}
+# (seconds each): the ternary and MPS ones and every binary one up to chi = 12;
+# the others time one layer's ascending map and extrapolate by flop count.
+def whole_eval(name):
+    kind, d_b, chi, L, prec, extra = WORKLOADS[name]
+    return extra.get("network", 0) in (1, 2) or chi <= 12
 DEFAULT_WORKLOAD = "xxz_chi32_L3_bf16"
 # Algorithmic flops of one energy/gradient evaluation as the GPU path counts
 # them inside L-BFGS steps (measured by this script's own GPU runs); used only
@@ -238,7 +241,7 @@ def oracle_sample(d_b, chi, L, seconds=10.0, seed=0, cplx=False):
 
 def oracle_eval_sample(wl, seconds=10.0, seed=0):
     """Time whole oracle energy/gradient evaluations of the workload (the
-    ternary oracle, or the MPS oracle) at its seeded point on the host cores,
+    binary, ternary or MPS oracle) at its seeded point on the host cores,
     at least one and until `seconds` have passed.  Returns (seconds per
     evaluation, evaluations)."""
     kind, d_b, chi, L, prec, extra = wl
@@ -249,9 +252,12 @@ def oracle_eval_sample(wl, seconds=10.0, seed=0):
         from oracle import mps
         A = point[0].reshape(chi, d_b, chi)
         run = lambda: mps.energy_grad(A, h)  # noqa: E731
-    else:
+    elif net == 1:
         from oracle import ternary as ot
         run = lambda: ot.energy_grad(h, point[0::2], point[1::2])  # noqa: E731
+    else:
+        from oracle import mera as om
+        run = lambda: om.energy_grad(h, point[0::2], point[1::2])  # noqa: E731
     n, t0 = 0, time.perf_counter()
     while True:
         run()
@@ -296,7 +302,7 @@ def run_reference(args, wl):
     kind, d_b, chi, L, prec, extra = wl
     cplx = extra.get("dtype", 0) == 1
     per = []
-    if args.workload in WHOLE_EVAL:
+    if whole_eval(args.workload):
         for i in range(args.warmup + args.steps):
             t, n = oracle_eval_sample(wl, seconds=args.ref_seconds)
             if i >= args.warmup:
@@ -313,15 +319,15 @@ def run_reference(args, wl):
         frac = part * ascend_flops(cf, cc) * (4 if cplx else 1) / flops_grad
         t = sum(per) / len(per)
         value = frac / t
-        sample = (f"oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}ascending map of layer {layer} "
-                  f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient evaluation's algorithmic flops "
-                  f"({flops_grad:.3g})")
+        sample = (f"extrapolated: oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}ascending map of "
+                  f"layer {layer} (chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient evaluation's "
+                  f"algorithmic flops ({flops_grad:.3g}), scaled by that fraction")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128" if cplx else "f64",
             "data": "synthetic", "config": {"workload": args.workload, "chi": chi, "n_trans": L},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "extrapolated": not whole_eval(args.workload)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -378,6 +384,10 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=6)
     ap.add_argument("--energy-once", action="store_true",
                     help="set the seeded point, run one energy/gradient evaluation and exit (profiling case)")
+    ap.add_argument("--shapes-out", default=None,
+                    help="per-shape profile: from the seeded point, one evaluation (filling the Krylov warm "
+                         "starts), then one L-BFGS iteration with the library's per-shape timing on; writes "
+                         "that table (mera_profile_dump) as CSV to this path and exits")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -414,6 +424,16 @@ def main():
     if args.energy_once:
         print(json.dumps({"workload": args.workload, "energy": m.energy(), "launches": m.launch_count()}))
         return
+    if args.shapes_out:
+        m.energy_grad()
+        m.stats(reset=True)
+        m.profile(True)
+        t0 = time.perf_counter()
+        info = m.lbfgs_step()
+        wall = time.perf_counter() - t0
+        m.profile_dump(args.shapes_out)
+        print(json.dumps({"workload": args.workload, "step_s": wall, "iter": info, "stats": m.stats()}))
+        return
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         m.lbfgs_step()
@@ -449,25 +469,35 @@ def main():
     value = grads_all / (t_ms / 1e3)
     gett_flops_per_grad = st["gett_flops"] / max(1, grads)
 
-    # end to end: host (pinned) tensors in, host gradient out, per evaluation
-    pinned = [torch.from_numpy(np.ascontiguousarray(t)).pin_memory() for t in m.get_tensors()]
+    # end to end: the call a user makes per evaluation, host (pinned) tensors
+    # in and the host gradient out.  The points are ones the optimisation
+    # visits (recorded one L-BFGS iteration apart after the timed steps) and
+    # are evaluated in reverse order, so each evaluation starts its Krylov
+    # solves from the previous point's solutions, one iteration away, as the
+    # evaluations inside the timed steps do.
     gout = [torch.empty(s, dtype=torch.complex128 if cplx else torch.float64).pin_memory() for s in m.shapes]
-    h2d = sum(t.numel() * t.element_size() for t in pinned)
-    d2h = sum(t.numel() * t.element_size() for t in gout) + 8
     big = chi >= 24
-    for _ in range(1 if big else 2):
-        m.set_tensors(pinned)
-        m.energy_grad_into(gout)
+    n_e2e = 1 if big else max(2, args.steps)
+    visited = []
+    for _ in range(n_e2e + 1):
+        visited.append([torch.from_numpy(np.ascontiguousarray(t)).pin_memory() for t in m.get_tensors()])
+        m.lbfgs_step()
+    visited.reverse()
+    h2d = sum(t.numel() * t.element_size() for t in visited[0])
+    d2h = sum(t.numel() * t.element_size() for t in gout) + 8
+    m.set_tensors(visited[0])  # untimed warm-up call
+    m.energy_grad_into(gout)
+    m.stats(reset=True)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    n_e2e = 1 if big else max(2, args.steps)
-    for _ in range(n_e2e):
-        m.set_tensors(pinned)
+    for k in range(n_e2e):
+        m.set_tensors(visited[1 + k])
         m.energy_grad_into(gout)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    st_e2e = m.stats(reset=True)
     t_e2e, _ = aggregate(t_e2e, 0, pg, "cuda")
     e2e_value = world * n_e2e / t_e2e
 
@@ -505,26 +535,31 @@ def main():
             "energy_last": infos[-1]["energy"],
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "call": "mera_set_tensors(host) + mera_energy_grad(grad -> host)"},
+                    "call": "mera_set_tensors(host) + mera_energy_grad(grad -> host)",
+                    "evaluations": n_e2e,
+                    "points": "visited by the optimisation, one L-BFGS iteration apart, in reverse order",
+                    "krylov_matvecs_per_grad": st_e2e["krylov_matvecs"] / max(1, n_e2e)},
             "gpu_launches": st["launches"],
             "memory": memory,
             "clocks": clocks.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if args.workload in WHOLE_EVAL:
+        if whole_eval(args.workload):
             t, n = oracle_eval_sample(wl, seconds=args.cpu_seconds)
             line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                                     "sample": f"{n} x oracle (NumPy FP64) energy/gradient evaluation of the "
-                                              f"workload at its seeded point, {t:.2f} s each"}
+                                              f"workload at its seeded point, {t:.2f} s each",
+                                    "extrapolated": False}
         else:
             t, n, layer, cf, cc, part = oracle_sample(d_b, chi, L, seconds=args.cpu_seconds, cplx=cplx)
             # the oracle contracts densely: a Z2 workload's fraction is of the dense count
             per_grad = FLOPS_PER_GRAD[args.workload] if extra.get("z2") else gett_flops_per_grad
             frac = part * ascend_flops(cf, cc) * (4 if cplx else 1) / per_grad
             line["cpu_baseline"] = {"value": frac / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-                                    "sample": f"{n} x oracle (NumPy FP64) {'one side of the ' if part < 1 else ''}"
-                                              f"ascending map of layer {layer} "
-                                              f"(chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one gradient "
-                                              f"evaluation's algorithmic flops"}
+                                    "sample": f"extrapolated: {n} x oracle (NumPy FP64) "
+                                              f"{'one side of the ' if part < 1 else ''}ascending map of layer "
+                                              f"{layer} (chi {cf}->{cc}), {t:.2f} s each = {frac:.3g} of one "
+                                              f"gradient evaluation's algorithmic flops, scaled by that fraction",
+                                    "extrapolated": True}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

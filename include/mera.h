@@ -324,7 +324,7 @@ int mera_profile(mera_t m, int enable);
  * (since creation or the last reset of mera_get_stats) to the file `path` as
  * CSV lines "M,N,K,path,calls,ms,tflops": path 0 is the FP64 contraction
  * kernel, otherwise 1000 * (1 + tensor-core kind: 0 TF32, 1 BF16) + 100 *
- * epilogue store mode + 10 * cluster CTAs along M + cluster CTAs along N;
+ * epilogue store mode;
  * tflops counts 2 M N K per call.  Rows with K = 0 time other phases:
  * path 91xx / 92xx the packing of a tensor-core product's first / second
  * operand into split planes (M, N = rows, packed length; xx = 10 if the
@@ -395,7 +395,10 @@ int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const 
  * call on a device looks up that array's device address (make it before any
  * stream capture).  All calls share the array and it keeps the last call's
  * partial sums: calls whose work overlaps on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.  The paper has no
+ * host threads) race and must be serialised by the caller.  Every call ends
+ * with a synchronisation of `stream`.  A CUDA error left pending by an
+ * earlier launch on the calling thread makes the call return MERA_ERR_CUDA
+ * before it launches anything (the error stays pending).  The paper has no
  * counterpart of this entry point. */
 int mera_dots_noalloc(const double* X, int64_t ldx, int k, const double* y, int64_t n, double* out,
                       void* stream);

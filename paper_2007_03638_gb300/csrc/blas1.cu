@@ -478,9 +478,14 @@ extern "C" int mera_dots_noalloc(const double* X, int64_t ldx, int k, const doub
   double* result = partial + (int64_t)NOALLOC_MAX_K * RBLOCKS;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nb = (int)std::min<int64_t>(RBLOCKS, std::max<int64_t>(1, (n + RT - 1) / RT));
+  // an error left pending by an earlier launch on this thread is reported
+  // (and left in place) before anything is launched, so that the check after
+  // the launches sees only this call's
+  if (cudaPeekAtLastError() != cudaSuccess) return MERA_ERR_CUDA;
   // every partial slot read below is written by this call, so nothing needs clearing
   dots_partial<<<dim3(nb, k), RT, 0, s>>>(X, ldx, y, n, partial);
   finish_partial<<<k, RT, 0, s>>>(partial, nb, result);
+  count_launch(2);
   if (cudaGetLastError() != cudaSuccess) return MERA_ERR_CUDA;
   if (cudaMemcpyAsync(out, result, sizeof(double) * k, cudaMemcpyDefault, s) != cudaSuccess)
     return MERA_ERR_CUDA;

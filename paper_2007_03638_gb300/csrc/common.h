@@ -44,7 +44,7 @@ struct Prof {
   int64_t gett_timed = 0;
   int64_t energy_grad_calls = 0;
   // per-shape table of the timed contractions: key = (M, N, K, path)
-  // with path = 0 FP64 GETT, else 1000 * kind + 100 * store mode + cluster
+  // with path = 0 FP64 GETT, else 1000 * (1 + kind) + 100 * store mode
   struct Shape {
     int64_t calls = 0;
     double ms = 0.0;

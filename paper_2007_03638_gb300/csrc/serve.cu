@@ -118,9 +118,17 @@ void worker(mera_server* sv) {
     }
     Request& r = *pick;
     r.busy = true;
+    // fields a worker may touch without the lock while busy is set: m and
+    // stream (no other thread uses them then); everything mera_server_poll
+    // reads is written only with the lock held
+    const int iters0 = r.iters;
+    const double gtol = r.gtol;
+    const int maxiter = r.maxiter, method = r.method;
     lk.unlock();
     int err = 0;
-    bool finished = false;
+    bool finished = false, stepped = false;
+    mera_iter_info info{};
+    std::string message;
     if (!r.m) {
       // first turn: build the problem on its own stream and load its point
       err = cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking) == cudaSuccess ? 0 : MERA_ERR_CUDA;
@@ -132,18 +140,21 @@ void worker(mera_server* sv) {
       }
     }
     if (!err) {
-      mera_iter_info info{};
-      err = r.method == 1 ? mera_cg_step(r.m, &info) : mera_lbfgs_step(r.m, &info);
+      err = method == 1 ? mera_cg_step(r.m, &info) : mera_lbfgs_step(r.m, &info);
       if (!err) {
-        r.iters++;
-        r.n_evals += info.n_evals;
-        r.energy = info.energy;
-        r.gnorm = info.gnorm;
-        finished = r.gnorm < r.gtol || r.iters >= r.maxiter;
+        stepped = true;
+        finished = info.gnorm < gtol || iters0 + 1 >= maxiter;
       }
     }
-    if (err) r.message = r.m ? mera_last_error(r.m) : "creation failed";
+    if (err) message = r.m ? mera_last_error(r.m) : "creation failed";
     lk.lock();
+    if (stepped) {
+      r.iters = iters0 + 1;
+      r.n_evals += info.n_evals;
+      r.energy = info.energy;
+      r.gnorm = info.gnorm;
+    }
+    if (err) r.message = message;
     r.busy = false;
     if (err || finished) {
       for (size_t k = 0; k < sv->running.size(); ++k)

@@ -87,22 +87,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-// Multicast load: the tile lands at the same shared-memory offset in every
-// CTA of `mask` (cluster ranks) and completes bytes on each one's barrier at
-// the same offset.
-__device__ __forceinline__ void tma_load_2d_mc(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
@@ -143,15 +127,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                    smem_u32(bar))
                : "memory");
 }
-// Arrive, once the MMAs issued so far complete, on the barrier at this
-// offset in every CTA of `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(smem_u32(bar)),
-               "h"(mask)
-               : "memory");
-}
-
 // Instruction descriptor: FP32 accumulator, K-major A and B, M=128, N=BN.
 template <int KIND, int BN>
 __host__ __device__ constexpr uint32_t idesc() {
@@ -173,15 +148,10 @@ struct Smem {
   int abort;
 };
 
-// Persistent kernel, one CTA per SM walking output tiles (N tiles fastest)
-// with a static stride.  With CH x CW > 1 the CTAs run in clusters of
-// CH (along M) x CW (along N) neighbouring tiles, walked together: the CW
-// CTAs of a cluster row need the same A tile and the CH CTAs of a cluster
-// column the same B tile, so each loads a 1/CW slice of its A tile and a 1/CH
-// slice of its B tile and multicasts it to the CTAs that share it, halving
-// (2 x 2) the operand traffic; a shared-memory stage is refilled once every
-// CTA it feeds has finished with it.  Warp roles (320 threads): warp 0 TMA producer,
-// warp 1 MMA issuer, warps 2..9 fold and store (warp w reads TMEM lanes
+// Persistent kernel, one CTA per SM walking output tiles with a static
+// stride; every CTA loads its own operand tiles (CTAs working at the same
+// time on neighbouring tiles share the long operand through L2).  Warp
+// roles (320 threads): warp 0 TMA producer, warp 1 MMA issuer, warps 2..9 fold and store (warp w reads TMEM lanes
 // 32*(w%4)..+31 = its rows, columns 64*((w-2)/4)..+63 of the accumulator).
 // The shared-memory ring, the tensor-memory accumulator ring and their
 // barriers run on across tiles, so loads and MMAs of tile i+1 proceed while
@@ -194,7 +164,7 @@ constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 32 * (2 + EPI_WARPS);
 constexpr int STG = 16;  // columns per staged store chunk
 
-template <int KIND, int BN, int CH, int CW>
+template <int KIND, int BN>
 __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_constant__ CUtensorMap a_hi,
                                                          const __grid_constant__ CUtensorMap a_lo,
                                                          const __grid_constant__ CUtensorMap b_hi,
@@ -216,30 +186,19 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   float* staging = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
   Smem* S = reinterpret_cast<Smem*>(staging + EPI_WARPS * 32 * (STG + 1));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int CS = CH * CW;                  // CTAs per cluster
-  constexpr int A_PART = A_BYTES / CW, B_PART = B_BYTES / CH;  // bytes of a plane one CTA loads
-  uint32_t crank = 0;
-  if (CS > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
-  const int ci = (int)(crank / CW), cj = (int)(crank % CW);  // position in the cluster
-  // cluster ranks sharing this CTA's A tile (same ci) and B tile (same cj)
-  uint16_t amask = 0, bmask = 0;
-  for (int j = 0; j < CW; ++j) amask |= (uint16_t)(1u << (ci * CW + j));
-  for (int i = 0; i < CH; ++i) bmask |= (uint16_t)(1u << (i * CW + cj));
-  const uint16_t cmask = amask | bmask;        // CTAs that fill this CTA's stages (and that it fills)
-  const int ntn = (int)((ep.N + BN - 1) / BN), ntm = (int)((ep.M + BM - 1) / BM);
-  const int64_t sn = (ntn + CW - 1) / CW, sm_ = (ntm + CH - 1) / CH;
-  const int64_t nt1 = sn * sm_;                // cluster tiles (one tile per CTA)
-  const int64_t ntiles = nt1 * ep.ksplit;      // work items (cluster tile, K slice)
-  const int64_t cid = blockIdx.x / CS, ncl = gridDim.x / CS;
-  // this CTA's output tile of cluster tile tt (rows past M or columns past N
-  // load zeros and store nothing).  The dimension with fewer tiles runs
+  const int64_t sn = (ep.N + BN - 1) / BN, sm_ = (ep.M + BM - 1) / BM;
+  const int64_t nt1 = sn * sm_;                // output tiles
+  const int64_t ntiles = nt1 * ep.ksplit;      // work items (tile, K slice)
+  const int64_t cid = blockIdx.x, ncl = gridDim.x;
+  // output tile tt (rows past M or columns past N load zeros and store
+  // nothing).  The dimension with fewer tiles runs
   // fastest, so CTAs working at the same time share the tiles of the long
   // operand, which streams through L2 once.
   const bool mfast = sm_ < sn;
   auto tile_of = [&](int64_t tt, int64_t& m0, int64_t& n0) {
     const int64_t cm = mfast ? tt % sm_ : tt / sn, cn = mfast ? tt / sm_ : tt % sn;
-    m0 = (cm * CH + ci) * (int64_t)BM;
-    n0 = (cn * CW + cj) * (int64_t)BN;
+    m0 = cm * (int64_t)BM;
+    n0 = cn * (int64_t)BN;
   };
   // K blocks of work item t: [kb_lo, kb_hi)
   auto krange = [&](int64_t t, int& lo, int& hi) {
@@ -251,7 +210,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&S->full[s], 1);
-      mbar_init(&S->empty[s], (uint32_t)__popc(cmask));  // one MMA commit per CTA it feeds
+      mbar_init(&S->empty[s], 1);  // the MMA issuer's commit
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(&S->acc_full[b], 1);
@@ -268,7 +227,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (CS > 1) cluster_sync_all();  // every peer's barriers are initialised before any multicast
   const uint32_t tmem = S->tmem;
 
   int64_t issued_loads = 0;
@@ -295,21 +253,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           uint8_t* st = base + s * STAGE_BYTES;
           mbar_expect_tx(&S->full[s], STAGE_BYTES);
           const int kx = kb * (KB_BYTES / (KIND == KIND_TF32 ? 4 : 2));
-          if (CW > 1) {
-            tma_load_2d_mc(&a_hi, &S->full[s], st + cj * A_PART, kx, m0 + cj * (BM / CW), amask);
-            tma_load_2d_mc(&a_lo, &S->full[s], st + A_BYTES + cj * A_PART, kx, m0 + cj * (BM / CW), amask);
-          } else {
-            tma_load_2d(&a_hi, &S->full[s], st, kx, m0);
-            tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, m0);
-          }
-          if (CH > 1) {
-            tma_load_2d_mc(&b_hi, &S->full[s], st + 2 * A_BYTES + ci * B_PART, kx, n0 + ci * (BN / CH), bmask);
-            tma_load_2d_mc(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES + ci * B_PART, kx, n0 + ci * (BN / CH),
-                           bmask);
-          } else {
-            tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, n0);
-            tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, n0);
-          }
+          tma_load_2d(&a_hi, &S->full[s], st, kx, m0);
+          tma_load_2d(&a_lo, &S->full[s], st + A_BYTES, kx, m0);
+          tma_load_2d(&b_hi, &S->full[s], st + 2 * A_BYTES, kx, n0);
+          tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, n0);
           issued_loads = kbg + 1;
         }
       }
@@ -346,10 +293,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
             mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
             mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
           }
-          if (CS > 1)
-            mma_commit_mc(&S->empty[s], cmask);
-          else
-            mma_commit(&S->empty[s]);
+          mma_commit(&S->empty[s]);
           if (last) {
             mma_commit(&S->acc_full[b]);
             ++gg;
@@ -592,8 +536,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
-  if (CS > 1) cluster_sync_all();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
@@ -792,51 +734,26 @@ int num_sms() {
   return n;
 }
 
-// Persistent launch: one CTA per SM (clusters of CH x CW CTAs as many as fit
-// at once), at most one per work item.  Returns false if clusters of this
-// shape cannot be resident (the caller then launches without clusters).
-template <int KIND, int BN, int CH, int CW>
-bool launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
+// Persistent launch: one CTA per SM, at most one per work item.
+template <int KIND, int BN>
+void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh, const CUtensorMap& bl,
             const TcEpilogue& ep, int64_t items, cudaStream_t s) {
-  constexpr int CS = CH * CW;
-  auto kern = tc_gemm_kernel<KIND, BN, CH, CW>;
-  static int max_clusters[64] = {};  // per device, 0 = not queried yet
+  auto kern = tc_gemm_kernel<KIND, BN>;
+  static bool configured[64] = {};  // per device: shared-memory limit raised
   static std::mutex mu;
   int dev = 0;
   MERA_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) throw Error(MERA_ERR_UNSUPPORTED, "tensor-core GEMM: device ordinal out of range");
   const size_t sm = smem_bytes<KIND, BN>();
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(NTHREADS);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = CS > 1 ? 1 : 0;
   {
     std::lock_guard<std::mutex> lk(mu);
-    if (!max_clusters[dev]) {
+    if (!configured[dev]) {
       MERA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      int n = num_sms();
-      if (CS > 1) {
-        cfg.gridDim = dim3(CS);
-        n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
-          (void)cudaGetLastError();
-          n = 0;
-        }
-      }
-      max_clusters[dev] = n > 0 ? n : -1;
+      configured[dev] = true;
     }
   }
-  if (max_clusters[dev] < 0) return false;
-  cfg.gridDim = dim3((unsigned)(std::min<int64_t>(items, max_clusters[dev]) * CS));
-  MERA_CUDA(cudaLaunchKernelEx(&cfg, kern, ah, al, bh, bl, ep));
-  return true;
+  const unsigned grid = (unsigned)std::min<int64_t>(items, num_sms());
+  kern<<<grid, NTHREADS, sm, s>>>(ah, al, bh, bl, ep);
 }
 
 }  // namespace
@@ -970,41 +887,13 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
     run.preload = run.mode >= 1 && !run.c_f64 && run.beta != 0.0 && pow2;
     run.bscale = run.preload ? (float)(run.beta / run.alpha) : 0.f;
   }
-  // cluster shape (CH along M x CW along N): 2 x 2 for split-K products
-  // (few output tiles, both operands long and streamed: sharing halves the
-  // traffic); elsewhere the long operand already streams once and clusters
-  // only cost residency.  MERA_TC_CLUSTER ("11", "12", "21", "22") overrides.
-  int ch = 1, cw = 1;
-  if (run.ksplit > 1) {
-    ch = mt >= 2 ? 2 : 1;
-    cw = nt >= 2 ? 2 : 1;
-  }
-  if (const char* env = std::getenv("MERA_TC_CLUSTER")) {
-    if (std::strlen(env) == 2 && (env[0] == '1' || env[0] == '2') && (env[1] == '1' || env[1] == '2')) {
-      ch = env[0] - '0';
-      cw = env[1] - '0';
-    }
-  }
-  auto go = [&](int h, int w) -> bool {
-    const CUtensorMap ah = make_map(a_hi, Mp, Kp, elem, BM / w), al = make_map(a_lo, Mp, Kp, elem, BM / w);
-    const CUtensorMap bh = make_map(b_hi, Np, Kp, elem, bn / h), bl = make_map(b_lo, Np, Kp, elem, bn / h);
-    const int64_t items = ((mt + h - 1) / h) * ((nt + w - 1) / w) * run.ksplit;
-    const int c = h * 10 + w;
-    if (kind == KIND_TF32) {
-      if (c == 11) return launch<KIND_TF32, 128, 1, 1>(ah, al, bh, bl, run, items, s);
-      if (c == 12) return launch<KIND_TF32, 128, 1, 2>(ah, al, bh, bl, run, items, s);
-      if (c == 21) return launch<KIND_TF32, 128, 2, 1>(ah, al, bh, bl, run, items, s);
-      return launch<KIND_TF32, 128, 2, 2>(ah, al, bh, bl, run, items, s);
-    }
-    if (c == 11) return launch<KIND_BF16, 128, 1, 1>(ah, al, bh, bl, run, items, s);
-    if (c == 12) return launch<KIND_BF16, 128, 1, 2>(ah, al, bh, bl, run, items, s);
-    if (c == 21) return launch<KIND_BF16, 128, 2, 1>(ah, al, bh, bl, run, items, s);
-    return launch<KIND_BF16, 128, 2, 2>(ah, al, bh, bl, run, items, s);
-  };
-  if (!go(ch, cw)) {
-    if (!go(1, 1)) throw Error(MERA_ERR_UNSUPPORTED, "tensor-core GEMM: kernel cannot be resident");
-    ch = cw = 1;
-  }
+  const CUtensorMap ah = make_map(a_hi, Mp, Kp, elem, BM), al = make_map(a_lo, Mp, Kp, elem, BM);
+  const CUtensorMap bh = make_map(b_hi, Np, Kp, elem, bn), bl = make_map(b_lo, Np, Kp, elem, bn);
+  const int64_t items = mt * nt * run.ksplit;
+  if (kind == KIND_TF32)
+    launch<KIND_TF32, 128>(ah, al, bh, bl, run, items, s);
+  else
+    launch<KIND_BF16, 128>(ah, al, bh, bl, run, items, s);
   count_launch();
   MERA_CHECK_LAUNCH();
   if (sp > 1) {
@@ -1014,7 +903,7 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
     count_launch();
     MERA_CHECK_LAUNCH();
   }
-  return 100 * run.mode + 10 * ch + cw;
+  return run.mode;
 }
 
 }  // namespace tc

@@ -55,8 +55,7 @@ void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, co
 // Mp a multiple of 128 covering M, Np a multiple of 128 covering N.
 // Products with too few output tiles to fill the GPU split K over several
 // CTAs (partials in splitk_ws, summed in a fixed order by a second kernel).
-// Returns the path taken: 100 * store mode + 10 * cluster CTAs along M +
-// cluster CTAs along N.
+// Returns the path taken: the epilogue store mode.
 int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, const void* a_lo,
                 int64_t Mp, const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep,
                 cudaStream_t s, float* splitk_ws = nullptr, size_t splitk_ws_bytes = 0);

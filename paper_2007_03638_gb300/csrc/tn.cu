@@ -580,7 +580,7 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
   const int path = tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (pr) {
-    pr->end(pair, 1000 * (kind + 1) + path, s);
+    pr->end(pair, 1000 * (kind + 1) + 100 * path, s);
     pr->gett_launches++;
     pr->gett_flops += 2.0 * (double)g.M * (double)g.N * (double)g.K;
   }

@@ -151,13 +151,22 @@ def footprint_bytes(cfg: Config) -> int:
 
 def dots_noalloc(X, y, k, n, ldx, out, stream=0):
     """Allocation-free batched dot products (see mera_dots_noalloc in mera.h):
-    X, y device arrays (torch CUDA tensors or raw pointers), out: host or device
-    array of k doubles.  Raises MeraError on a bad size."""
+    X, y float64 device arrays (torch CUDA tensors, or raw pointers whose
+    sizes the caller vouches for), out: host or device float64 array of at
+    least k elements.  Raises ValueError when an array is too short and
+    MeraError on a size the library rejects."""
     L = load()
-    xp = X if isinstance(X, int) else _ptr(X)
-    yp = y if isinstance(y, int) else _ptr(y)
-    rc = L.mera_dots_noalloc(C.c_void_p(xp), int(ldx), int(k), C.c_void_p(yp), int(n),
-                             C.c_void_p(_ptr(out)), C.c_void_p(stream))
+    k, n, ldx = int(k), int(n), int(ldx)
+    if k >= 1 and n >= 0:
+        need_x = (k - 1) * ldx + n if k > 1 else n
+        for name, a, need in (("X", X, need_x), ("y", y, n), ("out", out, k)):
+            size = None if isinstance(a, int) else (a.numel() if hasattr(a, "numel") else a.size)
+            if size is not None and size < need:
+                raise ValueError(f"dots_noalloc: {name} holds {size} elements, needs {need}")
+    xp = X if isinstance(X, int) else _ptr(X, np.float64)
+    yp = y if isinstance(y, int) else _ptr(y, np.float64)
+    rc = L.mera_dots_noalloc(C.c_void_p(xp), ldx, k, C.c_void_p(yp), n,
+                             C.c_void_p(_ptr(out, np.float64)), C.c_void_p(stream))
     if rc != 0:
         raise MeraError(rc, L.mera_strerror(rc).decode())
     return out

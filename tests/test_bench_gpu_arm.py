@@ -107,6 +107,11 @@ CONTRACT = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step
 def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", workload, "--steps", "2", "--warmup", "3",
                                       "--cpu-seconds", "0.1"])
+    kind, d_b, chi, L, prec, extra = bench.WORKLOADS[workload]
+    if extra.get("network", 0) == 0 and chi > 8:
+        # a whole binary oracle evaluation at chi = 12 takes tens of seconds on
+        # the CPU: its timing is replaced (the control flow is what is checked)
+        monkeypatch.setattr(bench, "oracle_eval_sample", lambda wl, seconds=10.0, seed=0: (30.0, 1))
     bench.main()
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for k in CONTRACT:
@@ -123,9 +128,11 @@ def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
     for k in ("value", "unit", "cores", "kind", "sample"):
         assert k in line["cpu_baseline"], k
     assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["extrapolated"] == (not bench.whole_eval(workload))
     for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
         assert k in line["e2e"], k
     assert line["e2e"]["h2d_bytes_per_step"] > 0
+    assert line["e2e"]["evaluations"] >= 1 and line["e2e"]["krylov_matvecs_per_grad"] >= 0
     for k in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert k in line["clocks"], k
     assert line["memory"]["device_bytes"] == 3 * 2**30 and line["memory"]["footprint_bytes"] > 0

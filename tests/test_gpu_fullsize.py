@@ -4,8 +4,8 @@ through properties that hold at any size, since the oracle cannot evaluate a
 chi = 32 network:
 
 * repeatability: two evaluations at the same point give bit-identical energy and
-  gradient (every reduction runs in a fixed order; split-K slices and cluster
-  products must not race);
+  gradient (every reduction runs in a fixed order; split-K slices must not
+  race);
 * tangency: W^dag G = 0 for the Grassmann isometries, W^dag G skew for the
   disentanglers (Eqs. stiefel_gradient, grassmann_gradient);
 * the variational bound: the energy per spin lies above the exact ground-state

@@ -210,3 +210,77 @@ def test_grassmann_gauge_invariance():
     e1 = om.energy(h3, us, ws)
     e2 = om.energy(h3, us2, ws2)
     assert abs(e1 - e2) < 1e-12
+
+
+def _site_rdm(psi, sites):
+    """Reduced density matrix of the listed sites (in that order) of a state tensor."""
+    d = [psi.shape[k] for k in sites]
+    p = np.moveaxis(psi, sites, list(range(len(sites)))).reshape(int(np.prod(d)), -1)
+    return p @ p.conj().T / np.vdot(psi, psi).real
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.complex128])
+def test_tensor_density_matrices_vs_dense_sites(dt):
+    """rho_w and rho_u of the binary network (Sec. 4: the density matrix on a
+    tensor's top legs) from a 3-site density matrix that is NOT averaged over
+    positions: the reduced state of coarse sites (0, 1, 2) of a random
+    periodic 4-site state.  rho_w must be the one-site state of coarse site 1
+    (the middle site); rho_u the two-site state of the fine pair (1, 2) of
+    W|psi> -- the right output of w on coarse site 0 and the left output of w
+    on coarse site 1, the pair a disentangler acts on -- both by partial trace
+    of the dense state.  A wrong site, a wrong pair, a transposed or
+    conjugated w fails here (the state has no symmetry that hides them)."""
+    rng = np.random.default_rng(21)
+    c, cp = 2, 3
+    w = inp._haar_like(rng, c * c, cp, dt)
+    top = rng.standard_normal((cp,) * 4) + (1j * rng.standard_normal((cp,) * 4) if dt == np.complex128 else 0)
+    top /= np.linalg.norm(top)
+    rho3 = _site_rdm(top, [0, 1, 2])
+    ru, rw = om.tensor_density_matrices([rho3], [w])
+    assert np.abs(rw - _site_rdm(top, [1])).max() < 1e-14
+    fine = bf.apply_isometry_layer(top, w)  # 8 fine sites, no disentanglers
+    assert np.abs(ru - _site_rdm(fine, [1, 2])).max() < 1e-14
+    # the other choices differ on this state (so the comparison above is sharp)
+    assert np.abs(rw - _site_rdm(top, [0])).max() > 1e-3
+    assert np.abs(ru - _site_rdm(fine, [3, 4])).max() > 1e-3
+    assert np.abs(ru - _site_rdm(fine, [0, 1])).max() > 1e-3
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.complex128])
+def test_tensor_density_matrices_vs_dense_average(dt):
+    """With the position-averaged 3-site density matrix of a periodic 4-site
+    state (the form the MERA's level density matrices have), rho_w is the
+    average one-site state and rho_u the average, over the four disentangler
+    positions (2j+1, 2j+2) of the fine chain W|psi>, of the two-site state;
+    both have unit trace and are Hermitian, positive semidefinite."""
+    rng = np.random.default_rng(22)
+    c, cp = 2, 3
+    w = inp._haar_like(rng, c * c, cp, dt)
+    top = rng.standard_normal((cp,) * 4) + (1j * rng.standard_normal((cp,) * 4) if dt == np.complex128 else 0)
+    top /= np.linalg.norm(top)
+    ru, rw = om.tensor_density_matrices([bf.averaged_rdm3(top)], [w])
+    one = sum(_site_rdm(top, [k]) for k in range(4)) / 4
+    assert np.abs(rw - one).max() < 1e-14
+    fine = bf.apply_isometry_layer(top, w)
+    two = sum(_site_rdm(fine, [(2 * j + 1) % 8, (2 * j + 2) % 8]) for j in range(4)) / 4
+    assert np.abs(ru - two).max() < 1e-14
+    for r in (ru, rw):
+        assert abs(np.trace(r) - 1) < 1e-13
+        assert np.abs(r - r.conj().T).max() < 1e-15
+        assert np.linalg.eigvalsh(r).min() > -1e-14
+
+
+def test_tensor_density_matrices_levels():
+    """Layer l's matrices come from the level above (rho_{l+1}); the
+    scale-invariant layer's from rho_S itself."""
+    rng = np.random.default_rng(23)
+    ws = [inp._haar_like(rng, 4, 3, np.float64), inp._haar_like(rng, 9, 3, np.float64)]
+    rhos = []
+    for _ in range(2):
+        t = rng.standard_normal((3,) * 4)
+        rhos.append(bf.averaged_rdm3(t / np.linalg.norm(t)))
+    out = om.tensor_density_matrices(rhos, ws)
+    r0 = om.tensor_density_matrices([rhos[1]], [ws[0]])
+    r1 = om.tensor_density_matrices([rhos[1]], [ws[1]])
+    for a, b in zip(out, r0 + r1):
+        assert np.abs(a - b).max() == 0.0
