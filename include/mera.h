@@ -72,7 +72,7 @@ enum {
     MERA_OK = 0,
     MERA_ERR_ARG = -1,            /* invalid argument / shape / config        */
     MERA_ERR_OOM = -2,            /* device allocation failed                 */
-    MERA_ERR_NONFINITE = -3,      /* NaN/Inf in energy or gradient            */
+    MERA_ERR_NONFINITE = -3,      /* NaN/Inf in an input, energy or gradient  */
     MERA_ERR_NOCONV = -4,         /* Krylov solve or line search not converged*/
     MERA_ERR_DEVICE_TIMEOUT = -5, /* a bounded device-side wait expired       */
     MERA_ERR_NOT_ISOMETRIC = -6,  /* input tensor violates W^dag W = 1        */
@@ -128,6 +128,11 @@ typedef struct {
                           from d_b = 4: blocked spin pairs must then be in a
                           basis whose first half is even); otherwise, and for
                           an MPS, MERA_ERR_UNSUPPORTED.                      */
+    double device_wait_s; /* limit, in seconds, of every wait of the
+                          tensor-core contraction kernel's pipeline (0 <
+                          device_wait_s <= 60; default 1): a wait that
+                          expires ends the kernel early and the call returns
+                          MERA_ERR_DEVICE_TIMEOUT (see mera_set_device_wait) */
 } mera_config;
 
 /* Network of the MERA (Sec. 4).  MERA_BINARY: the binary MERA described
@@ -166,7 +171,7 @@ typedef enum { MERA_BINARY = 0, MERA_TERNARY = 1, MERA_MPS = 2 } mera_network;
 
 /* Fill *cfg with defaults for (d_b, chi, n_trans): binary network, F64,
  * FP64 contractions, Grassmann isometries, preconditioner on, Krylov dim 20,
- * 2000 products, tol 1e-14, no recomputation, m = 8. */
+ * 2000 products, tol 1e-14, no recomputation, m = 8, device waits of 1 s. */
 void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
 
 /* Create a problem.  h3 is the 3-site Hamiltonian term on bottom sites,
@@ -179,8 +184,10 @@ void mera_config_default(mera_config* cfg, int d_b, int chi, int n_trans);
  * MERA_ERR_ARG (before any device work) for a config outside its ranges:
  * unknown dtype, prec or network; w_stiefel, precond, recompute_env or z2
  * not 0 or 1; krylov_tol not in (0, 1); krylov_maxiter, krylov_dim or lbfgs_m
- * below 1; a negative b_chunk; a Hamiltonian term that is not Hermitian
- * (|h - h^dag| above 1e-10 of its largest entry) or not finite. */
+ * below 1; a negative b_chunk; device_wait_s not in (0, 60]; a Hamiltonian
+ * term that is not Hermitian (|h - h^dag| above 1e-10 of its largest
+ * entry).  MERA_ERR_NONFINITE for a Hamiltonian term with a NaN or an
+ * infinite entry. */
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out);
 int mera_destroy(mera_t m);
 
@@ -189,8 +196,9 @@ int mera_num_tensors(mera_t m);
 int mera_tensor_shape(mera_t m, int i, int64_t* rows, int64_t* cols);
 
 /* Copy the point in / out (arrays in the tensor-list order above).
- * mera_set_tensors checks W^dag W = 1 to 1e-10 (MERA_ERR_NOT_ISOMETRIC) and
- * clears the optimiser history. */
+ * mera_set_tensors checks that every entry is finite (MERA_ERR_NONFINITE)
+ * and W^dag W = 1 to 1e-10 (MERA_ERR_NOT_ISOMETRIC), and clears the
+ * optimiser history; on an error the point is unchanged. */
 int mera_set_tensors(mera_t m, const void* const* tensors);
 int mera_get_tensors(mera_t m, void* const* tensors);
 
@@ -233,12 +241,13 @@ int mera_inner(mera_t m, const void* const* X, const void* const* Y, double* out
 
 /* Vector transport along the retraction from the current point (Eq. transport):
  * Y_i <- exp(alpha Q_{X_i}) Y_i, in place.  Call before mera_retract moves the
- * point. */
+ * point.  MERA_ERR_NONFINITE if X has a NaN or infinite entry. */
 int mera_transport(mera_t m, const void* const* X, double alpha, void* const* Y);
 
 /* Move the current point along the exponential retraction (Eq. retraction):
  * W_i <- exp(alpha Q_{X_i}) W_i, followed by re-isometrisation (polar factor).
- * If Xprime is not NULL it receives dR/dalpha = exp(alpha Q_X) X. */
+ * If Xprime is not NULL it receives dR/dalpha = exp(alpha Q_X) X.
+ * MERA_ERR_NONFINITE (point unchanged) if X has a NaN or infinite entry. */
 int mera_retract(mera_t m, const void* const* X, double alpha, void* const* Xprime);
 
 /* Hilbert-space preconditioner (Eq. preconditioner_solution) with the
@@ -357,6 +366,10 @@ typedef struct {
     double t_done;    /* -1 until finished                                       */
     size_t bytes;     /* device footprint the request was admitted with          */
     char message[160];/* detail of a failure (mera_last_error of the request)    */
+    int deferred;     /* times its creation ran out of device memory while other
+                         requests ran, so that it went back to the head of the
+                         queue until one of them finished (a creation that runs
+                         out of memory with nothing else running fails)       */
 } mera_request_status;
 
 int mera_server_create(size_t mem_budget_bytes, int n_workers, mera_server_t* out);
@@ -379,6 +392,36 @@ int mera_server_destroy(mera_server_t sv);
  * bounded device-side wait expired. */
 int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C,
               void* stream);
+
+/* Change the limit of the tensor-core kernel's pipeline waits of an
+ * existing object (mera_config.device_wait_s; 0 < seconds <= 60, else
+ * MERA_ERR_ARG).  When a wait expires the kernel stops issuing work, waits
+ * for the copies and tensor-core operations it has already issued, frees its
+ * tensor memory and returns; the call that ran it returns
+ * MERA_ERR_DEVICE_TIMEOUT and the object stays usable: its point is
+ * unchanged and the next evaluation starts its Krylov solves afresh.  A
+ * limit far below the kernel's normal latencies makes every mixed-precision
+ * evaluation end this way (the way this error path is tested).  The paper
+ * has no counterpart of this entry point. */
+int mera_set_device_wait(mera_t m, double seconds);
+
+/* Device allocator for every buffer the library allocates (tensors, level
+ * operators, Krylov vectors, workspaces, offset tables), process-wide.
+ * alloc(bytes, user) returns device memory of at least `bytes` bytes,
+ * aligned to 256 bytes, or NULL when it cannot: the call that needed the
+ * memory then frees what it had allocated and returns MERA_ERR_OOM (the
+ * server defers the admission of a request whose creation failed this way
+ * while others run, and fails it only when it is alone).  dealloc(ptr,
+ * user) takes back a pointer alloc returned.  alloc = NULL restores
+ * cudaMalloc / cudaFree.  Every buffer is freed with the deallocator of the
+ * allocator that made it.  Set it while no other thread is inside the
+ * library.  Lets a caller route the library's memory through its own pool
+ * (for example a framework's caching allocator) or bound it.  MERA_ERR_ARG
+ * if alloc is set and dealloc is NULL.  The paper has no counterpart of
+ * this entry point. */
+typedef void* (*mera_alloc_fn)(size_t bytes, void* user);
+typedef void (*mera_free_fn)(void* ptr, void* user);
+int mera_set_allocator(mera_alloc_fn alloc, mera_free_fn dealloc, void* user);
 
 /* Allocation-free batched dot products, for callers that cannot allocate
  * device memory (a host application that owns the whole GPU memory and

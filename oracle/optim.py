@@ -246,6 +246,19 @@ def lbfgs(problem, point, m=8, maxiter=100, gtol=1e-6, callback=None, maxeval=20
     return point, e, hist
 
 
+def hz_beta(inner, y, Pg2, Py, d2, G2, gnorm_old, eta=0.01):
+    """The preconditioned Hager-Zhang coefficient of the new direction
+    d' = -P(g') + beta d (Sec. 3 uses the Hager-Zhang scheme):
+    beta = (<y, P g'> - 2 <y, P y> <d, g'> / <d, y>) / <d, y>, y = g' - T(g),
+    bounded below by -1 / (|d| min(eta, |g|)) with g the gradient where the
+    searched direction d started.  All vectors at the new point (d and g
+    transported)."""
+    dy = inner(d2, y)
+    beta = (inner(y, Pg2) - 2.0 * inner(y, Py) * inner(d2, G2) / dy) / dy
+    dn = math.sqrt(inner(d2, d2))
+    return max(beta, -1.0 / (dn * min(eta, gnorm_old)))
+
+
 def cg(problem, point, maxiter=100, gtol=1e-6, eta=0.01, callback=None, maxeval=20):
     """Riemannian nonlinear CG with the preconditioned Hager-Zhang beta (Sec. 3)."""
     inner = geo.inner
@@ -280,11 +293,9 @@ def cg(problem, point, maxiter=100, gtol=1e-6, eta=0.01, callback=None, maxeval=
         p2, G2, aux2, d2 = pay
         y = lin(1.0, G2, -1.0, problem.transport(point, d, alpha, G))
         Pg2 = problem.precondition(p2, aux2, G2)
-        dy = inner(d2, y)
-        beta = (inner(y, Pg2) - 2.0 * inner(y, problem.precondition(p2, aux2, y))
-                * inner(d2, G2) / dy) / dy
-        dn = math.sqrt(inner(d2, d2))
-        beta = max(beta, -1.0 / (dn * min(eta, math.sqrt(inner(G2, G2)))))
+        # the lower bound takes the gradient where the searched direction
+        # started (|T(d)| = |d|: the transport is isometric)
+        beta = hz_beta(inner, y, Pg2, problem.precondition(p2, aux2, y), d2, G2, math.sqrt(inner(G, G)), eta)
         d = lin(-1.0, Pg2, beta, d2)
         point, e, G, aux, Pg, alpha_prev = p2, e2, G2, aux2, Pg2, alpha
     return point, e, hist

@@ -4,6 +4,18 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
+
+namespace mera {
+namespace {
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+}  // namespace
+Allocator current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+}  // namespace mera
 
 // ================================================================ C ABI ====
 using mera::Error;
@@ -15,6 +27,23 @@ struct Guard {
   ~Guard() { mera::g_prof = nullptr; }
 };
 
+// After a failed call: if a tensor-core wait expired during it, that is the
+// cause (an aborted product leaves garbage that later steps may report as
+// non-convergence or non-finite values), so the flag is cleared and the
+// error reported as MERA_ERR_DEVICE_TIMEOUT.  The Krylov warm starts are
+// invalid then too.
+bool take_device_flag(mera_t m) {
+  if (!m || !m->tc_err.p) return false;
+  int e = 0;
+  if (cudaMemcpyAsync(&e, m->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, m->s) != cudaSuccess ||
+      cudaStreamSynchronize(m->s) != cudaSuccess)
+    return false;
+  if (!e) return false;
+  (void)cudaMemsetAsync(m->tc_err.p, 0, sizeof(int), m->s);
+  m->have_rho = m->have_x = false;
+  return true;
+}
+
 template <class F>
 int wrap(mera_t m, F&& f) {
   Guard g(m);
@@ -22,6 +51,10 @@ int wrap(mera_t m, F&& f) {
     f();
     return MERA_OK;
   } catch (const Error& e) {
+    if (e.code != MERA_ERR_DEVICE_TIMEOUT && take_device_flag(m)) {
+      m->err = std::string("a bounded tensor-core wait expired (then: ") + e.what() + ")";
+      return MERA_ERR_DEVICE_TIMEOUT;
+    }
     if (m) m->err = e.what();
     return e.code;
   } catch (const std::bad_alloc&) {
@@ -39,6 +72,11 @@ void copy_in(mera_t m, const void* const* arr, double* flat) {
     MERA_CUDA(cudaMemcpyAsync(flat + m->offs[i], arr[i], sizeof(double) * m->rows[i] * m->cols[i] * m->rs,
                               cudaMemcpyDefault, m->s));
   }
+}
+// A step with a NaN or infinite entry has a non-finite squared norm.
+void check_finite_step(mera_t m, const double* X) {
+  const double q = m->red.dot(X, X, m->total, m->s);
+  if (!std::isfinite(q)) throw Error(MERA_ERR_NONFINITE, "the step has a non-finite entry");
 }
 void copy_out(mera_t m, const double* flat, void* const* arr) {
   for (int i = 0; i < m->nt; ++i) {
@@ -69,6 +107,7 @@ void mera_config_default(mera_config* c, int d_b, int chi, int n_trans) {
   c->b_chunk = 0;
   c->network = MERA_BINARY;
   c->z2 = 0;
+  c->device_wait_s = 1.0;
 }
 
 int mera_create(const mera_config* cfg, const void* h3, void* stream, mera_t* out) {
@@ -183,6 +222,7 @@ int mera_transport(mera_t m, const void* const* X, double alpha, void* const* Y)
   if (!m || !X || !Y || !std::isfinite(alpha)) return MERA_ERR_ARG;
   return wrap(m, [&] {
     copy_in(m, X, mera::P(m->dir2));
+    check_finite_step(m, mera::P(m->dir2));
     copy_in(m, (const void* const*)Y, mera::P(m->tmpv));
     mera::make_geom(*m, mera::P(m->Wcur), mera::P(m->dir2), alpha, m->s);
     mera::apply_transport(*m, mera::P(m->Wcur), mera::P(m->dir2), mera::P(m->tmpv), m->s);
@@ -194,6 +234,7 @@ int mera_retract(mera_t m, const void* const* X, double alpha, void* const* Xpri
   if (!m || !X || !std::isfinite(alpha)) return MERA_ERR_ARG;
   return wrap(m, [&] {
     copy_in(m, X, mera::P(m->dir2));
+    check_finite_step(m, mera::P(m->dir2));
     mera::make_geom(*m, mera::P(m->Wcur), mera::P(m->dir2), alpha, m->s);
     mera::apply_retract(*m, mera::P(m->Wcur), mera::P(m->dir2), mera::P(m->Wtry), m->s);
     if (Xprime) {
@@ -395,6 +436,22 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
 }
 
 int64_t mera_launch_count(mera_t m) { return m ? m->prof.launches : 0; }
+
+int mera_set_device_wait(mera_t m, double seconds) {
+  if (!m || !(seconds > 0.0 && seconds <= 60.0)) return MERA_ERR_ARG;
+  m->cfg.device_wait_s = seconds;
+  m->ex.wait_ns = (uint64_t)(seconds * 1e9);
+  return MERA_OK;
+}
+
+int mera_set_allocator(mera_alloc_fn alloc, mera_free_fn dealloc, void* user) {
+  if (alloc && !dealloc) return MERA_ERR_ARG;
+  std::lock_guard<std::mutex> lk(mera::g_alloc_mu);
+  mera::g_alloc.alloc = alloc;
+  mera::g_alloc.dealloc = alloc ? dealloc : nullptr;
+  mera::g_alloc.user = alloc ? user : nullptr;
+  return MERA_OK;
+}
 
 int mera_get_stats(mera_t m, mera_stats* out, int reset) {
   if (!m || !out) return MERA_ERR_ARG;

@@ -63,28 +63,55 @@ inline void count_launch(int n = 1) {
   if (g_prof) g_prof->launches += n;
 }
 
-// Owning device allocation.
+// The device allocator every DevBuf uses (mera_set_allocator): null alloc
+// means cudaMalloc / cudaFree.
+struct Allocator {
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*dealloc)(void*, void*) = nullptr;
+  void* user = nullptr;
+};
+Allocator current_allocator();
+
+// Owning device allocation; freed with the deallocator of the allocator that
+// made it.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  Allocator by;
   DevBuf() = default;
   explicit DevBuf(size_t n) { alloc(n); }
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), by(o.by) { o.p = nullptr; o.bytes = 0; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; by = o.by; o.p = nullptr; o.bytes = 0; }
     return *this;
   }
   ~DevBuf() { release(); }
   void alloc(size_t n) {
     release();
     if (n == 0) return;
-    MERA_CUDA(cudaMalloc(&p, n));
+    by = current_allocator();
+    if (by.alloc) {
+      p = by.alloc(n, by.user);
+      if (!p) throw Error(MERA_ERR_OOM, "the device allocator returned no memory for " + std::to_string(n) + " bytes");
+      if (reinterpret_cast<uintptr_t>(p) & 255) {
+        by.dealloc(p, by.user);
+        p = nullptr;
+        throw Error(MERA_ERR_ARG, "the device allocator returned memory not aligned to 256 bytes");
+      }
+    } else {
+      MERA_CUDA(cudaMalloc(&p, n));
+    }
     bytes = n;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (by.alloc)
+        by.dealloc(p, by.user);
+      else
+        cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
   }

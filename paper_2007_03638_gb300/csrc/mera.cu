@@ -121,6 +121,7 @@ void build_layers_net(Ctx& c) {
     c.ex.ws = c.tc_ws.p;
     c.ex.ws_bytes = ws_need;
     c.ex.err = c.tc_err.as<int>();
+    c.ex.wait_ns = (uint64_t)(c.cfg.device_wait_s * 1e9);
   }
 }
 
@@ -215,6 +216,7 @@ void build_layers(Ctx& c) {
         c.ex.keep_bytes[k] = kneed[k];
       }
     c.ex.err = c.tc_err.as<int>();
+    c.ex.wait_ns = (uint64_t)(c.cfg.device_wait_s * 1e9);
   }
   for (int l = 0; l <= c.L; ++l)
     for (int sd = 0; sd < 2; ++sd) {
@@ -239,6 +241,7 @@ void check_device_flag(Ctx& c, cudaStream_t s) {
   MERA_CUDA(cudaStreamSynchronize(s));
   if (e) {
     MERA_CUDA(cudaMemsetAsync(c.tc_err.p, 0, sizeof(int), s));
+    c.have_rho = c.have_x = false;  // the Krylov vectors may hold an aborted product's garbage
     throw Error(MERA_ERR_DEVICE_TIMEOUT, "tensor-core contraction: a bounded device-side wait expired");
   }
 }
@@ -317,6 +320,8 @@ int gmres(Ctx& c, const std::function<void(const double*, double*)>& op, const d
     ++applications;
     axpby(1.0, b, -1.0, w, n, s);  // w = b - A x
     const double beta = std::sqrt(c.red.dot(w, w, n, s));
+    // an expired tensor-core wait leaves garbage in w: stop at once
+    check_device_flag(c, s);
     if (beta <= tol * bnorm) return applications;
     if (applications >= maxit || !(beta < 1e300)) {
       throw Error(MERA_ERR_NOCONV, "GMRES: relative residual " + std::to_string(beta / bnorm));
@@ -376,6 +381,17 @@ int gmres(Ctx& c, const std::function<void(const double*, double*)>& op, const d
 }
 
 // --------------------------------------------------------- energy / grad ---
+#ifndef MERA_KRYLOV_FLOOR_SCALE
+#define MERA_KRYLOV_FLOOR_SCALE 1.0
+#endif
+// The relative residual a Krylov solve can reach is limited by the rounding
+// of the contractions that apply the superoperator: targets below this floor
+// are raised to it.
+double krylov_floor(int prec) {
+  const double f = prec == MERA_PREC_3XTF32 ? 2e-7 : prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
+  return f * MERA_KRYLOV_FLOOR_SCALE;
+}
+
 void project_tensor(Ctx& c, int i, const double* W, const double* D, double* G, cudaStream_t s) {
   const int64_t n = c.rows[i], p = c.cols[i];
   double* S = P(c.gtmp[0]);
@@ -402,13 +418,15 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
   }
   E.e = forward_energy(c, W, s);
   const int64_t cS = c.dims[L], n3 = opn(c, cS), n = n3 * n3;
-  const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
-  const double tol = std::max(c.cfg.krylov_tol, floor_tol);
+  const double tol = std::max(c.cfg.krylov_tol, krylov_floor(c.cfg.prec));
   double* rhoS = P(c.rho[L]);
   double* hL = P(c.h[L]);
   double* xs = P(c.x);
   const int64_t nr = n * c.rs;  // reals per chi^6 operator
+  // the warm start counts as valid again only once this solve has succeeded
+  // (a solve that throws may leave x partly updated or non-finite)
   if (!c.have_x) copy(xs, hL, nr, s);
+  c.have_x = false;
   auto op_x = [&](const double* v, double* out) {
     copy(out, v, nr, s);
     ascend(c, L, W, v, out, -1.0, s);
@@ -448,13 +466,13 @@ double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
     fill(0.0, rhoS, nr, s);
     add_id(c, 1.0 / (double)n3, rhoS, n3, s);
   }
+  c.have_rho = false;  // set again once the solve below has produced a finite fixed point
   double* bvec = P(c.bvec);
   fill(0.0, bvec, nr, s);
   add_id(c, 1.0 / (double)n3, bvec, n3, s);
   // the residual of a Krylov solve cannot fall below the rounding level of
   // the contractions that apply the superoperator
-  const double floor_tol = c.cfg.prec == MERA_PREC_3XTF32 ? 2e-7 : c.cfg.prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
-  const double tol = std::max(c.cfg.krylov_tol, floor_tol);
+  const double tol = std::max(c.cfg.krylov_tol, krylov_floor(c.cfg.prec));
   auto op_rho = [&](const double* v, double* out) {
     copy(out, v, nr, s);
     descend(c, L, v, out, -1.0, s);
@@ -474,11 +492,11 @@ double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
   if (!(std::fabs(tr) > 0)) throw Error(MERA_ERR_NONFINITE, "fixed point has zero trace");
   scal(1.0 / tr, rhoS, nr, s);
   herm(c, rhoS, n3, s);
-  c.have_rho = true;
   // Tr(h rho) = Re sum_ij h_ij conj(rho_ij): the real dot product of the arrays
   const double e = c.red.dot(P(c.h[L]), rhoS, nr, s);
   check_device_flag(c, s);
   if (!std::isfinite(e)) throw Error(MERA_ERR_NONFINITE, "non-finite energy");
+  c.have_rho = true;
   return e;
 }
 
@@ -668,6 +686,8 @@ void check_isometric(Ctx& c, const double* W, cudaStream_t s) {
     mm(c, 'C', 'N', p, p, n, 1.0, W + c.offs[i], p, W + c.offs[i], p, 0.0, S, p, s);
     add_id(c, -1.0, S, p, s);
     const double r = std::sqrt(c.red.dot(S, S, p * p * c.rs, s));
+    // a NaN or infinite entry of W makes W^dag W - 1 non-finite
+    if (!std::isfinite(r)) throw Error(MERA_ERR_NONFINITE, "tensor " + std::to_string(i) + " has a non-finite entry");
     if (!(r < 1e-10)) throw Error(MERA_ERR_NOT_ISOMETRIC, "tensor " + std::to_string(i) + " has |W^T W - 1| = " + std::to_string(r));
   }
 }
@@ -682,18 +702,20 @@ std::string config_range_error(const mera_config& cfg) {
   if (!(cfg.krylov_tol > 0.0 && cfg.krylov_tol < 1.0)) return "need 0 < krylov_tol < 1";
   if (cfg.krylov_maxiter < 1 || cfg.krylov_dim < 1 || cfg.lbfgs_m < 1) return "need krylov_maxiter, krylov_dim, lbfgs_m >= 1";
   if (cfg.b_chunk < 0) return "need b_chunk >= 0";
+  if (!(cfg.device_wait_s > 0.0 && cfg.device_wait_s <= 60.0)) return "need 0 < device_wait_s <= 60";
   return "";
 }
 
 // The Hamiltonian term (n x n on the device) must be Hermitian: |h - h^dag|
-// at most 1e-10 of its largest entry, else MERA_ERR_ARG.
+// at most 1e-10 of its largest entry, else MERA_ERR_ARG (MERA_ERR_NONFINITE
+// for a NaN or infinite entry).
 void check_hermitian(Ctx& c, const double* dev, int64_t n, cudaStream_t s) {
   std::vector<double> h((size_t)(n * n * c.rs));
   MERA_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
   MERA_CUDA(cudaStreamSynchronize(s));
   double big = 0.0, bad = 0.0;
   for (const double x : h)
-    if (!std::isfinite(x)) throw Error(MERA_ERR_ARG, "the Hamiltonian term is not finite");
+    if (!std::isfinite(x)) throw Error(MERA_ERR_NONFINITE, "the Hamiltonian term is not finite");
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = 0; j < n; ++j) {
       const double* a = h.data() + (i * n + j) * c.rs;

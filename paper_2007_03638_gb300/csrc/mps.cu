@@ -60,6 +60,7 @@ double mps_energy(Ctx& c, const double* A, cudaStream_t s) {
   fill(0.0, bvec, nr, s);
   add_id(c, 1.0 / (double)D, bvec, D, s);
   if (!c.have_rho) copy(rho, bvec, nr, s);
+  c.have_rho = false;  // valid again once the solve below has succeeded
   // (1 - E_R + |b)(1|) rho = b, b = 1/D: the fixed point with Tr rho = 1
   auto op_rho = [&](const double* v, double* out) {
     copy(out, v, nr, s);
@@ -79,6 +80,7 @@ double mps_energy(Ctx& c, const double* A, cudaStream_t s) {
   if (!(std::fabs(tr) > 0)) throw Error(MERA_ERR_NONFINITE, "MPS fixed point has zero trace");
   scal(1.0 / tr, rho, nr, s);
   herm(c, rho, D, s);
+  if (!std::isfinite(tr)) throw Error(MERA_ERR_NONFINITE, "MPS fixed point is not finite");
   c.have_rho = true;
   // B[(a s), (t c)] = A[(a s), b] A[b, (t c)]
   mm(c, 'N', 'N', D * d, d * D, D, 1.0, A, D, A, d * D, 0.0, P(c.mB), d * D, s);
@@ -116,6 +118,7 @@ void mps_energy_grad(Ctx& c, const double* A, Eval& E, cudaStream_t s) {
     copy(Hl, hl, nr, s);
     copy(Hr, hr, nr, s);
   }
+  c.have_x = false;  // valid again once both solves below have succeeded
   // (1 - E_L + |1)(rho|) H_l = h_l: the added term is Tr(rho v) 1
   auto op_l = [&](const double* v, double* out) {
     copy(out, v, nr, s);

@@ -387,9 +387,13 @@ void cg_step(Ctx& c, mera_iter_info* info, cudaStream_t s) {
     precondition(c, En, Wn, y, Py, s);
     beta = (inner(c, y, Pg, s) - 2.0 * inner(c, y, Py, s) * inner(c, d2, P(En.G), s) / dy) / dy;
   }
+  // Hager-Zhang's lower bound -1 / (|d_k| min(eta, |g_k|)): d_k the direction
+  // just searched (transported; the transport is isometric), g_k the gradient
+  // at the point it started from, eta = 0.01
   const double dn = std::sqrt(inner(c, d2, d2, s));
+  const double gn_old = std::sqrt(inner(c, G, G, s));
   const double gn = std::sqrt(inner(c, P(En.G), P(En.G), s));
-  beta = std::max(beta, -1.0 / (dn * std::min(0.01, gn)));
+  beta = std::max(beta, -1.0 / (dn * std::min(0.01, gn_old)));
   // new direction d = -Pg + beta T(d)
   axpby(-1.0, Pg, beta, d2, c.total, s);
   copy(d, d2, c.total, s);

@@ -42,7 +42,7 @@ struct Request {
   cudaStream_t stream = nullptr;
   int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
   bool busy = false;
-  int iters = 0, n_evals = 0, error = 0;
+  int iters = 0, n_evals = 0, error = 0, deferred = 0;
   std::string message;
   double energy = 0.0, gnorm = 0.0;
   clk::time_point t_submit, t_admit, t_done;
@@ -64,6 +64,10 @@ struct mera_server {
   int device = 0;
   std::vector<std::thread> workers;
   int64_t done = 0, failed = 0, submitted = 0;
+  // a request whose creation ran out of device memory while others ran went
+  // back to the head of the queue; nothing is admitted until one of those
+  // finishes (done + failed passes this mark); -1: no such wait
+  int64_t defer_mark = -1;
   clk::time_point t0 = clk::now();
 };
 
@@ -85,6 +89,10 @@ void finish(mera_server* sv, Request& r, int err) {
 
 // Admit queued requests in arrival order while they fit (caller holds mu).
 void admit_locked(mera_server* sv) {
+  if (sv->defer_mark >= 0) {
+    if (sv->done + sv->failed <= sv->defer_mark && !sv->running.empty()) return;
+    sv->defer_mark = -1;
+  }
   while (!sv->queue.empty()) {
     Request& r = *sv->reqs[sv->queue.front()];
     if (sv->in_use + r.bytes > sv->budget && !sv->running.empty()) break;  // wait for memory
@@ -148,6 +156,24 @@ void worker(mera_server* sv) {
     }
     if (err) message = r.m ? mera_last_error(r.m) : "creation failed";
     lk.lock();
+    if (err == MERA_ERR_OOM && !r.m && sv->running.size() > 1) {
+      // the memory the footprint promised is not there (another user, a
+      // bounded allocator): wait for a running request to finish, then retry
+      if (r.stream) cudaStreamDestroy(r.stream);
+      r.stream = nullptr;
+      for (size_t k = 0; k < sv->running.size(); ++k)
+        if (sv->running[k] == r.id) {
+          sv->running.erase(sv->running.begin() + k);
+          break;
+        }
+      sv->in_use -= r.bytes;
+      r.state = 0;
+      r.busy = false;
+      sv->queue.push_front(r.id);
+      sv->defer_mark = sv->done + sv->failed;
+      r.deferred++;
+      continue;
+    }
     if (stepped) {
       r.iters = iters0 + 1;
       r.n_evals += info.n_evals;
@@ -243,6 +269,7 @@ int mera_server_poll(mera_server_t sv, int64_t id, mera_request_status* st) {
   st->t_done = r.state >= 2 ? sec(r.t_done) : -1.0;
   st->bytes = r.bytes;
   std::snprintf(st->message, sizeof(st->message), "%s", r.message.c_str());
+  st->deferred = r.deferred;
   return MERA_OK;
 }
 

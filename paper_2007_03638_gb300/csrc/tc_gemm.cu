@@ -45,11 +45,16 @@ namespace {
 #ifndef MERA_TC_STAGES
 #define MERA_TC_STAGES 3
 #endif
+#ifndef MERA_TC_COMPENSATED
+#define MERA_TC_COMPENSATED 0   // 1: compensated (Kahan) folding of the accumulator groups
+#endif
 
 constexpr int BM = 128;
 constexpr int STAGES = MERA_TC_STAGES;
 constexpr int KB_BYTES = 128;               // K block = one 128-byte swizzle row
-constexpr uint64_t WAIT_NS = 1000000000ull;  // bounded waits: 1 s
+// limit of the waits that drain this CTA's own copies and MMAs after an
+// abort (they complete in microseconds; the limit only bounds a broken case)
+constexpr uint64_t DRAIN_NS = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -75,15 +80,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false on expiry.
+// Wait of at most limit_ns nanoseconds; false on expiry.
 // The timer is read once per 256 polls (try_wait itself suspends the warp
-// for a while before it reports an incomplete phase).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// for a while before it reports an incomplete phase); a limit below the
+// time of 256 polls is checked at the first poll.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
+  const uint32_t every = limit_ns < 100000ull ? 0u : 255u;
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 255u) == 0 && gtimer() - t0 > WAIT_NS) return false;
+    if ((it & every) == 0 && gtimer() - t0 > limit_ns) return false;
   }
 }
 
@@ -144,6 +151,7 @@ struct Smem {
   uint64_t empty[STAGES];
   uint64_t acc_full[NACC];
   uint64_t acc_empty[NACC];
+  uint64_t drain;  // MMA completion after an abort
   uint32_t tmem;
   int abort;
 };
@@ -216,6 +224,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       mbar_init(&S->acc_full[b], 1);
       mbar_init(&S->acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
     }
+    mbar_init(&S->drain, 1);
     S->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -244,7 +253,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
         krange(t, klo, khi);
         for (int kb = klo; kb < khi; ++kb, ++kbg) {
           const int s = (int)(kbg % STAGES);
-          if (kbg >= STAGES && !mbar_wait(&S->empty[s], (uint32_t)((kbg / STAGES) - 1) & 1)) {
+          if (kbg >= STAGES && !mbar_wait(&S->empty[s], (uint32_t)((kbg / STAGES) - 1) & 1, ep.wait_ns)) {
             atomicExch(&S->abort, 1);
             stop = true;
             break;
@@ -274,8 +283,12 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           const bool first = ((kb - klo) % PROMOTE) == 0;
           const bool last = ((kb - klo) % PROMOTE) == PROMOTE - 1 || kb == khi - 1;
           const int b = (int)(gg % NACC);
-          if (!mbar_wait(&S->full[s], (uint32_t)(kbg / STAGES) & 1)) { atomicExch(&S->abort, 1); stop = true; break; }
-          if (first && gg >= NACC && !mbar_wait(&S->acc_empty[b], (uint32_t)((gg / NACC) - 1) & 1)) {
+          if (!mbar_wait(&S->full[s], (uint32_t)(kbg / STAGES) & 1, ep.wait_ns)) {
+            atomicExch(&S->abort, 1);
+            stop = true;
+            break;
+          }
+          if (first && gg >= NACC && !mbar_wait(&S->acc_empty[b], (uint32_t)((gg / NACC) - 1) & 1, ep.wait_ns)) {
             atomicExch(&S->abort, 1);
             stop = true;
             break;
@@ -323,6 +336,14 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       float acc[HC];
 #pragma unroll
       for (int j = 0; j < HC; ++j) acc[j] = 0.f;
+#if MERA_TC_COMPENSATED
+      // Kahan compensation of each column's running sum, kept as BF16 pairs
+      // (a compensation term is below half an ulp of its sum: 8 significant
+      // bits of it leave the compensated sum within 2^-9 ulp per fold)
+      uint32_t cmp[HC / 2];
+#pragma unroll
+      for (int j = 0; j < HC / 2; ++j) cmp[j] = 0u;
+#endif
       if (ep.preload && rvalid) {
         // acc = (beta / alpha) C: loads issued now, their latency hidden by this tile's MMAs
         const float* C = static_cast<const float*>(ep.C);
@@ -361,9 +382,33 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       }
       for (int g = 0; g < gpt; ++g, ++gg) {
         const int b = (int)(gg % NACC);
-        if (!mbar_wait(&S->acc_full[b], (uint32_t)(gg / NACC) & 1)) { ok = false; break; }
+        if (!mbar_wait(&S->acc_full[b], (uint32_t)(gg / NACC) & 1, ep.wait_ns)) { ok = false; break; }
         if (*(volatile int*)&S->abort) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#if MERA_TC_COMPENSATED
+#pragma unroll
+        for (int c0 = 0; c0 < HC; c0 += 16) {
+          uint32_t r[16];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const float2 cf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&cmp[(c0 + j) / 2]));
+            const float y0 = __uint_as_float(r[j]) - cf.x, y1 = __uint_as_float(r[j + 1]) - cf.y;
+            const float t0 = acc[c0 + j] + y0, t1 = acc[c0 + j + 1] + y1;
+            const __nv_bfloat162 cn = __floats2bfloat162_rn((t0 - acc[c0 + j]) - y0, (t1 - acc[c0 + j + 1]) - y1);
+            cmp[(c0 + j) / 2] = *reinterpret_cast<const uint32_t*>(&cn);
+            acc[c0 + j] = t0;
+            acc[c0 + j + 1] = t1;
+          }
+        }
+#else
 #pragma unroll
         for (int c0 = 0; c0 < HC; c0 += 64) {
           // two 32-column loads in flight, one wait
@@ -391,12 +436,21 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
 #pragma unroll
           for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(r[j]);
         }
+#endif
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
       }
       if (!ok) break;
+#if MERA_TC_COMPENSATED
+#pragma unroll
+      for (int j = 0; j < HC; j += 2) {
+        const float2 cf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&cmp[j / 2]));
+        acc[j] -= cf.x;
+        acc[j + 1] -= cf.y;
+      }
+#endif
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0 && !ep.preload;
       void* Cbase = ep.ksplit > 1 ? static_cast<void*>(static_cast<float*>(ep.C) + (t / nt1) * ep.split_stride)
                                   : ep.C;
@@ -528,10 +582,17 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   __syncthreads();
   if (*(volatile int*)&S->abort) {
     if (threadIdx.x == 0) atomicExch(ep.err, 1);
-    // drain this CTA's copies still in flight (at most the last STAGES, bounded waits)
+    // drain this CTA's copies still in flight (at most the last STAGES)
     if (warp == 0 && lane == 0) {
       const int64_t lo = issued_loads > STAGES ? issued_loads - STAGES : 0;
-      for (int64_t kb = lo; kb < issued_loads; ++kb) mbar_wait(&S->full[kb % STAGES], (uint32_t)(kb / STAGES) & 1);
+      for (int64_t kb = lo; kb < issued_loads; ++kb)
+        mbar_wait(&S->full[kb % STAGES], (uint32_t)(kb / STAGES) & 1, DRAIN_NS);
+    }
+    // and the MMAs it issued: a commit tracks every earlier tcgen05 operation
+    // of the issuing thread, so tensor memory is freed only after they finish
+    if (warp == 1 && lane == 0) {
+      mma_commit(&S->drain);
+      mbar_wait(&S->drain, 0, DRAIN_NS);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -30,6 +30,7 @@ struct TcEpilogue {
   int preload = 0;
   float bscale = 0.f;  // beta / alpha (exact: alpha is a power of two)
   int* err = nullptr;  // set to 1 by a CTA whose bounded wait expired
+  uint64_t wait_ns = 1000000000ull;  // limit of each pipeline wait (default 1 s)
   // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
   // writing a plain row-major partial at C + s * split_stride
   int ksplit = 1, kbs = 0;

@@ -577,6 +577,7 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   ep.rows = g.c_rows;
   ep.vec = g.c_vec;
   ep.err = ex.err;
+  ep.wait_ns = ex.wait_ns;
   pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
   const int path = tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (pr) {

@@ -163,6 +163,7 @@ struct Exec {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int* err = nullptr;  // device flag set by an expired bounded wait
+  uint64_t wait_ns = 1000000000ull;  // limit of each tensor-core pipeline wait
   // two slots for packed operands that stay the same over a loop of products
   // (the loop-invariant factor of the sliced chain): packed once, reused
   void* keep[2] = {nullptr, nullptr};

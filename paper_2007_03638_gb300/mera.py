@@ -38,7 +38,7 @@ class Config(C.Structure):
                 ("prec", C.c_int), ("w_stiefel", C.c_int), ("precond", C.c_int),
                 ("krylov_dim", C.c_int), ("krylov_maxiter", C.c_int), ("krylov_tol", C.c_double),
                 ("recompute_env", C.c_int), ("lbfgs_m", C.c_int), ("b_chunk", C.c_int), ("network", C.c_int),
-                ("z2", C.c_int)]
+                ("z2", C.c_int), ("device_wait_s", C.c_double)]
 
 
 class IterInfo(C.Structure):
@@ -57,7 +57,47 @@ class RequestStatus(C.Structure):
     _fields_ = [("state", C.c_int), ("error", C.c_int), ("iters", C.c_int), ("n_evals", C.c_int),
                 ("energy", C.c_double), ("gnorm", C.c_double), ("t_submit", C.c_double),
                 ("t_admit", C.c_double), ("t_done", C.c_double), ("bytes", C.c_size_t),
-                ("message", C.c_char * 160)]
+                ("message", C.c_char * 160), ("deferred", C.c_int)]
+
+
+# device allocator callbacks of mera_set_allocator
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_allocator_refs = None  # the installed callbacks, kept alive while installed
+
+
+def set_allocator(alloc=None, free=None):
+    """Route every device buffer the library allocates through alloc(nbytes)
+    -> int device pointer (0 when it cannot) and free(ptr) (see
+    mera_set_allocator in mera.h); set_allocator() restores cudaMalloc.
+    The callbacks run on whichever thread allocates, with the GIL taken."""
+    global _allocator_refs
+    L = load()
+    if alloc is None:
+        rc = L.mera_set_allocator(C.cast(None, ALLOC_FN), C.cast(None, FREE_FN), None)
+        _allocator_refs = None
+    else:
+        a = ALLOC_FN(lambda n, user: alloc(int(n)) or None)
+        f = FREE_FN(lambda p, user: free(int(p)))
+        rc = L.mera_set_allocator(a, f, None)
+        _allocator_refs = (a, f)
+    if rc != 0:
+        raise MeraError(rc, L.mera_strerror(rc).decode())
+
+
+def use_torch_allocator():
+    """Route the library's device memory through PyTorch's caching allocator
+    on the current device (its memory then shows in torch.cuda's statistics
+    and is reused across objects)."""
+    import torch
+    dev = torch.cuda.current_device()
+
+    def alloc(n):
+        try:
+            return torch.cuda.caching_allocator_alloc(n, device=dev)
+        except RuntimeError:  # out of memory: the library reports MERA_ERR_OOM
+            return 0
+    set_allocator(alloc, lambda p: torch.cuda.caching_allocator_delete(p))
 
 
 class SolveOpts(C.Structure):
@@ -74,7 +114,8 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_project", "mera_inner", "mera_transport", "mera_retract", "mera_precondition",
            "mera_lbfgs_step", "mera_cg_step", "mera_gd_step", "mera_ev_sweep", "mera_solve", "mera_footprint_bytes",
            "mera_launch_count", "mera_get_stats", "mera_profile", "mera_profile_dump", "mera_dots_noalloc",
-           "mera_gemm", "mera_strerror", "mera_last_error", "mera_server_create",
+           "mera_gemm", "mera_strerror", "mera_last_error", "mera_server_create", "mera_set_device_wait",
+           "mera_set_allocator",
            "mera_server_submit", "mera_server_poll", "mera_server_wait", "mera_server_destroy"]
 
 _lib = None
@@ -125,6 +166,8 @@ def load(path: str = LIB_PATH):
         "mera_server_poll": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(RequestStatus)]),
         "mera_server_wait": (C.c_int, [C.c_void_p, C.c_double]),
         "mera_server_destroy": (C.c_int, [C.c_void_p]),
+        "mera_set_device_wait": (C.c_int, [C.c_void_p, C.c_double]),
+        "mera_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
         "mera_strerror": (C.c_char_p, [C.c_int]),
         "mera_last_error": (C.c_char_p, [C.c_void_p]),
     }
@@ -286,6 +329,10 @@ class Mera:
         self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype),
                                             _ptrs(D, keep, self.dtype) if deriv else None))
         return (e.value, G, D) if deriv else (e.value, G)
+
+    def set_device_wait(self, seconds):
+        """Limit of each tensor-core pipeline wait (mera_set_device_wait)."""
+        self._check(self.L.mera_set_device_wait(self.h, float(seconds)))
 
     def energy_grad_into(self, G):
         """Energy, with the gradient written into the given arrays (host or device)."""

@@ -149,7 +149,8 @@ def test_create_refuses_configs_out_of_range(lib):
     h = np.zeros((64, 64))
     bad = [dict(precond=2), dict(krylov_tol=0.0), dict(krylov_tol=float("nan")), dict(krylov_tol=1.5),
            dict(krylov_maxiter=0), dict(krylov_dim=0), dict(lbfgs_m=0), dict(b_chunk=-1), dict(w_stiefel=3),
-           dict(recompute_env=-1), dict(network=7), dict(dtype=5), dict(prec=9), dict(z2=3)]
+           dict(recompute_env=-1), dict(network=7), dict(dtype=5), dict(prec=9), dict(z2=3),
+           dict(device_wait_s=0.0), dict(device_wait_s=61.0), dict(device_wait_s=float("nan"))]
     for kw in bad:
         cfg = gm.default_config(4, 8, 3, **kw)
         handle = C.c_void_p()
@@ -157,3 +158,32 @@ def test_create_refuses_configs_out_of_range(lib):
         assert rc == -1 and not handle.value, kw
         if "network" not in kw:
             assert gm.footprint_bytes(cfg) == 0, kw
+
+
+def test_allocator_hook_arguments(lib):
+    """mera_set_allocator needs a deallocator with an allocator; NULL
+    restores the CUDA allocator (host-side bookkeeping only)."""
+    from paper_2007_03638_gb300 import mera as gm
+    a = gm.ALLOC_FN(lambda n, user: None)
+    assert lib.mera_set_allocator(a, gm.C.cast(None, gm.FREE_FN), None) == -1
+    assert lib.mera_set_allocator(gm.C.cast(None, gm.ALLOC_FN), gm.C.cast(None, gm.FREE_FN), None) == 0
+    gm.set_allocator(lambda n: 0, lambda p: None)
+    gm.set_allocator()
+
+
+def test_dots_noalloc_wrapper_checks_sizes(lib):
+    """The binding refuses arrays shorter than the sizes it passes on, before
+    any call into the library."""
+    import numpy as np
+    import pytest
+
+    from paper_2007_03638_gb300 import mera as gm
+    x, y = np.zeros(20), np.zeros(8)
+    with pytest.raises(ValueError):
+        gm.dots_noalloc(x, y, 3, 8, 8, np.zeros(3))      # X needs 2 * 8 + 8 = 24
+    with pytest.raises(ValueError):
+        gm.dots_noalloc(np.zeros(24), y, 3, 8, 8, np.zeros(2))  # out needs 3
+    with pytest.raises(ValueError):
+        gm.dots_noalloc(np.zeros(24), np.zeros(7), 3, 8, 8, np.zeros(3))
+    with pytest.raises(TypeError):
+        gm.dots_noalloc(np.zeros(24, dtype=np.complex128), y, 3, 8, 8, np.zeros(3))

@@ -164,6 +164,25 @@ def test_lbfgs_matches_oracle_trajectory(gm):
         assert np.abs(t.T @ t - np.eye(t.shape[1])).max() < 1e-13
 
 
+@pytest.mark.parametrize("kind,seed", [("ising", 0), ("xxz", 2)])
+def test_cg_matches_oracle_trajectory(gm, kind, seed):
+    """Config-1 shapes: the first nonlinear-CG iterations (preconditioned
+    Hager-Zhang beta with its eta bound, Sec. 3) follow the oracle's energies
+    and gradient norms (same starting point, same algorithm)."""
+    us, ws = inp.random_mera(4, 4, 2, seed=seed)
+    h3 = _ham(4, kind)
+    m = gm.Mera(gm.default_config(4, 4, 2), h3)
+    m.set_tensors(_flat(us, ws))
+    got = [m.cg_step() for _ in range(8)]
+    prob = oo.MeraProblem(h3)
+    _, _, hist = oo.cg(prob, _flat(us, ws), maxiter=9)
+    for g, r in zip(got, hist[1:9]):
+        assert abs(g["energy"] - r["energy"]) < 1e-9 * abs(r["energy"]), (g, r)
+        assert abs(g["gnorm"] - r["gnorm"]) < 1e-6 * r["gnorm"], (g, r)
+    for t in m.get_tensors():
+        assert np.abs(t.T @ t - np.eye(t.shape[1])).max() < 1e-13
+
+
 def test_cg_decreases(gm):
     us, ws = inp.random_mera(4, 4, 2, seed=2)
     m = gm.Mera(gm.default_config(4, 4, 2), _ham(4, "xxz"))

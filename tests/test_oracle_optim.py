@@ -137,3 +137,50 @@ def test_mera_gd_short_run():
     es = [h["energy"] for h in hist]
     assert all(b <= a + 1e-14 for a, b in zip(es, es[1:]))
     assert e / 2 > inp.EXACT_ISING_CRITICAL
+
+
+def test_hz_beta_with_exact_steps_gives_conjugate_directions():
+    """On a strictly convex quadratic with exact line searches <d, g'> = 0, so
+    the Hager-Zhang coefficient reduces to Hestenes-Stiefel's and nonlinear CG
+    is linear CG: successive directions are A-conjugate and the minimiser is
+    reached in n steps (textbook; Nocedal-Wright Thm. 5.2/5.3).  The bound
+    does not act here (beta > 0)."""
+    rng = np.random.default_rng(4)
+    n = 7
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    A = Q @ np.diag(np.linspace(1.0, 9.0, n)) @ Q.T
+    b = rng.standard_normal(n)
+    inner = lambda u, v: float(np.dot(u, v))  # noqa: E731
+    x = np.zeros(n)
+    g = A @ x - b
+    d = -g
+    dirs = []
+    for _ in range(n):
+        alpha = -inner(g, d) / inner(d, A @ d)
+        x = x + alpha * d
+        g2 = A @ x - b
+        dirs.append(d)
+        if np.linalg.norm(g2) < 1e-13:
+            break
+        y = g2 - g
+        beta = oo.hz_beta(inner, y, g2, y, d, g2, np.linalg.norm(g))
+        assert beta > 0
+        d = -g2 + beta * d
+        g = g2
+    assert np.linalg.norm(A @ x - b) < 1e-10
+    for i in range(len(dirs)):
+        for j in range(i):
+            assert abs(dirs[i] @ A @ dirs[j]) < 1e-10 * np.linalg.norm(dirs[i]) * np.linalg.norm(dirs[j])
+
+
+def test_hz_beta_bound_uses_the_previous_gradient():
+    """The lower bound -1/(|d| min(eta, |g|)) acts when beta is very negative;
+    it takes |g| of the point the direction started from."""
+    inner = lambda u, v: float(np.dot(u, v))  # noqa: E731
+    d = np.array([1.0, 0.0])
+    y = np.array([1e-3, -1.0])   # <d, y> = 1e-3, <y, g'> = -5: beta = -5000
+    g2 = np.array([0.0, 5.0])
+    b = oo.hz_beta(inner, y, g2, y, d, g2, gnorm_old=0.004, eta=0.01)
+    assert b == pytest.approx(-1.0 / (1.0 * 0.004))
+    b = oo.hz_beta(inner, y, g2, y, d, g2, gnorm_old=2.0, eta=0.01)
+    assert b == pytest.approx(-1.0 / (1.0 * 0.01))
