@@ -39,7 +39,7 @@ from paper_2007_03638_gb300 import inputs as inp  # noqa: E402
 
 WORKLOADS = {
     # name: (hamiltonian, d_b, chi, n_trans, prec, extra config)
-    # prec: 0 FP64, 1 3xTF32, 2 split-BF16
+    # prec: 0 FP64, 1 3xTF32, 2 split-BF16, 3 scaled split-FP16
     "ising_chi4_L2_fp64": ("ising", 4, 4, 2, 0, {}),
     "ising_chi8_L3_fp64": ("ising", 4, 8, 3, 0, {}),
     "ising_chi12_L3_fp64": ("ising", 4, 12, 3, 0, {}),
@@ -51,6 +51,10 @@ WORKLOADS = {
     "xxz_chi24_L3_bf16": ("xxz", 4, 24, 3, 2, {"lbfgs_m": 16}),
     "xxz_chi32_L3_3xtf32": ("xxz", 4, 32, 3, 1, {"lbfgs_m": 16, "krylov_dim": 4}),
     "xxz_chi32_L3_bf16": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4}),
+    "xxz_chi32_L3_fp16": ("xxz", 4, 32, 3, 3, {"lbfgs_m": 16, "krylov_dim": 4}),
+    "xxz_chi24_L3_fp16": ("xxz", 4, 24, 3, 3, {"lbfgs_m": 16}),
+    "xxz_chi16_L3_fp16": ("xxz", 4, 16, 3, 3, {"lbfgs_m": 16}),
+    "ising_chi12_L3_fp16": ("ising", 4, 12, 3, 3, {}),
     # the same with environment recomputation (one set of intermediates for all layers)
     "xxz_chi32_L3_bf16_recompute": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4, "recompute_env": 1}),
     # extra config fields: network 1 = ternary, 2 = uniform MPS (chi = bond
@@ -76,9 +80,11 @@ DEFAULT_WORKLOAD = "xxz_chi32_L3_bf16"
 # to express the reference arm's bounded sample in gradient evaluations.
 FLOPS_PER_GRAD = {
     "xxz_chi32_L3_bf16": 4.1e15, "xxz_chi32_L3_3xtf32": 4.1e15, "xxz_chi32_L3_bf16_recompute": 4.1e15,
-    "xxz_chi24_L3_3xtf32": 4.7e14, "xxz_chi24_L3_bf16": 4.7e14,
-    "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13,
+    "xxz_chi32_L3_fp16": 4.1e15,
+    "xxz_chi24_L3_3xtf32": 4.7e14, "xxz_chi24_L3_bf16": 4.7e14, "xxz_chi24_L3_fp16": 4.7e14,
+    "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13, "xxz_chi16_L3_fp16": 1.2e13,
     "ising_chi12_L3_fp64": 1.6e12, "ising_chi12_L3_3xtf32": 1.13e12, "ising_chi12_L3_bf16": 1.13e12,
+    "ising_chi12_L3_fp16": 1.13e12,
     "ising_chi8_L3_fp64": 5e10, "ising_chi4_L2_fp64": 1.2e8,
     # complex workloads: 4 x the real workload's (8 real flops per complex
     # multiply-add), an estimate until measured
@@ -104,7 +110,9 @@ def tensor_peaks():
     except (OSError, KeyError, ValueError):
         bf16 = 1.9e15
         src = "fallback bf16 1.9 PFLOP/s"
-    return {2: (bf16, src), 1: (bf16 * 1.1 / 2.25, src + " x nominal tf32/bf16 ratio 1.1/2.25")}
+    # FP16 products (kind::f16) run at the BF16 rate
+    return {2: (bf16, src), 3: (bf16, src + " (fp16 = bf16 rate)"),
+            1: (bf16 * 1.1 / 2.25, src + " x nominal tf32/bf16 ratio 1.1/2.25")}
 
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture of the
@@ -507,7 +515,7 @@ def main():
             "gett_c128_kernel" if cplx else "gett_f64_kernel", "alu"
     else:
         peak, psrc = tensor_peaks()[prec]
-        kname, bound = "tc_gemm_kernel (%s)" % ("3xTF32" if prec == 1 else "split-BF16"), "tensor"
+        kname, bound = "tc_gemm_kernel (%s)" % {1: "3xTF32", 2: "split-BF16", 3: "split-FP16"}[prec], "tensor"
     roof = {"bound": bound, "kernel": kname, "achieved": achieved / 1e12 if achieved else None,
             "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak if achieved else None,
@@ -520,10 +528,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": ("complex " if cplx else "") + ["f64", "tf32x3+f32acc (f64 Krylov/geometry)",
-                                                     "bf16x3+f32acc (f64 Krylov/geometry)"][prec],
+                                                     "bf16x3+f32acc (f64 Krylov/geometry)",
+                                                     "fp16x3 scaled+f32acc (f64 Krylov/geometry)"][prec],
             "data": "synthetic",
             "config": {"workload": args.workload, "hamiltonian": kind, "d_b": d_b, "chi": chi,
-                       "n_trans": L, "prec": ["fp64", "3xtf32", "split_bf16"][prec],
+                       "n_trans": L, "prec": ["fp64", "3xtf32", "split_bf16", "split_fp16"][prec],
                        "network": ["binary", "ternary", "mps"][net], "z2": bool(extra.get("z2", 0)),
                        "element": "complex128" if cplx else "float64",
                        "step": "one L-BFGS iteration (m=%d)" % extra.get("lbfgs_m", 8), "l2": "flushed (256 MiB write) between steps",

@@ -85,8 +85,18 @@ typedef enum { MERA_F64 = 0, MERA_C128 = 1 } mera_dtype;
 /* Arithmetic of the bulk contractions (ascending/descending maps and
  * environments).  FP64 keeps everything in double; the mixed modes run the
  * contractions on tensor cores with FP32 accumulation and keep the Krylov
- * solves, reductions, geometry and line search in FP64. */
-typedef enum { MERA_PREC_FP64 = 0, MERA_PREC_3XTF32 = 1, MERA_PREC_SPLIT_BF16 = 2 } mera_prec;
+ * solves, reductions, geometry and line search in FP64.  Each operand x is
+ * split into a high and a low plane, x = hi + lo, and a product takes
+ * hi*hi + hi*lo + lo*hi:
+ *   MERA_PREC_3XTF32      TF32 planes (about 22 significant bits), kind::tf32;
+ *   MERA_PREC_SPLIT_BF16  BF16 planes (about 16 bits), kind::f16 at twice the
+ *                         TF32 rate;
+ *   MERA_PREC_SPLIT_FP16  FP16 planes of the operand scaled by a power of two
+ *                         chosen from its largest entry (about 22 bits, as
+ *                         3xTF32, at the BF16 rate); the scale is divided out
+ *                         exactly when the product is stored. */
+typedef enum { MERA_PREC_FP64 = 0, MERA_PREC_3XTF32 = 1, MERA_PREC_SPLIT_BF16 = 2,
+               MERA_PREC_SPLIT_FP16 = 3 } mera_prec;
 
 typedef struct {
     int d_b;           /* bottom site dimension (4: two spins blocked)        */
@@ -385,8 +395,8 @@ int mera_server_destroy(mera_server_t sv);
 
 /* C = A B for row-major double matrices A (M x K), B (K x N), C (M x N) on
  * the device, with the contraction arithmetic of the given mera_prec:
- * FP64 (the FP64 contraction kernel) or the tensor-core kernel with 3xTF32 /
- * split-BF16 operands and FP32 accumulation.  Exposes the arithmetic of each
+ * FP64 (the FP64 contraction kernel) or the tensor-core kernel with 3xTF32,
+ * split-BF16 or scaled split-FP16 operands and FP32 accumulation.  Exposes the arithmetic of each
  * mode for checking (Sec. 4 contractions are built from this product);
  * allocates its temporary operand planes.  MERA_ERR_DEVICE_TIMEOUT if a
  * bounded device-side wait expired. */

@@ -370,7 +370,7 @@ size_t footprint_net(const mera_config* cfg) {
 size_t mera_footprint_bytes(const mera_config* cfg) {
   if (!cfg || !mera::config_range_error(*cfg).empty()) return 0;
   if (cfg->dtype != MERA_F64 && cfg->dtype != MERA_C128) return 0;
-  if (cfg->prec != MERA_PREC_FP64 && cfg->prec != MERA_PREC_3XTF32 && cfg->prec != MERA_PREC_SPLIT_BF16) return 0;
+  if (cfg->prec < MERA_PREC_FP64 || cfg->prec > MERA_PREC_SPLIT_FP16) return 0;
   if (cfg->z2 != 0 && (cfg->z2 != 1 || cfg->network == MERA_MPS)) return 0;
   if (cfg->network == MERA_MPS) return footprint_mps(cfg);
   if (cfg->d_b < 2 || cfg->chi < 2 || cfg->n_trans < 1) return 0;
@@ -530,18 +530,24 @@ int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const 
       MERA_CUDA(cudaStreamSynchronize(s));
       return;
     }
-    if (prec != MERA_PREC_3XTF32 && prec != MERA_PREC_SPLIT_BF16) throw Error(MERA_ERR_ARG, "bad precision");
-    const int kind = prec == MERA_PREC_3XTF32 ? mera::tc::KIND_TF32 : mera::tc::KIND_BF16;
-    const int elem = kind == mera::tc::KIND_TF32 ? 4 : 2;
+    if (prec != MERA_PREC_3XTF32 && prec != MERA_PREC_SPLIT_BF16 && prec != MERA_PREC_SPLIT_FP16)
+      throw Error(MERA_ERR_ARG, "bad precision");
+    const int kind = mera::tc::kind_of_prec(prec);
+    const int elem = mera::tc::kind_elem(kind);
     const int64_t Kp = mera::tc::padded_k(K, kind);
     const int64_t Mp = mera::tc::round_up(std::max<int64_t>(M, 1), 128), Np = mera::tc::round_up(std::max<int64_t>(N, 1), 128);
     mera::DevBuf ah(elem * Mp * Kp), al(elem * Mp * Kp), bh(elem * Np * Kp), bl(elem * Np * Kp), err(sizeof(int));
     const size_t skb = mera::tc::splitk_bytes(M, N, Kp, kind);
-    mera::DevBuf part(skb);
+    mera::DevBuf part(skb), amax(2 * sizeof(unsigned));
+    unsigned* am = amax.as<unsigned>();
     MERA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    mera::tc::pack_split(A, true, nullptr, K, nullptr, 1, M, K, Mp, Kp, kind, ah.p, al.p, false, s);
-    mera::tc::pack_split(B, true, nullptr, 1, nullptr, N, N, K, Np, Kp, kind, bh.p, bl.p, true, s);
+    mera::tc::pack_split(A, true, nullptr, K, nullptr, 1, M, K, Mp, Kp, kind, ah.p, al.p, false, s, am);
+    mera::tc::pack_split(B, true, nullptr, 1, nullptr, N, N, K, Np, Kp, kind, bh.p, bl.p, true, s, am + 1);
     mera::tc::TcEpilogue ep;
+    if (kind == mera::tc::KIND_F16) {
+      ep.a_amax = am;
+      ep.b_amax = am + 1;
+    }
     ep.C = C;
     ep.c_f64 = 1;
     ep.cms = N;

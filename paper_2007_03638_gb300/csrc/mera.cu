@@ -388,7 +388,9 @@ int gmres(Ctx& c, const std::function<void(const double*, double*)>& op, const d
 // of the contractions that apply the superoperator: targets below this floor
 // are raised to it.
 double krylov_floor(int prec) {
-  const double f = prec == MERA_PREC_3XTF32 ? 2e-7 : prec == MERA_PREC_SPLIT_BF16 ? 2e-5 : 0.0;
+  const double f = prec == MERA_PREC_3XTF32 || prec == MERA_PREC_SPLIT_FP16 ? 2e-7
+                   : prec == MERA_PREC_SPLIT_BF16                         ? 2e-5
+                                                                          : 0.0;
   return f * MERA_KRYLOV_FLOOR_SCALE;
 }
 
@@ -796,7 +798,7 @@ void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s) {
   if (cfg.dtype != MERA_F64 && cfg.dtype != MERA_C128) throw Error(MERA_ERR_ARG, "unknown dtype");
   c.cplx = cfg.dtype == MERA_C128;
   c.rs = c.cplx ? 2 : 1;
-  if (cfg.prec != MERA_PREC_FP64 && cfg.prec != MERA_PREC_3XTF32 && cfg.prec != MERA_PREC_SPLIT_BF16)
+  if (cfg.prec < MERA_PREC_FP64 || cfg.prec > MERA_PREC_SPLIT_FP16)
     throw Error(MERA_ERR_ARG, "unknown precision mode");
   if (cfg.network != MERA_BINARY && cfg.network != MERA_TERNARY && cfg.network != MERA_MPS)
     throw Error(MERA_ERR_ARG, "unknown network");

@@ -42,6 +42,9 @@ namespace {
 #ifndef MERA_TC_PROMOTE_BF16
 #define MERA_TC_PROMOTE_BF16 2
 #endif
+#ifndef MERA_TC_PROMOTE_F16
+#define MERA_TC_PROMOTE_F16 1
+#endif
 #ifndef MERA_TC_STAGES
 #define MERA_TC_STAGES 3
 #endif
@@ -135,11 +138,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 // Instruction descriptor: FP32 accumulator, K-major A and B, M=128, N=BN.
+// Operand format: TF32 = 2 (kind::tf32); BF16 = 1, F16 = 0 (kind::f16).
+template <int KIND>
+__host__ __device__ constexpr uint32_t operand_format() {
+  return KIND == KIND_TF32 ? 2u : (KIND == KIND_BF16 ? 1u : 0u);
+}
 template <int KIND, int BN>
 __host__ __device__ constexpr uint32_t idesc() {
   return (1u << 4)                                   // D format: F32
-         | ((KIND == KIND_TF32 ? 2u : 1u) << 7)      // A format: TF32 / BF16
-         | ((KIND == KIND_TF32 ? 2u : 1u) << 10)     // B format
+         | (operand_format<KIND>() << 7)             // A format
+         | (operand_format<KIND>() << 10)            // B format
          | ((uint32_t)(BN >> 3) << 17)               // N / 8
          | ((uint32_t)(BM >> 4) << 24);              // M / 16
 }
@@ -187,7 +195,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   // K blocks accumulated in one tensor-memory buffer before it is folded:
   // one for TF32 (the truncation error then stays near FP32 level), two for
   // BF16 (its split error, ~1e-5, dominates the truncation of 128 products)
-  constexpr int PROMOTE = KIND == KIND_TF32 ? MERA_TC_PROMOTE_TF32 : MERA_TC_PROMOTE_BF16;
+  constexpr int PROMOTE =
+      KIND == KIND_TF32 ? MERA_TC_PROMOTE_TF32 : (KIND == KIND_BF16 ? MERA_TC_PROMOTE_BF16 : MERA_TC_PROMOTE_F16);
   constexpr int HC = BN / 2;               // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -322,6 +331,15 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
     float* stg = staging + (warp - 2) * 32 * (STG + 1);
     int64_t gg = 0;
     bool ok = true;
+    // FP16 planes hold 2^(e_A + e_B) times the operands' product: the store
+    // divides by that power of two (exact), the preload multiplies by it
+    double alpha_eff = ep.alpha;
+    float bscale = ep.bscale;
+    if (ep.a_amax) {
+      const int k = f16_scale_exp(*ep.a_amax) + f16_scale_exp(*ep.b_amax);
+      alpha_eff = ldexp(ep.alpha, -k);
+      bscale = (float)ldexp((double)ep.bscale, k);
+    }
     for (int64_t t = cid; t < ntiles && ok; t += ncl) {
       int64_t m0, n0;
       tile_of(t % nt1, m0, n0);
@@ -351,7 +369,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
 #pragma unroll
           for (int j = 0; j < HC; ++j) {
             const int64_t n = nbase + j;
-            if (n < ep.N) acc[j] = ep.bscale * C[my_off + (ep.cn ? ep.cn[n] : n * ep.cns)];
+            if (n < ep.N) acc[j] = bscale * C[my_off + (ep.cn ? ep.cn[n] : n * ep.cns)];
           }
         } else if (ep.mode == 2) {
 #pragma unroll
@@ -365,7 +383,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
                            "=f"(o[7])
                          : "l"(p));
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[8 * c + j] = ep.bscale * o[j];
+            for (int j = 0; j < 8; ++j) acc[8 * c + j] = bscale * o[j];
           }
         } else {
 #pragma unroll
@@ -373,10 +391,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
             const int64_t n = nbase + 4 * c;
             if (n >= ep.N) continue;
             const float4 o = *reinterpret_cast<const float4*>(C + my_off + (ep.cn ? ep.cn[n] : n));
-            acc[4 * c] = ep.bscale * o.x;
-            acc[4 * c + 1] = ep.bscale * o.y;
-            acc[4 * c + 2] = ep.bscale * o.z;
-            acc[4 * c + 3] = ep.bscale * o.w;
+            acc[4 * c] = bscale * o.x;
+            acc[4 * c + 1] = bscale * o.y;
+            acc[4 * c + 2] = bscale * o.z;
+            acc[4 * c + 3] = bscale * o.w;
           }
         }
       }
@@ -454,8 +472,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0 && !ep.preload;
       void* Cbase = ep.ksplit > 1 ? static_cast<void*>(static_cast<float*>(ep.C) + (t / nt1) * ep.split_stride)
                                   : ep.C;
-      const double alpha = ep.alpha, beta = ep.beta;
-      const float alpha_f = (float)ep.alpha, beta_f = (float)ep.beta;
+      const double alpha = alpha_eff, beta = ep.beta;
+      const float alpha_f = (float)alpha_eff, beta_f = (float)ep.beta;
       if (ep.mode == 1) {
         // lanes = 32 consecutive rows = 32 consecutive elements: one
         // coalesced 128-byte (float) store per column, no transpose
@@ -610,11 +628,33 @@ __device__ __forceinline__ float tf32_round(float x) {
 }
 
 // Split 8 consecutive values of one plane row into hi/lo and write them as
-// one 16-byte (BF16) or 32-byte (TF32) piece per plane; i = row * Kp + k,
-// k a multiple of 8.
+// one 16-byte (BF16, FP16) or 32-byte (TF32) piece per plane; i = row * Kp + k,
+// k a multiple of 8.  FP16: the values are multiplied by 2^e first (exact).
 template <int KIND, typename T>
-__device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo, int64_t i) {
-  if (KIND == KIND_TF32) {
+__device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo, int64_t i, int e) {
+  if (KIND == KIND_F16) {
+    uint32_t h2[4], l2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __half hh[2], ll[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (sizeof(T) == 8) {
+          const double y = ldexp((double)v[2 * j + t], e);
+          hh[t] = __double2half(y);
+          ll[t] = __double2half(y - (double)__half2float(hh[t]));
+        } else {
+          const float y = ldexpf((float)v[2 * j + t], e);
+          hh[t] = __float2half_rn(y);
+          ll[t] = __float2half_rn(y - __half2float(hh[t]));
+        }
+      }
+      h2[j] = (uint32_t)__half_as_ushort(hh[0]) | ((uint32_t)__half_as_ushort(hh[1]) << 16);
+      l2[j] = (uint32_t)__half_as_ushort(ll[0]) | ((uint32_t)__half_as_ushort(ll[1]) << 16);
+    }
+    *reinterpret_cast<uint4*>(static_cast<__half*>(hi) + i) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+    *reinterpret_cast<uint4*>(static_cast<__half*>(lo) + i) = make_uint4(l2[0], l2[1], l2[2], l2[3]);
+  } else if (KIND == KIND_TF32) {
     float h[8], l[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -650,10 +690,11 @@ __device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo
 template <typename Src, int KIND>
 __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt, int64_t rs,
                                   const int64_t* __restrict__ kt, int64_t ks, int64_t R, int64_t K,
-                                  int64_t Rp, int64_t Kp, void* hi, void* lo) {
+                                  int64_t Rp, int64_t Kp, void* hi, void* lo, const unsigned* amax) {
   const int64_t r = (int64_t)blockIdx.x * 8 + threadIdx.y;
   const int64_t k0 = ((int64_t)blockIdx.y * 32 + threadIdx.x) * 8;
   if (r >= Rp || k0 >= Kp) return;
+  const int e = KIND == KIND_F16 ? f16_scale_exp(*amax) : 0;
   Src v[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = (Src)0;
@@ -680,7 +721,7 @@ __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __
       }
     }
   }
-  store_split8<KIND>(v, hi, lo, r * Kp + k0);
+  store_split8<KIND>(v, hi, lo, r * Kp + k0, e);
 }
 
 // Same packing through a 64 x 64 shared-memory tile, for sources whose
@@ -689,7 +730,8 @@ __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __
 template <typename Src, int KIND>
 __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt,
                                         int64_t rs, const int64_t* __restrict__ kt, int64_t ks, int64_t R,
-                                        int64_t K, int64_t Rp, int64_t Kp, void* hi, void* lo) {
+                                        int64_t K, int64_t Rp, int64_t Kp, void* hi, void* lo,
+                                        const unsigned* amax) {
   __shared__ Src tile[64][65];  // [k][r]
   __shared__ int64_t roffs[64];
   const int t = threadIdx.x;
@@ -712,6 +754,7 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
   const int rl = t >> 2, kc = (t & 3) * 16;
   const int64_t r = r0 + rl;
   if (r >= Rp) return;
+  const int e = KIND == KIND_F16 ? f16_scale_exp(*amax) : 0;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int64_t k = k0 + kc + 8 * h;
@@ -719,7 +762,40 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
     Src v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = tile[kc + 8 * h + j][rl];
-    store_split8<KIND>(v, hi, lo, r * Kp + k);
+    store_split8<KIND>(v, hi, lo, r * Kp + k, e);
+  }
+}
+
+// max |src| over the view r < R, k < K (offsets as in the packing), as float
+// bits into *amax (which starts at 0): non-negative floats order like their
+// bit patterns, so an unsigned atomicMax of the bits is a float maximum; a
+// NaN entry (bits above every finite value) makes the maximum NaN.  Threads
+// run along the source's stride-1 index (k, or r when rows_fast).
+template <typename Src>
+__global__ void amax_kernel(const Src* __restrict__ src, const int64_t* __restrict__ rt, int64_t rs,
+                            const int64_t* __restrict__ kt, int64_t ks, int64_t R, int64_t K, int rows_fast,
+                            unsigned* amax) {
+  __shared__ unsigned wmax[8];
+  unsigned m = 0u;
+  const int64_t F = rows_fast ? R : K, S = rows_fast ? K : R;
+  for (int64_t j = blockIdx.y; j < S; j += gridDim.y) {
+    const int64_t so = rows_fast ? (kt ? kt[j] : j * ks) : (rt ? rt[j] : j * rs);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t fo = rows_fast ? (rt ? rt[i] : i * rs) : (kt ? kt[i] : i * ks);
+      const unsigned b = __float_as_uint(fabsf((float)src[so + fo]));
+      m = b > m ? b : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wmax[w] > m ? wmax[w] : m;
+    if (m) atomicMax(amax, m);
   }
 }
 
@@ -727,6 +803,8 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit, int64_t M, int64_t N,
                                      TcEpilogue ep) {
   const int64_t total = M * N;
+  const double alpha = ep.a_amax ? ldexp(ep.alpha, -(f16_scale_exp(*ep.a_amax) + f16_scale_exp(*ep.b_amax)))
+                                 : ep.alpha;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
@@ -735,11 +813,11 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit,
     const int64_t idx = (ep.cm ? ep.cm[m] : m * ep.cms) + (ep.cn ? ep.cn[n] : n * ep.cns);
     if (ep.c_f64) {
       double* C = static_cast<double*>(ep.C);
-      const double v = ep.alpha * (double)acc;
+      const double v = alpha * (double)acc;
       C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
     } else {
       float* C = static_cast<float*>(ep.C);
-      const float v = (float)ep.alpha * acc;
+      const float v = (float)alpha * acc;
       C[idx] = ep.beta != 0.0 ? fmaf((float)ep.beta, C[idx], v) : v;
     }
   }
@@ -760,7 +838,8 @@ void load_encode() {
   if (!g_encode) throw Error(MERA_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
 }
 
-CUtensorMap make_map(const void* ptr, int64_t rows, int64_t kp, int elem, int box_rows) {
+CUtensorMap make_map(const void* ptr, int64_t rows, int64_t kp, int kind, int box_rows) {
+  const int elem = kind_elem(kind);
   CUtensorMap m;
   const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(kp * elem)};
@@ -768,7 +847,10 @@ CUtensorMap make_map(const void* ptr, int64_t rows, int64_t kp, int elem, int bo
   const cuuint32_t es[2] = {1, 1};
   if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((kp * elem) & 15))
     throw Error(MERA_ERR_ARG, "tensor map: base or row pitch not 16-byte aligned");
-  CUresult r = g_encode(&m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  const CUtensorMapDataType dt = kind == KIND_TF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : kind == KIND_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = g_encode(&m, dt, 2,
                         const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -824,43 +906,58 @@ int64_t padded_k(int64_t K, int kind) {
   return (K + kb - 1) / kb * kb;
 }
 
-void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
-                int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, bool rows_fast,
-                cudaStream_t s) {
-  if (Kp % 32 || Rp % 64) throw Error(MERA_ERR_ARG, "pack_split: Kp must be a multiple of 32, Rp of 64");
+namespace {
+template <int KIND>
+void launch_pack(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
+                 int64_t R, int64_t K, int64_t Rp, int64_t Kp, void* hi, void* lo, bool rows_fast,
+                 const unsigned* amax, cudaStream_t s) {
   if (rows_fast) {
     if (Rp / 64 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: too many rows");
     const dim3 grid((unsigned)((Kp + 63) / 64), (unsigned)(Rp / 64));
-    if (kind == KIND_TF32) {
-      if (src_f64)
-        pack_split_tiled_kernel<double, KIND_TF32><<<grid, 256, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
-      else
-        pack_split_tiled_kernel<float, KIND_TF32><<<grid, 256, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
-    } else {
-      if (src_f64)
-        pack_split_tiled_kernel<double, KIND_BF16><<<grid, 256, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
-      else
-        pack_split_tiled_kernel<float, KIND_BF16><<<grid, 256, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
-    }
-    count_launch();
-    MERA_CHECK_LAUNCH();
-    return;
-  }
-  if ((Kp + 255) / 256 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: K too long");
-  const dim3 grid((unsigned)(Rp / 8), (unsigned)((Kp + 255) / 256)), blk(32, 8);
-  if (kind == KIND_TF32) {
     if (src_f64)
-      pack_split_kernel<double, KIND_TF32><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_tiled_kernel<double, KIND><<<grid, 256, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp,
+                                                                 hi, lo, amax);
     else
-      pack_split_kernel<float, KIND_TF32><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_tiled_kernel<float, KIND><<<grid, 256, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp,
+                                                                hi, lo, amax);
   } else {
+    if ((Kp + 255) / 256 > 65535) throw Error(MERA_ERR_UNSUPPORTED, "pack_split: K too long");
+    const dim3 grid((unsigned)(Rp / 8), (unsigned)((Kp + 255) / 256)), blk(32, 8);
     if (src_f64)
-      pack_split_kernel<double, KIND_BF16><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_kernel<double, KIND><<<grid, blk, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi,
+                                                           lo, amax);
     else
-      pack_split_kernel<float, KIND_BF16><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo);
+      pack_split_kernel<float, KIND><<<grid, blk, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo,
+                                                          amax);
   }
   count_launch();
   MERA_CHECK_LAUNCH();
+}
+}  // namespace
+
+void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
+                int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, bool rows_fast,
+                cudaStream_t s, unsigned* amax) {
+  if (Kp % 32 || Rp % 64) throw Error(MERA_ERR_ARG, "pack_split: Kp must be a multiple of 32, Rp of 64");
+  if (kind == KIND_F16) {
+    if (!amax) throw Error(MERA_ERR_ARG, "pack_split: FP16 planes need a word for the operand's maximum");
+    MERA_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), s));
+    if (R > 0 && K > 0) {
+      const int64_t F = rows_fast ? R : K, S = rows_fast ? K : R;
+      const dim3 grid((unsigned)std::min<int64_t>((F + 255) / 256, 16), (unsigned)std::min<int64_t>(S, 8192));
+      if (src_f64)
+        amax_kernel<double><<<grid, 256, 0, s>>>((const double*)src, rt, rs, kt, ks, R, K, rows_fast ? 1 : 0, amax);
+      else
+        amax_kernel<float><<<grid, 256, 0, s>>>((const float*)src, rt, rs, kt, ks, R, K, rows_fast ? 1 : 0, amax);
+      count_launch();
+      MERA_CHECK_LAUNCH();
+    }
+    launch_pack<KIND_F16>(src, src_f64, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo, rows_fast, amax, s);
+  } else if (kind == KIND_TF32) {
+    launch_pack<KIND_TF32>(src, src_f64, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo, rows_fast, nullptr, s);
+  } else {
+    launch_pack<KIND_BF16>(src, src_f64, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo, rows_fast, nullptr, s);
+  }
 }
 
 namespace {
@@ -904,7 +1001,7 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
                  const void* b_hi, const void* b_lo, int64_t Np, const TcEpilogue& ep_in, cudaStream_t s,
                  float* splitk_ws, size_t splitk_ws_bytes) {
   load_encode();
-  const int elem = kind == KIND_TF32 ? 4 : 2;
+  const int elem = kind_elem(kind);
   const int bn = 128;
   TcEpilogue ep = ep_in;
   ep.M = M;
@@ -948,19 +1045,26 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
     run.preload = run.mode >= 1 && !run.c_f64 && run.beta != 0.0 && pow2;
     run.bscale = run.preload ? (float)(run.beta / run.alpha) : 0.f;
   }
-  const CUtensorMap ah = make_map(a_hi, Mp, Kp, elem, BM), al = make_map(a_lo, Mp, Kp, elem, BM);
-  const CUtensorMap bh = make_map(b_hi, Np, Kp, elem, bn), bl = make_map(b_lo, Np, Kp, elem, bn);
+  if (kind == KIND_F16 && (!run.a_amax || !run.b_amax))
+    throw Error(MERA_ERR_ARG, "gemm_packed: FP16 planes need their operands' maxima");
+  const CUtensorMap ah = make_map(a_hi, Mp, Kp, kind, BM), al = make_map(a_lo, Mp, Kp, kind, BM);
+  const CUtensorMap bh = make_map(b_hi, Np, Kp, kind, bn), bl = make_map(b_lo, Np, Kp, kind, bn);
   const int64_t items = mt * nt * run.ksplit;
   if (kind == KIND_TF32)
     launch<KIND_TF32, 128>(ah, al, bh, bl, run, items, s);
-  else
+  else if (kind == KIND_BF16)
     launch<KIND_BF16, 128>(ah, al, bh, bl, run, items, s);
+  else
+    launch<KIND_F16, 128>(ah, al, bh, bl, run, items, s);
   count_launch();
   MERA_CHECK_LAUNCH();
   if (sp > 1) {
     const int64_t total = M * N;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(splitk_ws, run.ksplit, M, N, ep);
+    // the partials are already divided by the FP16 scales (their kernel ran with them)
+    TcEpilogue red = ep;
+    red.a_amax = red.b_amax = nullptr;
+    splitk_reduce_kernel<<<blocks, 256, 0, s>>>(splitk_ws, run.ksplit, M, N, red);
     count_launch();
     MERA_CHECK_LAUNCH();
   }

@@ -2,11 +2,32 @@
 #pragma once
 #include "common.h"
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace mera {
 namespace tc {
 
-enum { KIND_TF32 = 0, KIND_BF16 = 1 };
+// Operand planes: TF32 (hi/lo, kind::tf32), BF16 (hi/lo, kind::f16) or FP16
+// (hi/lo of the operand scaled by a power of two, kind::f16).
+enum { KIND_TF32 = 0, KIND_BF16 = 1, KIND_F16 = 2 };
+inline int kind_elem(int kind) { return kind == KIND_TF32 ? 4 : 2; }
+// Plane kind of a mixed-precision mode (mera_prec).
+inline int kind_of_prec(int prec) {
+  return prec == MERA_PREC_3XTF32 ? KIND_TF32 : prec == MERA_PREC_SPLIT_FP16 ? KIND_F16 : KIND_BF16;
+}
+
+// FP16 planes: the operand is multiplied by 2^e, e = 14 - E with
+// max|x| = m 2^E (m in [0.5, 1)), so that its largest entry lies in
+// [2^13, 2^14) and its low plane keeps 11 significant bits down to entries
+// 2^-17 of the largest; amax_bits is the float bit pattern of max|x|.
+// A zero or non-finite maximum gives e = 0; e is clamped to [-100, 100]
+// (operands whose entries all lie below 2^-86 keep fewer bits).
+__host__ __device__ inline int f16_scale_exp(unsigned amax_bits) {
+  const unsigned ex = (amax_bits >> 23) & 0xFFu;
+  if (ex == 0xFFu || (amax_bits & 0x7FFFFFFFu) == 0u) return 0;
+  const int e = ex == 0u ? 100 : 14 - ((int)ex - 126);  // E = ex - 126 for m in [0.5, 1)
+  return e > 100 ? 100 : (e < -100 ? -100 : e);
+}
 
 // Output side of one tensor-core contraction (offset tables as in GettCall).
 struct TcEpilogue {
@@ -30,6 +51,10 @@ struct TcEpilogue {
   int preload = 0;
   float bscale = 0.f;  // beta / alpha (exact: alpha is a power of two)
   int* err = nullptr;  // set to 1 by a CTA whose bounded wait expired
+  // FP16 planes: device words holding the float bits of max|A| and max|B|;
+  // the products are divided by 2^(e_A + e_B) (f16_scale_exp) in the store
+  const unsigned* a_amax = nullptr;
+  const unsigned* b_amax = nullptr;
   uint64_t wait_ns = 1000000000ull;  // limit of each pipeline wait (default 1 s)
   // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
   // writing a plain row-major partial at C + s * split_stride
@@ -47,10 +72,12 @@ int64_t padded_k(int64_t K, int kind);
 // planes of [Rp x Kp] row-major tensor-core values.
 // rows_fast: the source's stride-1 index runs along r (a tiled transpose keeps
 // both the reads and the plane writes coalesced).  Kp must be a multiple of
-// 32 and Rp of 64 (padded_k and round_up(., 128) give both).
+// 32 and Rp of 64 (padded_k and round_up(., 128) give both).  KIND_F16: amax
+// (a device word) receives the float bits of max|src| over the view first,
+// and the planes hold the operand scaled by 2^f16_scale_exp(amax).
 void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt,
                 int64_t ks, int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi,
-                void* lo, bool rows_fast, cudaStream_t s);
+                void* lo, bool rows_fast, cudaStream_t s, unsigned* amax = nullptr);
 
 // C tile loop over packed planes: A [Mp x Kp], B [Np x Kp] (both K-major),
 // Mp a multiple of 128 covering M, Np a multiple of 128 covering N.

@@ -434,22 +434,26 @@ double SideNet::forward_flops() const {
   return f;
 }
 
+// Workspace of one tensor-core product: two words for the operands' maxima
+// (FP16 planes), the four planes, the split-K partials; 1024-byte aligned
+// regions.
 size_t tc_workspace_bytes(const GettCall& g, int prec) {
   if (prec == MERA_PREC_FP64) return 0;
-  const int kind = prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
-  const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
+  const int kind = tc::kind_of_prec(prec);
+  const size_t elem = tc::kind_elem(kind);
   const int64_t Kp = tc::padded_k(g.K, kind);
   const int64_t Mp = tc::round_up(g.M, 128), Np = tc::round_up(g.N, 128);
-  return 5 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind);
+  return 6 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind);
 }
 
+// A keep slot: the operand's maximum word, then its two planes.
 size_t tc_keep_bytes(const GettCall& g, int prec, int side) {
   if (prec == MERA_PREC_FP64 || side == 0) return 0;
-  const int kind = prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
-  const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
+  const int kind = tc::kind_of_prec(prec);
+  const size_t elem = tc::kind_elem(kind);
   const int64_t Kp = tc::padded_k(g.K, kind);
   const int64_t Rp = tc::round_up(side == 1 ? g.M : g.N, 128);
-  return 2048 + elem * 2 * (size_t)Rp * (size_t)Kp;
+  return 3 * 1024 + elem * 2 * (size_t)Rp * (size_t)Kp;
 }
 
 void keep_need(const SideNet& net, int prec, size_t need[2]) {
@@ -527,14 +531,16 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   const GettCall g = flip ? transposed(g0) : g0;
   int kside = keep ? keep->side : 0;  // kept operand, as a side of g
   if (flip && kside) kside = 3 - kside;
-  const int kind = ex.prec == MERA_PREC_3XTF32 ? tc::KIND_TF32 : tc::KIND_BF16;
-  const size_t elem = kind == tc::KIND_TF32 ? 4 : 2;
+  const int kind = tc::kind_of_prec(ex.prec);
+  const size_t elem = tc::kind_elem(kind);
   const int64_t Kp = tc::padded_k(g.K, kind);
   const int64_t Mp = tc::round_up(g.M, 128), Np = tc::round_up(g.N, 128);
   if (tc_workspace_bytes(g, ex.prec) > ex.ws_bytes) throw Error(MERA_ERR_ARG, "contract: workspace too small");
   auto align = [](size_t o) { return (o + 1023) & ~size_t(1023); };
   char* w = static_cast<char*>(ex.ws);
-  size_t o = 0;
+  unsigned* amax_a = reinterpret_cast<unsigned*>(w);  // maxima of the operands (FP16 planes)
+  unsigned* amax_b = amax_a + 1;
+  size_t o = 1024;
   void* ah = w + o; o = align(o + elem * Mp * Kp);
   void* al = w + o; o = align(o + elem * Mp * Kp);
   void* bh = w + o; o = align(o + elem * Np * Kp);
@@ -548,8 +554,9 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
       throw Error(MERA_ERR_ARG, "contract: keep slot missing or too small");
     char* k = static_cast<char*>(ex.keep[slot]);
     const int64_t Rp = kside == 1 ? Mp : Np;
-    (kside == 1 ? ah : bh) = k;
-    (kside == 1 ? al : bl) = k + align(elem * Rp * Kp);
+    (kside == 1 ? amax_a : amax_b) = reinterpret_cast<unsigned*>(k);
+    (kside == 1 ? ah : bh) = k + 1024;
+    (kside == 1 ? al : bl) = k + 1024 + align(elem * Rp * Kp);
   }
   const bool pack_a = !(kside == 1 && keep->valid), pack_b = !(kside == 2 && keep->valid);
   // A rows = M group, A columns = K group; B rows (of the packed K-major plane) = N group
@@ -557,12 +564,14 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   int64_t pair = -1;
   if (pack_a) {
     pair = pr ? pr->begin(g.M, g.K, 0, s) : -1;
-    tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s);
+    tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s,
+                   amax_a);
     if (pr) pr->end(pair, 9100 + (g.a_rfast ? 10 : 0) + (g.a32 ? 1 : 0), s);
   }
   if (pack_b) {
     pair = pr ? pr->begin(g.N, g.K, 0, s) : -1;
-    tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s);
+    tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s,
+                   amax_b);
     if (pr) pr->end(pair, 9200 + (g.b_rfast ? 10 : 0) + (g.b32 ? 1 : 0), s);
   }
   tc::TcEpilogue ep;
@@ -578,6 +587,10 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   ep.vec = g.c_vec;
   ep.err = ex.err;
   ep.wait_ns = ex.wait_ns;
+  if (kind == tc::KIND_F16) {
+    ep.a_amax = amax_a;
+    ep.b_amax = amax_b;
+  }
   pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
   const int path = tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (pr) {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmera.so")
 
 MERA_F64, MERA_C128 = 0, 1
 MERA_BINARY, MERA_TERNARY, MERA_MPS = 0, 1, 2
-PREC_FP64, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
+PREC_FP64, PREC_3XTF32, PREC_SPLIT_BF16, PREC_SPLIT_FP16 = 0, 1, 2, 3
 
 ERRORS = {
     -1: "MERA_ERR_ARG", -2: "MERA_ERR_OOM", -3: "MERA_ERR_NONFINITE", -4: "MERA_ERR_NOCONV",

@@ -28,7 +28,7 @@ def test_header_is_c99_and_links(tmp_path):
     assert os.path.exists(_build(tmp_path))
 
 
-@pytest.mark.gpu_pending
+@pytest.mark.gpu
 def test_c_program_optimises(tmp_path):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():

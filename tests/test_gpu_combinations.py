@@ -9,7 +9,7 @@ from oracle import mps as om_mps
 from oracle import ternary as ot
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")

@@ -14,7 +14,7 @@ from oracle import mera as om
 from oracle import ternary as ot
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -45,6 +45,8 @@ CASES = [  # prec, tol, chi, n_trans, b_chunk, seed
     (1, 2e-6, 4, 2, 0, 0),
     (2, 2e-4, 4, 2, 0, 1),
     (1, 2e-6, 8, 3, 4, 2),  # the chi^9 chain sliced over b (4 values per slice)
+    (3, 2e-6, 4, 2, 0, 3),  # scaled split-FP16
+    (3, 2e-6, 8, 3, 4, 4),
 ]
 
 

@@ -11,7 +11,7 @@ import pytest
 from oracle import mera as om
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
@@ -61,7 +61,7 @@ def test_hamiltonian_checks(gm):
     bad[3, 3] = np.nan
     with pytest.raises(gm.MeraError) as ei:
         gm.Mera(gm.default_config(4, 4, 2), bad)
-    assert ei.value.code == -1
+    assert ei.value.code == -3  # MERA_ERR_NONFINITE
     hc = h3.astype(np.complex128)
     hc[0, 1] += 1e-3j
     hc[1, 0] -= 1e-3j  # still Hermitian

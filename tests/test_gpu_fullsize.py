@@ -20,7 +20,7 @@ import pytest
 
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = [pytest.mark.gpu_pending, pytest.mark.slow]
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 @pytest.fixture(scope="module")

@@ -7,7 +7,7 @@ import pytest
 from oracle import optim as oo
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")

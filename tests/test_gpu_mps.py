@@ -12,7 +12,7 @@ from oracle import geometry as geo
 from oracle import mps as om
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
 

@@ -199,6 +199,10 @@ MIXED = [
     (1, 2e-6, 3, 5, 2, "random", 2),
     (2, 2e-4, 4, 4, 2, "ising", 0),
     (2, 2e-4, 4, 8, 3, "ising", 3),
+    (3, 2e-6, 4, 4, 2, "ising", 0),
+    (3, 2e-6, 4, 8, 3, "xxz", 1),
+    (3, 2e-6, 3, 5, 2, "random", 2),
+    (3, 2e-6, 4, 8, 3, "ising", 3),
 ]
 
 

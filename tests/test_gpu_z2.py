@@ -14,7 +14,7 @@ from oracle import ternary as ot
 from oracle import z2
 from paper_2007_03638_gb300 import inputs as inp
 
-pytestmark = pytest.mark.gpu_pending
+pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
 
