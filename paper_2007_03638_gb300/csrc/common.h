@@ -156,6 +156,16 @@ struct GettCall {
   GettOperand ar, br, cr;
   int cr_rows = 0, cr_vec = 1, cr_rows_t = 0, cr_vec_t = 1;
   int has_rv = 0;
+  // Largest magnitudes, as float bit patterns in device words (scaled
+  // split-FP16 mode; ignored by the other modes): a_amax / b_amax, when set,
+  // bound max|A| / max|B| (known from the operand's producer, so that the
+  // packing need not reduce the operand first); c_amax, when set, receives
+  // max|C| of the values this product stores (started at 0 when beta = 0,
+  // unless c_amax_started: an earlier part of the same output already began it).
+  const unsigned* a_amax = nullptr;
+  const unsigned* b_amax = nullptr;
+  unsigned* c_amax = nullptr;
+  int c_amax_started = 0;
 };
 void gett_f64(const GettCall& g, cudaStream_t s);
 

@@ -22,6 +22,7 @@ struct Layer {
   std::unique_ptr<SideNet> net[2];
   SideBufs buf[2];
   std::vector<DevBuf> own[2];
+  DevBuf amax[2];  // the sides' node maxima (scaled split-FP16)
   // ternary network: sides L, C, R
   std::unique_ptr<Net> tnet[3];
   NetBufs tbuf[3];

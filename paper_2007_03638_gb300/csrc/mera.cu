@@ -174,6 +174,11 @@ void build_layers(Ctx& c) {
       ly.buf[sd].f32 = mixed;
       ly.buf[sd].cplx = c.cplx;
       ly.buf[sd].ex = &c.ex;
+      if (c.cfg.prec == MERA_PREC_SPLIT_FP16) {
+        ly.amax[sd].alloc(2 * SideNet::NNODE * sizeof(unsigned));
+        MERA_CUDA(cudaMemsetAsync(ly.amax[sd].p, 0, ly.amax[sd].bytes, c.s));
+        ly.buf[sd].amax = ly.amax[sd].as<unsigned>();
+      }
       size_t need = 0;
       for (int node : {12, 15}) need += net.alloc_size(node);
       for (int node = 11; node < 20; ++node) need += net.alloc_size(node);

@@ -335,6 +335,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
     // divides by that power of two (exact), the preload multiplies by it
     double alpha_eff = ep.alpha;
     float bscale = ep.bscale;
+    float smax = 0.f;  // largest |value| this thread stores (for ep.c_amax)
     if (ep.a_amax) {
       const int k = f16_scale_exp(*ep.a_amax) + f16_scale_exp(*ep.b_amax);
       alpha_eff = ldexp(ep.alpha, -k);
@@ -493,11 +494,15 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
               if (f64out) {
                 double* C = static_cast<double*>(Cbase);
                 const double v = alpha * (double)acc[c0 + j];
-                C[idx] = acc_c ? fma(beta, C[idx], v) : v;
+                const double o = acc_c ? fma(beta, C[idx], v) : v;
+                C[idx] = o;
+                smax = fmaxf(smax, fabsf((float)o));
               } else {
                 float* C = static_cast<float*>(Cbase);
                 const float v = alpha_f * acc[c0 + j];
-                C[idx] = acc_c ? fmaf(beta_f, C[idx], v) : v;
+                const float o = acc_c ? fmaf(beta_f, C[idx], v) : v;
+                C[idx] = o;
+                smax = fmaxf(smax, fabsf(o));
               }
             }
           }
@@ -531,6 +536,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = fmaf(beta_f, o[j], v[j]);
               }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) smax = fmaxf(smax, fabsf(v[j]));
               asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
                            "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
                            : "memory");
@@ -549,6 +556,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
                 v.z = fmaf(beta_f, o.z, v.z);
                 v.w = fmaf(beta_f, o.w, v.w);
               }
+              smax = fmaxf(smax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
               *p = v;
             }
           }
@@ -584,18 +592,32 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
             if (f64out) {
               const double v = alpha * (double)tv[j];
               double* C = static_cast<double*>(Cbase);
-              C[idx] = acc_c ? fma(beta, C[idx], v) : v;
+              const double o = acc_c ? fma(beta, C[idx], v) : v;
+              C[idx] = o;
+              smax = fmaxf(smax, fabsf((float)o));
             } else {
               // float output: FP32 arithmetic (the FP64 pipe is a few ops per clock per SM)
               float* C = static_cast<float*>(Cbase);
               const float v = alpha_f * tv[j];
-              C[idx] = acc_c ? fmaf(beta_f, C[idx], v) : v;
+              const float o = acc_c ? fmaf(beta_f, C[idx], v) : v;
+              C[idx] = o;
+              smax = fmaxf(smax, fabsf(o));
             }
           }
         }
       }
     }
     if (!ok) atomicExch(&S->abort, 1);
+    if (ep.c_amax && ep.ksplit == 1) {
+      // one atomic per warp; fabsf values order like their bit patterns
+      unsigned m = __float_as_uint(smax);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+      }
+      if (lane == 0 && m) atomicMax(ep.c_amax, m);
+    }
   }
   __syncthreads();
   if (*(volatile int*)&S->abort) {
@@ -803,6 +825,7 @@ __global__ void amax_kernel(const Src* __restrict__ src, const int64_t* __restri
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit, int64_t M, int64_t N,
                                      TcEpilogue ep) {
   const int64_t total = M * N;
+  float smax = 0.f;
   const double alpha = ep.a_amax ? ldexp(ep.alpha, -(f16_scale_exp(*ep.a_amax) + f16_scale_exp(*ep.b_amax)))
                                  : ep.alpha;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -814,12 +837,25 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit,
     if (ep.c_f64) {
       double* C = static_cast<double*>(ep.C);
       const double v = alpha * (double)acc;
-      C[idx] = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+      const double o = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
+      C[idx] = o;
+      smax = fmaxf(smax, fabsf((float)o));
     } else {
       float* C = static_cast<float*>(ep.C);
       const float v = (float)alpha * acc;
-      C[idx] = ep.beta != 0.0 ? fmaf((float)ep.beta, C[idx], v) : v;
+      const float o = ep.beta != 0.0 ? fmaf((float)ep.beta, C[idx], v) : v;
+      C[idx] = o;
+      smax = fmaxf(smax, fabsf(o));
     }
+  }
+  if (ep.c_amax) {
+    unsigned m = __float_as_uint(smax);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
+      m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(ep.c_amax, m);
   }
 }
 
@@ -937,9 +973,11 @@ void launch_pack(const void* src, bool src_f64, const int64_t* rt, int64_t rs, c
 
 void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt, int64_t ks,
                 int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi, void* lo, bool rows_fast,
-                cudaStream_t s, unsigned* amax) {
+                cudaStream_t s, unsigned* amax, const unsigned* amax_known) {
   if (Kp % 32 || Rp % 64) throw Error(MERA_ERR_ARG, "pack_split: Kp must be a multiple of 32, Rp of 64");
-  if (kind == KIND_F16) {
+  if (kind == KIND_F16 && amax_known) {
+    launch_pack<KIND_F16>(src, src_f64, rt, rs, kt, ks, R, K, Rp, Kp, hi, lo, rows_fast, amax_known, s);
+  } else if (kind == KIND_F16) {
     if (!amax) throw Error(MERA_ERR_ARG, "pack_split: FP16 planes need a word for the operand's maximum");
     MERA_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), s));
     if (R > 0 && K > 0) {

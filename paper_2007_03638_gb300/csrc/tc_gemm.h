@@ -55,6 +55,9 @@ struct TcEpilogue {
   // the products are divided by 2^(e_A + e_B) (f16_scale_exp) in the store
   const unsigned* a_amax = nullptr;
   const unsigned* b_amax = nullptr;
+  // when set, every stored |C| value is folded into this word (atomicMax of
+  // the float bits; split-K: by the reduction kernel)
+  unsigned* c_amax = nullptr;
   uint64_t wait_ns = 1000000000ull;  // limit of each pipeline wait (default 1 s)
   // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
   // writing a plain row-major partial at C + s * split_stride
@@ -75,9 +78,12 @@ int64_t padded_k(int64_t K, int kind);
 // 32 and Rp of 64 (padded_k and round_up(., 128) give both).  KIND_F16: amax
 // (a device word) receives the float bits of max|src| over the view first,
 // and the planes hold the operand scaled by 2^f16_scale_exp(amax).
+// amax_known: a device word already bounding max|src| (no reduction pass;
+// the planes use it, and amax is not written).
 void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, const int64_t* kt,
                 int64_t ks, int64_t R, int64_t K, int64_t Rp, int64_t Kp, int kind, void* hi,
-                void* lo, bool rows_fast, cudaStream_t s, unsigned* amax = nullptr);
+                void* lo, bool rows_fast, cudaStream_t s, unsigned* amax = nullptr,
+                const unsigned* amax_known = nullptr);
 
 // C tile loop over packed planes: A [Mp x Kp], B [Np x Kp] (both K-major),
 // Mp a multiple of 128 covering M, Np a multiple of 128 covering N.

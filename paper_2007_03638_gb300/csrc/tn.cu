@@ -488,6 +488,8 @@ GettCall transposed(const GettCall& g) {
   h.c_vec = g.c_vec_t;
   h.c_rows_t = g.c_rows;
   h.c_vec_t = g.c_vec;
+  h.a_amax = g.b_amax;
+  h.b_amax = g.a_amax;
   return h;
 }
 }  // namespace
@@ -506,6 +508,9 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
     auto part_ptr = [](const double* p, bool f32, int comp) {
       return f32 ? reinterpret_cast<const double*>(reinterpret_cast<const float*>(p) + comp) : p + comp;
     };
+    // the output's maximum covers both components: begun once for all parts
+    const bool track = g0.c_amax && ex.prec == MERA_PREC_SPLIT_FP16;
+    if (track && g0.beta == 0.0 && !g0.c_amax_started) MERA_CUDA(cudaMemsetAsync(g0.c_amax, 0, sizeof(unsigned), s));
     for (const ComplexPart& pt : complex_parts(g0.a_conj != 0, g0.b_conj != 0)) {
       GettCall h = g0;
       h.cplx = h.a_conj = h.b_conj = h.has_rv = 0;
@@ -521,6 +526,7 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
       h.C = const_cast<double*>(part_ptr(g0.C, g0.c32, pt.cc));
       h.alpha = pt.sign * g0.alpha;
       h.beta = pt.first ? g0.beta : 1.0;
+      h.c_amax_started = 1;
       contract(h, ex, s, nullptr);
     }
     return;
@@ -559,19 +565,41 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
     (kside == 1 ? al : bl) = k + 1024 + align(elem * Rp * Kp);
   }
   const bool pack_a = !(kside == 1 && keep->valid), pack_b = !(kside == 2 && keep->valid);
+  // FP16 planes: an operand's maximum known from its producer is used as it
+  // is (no reduction pass); a kept operand carries its maximum in its slot
+  const unsigned* known_a = nullptr;
+  const unsigned* known_b = nullptr;
+  if (kind == tc::KIND_F16) {
+    if (g.a_amax) {
+      if (kside == 1) {
+        if (pack_a) MERA_CUDA(cudaMemcpyAsync(amax_a, g.a_amax, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
+      } else {
+        known_a = g.a_amax;
+      }
+    }
+    if (g.b_amax) {
+      if (kside == 2) {
+        if (pack_b) MERA_CUDA(cudaMemcpyAsync(amax_b, g.b_amax, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
+      } else {
+        known_b = g.b_amax;
+      }
+    }
+  }
+  const bool copied_a = kind == tc::KIND_F16 && g.a_amax && kside == 1;  // slot word already holds it
+  const bool copied_b = kind == tc::KIND_F16 && g.b_amax && kside == 2;
   // A rows = M group, A columns = K group; B rows (of the packed K-major plane) = N group
   Prof* pr = g_prof;
   int64_t pair = -1;
   if (pack_a) {
     pair = pr ? pr->begin(g.M, g.K, 0, s) : -1;
     tc::pack_split(g.A, !g.a32, g.a.t0, g.a.s0, g.a.t1, g.a.s1, g.M, g.K, Mp, Kp, kind, ah, al, g.a_rfast, s,
-                   amax_a);
+                   amax_a, known_a ? known_a : (copied_a ? amax_a : nullptr));
     if (pr) pr->end(pair, 9100 + (g.a_rfast ? 10 : 0) + (g.a32 ? 1 : 0), s);
   }
   if (pack_b) {
     pair = pr ? pr->begin(g.N, g.K, 0, s) : -1;
     tc::pack_split(g.B, !g.b32, g.b.t1, g.b.s1, g.b.t0, g.b.s0, g.N, g.K, Np, Kp, kind, bh, bl, g.b_rfast, s,
-                   amax_b);
+                   amax_b, known_b ? known_b : (copied_b ? amax_b : nullptr));
     if (pr) pr->end(pair, 9200 + (g.b_rfast ? 10 : 0) + (g.b32 ? 1 : 0), s);
   }
   tc::TcEpilogue ep;
@@ -588,8 +616,12 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   ep.err = ex.err;
   ep.wait_ns = ex.wait_ns;
   if (kind == tc::KIND_F16) {
-    ep.a_amax = amax_a;
-    ep.b_amax = amax_b;
+    ep.a_amax = known_a ? known_a : amax_a;
+    ep.b_amax = known_b ? known_b : amax_b;
+    if (g.c_amax) {
+      if (g.beta == 0.0 && !g.c_amax_started) MERA_CUDA(cudaMemsetAsync(g.c_amax, 0, sizeof(unsigned), s));
+      ep.c_amax = g.c_amax;
+    }
   }
   pair = pr ? pr->begin(g.M, g.N, g.K, s) : -1;
   const int path = tc::gemm_packed(kind, g.M, g.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
@@ -609,9 +641,16 @@ constexpr int EXT = -1;  // an external buffer (operator, seed, output): double,
 // Run one plan.  Operands are identified by node id (or EXT): leaves and
 // externals are double, internal nodes float in mixed mode; conjugated
 // leaves are read conjugated.
+// aa, ba, ca: the operands' and the output's maximum words (see SideBufs::amax);
+// cstart: the output's maximum was begun by an earlier slice of the same buffer.
 void run(const SideBufs& b, const GemmPlan& p, const double* A, int an, const double* B, int bn, double* C,
-         int cn, double alpha, double beta, cudaStream_t s, const Keep* keep = nullptr) {
+         int cn, double alpha, double beta, cudaStream_t s, const Keep* keep = nullptr,
+         const unsigned* aa = nullptr, const unsigned* ba = nullptr, unsigned* ca = nullptr, int cstart = 0) {
   GettCall g = p.proto;
+  g.a_amax = aa;
+  g.b_amax = ba;
+  g.c_amax = ca;
+  g.c_amax_started = cstart;
   g.A = A;
   g.B = B;
   g.C = C;
@@ -628,6 +667,14 @@ void run(const SideBufs& b, const GemmPlan& p, const double* A, int an, const do
 inline const double* value(const SideBufs& b, int node) {
   return node < SideNet::NLEAF ? b.leaf[node] : b.val[node];
 }
+// maximum words of an internal node's value and adjoint (null for leaves,
+// the root and when the buffers carry none)
+inline unsigned* vmax(const SideBufs& b, int node) {
+  return b.amax && internal(node) ? b.amax + node : nullptr;
+}
+inline unsigned* amax_adj(const SideBufs& b, int node) {
+  return b.amax && internal(node) ? b.amax + SideNet::NNODE + node : nullptr;
+}
 // Advance a node pointer by `off` elements of its storage type.
 inline double* offp(const SideBufs& b, const double* p, int64_t off) {
   char* c = reinterpret_cast<char*>(const_cast<double*>(p));
@@ -638,7 +685,8 @@ inline double* offp(const SideBufs& b, const double* p, int64_t off) {
 void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
   for (int node : {11, 14, 16, 19}) {
     const int l = SideNet::left(node), r = SideNet::right(node);
-    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s);
+    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s, nullptr, vmax(b, l),
+        vmax(b, r), vmax(b, node));
   }
 }
 
@@ -650,17 +698,20 @@ void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, do
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
         const Keep k3{1, 0, b0 > 0}, k6{2, 1, b0 > 0};
         run(b, net.f5c(), b.val[13], 13, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.val[15], 15,
-            1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr);
+            1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr, vmax(b, 13), vmax(b, 14), vmax(b, 15));
         run(b, net.f7c(), b.val[15], 15, b.val[16], 16, offp(b, b.val[17], b0 * net.b_stride_n7()), 17,
-            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr);
+            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr, vmax(b, 15), vmax(b, 16), vmax(b, 17), b0 > 0);
       }
       continue;
     }
     if (net.sliced() && node == 17) continue;
     const int l = SideNet::left(node), r = SideNet::right(node);
-    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s);
+    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s, nullptr, vmax(b, l),
+        vmax(b, r), vmax(b, node));
   }
-  if (out) run(b, net.fwd(SideNet::ROOT), b.val[18], 18, b.val[19], 19, out, EXT, alpha, beta, s);
+  if (out)
+    run(b, net.fwd(SideNet::ROOT), b.val[18], 18, b.val[19], 19, out, EXT, alpha, beta, s, nullptr, vmax(b, 18),
+        vmax(b, 19));
 }
 
 void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out, double alpha_op,
@@ -682,13 +733,13 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
         const Keep k6{2, 1, b0 > 0}, k3{1, 0, b0 > 0};
         run(b, net.b7c(), offp(b, b.adj[17], b0 * net.b_stride_n7()), 17, b.val[16], 16, b.adj[15], 15,
-            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr);
+            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr, amax_adj(b, 17), vmax(b, 16), amax_adj(b, 15));
         if (need[13])
           run(b, net.b5lc(), b.adj[15], 15, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.adj[13], 13,
-              1.0, b0 == 0 ? 0.0 : 1.0, s);
+              1.0, b0 == 0 ? 0.0 : 1.0, s, nullptr, amax_adj(b, 15), vmax(b, 14), amax_adj(b, 13));
         if (need[14])
           run(b, net.b5rc(), b.val[13], 13, b.adj[15], 15, offp(b, b.adj[14], b0 * net.b_stride_n4()), 14,
-              1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr);
+              1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr, vmax(b, 13), amax_adj(b, 15), amax_adj(b, 14), b0 > 0);
       }
       continue;
     }
@@ -710,10 +761,14 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
       // a leaf's adjoint goes to an external accumulator
       const int dn_id = node != SideNet::ROOT ? node : EXT;
       const int out_id = c >= SideNet::NLEAF ? c : EXT;
+      unsigned* dn_max = amax_adj(b, node);  // null for the root's (external) seed
+      unsigned* out_max = c >= SideNet::NLEAF ? amax_adj(b, c) : nullptr;
       if (side == 0)
-        run(b, net.bwd_left(node), dn, dn_id, value(b, r), r, out, out_id, alpha, beta, s);
+        run(b, net.bwd_left(node), dn, dn_id, value(b, r), r, out, out_id, alpha, beta, s, nullptr, dn_max,
+            vmax(b, r), out_max);
       else
-        run(b, net.bwd_right(node), value(b, l), l, dn, dn_id, out, out_id, alpha, beta, s);
+        run(b, net.bwd_right(node), value(b, l), l, dn, dn_id, out, out_id, alpha, beta, s, nullptr, vmax(b, l),
+            dn_max, out_max);
     }
   }
 }

@@ -194,6 +194,10 @@ struct SideBufs {
   bool f32 = false;
   bool cplx = false;   // interleaved complex data; conjugated leaves 1,3,4,7,9 read conjugated
   const Exec* ex = nullptr;
+  // scaled split-FP16: 2 * NNODE device words, max|val[i]| at amax[i] and
+  // max|adj[i]| at amax[NNODE + i] for internal nodes, written by the
+  // products that store those buffers (null: operands are reduced when packed)
+  unsigned* amax = nullptr;
 };
 
 // Subtrees that do not contain the operator leaf: N1, N4, N6, N9.

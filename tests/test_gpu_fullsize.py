@@ -1,5 +1,6 @@
 """The benchmark workload at full size on the GPU (XXZ Delta = 1, chi = 32, three
-transition layers, split-BF16, the launch configuration bench.py times), checked
+transition layers, split-BF16 and scaled split-FP16, the launch configuration
+bench.py times), checked
 through properties that hold at any size, since the oracle cannot evaluate a
 chi = 32 network:
 
@@ -23,8 +24,8 @@ from paper_2007_03638_gb300 import inputs as inp
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-@pytest.fixture(scope="module")
-def problem():
+@pytest.fixture(scope="module", params=[2, 3], ids=["split_bf16", "split_fp16"])
+def problem(request):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -33,7 +34,7 @@ def problem():
     from paper_2007_03638_gb300 import mera as gm
     chi, L = 32, 3
     h3 = inp.three_site_blocked(inp.xxz_bond(1.0))
-    cfg = gm.default_config(4, chi, L, prec=gm.PREC_SPLIT_BF16, lbfgs_m=16, krylov_dim=4)
+    cfg = gm.default_config(4, chi, L, prec=request.param, lbfgs_m=16, krylov_dim=4)
     m = gm.Mera(cfg, h3)
     us, ws = inp.random_mera(4, chi, L, seed=0)
     point = [t for p in zip(us, ws) for t in p]
