@@ -360,8 +360,16 @@ int mera_profile_dump(mera_t m, const char* path);
  * memory budget; each admitted request owns a mera_t on its own stream, so
  * its state stays on the device until it finishes, and n_workers host
  * threads take turns stepping the running requests one iteration at a time
- * (their kernels overlap on the GPU).  A request stops when |G| < gtol or
- * after maxiter iterations.  Results do not depend on the mix. */
+ * (their kernels overlap on the GPU).  Requests with the same configuration
+ * of the binary network (real tensors, unsliced chi^9 chain: chi <= 16 from
+ * d_b = 4) form a cohort: their energy/gradient evaluations that are due at
+ * the same time (within a gathering window of 1.5 ms) run together, every
+ * contraction one batched launch over up to 8 of them and their Krylov
+ * solves in lockstep, on the cohort's own stream; the cohort's workspace
+ * (the planes of 8 members) counts against the budget while it lives.  A
+ * request stops when |G| < gtol or after maxiter iterations.  Results do not
+ * depend on the mix: each request's arithmetic is that of the request
+ * alone. */
 typedef struct mera_server* mera_server_t;
 
 typedef struct {
@@ -380,6 +388,8 @@ typedef struct {
                          requests ran, so that it went back to the head of the
                          queue until one of them finished (a creation that runs
                          out of memory with nothing else running fails)       */
+    int batched_evals;/* energy/gradient evaluations that ran together with
+                         other requests of its cohort (batched launches)       */
 } mera_request_status;
 
 int mera_server_create(size_t mem_budget_bytes, int n_workers, mera_server_t* out);

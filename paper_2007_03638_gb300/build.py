@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(BUILD, "libmera.so")
-SOURCES = ["gett.cu", "blas1.cu", "linalg.cu", "tn.cu", "tnet.cu", "tc_gemm.cu", "mera.cu", "mps.cu", "geom.cu",
-           "optim.cu", "abi.cu", "serve.cu", "init.cu"]
+SOURCES = ["gett.cu", "blas1.cu", "linalg.cu", "tn.cu", "tnet.cu", "tc_gemm.cu", "mera.cu", "group.cu", "mps.cu",
+           "geom.cu", "optim.cu", "abi.cu", "serve.cu", "init.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "-diag-suppress", "550"]

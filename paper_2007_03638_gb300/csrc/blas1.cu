@@ -277,6 +277,27 @@ void Reducer::init(int max_vectors) {
   partial.alloc(sizeof(double) * (size_t)nblocks * max_vectors);
   result.alloc(sizeof(double) * (size_t)max_vectors);
   host.resize(max_vectors);
+  pinned.alloc(sizeof(double) * (size_t)max_vectors);
+}
+
+void Reducer::dots_async(const double* X, int64_t ldx, int k, const double* y, int64_t n, cudaStream_t s) {
+  if ((size_t)k > host.size()) throw Error(MERA_ERR_ARG, "Reducer: too many vectors");
+  int nb = (int)std::min<int64_t>(nblocks, std::max<int64_t>(1, (n + RT - 1) / RT));
+  dim3 grid(nb, k);
+  dots_partial<<<grid, RT, 0, s>>>(X, ldx, y, n, partial.as<double>());
+  finish_partial<<<k, RT, 0, s>>>(partial.as<double>(), nb, result.as<double>());
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  MERA_CUDA(cudaMemcpyAsync(pinned.p, result.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+}
+
+void Reducer::trace_async(const double* a, int64_t n, cudaStream_t s) {
+  int nb = (int)std::min<int64_t>(nblocks, std::max<int64_t>(1, (n + RT - 1) / RT));
+  trace_partial<<<nb, RT, 0, s>>>(a, n, partial.as<double>());
+  finish_partial<<<1, RT, 0, s>>>(partial.as<double>(), nb, result.as<double>());
+  count_launch(2);
+  MERA_CHECK_LAUNCH();
+  MERA_CUDA(cudaMemcpyAsync(pinned.p, result.p, sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
 void Reducer::dots(const double* X, int64_t ldx, int k, const double* y, int64_t n,

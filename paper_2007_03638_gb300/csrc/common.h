@@ -179,12 +179,34 @@ void gemm_f64(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha,
 
 // ---------------------------------------------------------- BLAS-1 etc ----
 // Deterministic reductions: fixed grid, fixed per-thread ranges, two passes.
+// Page-locked host memory (asynchronous device-to-host copies).
+struct PinnedBuf {
+  void* p = nullptr;
+  PinnedBuf() = default;
+  PinnedBuf(const PinnedBuf&) = delete;
+  PinnedBuf& operator=(const PinnedBuf&) = delete;
+  ~PinnedBuf() { if (p) cudaFreeHost(p); }
+  void alloc(size_t n) {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    MERA_CUDA(cudaMallocHost(&p, n));
+  }
+};
+
 struct Reducer {
   DevBuf partial;    // per-block partial sums
   DevBuf result;     // device results
   std::vector<double> host;
+  PinnedBuf pinned;  // results of the asynchronous forms
   int nblocks = 0;
   void init(int max_vectors);
+  // Asynchronous forms of dots and trace (the same kernels and order): the
+  // results reach pinned_results() when the stream gets there; the caller
+  // synchronises the stream before reading them (several objects' reductions
+  // then share one synchronisation).
+  void dots_async(const double* X, int64_t ldx, int k, const double* y, int64_t n, cudaStream_t s);
+  void trace_async(const double* a, int64_t n, cudaStream_t s);
+  const double* pinned_results() const { return static_cast<const double*>(pinned.p); }
   // out[i] = sum_j X_i[j] * y[j] for i < k, where X_i = X + i*ldx
   void dots(const double* X, int64_t ldx, int k, const double* y, int64_t n, cudaStream_t s,
             double* out_host);

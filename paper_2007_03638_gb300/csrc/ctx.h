@@ -10,6 +10,7 @@
 #include "tnet.h"
 
 #include <algorithm>
+#include <exception>
 #include <functional>
 #include <memory>
 #include <string>
@@ -106,6 +107,11 @@ struct mera_ctx {
   mera::Prof prof;
   int64_t matvecs = 0;
   std::string err;
+  // serving: evaluations go to the problem's cohort (same-configuration
+  // problems evaluated together, group.cu) instead of running alone
+  void (*cohort_eval)(void* cohort, mera_ctx& c, const double* W, mera::Eval& E) = nullptr;
+  void* cohort = nullptr;
+  int64_t evals_batched = 0;  // evaluations that ran together with other problems
 };
 
 namespace mera {
@@ -163,6 +169,25 @@ void check_z2_point(Ctx& c, const double* W, cudaStream_t s);
 void create(Ctx& c, const mera_config& cfg, const void* h3, cudaStream_t s);
 // why cfg's flags, tolerances or counts are out of range ("" if they are not)
 std::string config_range_error(const mera_config& cfg);
+
+// binds a side's leaves: operator op, disentangler u, isometry w (mera.cu)
+void bind_leaves(Layer& ly, int side, const double* op, const double* u, const double* w);
+// floor of the Krylov solves' relative residual in a precision mode
+double krylov_floor(int prec);
+// per-tensor density matrices of the preconditioner at the last evaluation
+void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
+
+// ---- group.cu ----
+// Evaluations of nb problems (binary network, real tensors, the same
+// configuration) in lockstep: cs[k] at point Ws[k] into Es[k] (the energy
+// only when grad is false); every product is one batched launch over the
+// members with the workspace and wait flag of ex, on stream s.  Member k's
+// arithmetic is that of its evaluation alone.  errs[k] receives member k's
+// failure (null when it succeeded); the others are unaffected by it.
+void eval_group(Ctx* const* cs, const double* const* Ws, Eval* const* Es, int nb, bool grad, const Exec& ex,
+                cudaStream_t s, std::exception_ptr* errs);
+// the binary, real, unsliced problems whose evaluation runs in eval_group
+bool grouped_eval(const Ctx& c);
 
 // ---- mps.cu ----
 double mps_energy(Ctx& c, const double* A, cudaStream_t s);

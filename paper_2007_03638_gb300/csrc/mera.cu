@@ -415,8 +415,30 @@ void gradient_pass(Ctx& c, const double* W, Eval& E, cudaStream_t s);
 // Energy only: up-sweep, scale-invariant fixed point, e = Tr(h_L rho_S).
 double forward_energy(Ctx& c, const double* W, cudaStream_t s);
 
+bool grouped_eval(const Ctx& c) { return !c.gnet && !c.mps && !c.cplx; }
+
+namespace {
+// A single problem on the lockstep path: a group of one.
+void eval_single(Ctx& c, const double* W, Eval& E, bool grad, cudaStream_t s) {
+  Ctx* cs[1] = {&c};
+  const double* Ws[1] = {W};
+  Eval* Es[1] = {&E};
+  std::exception_ptr err[1];
+  eval_group(cs, Ws, Es, 1, grad, c.ex, s, err);
+  if (err[0]) std::rethrow_exception(err[0]);
+}
+}  // namespace
+
 // Full evaluation at point W into E.
 void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
+  if (c.cohort_eval) {
+    c.cohort_eval(c.cohort, c, W, E);
+    return;
+  }
+  if (grouped_eval(c)) {
+    eval_single(c, W, E, true, s);
+    return;
+  }
   const int L = c.L;
   c.prof.energy_grad_calls++;
   if (c.mps) {
@@ -455,6 +477,11 @@ void energy_grad(Ctx& c, const double* W, Eval& E, cudaStream_t s) {
 
 double forward_energy(Ctx& c, const double* W, cudaStream_t s) {
   if (c.mps) return mps_energy(c, W, s);
+  if (grouped_eval(c)) {
+    Eval e;  // receives the energy only
+    eval_single(c, W, e, false, s);
+    return e.e;
+  }
   const int L = c.L;
   // up-sweep
   copy(P(c.h[0]), P(c.h0), opn(c, c.dims[0]) * opn(c, c.dims[0]) * c.rs, s);

@@ -8,11 +8,18 @@
 // until it finishes.  Worker threads take turns over the running requests,
 // one L-BFGS (or CG) iteration at a time, so the kernels of different
 // requests overlap on the GPU while each request's host-side control (line
-// search, Krylov scalars) waits only for its own stream.  A request's
+// search, Krylov scalars) waits only for its own stream.
+//
+// Requests with the same network configuration (binary, real, unsliced)
+// form a cohort: their energy/gradient evaluations meet at a rendezvous, and
+// the evaluations waiting there run together (eval_group: one batched
+// tensor-core launch per contraction for all of them, the Krylov solves in
+// lockstep) on the cohort's stream.  An evaluation waits for the cohort's
+// other stepping requests at most a short gathering window.  A request's
 // arithmetic does not depend on what else is running (every kernel has a
-// fixed reduction order), so its result is the same alone and in the mix.
-#include "common.h"
-#include "../../include/mera.h"
+// fixed reduction order and a batched product computes each member as it
+// would alone), so its result is the same alone and in the mix.
+#include "ctx.h"
 
 #include <chrono>
 #include <cstdio>
@@ -28,6 +35,105 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
+// Same-configuration problems evaluated together (see the file comment).
+struct Cohort {
+  std::mutex mu;
+  std::condition_variable cv;
+  int stepping = 0;  // its requests inside an iteration step
+  int refs = 0;      // its requests with a live problem
+  struct Pend {
+    mera_ctx* c = nullptr;
+    const double* W = nullptr;
+    mera::Eval* E = nullptr;
+    bool done = false;
+    int nb = 0;
+    std::exception_ptr err;
+  };
+  std::vector<Pend*> pending;
+  clk::time_point first;  // arrival of the oldest pending evaluation
+  bool driving = false;
+  cudaStream_t s = nullptr;
+  mera::DevBuf ws, flag;
+  mera::Exec ex;
+  size_t bytes = 0;
+  ~Cohort() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+// How long an evaluation waits for the cohort's other stepping requests.
+constexpr auto kGather = std::chrono::microseconds(1500);
+
+void cohort_eval(void* co, mera_ctx& c, const double* W, mera::Eval& E) {
+  Cohort& h = *static_cast<Cohort*>(co);
+  MERA_CUDA(cudaStreamSynchronize(c.s));  // the member's own stream has produced W
+  Cohort::Pend p;
+  p.c = &c;
+  p.W = W;
+  p.E = &E;
+  std::unique_lock<std::mutex> lk(h.mu);
+  if (h.pending.empty()) h.first = clk::now();
+  h.pending.push_back(&p);
+  h.cv.notify_all();
+  constexpr int MAXB = mera::tc::TcEpilogue::MAXB;
+  while (!p.done) {
+    const int np = (int)h.pending.size();
+    const bool ready = np >= h.stepping || np >= MAXB || clk::now() - h.first > kGather;
+    if (!h.driving && np > 0 && ready) {
+      h.driving = true;
+      const int nb = std::min(np, MAXB);
+      std::vector<Cohort::Pend*> batch(h.pending.begin(), h.pending.begin() + nb);
+      h.pending.erase(h.pending.begin(), h.pending.begin() + nb);
+      if (!h.pending.empty()) h.first = clk::now();
+      lk.unlock();
+      mera_ctx* cs[MAXB];
+      const double* Ws[MAXB];
+      mera::Eval* Es[MAXB];
+      std::exception_ptr errs[MAXB];
+      for (int k = 0; k < nb; ++k) {
+        cs[k] = batch[k]->c;
+        Ws[k] = batch[k]->W;
+        Es[k] = batch[k]->E;
+      }
+      try {
+        mera::eval_group(cs, Ws, Es, nb, true, h.ex, h.s, errs);
+        MERA_CUDA(cudaStreamSynchronize(h.s));  // results complete before the members go on
+      } catch (...) {
+        for (int k = 0; k < nb; ++k) errs[k] = std::current_exception();
+      }
+      lk.lock();
+      for (int k = 0; k < nb; ++k) {
+        batch[k]->err = errs[k];
+        batch[k]->nb = nb;
+        batch[k]->done = true;
+      }
+      h.driving = false;
+      h.cv.notify_all();
+    } else {
+      h.cv.wait_for(lk, std::chrono::microseconds(100));
+    }
+  }
+  lk.unlock();
+  if (p.nb > 1) ++c.evals_batched;
+  if (p.err) std::rethrow_exception(p.err);
+}
+
+// Requests that may share a cohort: the same network configuration, binary,
+// real, without slicing of the chi^9 chain (the fields that decide the
+// plans, the arithmetic and the workspace).
+std::string cohort_key(const mera_config& c) {
+  return std::to_string(c.d_b) + "/" + std::to_string(c.chi) + "/" + std::to_string(c.n_trans) + "/" +
+         std::to_string(c.prec) + "/" + std::to_string(c.w_stiefel) + "/" + std::to_string(c.precond) + "/" +
+         std::to_string(c.krylov_dim) + "/" + std::to_string(c.recompute_env) + "/" + std::to_string(c.b_chunk);
+}
+bool cohort_eligible(const mera_config& cfg, const mera_ctx& m) {
+  if (cfg.network != MERA_BINARY || cfg.dtype != MERA_F64 || cfg.z2 || !mera::grouped_eval(m)) return false;
+  for (const auto& ly : m.layers)
+    for (int sd = 0; sd < 2; ++sd)
+      if (!ly.net[sd] || ly.net[sd]->sliced()) return false;
+  return true;
+}
+
 struct Request {
   int64_t id = 0;
   mera_config cfg{};
@@ -40,6 +146,8 @@ struct Request {
   // run state
   mera_t m = nullptr;
   cudaStream_t stream = nullptr;
+  Cohort* cohort = nullptr;
+  int batched = 0;  // evaluations run together with other requests
   int state = 0;  // 0 queued, 1 running, 2 done, 3 failed
   bool busy = false;
   int iters = 0, n_evals = 0, error = 0, deferred = 0;
@@ -64,6 +172,7 @@ struct mera_server {
   int device = 0;
   std::vector<std::thread> workers;
   int64_t done = 0, failed = 0, submitted = 0;
+  std::map<std::string, std::unique_ptr<Cohort>> cohorts;
   // a request whose creation ran out of device memory while others ran went
   // back to the head of the queue; nothing is admitted until one of those
   // finishes (done + failed passes this mark); -1: no such wait
@@ -73,10 +182,62 @@ struct mera_server {
 
 namespace {
 
+// Leave the request's cohort (caller holds mu); the last one frees it.
+void leave_cohort(mera_server* sv, Request& r) {
+  if (!r.cohort) return;
+  Cohort* h = r.cohort;
+  r.cohort = nullptr;
+  if (--h->refs > 0) return;
+  for (auto it = sv->cohorts.begin(); it != sv->cohorts.end(); ++it)
+    if (it->second.get() == h) {
+      sv->in_use -= h->bytes;
+      sv->cohorts.erase(it);
+      break;
+    }
+}
+
+// Join (or found) the cohort of the request's configuration (caller holds
+// mu).  The cohort's workspace holds the planes of as many members as a
+// batched product takes; without the memory the request runs alone.
+void join_cohort(mera_server* sv, Request& r) {
+  if (!cohort_eligible(r.cfg, *r.m)) return;
+  const std::string key = cohort_key(r.cfg);
+  auto it = sv->cohorts.find(key);
+  if (it == sv->cohorts.end()) {
+    auto h = std::make_unique<Cohort>();
+    try {
+      constexpr int MAXB = mera::tc::TcEpilogue::MAXB;
+      h->ex = r.m->ex;
+      h->ex.keep[0] = h->ex.keep[1] = nullptr;
+      h->ex.keep_bytes[0] = h->ex.keep_bytes[1] = 0;
+      if (r.m->ex.prec != MERA_PREC_FP64) {
+        h->ws.alloc((size_t)MAXB * r.m->ex.ws_bytes);
+        h->flag.alloc(sizeof(int));
+        MERA_CUDA(cudaMemset(h->flag.p, 0, sizeof(int)));
+        h->ex.ws = h->ws.p;
+        h->ex.ws_bytes = h->ws.bytes;
+        h->ex.err = h->flag.as<int>();
+      }
+      MERA_CUDA(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+      h->bytes = h->ws.bytes + h->flag.bytes;
+    } catch (...) {
+      return;  // no memory for a cohort: this request evaluates alone
+    }
+    sv->in_use += h->bytes;
+    it = sv->cohorts.emplace(key, std::move(h)).first;
+  }
+  Cohort* h = it->second.get();
+  ++h->refs;
+  r.cohort = h;
+  r.m->cohort = h;
+  r.m->cohort_eval = &cohort_eval;
+}
+
 void finish(mera_server* sv, Request& r, int err) {
   r.state = err ? 3 : 2;
   r.error = err;
   r.t_done = clk::now();
+  leave_cohort(sv, r);
   if (r.m) mera_destroy(r.m);
   r.m = nullptr;
   if (r.stream) cudaStreamDestroy(r.stream);
@@ -146,9 +307,23 @@ void worker(mera_server* sv) {
         for (auto& t : r.tensors) ptrs.push_back(t.data());
         err = mera_set_tensors(r.m, ptrs.data());
       }
+      if (!err) {
+        std::lock_guard<std::mutex> g(sv->mu);
+        join_cohort(sv, r);
+      }
     }
     if (!err) {
+      Cohort* h = r.cohort;
+      if (h) {
+        std::lock_guard<std::mutex> g(h->mu);
+        ++h->stepping;
+      }
       err = method == 1 ? mera_cg_step(r.m, &info) : mera_lbfgs_step(r.m, &info);
+      if (h) {
+        std::lock_guard<std::mutex> g(h->mu);
+        --h->stepping;
+        h->cv.notify_all();  // an evaluation waiting for this request's next one need not
+      }
       if (!err) {
         stepped = true;
         finished = info.gnorm < gtol || iters0 + 1 >= maxiter;
@@ -179,6 +354,7 @@ void worker(mera_server* sv) {
       r.n_evals += info.n_evals;
       r.energy = info.energy;
       r.gnorm = info.gnorm;
+      r.batched = (int)r.m->evals_batched;
     }
     if (err) r.message = message;
     r.busy = false;
@@ -270,6 +446,7 @@ int mera_server_poll(mera_server_t sv, int64_t id, mera_request_status* st) {
   st->bytes = r.bytes;
   std::snprintf(st->message, sizeof(st->message), "%s", r.message.c_str());
   st->deferred = r.deferred;
+  st->batched_evals = r.batched;
   return MERA_OK;
 }
 

@@ -48,9 +48,6 @@ namespace {
 #ifndef MERA_TC_STAGES
 #define MERA_TC_STAGES 3
 #endif
-#ifndef MERA_TC_COMPENSATED
-#define MERA_TC_COMPENSATED 0   // 1: compensated (Kahan) folding of the accumulator groups
-#endif
 
 constexpr int BM = 128;
 constexpr int STAGES = MERA_TC_STAGES;
@@ -204,8 +201,9 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   Smem* S = reinterpret_cast<Smem*>(staging + EPI_WARPS * 32 * (STG + 1));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t sn = (ep.N + BN - 1) / BN, sm_ = (ep.M + BM - 1) / BM;
-  const int64_t nt1 = sn * sm_;                // output tiles
-  const int64_t ntiles = nt1 * ep.ksplit;      // work items (tile, K slice)
+  const int64_t nt1 = sn * sm_;                // output tiles of one member
+  const int64_t per_member = nt1 * ep.ksplit;  // work items (tile, K slice) of one member
+  const int64_t ntiles = per_member * ep.nb;   // work items of all members, member slowest
   const int64_t cid = blockIdx.x, ncl = gridDim.x;
   // output tile tt (rows past M or columns past N load zeros and store
   // nothing).  The dimension with fewer tiles runs
@@ -219,7 +217,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   };
   // K blocks of work item t: [kb_lo, kb_hi)
   auto krange = [&](int64_t t, int& lo, int& hi) {
-    const int sp = (int)(t / nt1);
+    const int sp = (int)((t % per_member) / nt1);
     lo = ep.ksplit > 1 ? sp * ep.kbs : 0;
     hi = ep.ksplit > 1 ? min(ep.kblocks, lo + ep.kbs) : ep.kblocks;
   };
@@ -257,7 +255,8 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       for (int64_t t = cid; t < ntiles && !stop; t += ncl) {
         int64_t m0l, n0l;
         tile_of(t % nt1, m0l, n0l);
-        const int m0 = (int)m0l, n0 = (int)n0l;
+        const int64_t mb = t / per_member;  // member
+        const int m0 = (int)(m0l + mb * ep.a_member_rows), n0 = (int)(n0l + mb * ep.b_member_rows);
         int klo, khi;
         krange(t, klo, khi);
         for (int kb = klo; kb < khi; ++kb, ++kbg) {
@@ -335,13 +334,34 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
     // divides by that power of two (exact), the preload multiplies by it
     double alpha_eff = ep.alpha;
     float bscale = ep.bscale;
-    float smax = 0.f;  // largest |value| this thread stores (for ep.c_amax)
-    if (ep.a_amax) {
-      const int k = f16_scale_exp(*ep.a_amax) + f16_scale_exp(*ep.b_amax);
-      alpha_eff = ldexp(ep.alpha, -k);
-      bscale = (float)ldexp((double)ep.bscale, k);
-    }
+    float smax = 0.f;  // largest |value| this thread stores for the current member
+    int64_t cur = -1;  // member of the previous work item
+    // fold smax into the member's maximum word (one atomic per warp)
+    auto flush_max = [&](int64_t mb) {
+      if (mb < 0 || ep.ksplit > 1 || !ep.member_cmax[mb]) return;
+      unsigned m = __float_as_uint(smax);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+      }
+      if (lane == 0 && m) atomicMax(ep.member_cmax[mb], m);
+      smax = 0.f;
+    };
     for (int64_t t = cid; t < ntiles && ok; t += ncl) {
+      const int64_t mb = t / per_member;
+      if (mb != cur) {
+        flush_max(cur);
+        cur = mb;
+        alpha_eff = ep.alpha;
+        bscale = ep.bscale;
+        if (ep.member_amax_a[mb]) {
+          const int k = f16_scale_exp(*ep.member_amax_a[mb]) + f16_scale_exp(*ep.member_amax_b[mb]);
+          alpha_eff = ldexp(ep.alpha, -k);
+          bscale = (float)ldexp((double)ep.bscale, k);
+        }
+      }
+      void* const Cm = ep.member_C[mb];
       int64_t m0, n0;
       tile_of(t % nt1, m0, n0);
       int klo, khi;
@@ -355,17 +375,9 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       float acc[HC];
 #pragma unroll
       for (int j = 0; j < HC; ++j) acc[j] = 0.f;
-#if MERA_TC_COMPENSATED
-      // Kahan compensation of each column's running sum, kept as BF16 pairs
-      // (a compensation term is below half an ulp of its sum: 8 significant
-      // bits of it leave the compensated sum within 2^-9 ulp per fold)
-      uint32_t cmp[HC / 2];
-#pragma unroll
-      for (int j = 0; j < HC / 2; ++j) cmp[j] = 0u;
-#endif
       if (ep.preload && rvalid) {
         // acc = (beta / alpha) C: loads issued now, their latency hidden by this tile's MMAs
-        const float* C = static_cast<const float*>(ep.C);
+        const float* C = static_cast<const float*>(Cm);
         if (ep.mode == 1) {
 #pragma unroll
           for (int j = 0; j < HC; ++j) {
@@ -404,30 +416,6 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
         if (!mbar_wait(&S->acc_full[b], (uint32_t)(gg / NACC) & 1, ep.wait_ns)) { ok = false; break; }
         if (*(volatile int*)&S->abort) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#if MERA_TC_COMPENSATED
-#pragma unroll
-        for (int c0 = 0; c0 < HC; c0 += 16) {
-          uint32_t r[16];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC + c0);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const float2 cf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&cmp[(c0 + j) / 2]));
-            const float y0 = __uint_as_float(r[j]) - cf.x, y1 = __uint_as_float(r[j + 1]) - cf.y;
-            const float t0 = acc[c0 + j] + y0, t1 = acc[c0 + j + 1] + y1;
-            const __nv_bfloat162 cn = __floats2bfloat162_rn((t0 - acc[c0 + j]) - y0, (t1 - acc[c0 + j + 1]) - y1);
-            cmp[(c0 + j) / 2] = *reinterpret_cast<const uint32_t*>(&cn);
-            acc[c0 + j] = t0;
-            acc[c0 + j + 1] = t1;
-          }
-        }
-#else
 #pragma unroll
         for (int c0 = 0; c0 < HC; c0 += 64) {
           // two 32-column loads in flight, one wait
@@ -455,24 +443,16 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
 #pragma unroll
           for (int j = 0; j < 64; ++j) acc[c0 + j] += __uint_as_float(r[j]);
         }
-#endif
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&S->acc_empty[b])) : "memory");
       }
       if (!ok) break;
-#if MERA_TC_COMPENSATED
-#pragma unroll
-      for (int j = 0; j < HC; j += 2) {
-        const float2 cf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&cmp[j / 2]));
-        acc[j] -= cf.x;
-        acc[j + 1] -= cf.y;
-      }
-#endif
       const bool f64out = ep.c_f64 != 0, acc_c = ep.beta != 0.0 && !ep.preload;
-      void* Cbase = ep.ksplit > 1 ? static_cast<void*>(static_cast<float*>(ep.C) + (t / nt1) * ep.split_stride)
-                                  : ep.C;
+      void* Cbase =
+          ep.ksplit > 1 ? static_cast<void*>(static_cast<float*>(Cm) + ((t % per_member) / nt1) * ep.split_stride)
+                        : Cm;
       const double alpha = alpha_eff, beta = ep.beta;
       const float alpha_f = (float)alpha_eff, beta_f = (float)ep.beta;
       if (ep.mode == 1) {
@@ -608,16 +588,7 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       }
     }
     if (!ok) atomicExch(&S->abort, 1);
-    if (ep.c_amax && ep.ksplit == 1) {
-      // one atomic per warp; fabsf values order like their bit patterns
-      unsigned m = __float_as_uint(smax);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
-        m = y > m ? y : m;
-      }
-      if (lane == 0 && m) atomicMax(ep.c_amax, m);
-    }
+    flush_max(cur);
   }
   __syncthreads();
   if (*(volatile int*)&S->abort) {
@@ -821,41 +792,44 @@ __global__ void amax_kernel(const Src* __restrict__ src, const int64_t* __restri
   }
 }
 
-// Sum of the split-K partials in a fixed order, then the real epilogue.
+// Sum of the split-K partials in a fixed order, then the real epilogue;
+// blockIdx.y = member (its partials at part + member * ksplit * M * N, the
+// FP16 scales already divided out by the product kernel).
 __global__ void splitk_reduce_kernel(const float* __restrict__ part, int ksplit, int64_t M, int64_t N,
                                      TcEpilogue ep) {
   const int64_t total = M * N;
+  const int mb = blockIdx.y;
+  const float* pm = part + (int64_t)mb * ksplit * total;
   float smax = 0.f;
-  const double alpha = ep.a_amax ? ldexp(ep.alpha, -(f16_scale_exp(*ep.a_amax) + f16_scale_exp(*ep.b_amax)))
-                                 : ep.alpha;
+  const double alpha = ep.alpha;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
-    for (int sp = 0; sp < ksplit; ++sp) acc += part[(int64_t)sp * total + i];
+    for (int sp = 0; sp < ksplit; ++sp) acc += pm[(int64_t)sp * total + i];
     const int64_t m = i / N, n = i % N;
     const int64_t idx = (ep.cm ? ep.cm[m] : m * ep.cms) + (ep.cn ? ep.cn[n] : n * ep.cns);
     if (ep.c_f64) {
-      double* C = static_cast<double*>(ep.C);
+      double* C = static_cast<double*>(ep.member_C[mb]);
       const double v = alpha * (double)acc;
       const double o = ep.beta != 0.0 ? fma(ep.beta, C[idx], v) : v;
       C[idx] = o;
       smax = fmaxf(smax, fabsf((float)o));
     } else {
-      float* C = static_cast<float*>(ep.C);
+      float* C = static_cast<float*>(ep.member_C[mb]);
       const float v = (float)alpha * acc;
       const float o = ep.beta != 0.0 ? fmaf((float)ep.beta, C[idx], v) : v;
       C[idx] = o;
       smax = fmaxf(smax, fabsf(o));
     }
   }
-  if (ep.c_amax) {
+  if (ep.member_cmax[mb]) {
     unsigned m = __float_as_uint(smax);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned y = __shfl_xor_sync(0xffffffffu, m, o);
       m = y > m ? y : m;
     }
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(ep.c_amax, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(ep.member_cmax[mb], m);
   }
 }
 
@@ -1045,17 +1019,33 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
   ep.M = M;
   ep.N = N;
   ep.kblocks = (int)(Kp / (KB_BYTES / elem));
+  const int nb = ep.nb;
+  if (nb < 1 || nb > TcEpilogue::MAXB) throw Error(MERA_ERR_ARG, "gemm_packed: member count out of range");
+  if (nb == 1) {
+    ep.member_C[0] = ep.C;
+    ep.member_amax_a[0] = ep.a_amax;
+    ep.member_amax_b[0] = ep.b_amax;
+    ep.member_cmax[0] = ep.c_amax;
+  }
+  ep.a_member_rows = Mp;
+  ep.b_member_rows = Np;
   const int64_t mt = (M + BM - 1) / BM, nt = (N + bn - 1) / bn;
   if (Mp < mt * BM || Np < nt * bn) throw Error(MERA_ERR_ARG, "gemm_packed: operand padding too small");
+  // the split count depends on one member's shape only, so that a member's
+  // arithmetic is the same alone and batched
   int sp = choose_split(M, N, Kp, kind);
-  if (sp > 1 && (!splitk_ws || splitk_ws_bytes < sizeof(float) * (size_t)sp * M * N)) sp = 1;
+  if (sp > 1 && (!splitk_ws || splitk_ws_bytes < sizeof(float) * (size_t)sp * M * N * nb)) sp = 1;
   TcEpilogue run = ep;
   if (sp > 1) {
     run.ksplit = sp;
     run.kbs = (ep.kblocks + sp - 1) / sp;
     run.ksplit = (ep.kblocks + run.kbs - 1) / run.kbs;  // no empty slice
     run.split_stride = M * N;
-    run.C = splitk_ws;
+    for (int b = 0; b < nb; ++b) {
+      run.member_C[b] = splitk_ws + (size_t)b * run.ksplit * M * N;
+      run.member_cmax[b] = nullptr;
+    }
+    run.C = run.member_C[0];
     run.c_f64 = 0;
     run.cm = nullptr;
     run.cms = N;
@@ -1067,13 +1057,22 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
     run.vec = N % 8 == 0 ? 8 : N % 4 == 0 ? 4 : 1;
   }
   // store path: lanes = rows when rows are contiguous, else per-row vectors
-  // when the columns are (pointer alignment permitting), else the transpose
-  const uintptr_t cb = reinterpret_cast<uintptr_t>(run.C);
+  // when the columns are (pointer alignment permitting), else the transpose;
+  // every member's output has the same alignment class (they have the same
+  // layout), checked here because the path decides the rounding of beta != 0
+  auto align_class = [](const void* p) {
+    const uintptr_t c = reinterpret_cast<uintptr_t>(p);
+    return c % 32 == 0 ? 2 : c % 16 == 0 ? 1 : 0;
+  };
+  const int acls = align_class(run.member_C[0]);
+  for (int b = 1; b < nb; ++b)
+    if (align_class(run.member_C[b]) != acls)
+      throw Error(MERA_ERR_ARG, "gemm_packed: members' outputs differ in alignment");
   if (run.rows)
     run.mode = 1;
-  else if (!run.c_f64 && run.vec == 8 && cb % 32 == 0)
+  else if (!run.c_f64 && run.vec == 8 && acls == 2)
     run.mode = 2;
-  else if (!run.c_f64 && run.vec >= 4 && cb % 16 == 0)
+  else if (!run.c_f64 && run.vec >= 4 && acls >= 1)
     run.mode = 3;
   else
     run.mode = 0;
@@ -1083,11 +1082,13 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
     run.preload = run.mode >= 1 && !run.c_f64 && run.beta != 0.0 && pow2;
     run.bscale = run.preload ? (float)(run.beta / run.alpha) : 0.f;
   }
-  if (kind == KIND_F16 && (!run.a_amax || !run.b_amax))
-    throw Error(MERA_ERR_ARG, "gemm_packed: FP16 planes need their operands' maxima");
-  const CUtensorMap ah = make_map(a_hi, Mp, Kp, kind, BM), al = make_map(a_lo, Mp, Kp, kind, BM);
-  const CUtensorMap bh = make_map(b_hi, Np, Kp, kind, bn), bl = make_map(b_lo, Np, Kp, kind, bn);
-  const int64_t items = mt * nt * run.ksplit;
+  if (kind == KIND_F16)
+    for (int b = 0; b < nb; ++b)
+      if (!run.member_amax_a[b] || !run.member_amax_b[b])
+        throw Error(MERA_ERR_ARG, "gemm_packed: FP16 planes need their operands' maxima");
+  const CUtensorMap ah = make_map(a_hi, nb * Mp, Kp, kind, BM), al = make_map(a_lo, nb * Mp, Kp, kind, BM);
+  const CUtensorMap bh = make_map(b_hi, nb * Np, Kp, kind, bn), bl = make_map(b_lo, nb * Np, Kp, kind, bn);
+  const int64_t items = nb * mt * nt * run.ksplit;
   if (kind == KIND_TF32)
     launch<KIND_TF32, 128>(ah, al, bh, bl, run, items, s);
   else if (kind == KIND_BF16)
@@ -1098,10 +1099,10 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
   MERA_CHECK_LAUNCH();
   if (sp > 1) {
     const int64_t total = M * N;
-    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    const dim3 blocks((unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), (unsigned)nb);
     // the partials are already divided by the FP16 scales (their kernel ran with them)
     TcEpilogue red = ep;
-    red.a_amax = red.b_amax = nullptr;
+    for (int b = 0; b < nb; ++b) red.member_amax_a[b] = red.member_amax_b[b] = nullptr;
     splitk_reduce_kernel<<<blocks, 256, 0, s>>>(splitk_ws, run.ksplit, M, N, red);
     count_launch();
     MERA_CHECK_LAUNCH();

@@ -63,6 +63,18 @@ struct TcEpilogue {
   // writing a plain row-major partial at C + s * split_stride
   int ksplit = 1, kbs = 0;
   int64_t split_stride = 0;
+  // Batched products: nb members share the plan (shapes, tables, alpha,
+  // beta) and differ in data.  Member b's A planes are rows
+  // [b * a_member_rows, ...) of the A maps (B likewise), it writes
+  // member_C[b] and its maxima are member_amax_a/b[b], member_cmax[b]
+  // (gemm_packed fills member 0 from C, a_amax, b_amax, c_amax when nb = 1).
+  static constexpr int MAXB = 8;
+  int nb = 1;
+  int64_t a_member_rows = 0, b_member_rows = 0;
+  void* member_C[MAXB] = {};
+  const unsigned* member_amax_a[MAXB] = {};
+  const unsigned* member_amax_b[MAXB] = {};
+  unsigned* member_cmax[MAXB] = {};
 };
 
 // Bytes of split-K partials gemm_packed may use for an M x N product.

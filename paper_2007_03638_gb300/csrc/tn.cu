@@ -434,16 +434,16 @@ double SideNet::forward_flops() const {
   return f;
 }
 
-// Workspace of one tensor-core product: two words for the operands' maxima
-// (FP16 planes), the four planes, the split-K partials; 1024-byte aligned
-// regions.
-size_t tc_workspace_bytes(const GettCall& g, int prec) {
+// Workspace of one tensor-core product of nb members: two words per member
+// for the operands' maxima (FP16 planes), the members' four planes, the
+// split-K partials; 1024-byte aligned regions.
+size_t tc_workspace_bytes(const GettCall& g, int prec, int nb) {
   if (prec == MERA_PREC_FP64) return 0;
   const int kind = tc::kind_of_prec(prec);
   const size_t elem = tc::kind_elem(kind);
   const int64_t Kp = tc::padded_k(g.K, kind);
   const int64_t Mp = tc::round_up(g.M, 128), Np = tc::round_up(g.N, 128);
-  return 6 * 1024 + elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind);
+  return 6 * 1024 + (size_t)nb * (elem * 2 * (size_t)(Mp + Np) * (size_t)Kp + tc::splitk_bytes(g.M, g.N, Kp, kind));
 }
 
 // A keep slot: the operand's maximum word, then its two planes.
@@ -632,6 +632,85 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   }
 }
 
+void contract_batch(const GettCall* gs, int nb, const Exec& ex, cudaStream_t s) {
+  if (nb == 1) {
+    contract(gs[0], ex, s, nullptr);
+    return;
+  }
+  const GettCall& g0 = gs[0];
+  if (g0.M <= 0 || g0.N <= 0) return;
+  if (nb > tc::TcEpilogue::MAXB) throw Error(MERA_ERR_ARG, "contract_batch: too many members");
+  if (ex.prec == MERA_PREC_FP64 || g0.cplx) {
+    // FP64 and complex products run member by member
+    for (int b = 0; b < nb; ++b) contract(gs[b], ex, s, nullptr);
+    return;
+  }
+  // one tensor-core launch for every member: the same orientation and plan
+  // (tables of member 0: the members' tables are equal by construction)
+  const bool flip = g0.c_vec < 8 && g0.c_vec_t > g0.c_vec;
+  const int kind = tc::kind_of_prec(ex.prec);
+  const size_t elem = tc::kind_elem(kind);
+  GettCall g[tc::TcEpilogue::MAXB];
+  for (int b = 0; b < nb; ++b) g[b] = flip ? transposed(gs[b]) : gs[b];
+  const GettCall& h = g[0];
+  const int64_t Kp = tc::padded_k(h.K, kind);
+  const int64_t Mp = tc::round_up(h.M, 128), Np = tc::round_up(h.N, 128);
+  if (tc_workspace_bytes(h, ex.prec, nb) > ex.ws_bytes) throw Error(MERA_ERR_ARG, "contract_batch: workspace too small");
+  auto align = [](size_t o) { return (o + 1023) & ~size_t(1023); };
+  char* w = static_cast<char*>(ex.ws);
+  unsigned* amax = reinterpret_cast<unsigned*>(w);  // member b: words 2b (A), 2b + 1 (B)
+  size_t o = 1024;
+  char* ah = w + o; o = align(o + elem * nb * Mp * Kp);
+  char* al = w + o; o = align(o + elem * nb * Mp * Kp);
+  char* bh = w + o; o = align(o + elem * nb * Np * Kp);
+  char* bl = w + o; o = align(o + elem * nb * Np * Kp);
+  float* part = reinterpret_cast<float*>(w + o);
+  const size_t part_bytes = ex.ws_bytes > o ? ex.ws_bytes - o : 0;
+  tc::TcEpilogue ep;
+  ep.nb = nb;
+  Prof* pr = g_prof;
+  for (int b = 0; b < nb; ++b) {
+    const GettCall& x = g[b];
+    const bool f16 = kind == tc::KIND_F16;
+    int64_t pair = pr ? pr->begin(x.M, x.K, 0, s) : -1;
+    tc::pack_split(x.A, !x.a32, h.a.t0, h.a.s0, h.a.t1, h.a.s1, x.M, x.K, Mp, Kp, kind, ah + elem * b * Mp * Kp,
+                   al + elem * b * Mp * Kp, x.a_rfast, s, amax + 2 * b, f16 ? x.a_amax : nullptr);
+    if (pr) pr->end(pair, 9100 + (x.a_rfast ? 10 : 0) + (x.a32 ? 1 : 0), s);
+    pair = pr ? pr->begin(x.N, x.K, 0, s) : -1;
+    tc::pack_split(x.B, !x.b32, h.b.t1, h.b.s1, h.b.t0, h.b.s0, x.N, x.K, Np, Kp, kind, bh + elem * b * Np * Kp,
+                   bl + elem * b * Np * Kp, x.b_rfast, s, amax + 2 * b + 1, f16 ? x.b_amax : nullptr);
+    if (pr) pr->end(pair, 9200 + (x.b_rfast ? 10 : 0) + (x.b32 ? 1 : 0), s);
+    ep.member_C[b] = x.C;
+    if (f16) {
+      ep.member_amax_a[b] = x.a_amax ? x.a_amax : amax + 2 * b;
+      ep.member_amax_b[b] = x.b_amax ? x.b_amax : amax + 2 * b + 1;
+      if (x.c_amax) {
+        if (x.beta == 0.0 && !x.c_amax_started) MERA_CUDA(cudaMemsetAsync(x.c_amax, 0, sizeof(unsigned), s));
+        ep.member_cmax[b] = x.c_amax;
+      }
+    }
+  }
+  ep.C = g[0].C;
+  ep.alpha = h.alpha;
+  ep.beta = h.beta;
+  ep.cm = h.c.t0;
+  ep.cms = h.c.s0;
+  ep.cn = h.c.t1;
+  ep.cns = h.c.s1;
+  ep.c_f64 = h.c32 ? 0 : 1;
+  ep.rows = h.c_rows;
+  ep.vec = h.c_vec;
+  ep.err = ex.err;
+  ep.wait_ns = ex.wait_ns;
+  const int64_t pair = pr ? pr->begin(h.M, h.N, h.K, s) : -1;
+  const int path = tc::gemm_packed(kind, h.M, h.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
+  if (pr) {
+    pr->end(pair, 1000 * (kind + 1) + 100 * path, s);
+    pr->gett_launches++;
+    pr->gett_flops += 2.0 * (double)h.M * (double)h.N * (double)h.K * nb;
+  }
+}
+
 namespace {
 inline bool internal(int node) { return node >= SideNet::NLEAF && node != SideNet::ROOT; }
 // conjugated copies of u and w (bra side of <MERA| ... |MERA>)
@@ -641,28 +720,52 @@ constexpr int EXT = -1;  // an external buffer (operator, seed, output): double,
 // Run one plan.  Operands are identified by node id (or EXT): leaves and
 // externals are double, internal nodes float in mixed mode; conjugated
 // leaves are read conjugated.
-// aa, ba, ca: the operands' and the output's maximum words (see SideBufs::amax);
-// cstart: the output's maximum was begun by an earlier slice of the same buffer.
-void run(const SideBufs& b, const GemmPlan& p, const double* A, int an, const double* B, int bn, double* C,
-         int cn, double alpha, double beta, cudaStream_t s, const Keep* keep = nullptr,
-         const unsigned* aa = nullptr, const unsigned* ba = nullptr, unsigned* ca = nullptr, int cstart = 0) {
-  GettCall g = p.proto;
-  g.a_amax = aa;
-  g.b_amax = ba;
-  g.c_amax = ca;
-  g.c_amax_started = cstart;
-  g.A = A;
-  g.B = B;
-  g.C = C;
-  g.alpha = alpha;
-  g.beta = beta;
-  g.a32 = b.f32 && an != EXT && internal(an);
-  g.b32 = b.f32 && bn != EXT && internal(bn);
-  g.c32 = b.f32 && cn != EXT && internal(cn);
-  g.cplx = b.cplx;
-  g.a_conj = b.cplx && an != EXT && conj_leaf(an);
-  g.b_conj = b.cplx && bn != EXT && conj_leaf(bn);
-  contract(g, *b.ex, s, keep);
+// Operands of one member's product: pointers and maximum words (see
+// SideBufs::amax); cstart: the output's maximum was begun by an earlier
+// slice of the same buffer.
+struct Ops {
+  const double* A = nullptr;
+  const double* B = nullptr;
+  double* C = nullptr;
+  const unsigned* aa = nullptr;
+  const unsigned* ba = nullptr;
+  unsigned* ca = nullptr;
+  int cstart = 0;
+};
+
+// Run one plan for every member; ops(b, k) gives member k's operands.
+// Operands are identified by node id (or EXT): leaves and externals are
+// double, internal nodes float in mixed mode; conjugated leaves are read
+// conjugated.  One member: the product may keep an operand's planes.
+template <class F>
+void run_n(SideBufs* const* bs, int nb, const Exec& ex, const GemmPlan& p, int an, int bn, int cn, double alpha,
+           double beta, cudaStream_t s, const Keep* keep, F ops) {
+  GettCall g[tc::TcEpilogue::MAXB];
+  for (int k = 0; k < nb; ++k) {
+    const SideBufs& b = *bs[k];
+    const Ops o = ops(b, k);
+    GettCall& x = g[k];
+    x = p.proto;
+    x.A = o.A;
+    x.B = o.B;
+    x.C = o.C;
+    x.a_amax = o.aa;
+    x.b_amax = o.ba;
+    x.c_amax = o.ca;
+    x.c_amax_started = o.cstart;
+    x.alpha = alpha;
+    x.beta = beta;
+    x.a32 = b.f32 && an != EXT && internal(an);
+    x.b32 = b.f32 && bn != EXT && internal(bn);
+    x.c32 = b.f32 && cn != EXT && internal(cn);
+    x.cplx = b.cplx;
+    x.a_conj = b.cplx && an != EXT && conj_leaf(an);
+    x.b_conj = b.cplx && bn != EXT && conj_leaf(bn);
+  }
+  if (nb == 1)
+    contract(g[0], ex, s, keep);
+  else
+    contract_batch(g, nb, ex, s);
 }
 inline const double* value(const SideBufs& b, int node) {
   return node < SideNet::NLEAF ? b.leaf[node] : b.val[node];
@@ -682,40 +785,53 @@ inline double* offp(const SideBufs& b, const double* p, int64_t off) {
 }
 }  // namespace
 
-void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
+void side_prepare_n(const SideNet& net, SideBufs* const* bs, int nb, const Exec& ex, cudaStream_t s) {
   for (int node : {11, 14, 16, 19}) {
     const int l = SideNet::left(node), r = SideNet::right(node);
-    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s, nullptr, vmax(b, l),
-        vmax(b, r), vmax(b, node));
+    run_n(bs, nb, ex, net.fwd(node), l, r, node, 1.0, 0.0, s, nullptr, [&](const SideBufs& b, int) {
+      return Ops{value(b, l), value(b, r), b.val[node], vmax(b, l), vmax(b, r), vmax(b, node)};
+    });
   }
 }
 
-void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, double beta, cudaStream_t s) {
+void side_forward_n(const SideNet& net, SideBufs* const* bs, int nb, const Exec& ex, double* const* out,
+                    double alpha, double beta, cudaStream_t s) {
+  if (net.sliced() && nb > 1) throw Error(MERA_ERR_UNSUPPORTED, "side_forward: a sliced chain runs one member at a time");
   for (int node : {12, 13, 15, 17, 18}) {
     if (net.sliced() && node == 15) {
       // N5 = N3 x N4 and N7 = N5 x N6 one slice of the coarse leg b at a time
       // N3 and N6 are the same for every slice: their packed planes are kept
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
         const Keep k3{1, 0, b0 > 0}, k6{2, 1, b0 > 0};
-        run(b, net.f5c(), b.val[13], 13, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.val[15], 15,
-            1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr, vmax(b, 13), vmax(b, 14), vmax(b, 15));
-        run(b, net.f7c(), b.val[15], 15, b.val[16], 16, offp(b, b.val[17], b0 * net.b_stride_n7()), 17,
-            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr, vmax(b, 15), vmax(b, 16), vmax(b, 17), b0 > 0);
+        run_n(bs, 1, ex, net.f5c(), 13, 14, 15, 1.0, 0.0, s, ex.keep[0] ? &k3 : nullptr,
+              [&](const SideBufs& b, int) {
+                return Ops{b.val[13], offp(b, b.val[14], b0 * net.b_stride_n4()), b.val[15], vmax(b, 13),
+                           vmax(b, 14), vmax(b, 15)};
+              });
+        run_n(bs, 1, ex, net.f7c(), 15, 16, 17, 1.0, 0.0, s, ex.keep[1] ? &k6 : nullptr,
+              [&](const SideBufs& b, int) {
+                return Ops{b.val[15], b.val[16], offp(b, b.val[17], b0 * net.b_stride_n7()), vmax(b, 15),
+                           vmax(b, 16), vmax(b, 17), b0 > 0};
+              });
       }
       continue;
     }
     if (net.sliced() && node == 17) continue;
     const int l = SideNet::left(node), r = SideNet::right(node);
-    run(b, net.fwd(node), value(b, l), l, value(b, r), r, b.val[node], node, 1.0, 0.0, s, nullptr, vmax(b, l),
-        vmax(b, r), vmax(b, node));
+    run_n(bs, nb, ex, net.fwd(node), l, r, node, 1.0, 0.0, s, nullptr, [&](const SideBufs& b, int) {
+      return Ops{value(b, l), value(b, r), b.val[node], vmax(b, l), vmax(b, r), vmax(b, node)};
+    });
   }
   if (out)
-    run(b, net.fwd(SideNet::ROOT), b.val[18], 18, b.val[19], 19, out, EXT, alpha, beta, s, nullptr, vmax(b, 18),
-        vmax(b, 19));
+    run_n(bs, nb, ex, net.fwd(SideNet::ROOT), 18, 19, EXT, alpha, beta, s, nullptr, [&](const SideBufs& b, int k) {
+      return Ops{b.val[18], b.val[19], out[k], vmax(b, 18), vmax(b, 19)};
+    });
 }
 
-void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out, double alpha_op,
-                   bool need_env, double* du, double* dw, double alpha_env, cudaStream_t s) {
+void side_backward_n(const SideNet& net, SideBufs* const* bs, int nb, const Exec& ex, bool need_op,
+                     double* const* op_out, double alpha_op, bool need_env, double* const* du, double* const* dw,
+                     double alpha_env, cudaStream_t s) {
+  if (net.sliced() && nb > 1) throw Error(MERA_ERR_UNSUPPORTED, "side_backward: a sliced chain runs one member at a time");
   // which nodes need an adjoint: subtree contains the operator (need_op) or a
   // conjugated u/w leaf (need_env)
   bool need[SideNet::NNODE] = {};
@@ -732,45 +848,79 @@ void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out
       // N6 and N3 are the same for every slice: their packed planes are kept
       for (int64_t b0 = 0; b0 < net.coarse(); b0 += net.chunk()) {
         const Keep k6{2, 1, b0 > 0}, k3{1, 0, b0 > 0};
-        run(b, net.b7c(), offp(b, b.adj[17], b0 * net.b_stride_n7()), 17, b.val[16], 16, b.adj[15], 15,
-            1.0, 0.0, s, b.ex->keep[1] ? &k6 : nullptr, amax_adj(b, 17), vmax(b, 16), amax_adj(b, 15));
+        run_n(bs, 1, ex, net.b7c(), 17, 16, 15, 1.0, 0.0, s, ex.keep[1] ? &k6 : nullptr,
+              [&](const SideBufs& b, int) {
+                return Ops{offp(b, b.adj[17], b0 * net.b_stride_n7()), b.val[16], b.adj[15], amax_adj(b, 17),
+                           vmax(b, 16), amax_adj(b, 15)};
+              });
         if (need[13])
-          run(b, net.b5lc(), b.adj[15], 15, offp(b, b.val[14], b0 * net.b_stride_n4()), 14, b.adj[13], 13,
-              1.0, b0 == 0 ? 0.0 : 1.0, s, nullptr, amax_adj(b, 15), vmax(b, 14), amax_adj(b, 13));
+          run_n(bs, 1, ex, net.b5lc(), 15, 14, 13, 1.0, b0 == 0 ? 0.0 : 1.0, s, nullptr,
+                [&](const SideBufs& b, int) {
+                  return Ops{b.adj[15], offp(b, b.val[14], b0 * net.b_stride_n4()), b.adj[13], amax_adj(b, 15),
+                             vmax(b, 14), amax_adj(b, 13)};
+                });
         if (need[14])
-          run(b, net.b5rc(), b.val[13], 13, b.adj[15], 15, offp(b, b.adj[14], b0 * net.b_stride_n4()), 14,
-              1.0, 0.0, s, b.ex->keep[0] ? &k3 : nullptr, vmax(b, 13), amax_adj(b, 15), amax_adj(b, 14), b0 > 0);
+          run_n(bs, 1, ex, net.b5rc(), 13, 15, 14, 1.0, 0.0, s, ex.keep[0] ? &k3 : nullptr,
+                [&](const SideBufs& b, int) {
+                  return Ops{b.val[13], b.adj[15], offp(b, b.adj[14], b0 * net.b_stride_n4()), vmax(b, 13),
+                             amax_adj(b, 15), amax_adj(b, 14), b0 > 0};
+                });
       }
       continue;
     }
     const int l = SideNet::left(node), r = SideNet::right(node);
-    const double* dn = b.adj[node];
     for (int side = 0; side < 2; ++side) {
       const int c = side == 0 ? l : r;
       if (!need[c]) continue;
-      double* out;
       double alpha = 1.0, beta = 0.0;
       if (c == 0) {
-        out = op_out; alpha = alpha_op; beta = 1.0;
+        alpha = alpha_op; beta = 1.0;
       } else if (c < SideNet::NLEAF) {
-        out = (c == 1 || c == 3) ? du : dw; alpha = alpha_env; beta = 1.0;
-      } else {
-        out = b.adj[c];
+        alpha = alpha_env; beta = 1.0;
       }
+      auto out_of = [&](const SideBufs& b, int k) -> double* {
+        if (c == 0) return op_out[k];
+        if (c < SideNet::NLEAF) return (c == 1 || c == 3) ? du[k] : dw[k];
+        return b.adj[c];
+      };
       // the adjoint of node is internal (node id) unless node is the root (seed rho: external);
       // a leaf's adjoint goes to an external accumulator
       const int dn_id = node != SideNet::ROOT ? node : EXT;
       const int out_id = c >= SideNet::NLEAF ? c : EXT;
-      unsigned* dn_max = amax_adj(b, node);  // null for the root's (external) seed
-      unsigned* out_max = c >= SideNet::NLEAF ? amax_adj(b, c) : nullptr;
       if (side == 0)
-        run(b, net.bwd_left(node), dn, dn_id, value(b, r), r, out, out_id, alpha, beta, s, nullptr, dn_max,
-            vmax(b, r), out_max);
+        run_n(bs, nb, ex, net.bwd_left(node), dn_id, r, out_id, alpha, beta, s, nullptr,
+              [&](const SideBufs& b, int k) {
+                return Ops{b.adj[node], value(b, r), out_of(b, k), amax_adj(b, node), vmax(b, r),
+                           c >= SideNet::NLEAF ? amax_adj(b, c) : nullptr};
+              });
       else
-        run(b, net.bwd_right(node), value(b, l), l, dn, dn_id, out, out_id, alpha, beta, s, nullptr, vmax(b, l),
-            dn_max, out_max);
+        run_n(bs, nb, ex, net.bwd_right(node), l, dn_id, out_id, alpha, beta, s, nullptr,
+              [&](const SideBufs& b, int k) {
+                return Ops{value(b, l), b.adj[node], out_of(b, k), vmax(b, l), amax_adj(b, node),
+                           c >= SideNet::NLEAF ? amax_adj(b, c) : nullptr};
+              });
     }
   }
+}
+
+void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s) {
+  SideBufs* bs[1] = {&b};
+  side_prepare_n(net, bs, 1, *b.ex, s);
+}
+
+void side_forward(const SideNet& net, SideBufs& b, double* out, double alpha, double beta, cudaStream_t s) {
+  SideBufs* bs[1] = {&b};
+  double* o[1] = {out};
+  side_forward_n(net, bs, 1, *b.ex, out ? o : nullptr, alpha, beta, s);
+}
+
+void side_backward(const SideNet& net, SideBufs& b, bool need_op, double* op_out, double alpha_op,
+                   bool need_env, double* du, double* dw, double alpha_env, cudaStream_t s) {
+  SideBufs* bs[1] = {&b};
+  double* oo[1] = {op_out};
+  double* u[1] = {du};
+  double* w[1] = {dw};
+  side_backward_n(net, bs, 1, *b.ex, need_op, oo, alpha_op, need_env, u, w, alpha_env, s);
 }
 
 }  // namespace mera

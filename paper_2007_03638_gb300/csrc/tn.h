@@ -178,7 +178,14 @@ struct Keep {
   bool valid = false;
 };
 void contract(const GettCall& g, const Exec& ex, cudaStream_t s, const Keep* keep = nullptr);
-size_t tc_workspace_bytes(const GettCall& g, int prec);
+// The same plan for nb members (nb <= tc::TcEpilogue::MAXB) with different
+// data (gs[k] differ only in data pointers and maximum words; their tables
+// are equal): the tensor-core modes pack every member's operands and run one
+// product launch over all of them, each member's arithmetic being that of
+// contract(gs[k]); FP64 and complex products run member by member.
+void contract_batch(const GettCall* gs, int nb, const Exec& ex, cudaStream_t s);
+// Workspace a product needs (nb members batched).
+size_t tc_workspace_bytes(const GettCall& g, int prec, int nb = 1);
 // Bytes of the packed planes of one operand (side 1 = A, 2 = B) of g.
 size_t tc_keep_bytes(const GettCall& g, int prec, int side);
 // Keep-slot sizes the sliced chain of a SideNet needs (slot 0: N3, slot 1: N6).
@@ -199,6 +206,17 @@ struct SideBufs {
   // products that store those buffers (null: operands are reduced when packed)
   unsigned* amax = nullptr;
 };
+
+// Batched forms: the same network for nb members (one SideBufs each, equal
+// plans), every product one contract_batch over the members with the
+// workspace of ex; out, op_out, du, dw: one pointer per member.  A sliced
+// chain runs one member only.
+void side_prepare_n(const SideNet& net, SideBufs* const* bs, int nb, const Exec& ex, cudaStream_t s);
+void side_forward_n(const SideNet& net, SideBufs* const* bs, int nb, const Exec& ex, double* const* out,
+                    double alpha, double beta, cudaStream_t s);
+void side_backward_n(const SideNet& net, SideBufs* const* bs, int nb, const Exec& ex, bool need_op,
+                     double* const* op_out, double alpha_op, bool need_env, double* const* du, double* const* dw,
+                     double alpha_env, cudaStream_t s);
 
 // Subtrees that do not contain the operator leaf: N1, N4, N6, N9.
 void side_prepare(const SideNet& net, SideBufs& b, cudaStream_t s);

@@ -57,7 +57,7 @@ class RequestStatus(C.Structure):
     _fields_ = [("state", C.c_int), ("error", C.c_int), ("iters", C.c_int), ("n_evals", C.c_int),
                 ("energy", C.c_double), ("gnorm", C.c_double), ("t_submit", C.c_double),
                 ("t_admit", C.c_double), ("t_done", C.c_double), ("bytes", C.c_size_t),
-                ("message", C.c_char * 160), ("deferred", C.c_int)]
+                ("message", C.c_char * 160), ("deferred", C.c_int), ("batched_evals", C.c_int)]
 
 
 # device allocator callbacks of mera_set_allocator

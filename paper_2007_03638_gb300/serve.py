@@ -1,8 +1,9 @@
 """Serving many MERA optimisations on one GPU (binding of mera_server_*).
 
 ``Server`` wraps the library's native scheduler: requests are admitted by
-device footprint, each keeps its state on the device on its own stream, and
-worker threads interleave their iterations.  ``poisson_stream`` builds the
+device footprint, each keeps its state on the device on its own stream,
+worker threads interleave their iterations, and the energy/gradient
+evaluations of same-configuration requests run together as batched launches.  ``poisson_stream`` builds the
 seeded request stream of the serving workload (Ising with transverse field
 h ~ U[0.5, 1.5] or XXZ with Delta ~ U[0, 2], bond dimension drawn from a set,
 exponential inter-arrival gaps); ``run_stream`` replays it in real time and
@@ -115,7 +116,8 @@ def run_stream(reqs, budget_bytes, workers=4, gtol=1e-6, maxiter=100, timeout=36
     res = [sv.poll(i) for i in ids]
     sv.close()
     lat = [x["t_done"] - x["t_submit"] for x in res]
-    return _summary(lat, wall, [{k: x[k] for k in ("state", "iters", "energy", "gnorm", "error", "message")}
+    return _summary(lat, wall, [{k: x[k] for k in ("state", "iters", "energy", "gnorm", "error", "message",
+                                                    "batched_evals", "n_evals")}
                                 for x in res])
 
 

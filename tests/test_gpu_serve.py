@@ -18,14 +18,18 @@ def sv():
 
 
 def test_same_alone_and_in_the_mix(sv):
-    reqs = sv.poisson_stream(6, rate=200.0, chis=(4, 8), seed=3)
-    mixed = sv.run_stream(reqs, budget_bytes=8 << 30, workers=4, maxiter=12)
+    """Requests of the same bond dimension evaluate together (batched launches
+    over a cohort), the others overlap on their streams; every result equals
+    the request's result alone, bit for bit."""
+    reqs = sv.poisson_stream(8, rate=400.0, chis=(4, 8), seed=3)
+    mixed = sv.run_stream(reqs, budget_bytes=8 << 30, workers=8, maxiter=12)
     alone = sv.run_sequential(reqs, maxiter=12)
     for a, b in zip(mixed["results"], alone["results"]):
         assert a["state"] == 2
         assert a["iters"] == b["iters"]
-        assert abs(a["energy"] - b["energy"]) <= 1e-12 * max(1.0, abs(b["energy"]))
-        assert abs(a["gnorm"] - b["gnorm"]) <= 1e-10 * max(1.0, abs(b["gnorm"]))
+        assert a["energy"] == b["energy"]
+        assert a["gnorm"] == b["gnorm"]
+    assert sum(r["batched_evals"] for r in mixed["results"]) > 0
     assert mixed["p99_latency_s"] >= mixed["p50_latency_s"] > 0
 
 
