@@ -79,6 +79,9 @@ class _Mera:
     def launch_count(self):
         return 0
 
+    def close(self):
+        pass
+
 
 @pytest.fixture
 def fake_device(monkeypatch):
@@ -94,7 +97,13 @@ def fake_device(monkeypatch):
     monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
     empty = torch.empty
     monkeypatch.setattr(torch, "empty", lambda *a, device=None, **k: empty(*a, **k))
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
     monkeypatch.setattr(gm, "Mera", _Mera)
+    # the serving stream needs the native server: its summary is a stand-in here
+    monkeypatch.setattr(bench, "serve_measure", lambda n, chis, maxiter, workers, prec, seed: {
+        "metric": "serve solves/s", "value": 1.0, "unit": "solves/s", "p50_latency_s": 0.5, "p99_latency_s": 0.9,
+        "sequential": {"solves_per_s": 0.5}, "same_results_alone_and_mixed": True, "batched_evaluations": 3,
+        "deviation": "stand-in", "config": {"requests": n, "chis": list(chis)}})
 
 
 CONTRACT = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
@@ -136,3 +145,5 @@ def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
     for k in ("sm_mhz", "sm_max_mhz", "reasons"):
         assert k in line["clocks"], k
     assert line["memory"]["device_bytes"] == 3 * 2**30 and line["memory"]["footprint_bytes"] > 0
+    for k in ("value", "p50_latency_s", "p99_latency_s", "sequential", "same_results_alone_and_mixed", "deviation"):
+        assert k in line["serve"], k
