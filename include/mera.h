@@ -413,6 +413,14 @@ int mera_server_destroy(mera_server_t sv);
 int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const double* B, double* C,
               void* stream);
 
+/* Forget the Krylov warm starts: the next evaluation starts its
+ * scale-invariant solves (App. B) from the default guesses (rho = 1/chi^3,
+ * x = h_S) instead of the last solutions.  Evaluations from a fresh object,
+ * or after this call, at the same point are bit-identical (every reduction
+ * runs in a fixed order); warm-started ones agree to the Krylov tolerance.
+ * The paper has no counterpart of this entry point. */
+int mera_reset_warm_starts(mera_t m);
+
 /* Change the limit of the tensor-core kernel's pipeline waits of an
  * existing object (mera_config.device_wait_s; 0 < seconds <= 60, else
  * MERA_ERR_ARG).  When a wait expires the kernel stops issuing work, waits

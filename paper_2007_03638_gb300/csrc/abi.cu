@@ -437,6 +437,12 @@ size_t mera_footprint_bytes(const mera_config* cfg) {
 
 int64_t mera_launch_count(mera_t m) { return m ? m->prof.launches : 0; }
 
+int mera_reset_warm_starts(mera_t m) {
+  if (!m) return MERA_ERR_ARG;
+  m->have_rho = m->have_x = false;
+  return MERA_OK;
+}
+
 int mera_set_device_wait(mera_t m, double seconds) {
   if (!m || !(seconds > 0.0 && seconds <= 60.0)) return MERA_ERR_ARG;
   m->cfg.device_wait_s = seconds;

@@ -43,7 +43,7 @@ namespace {
 #define MERA_TC_PROMOTE_BF16 2
 #endif
 #ifndef MERA_TC_PROMOTE_F16
-#define MERA_TC_PROMOTE_F16 1
+#define MERA_TC_PROMOTE_F16 2
 #endif
 #ifndef MERA_TC_STAGES
 #define MERA_TC_STAGES 3
@@ -623,8 +623,10 @@ __device__ __forceinline__ float tf32_round(float x) {
 // Split 8 consecutive values of one plane row into hi/lo and write them as
 // one 16-byte (BF16, FP16) or 32-byte (TF32) piece per plane; i = row * Kp + k,
 // k a multiple of 8.  FP16: the values are multiplied by 2^e first (exact).
-template <int KIND, typename T>
-__device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo, int64_t i, int e) {
+// The values arrive as floats (an FP64 source is rounded once, to 24 bits:
+// the two planes keep at most 22 of them), so the split is FP32 arithmetic.
+template <int KIND>
+__device__ __forceinline__ void store_split8(const float (&v)[8], void* hi, void* lo, int64_t i, int e) {
   if (KIND == KIND_F16) {
     uint32_t h2[4], l2[4];
 #pragma unroll
@@ -632,15 +634,9 @@ __device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo
       __half hh[2], ll[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        if (sizeof(T) == 8) {
-          const double y = ldexp((double)v[2 * j + t], e);
-          hh[t] = __double2half(y);
-          ll[t] = __double2half(y - (double)__half2float(hh[t]));
-        } else {
-          const float y = ldexpf((float)v[2 * j + t], e);
-          hh[t] = __float2half_rn(y);
-          ll[t] = __float2half_rn(y - __half2float(hh[t]));
-        }
+        const float y = ldexpf(v[2 * j + t], e);
+        hh[t] = __float2half_rn(y);
+        ll[t] = __float2half_rn(y - __half2float(hh[t]));
       }
       h2[j] = (uint32_t)__half_as_ushort(hh[0]) | ((uint32_t)__half_as_ushort(hh[1]) << 16);
       l2[j] = (uint32_t)__half_as_ushort(ll[0]) | ((uint32_t)__half_as_ushort(ll[1]) << 16);
@@ -651,8 +647,8 @@ __device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo
     float h[8], l[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      h[j] = tf32_round((float)v[j]);
-      l[j] = tf32_round((float)(v[j] - (T)h[j]));
+      h[j] = tf32_round(v[j]);
+      l[j] = tf32_round(v[j] - h[j]);
     }
     float4* ph = reinterpret_cast<float4*>(static_cast<float*>(hi) + i);
     float4* pl = reinterpret_cast<float4*>(static_cast<float*>(lo) + i);
@@ -664,9 +660,9 @@ __device__ __forceinline__ void store_split8(const T (&v)[8], void* hi, void* lo
     uint32_t h2[4], l2[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const __nv_bfloat16 a = __float2bfloat16_rn((float)v[2 * j]), b = __float2bfloat16_rn((float)v[2 * j + 1]);
-      const __nv_bfloat16 la = __float2bfloat16_rn((float)(v[2 * j] - (T)__bfloat162float(a)));
-      const __nv_bfloat16 lb = __float2bfloat16_rn((float)(v[2 * j + 1] - (T)__bfloat162float(b)));
+      const __nv_bfloat16 a = __float2bfloat16_rn(v[2 * j]), b = __float2bfloat16_rn(v[2 * j + 1]);
+      const __nv_bfloat16 la = __float2bfloat16_rn(v[2 * j] - __bfloat162float(a));
+      const __nv_bfloat16 lb = __float2bfloat16_rn(v[2 * j + 1] - __bfloat162float(b));
       h2[j] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
       l2[j] = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
     }
@@ -688,9 +684,9 @@ __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __
   const int64_t k0 = ((int64_t)blockIdx.y * 32 + threadIdx.x) * 8;
   if (r >= Rp || k0 >= Kp) return;
   const int e = KIND == KIND_F16 ? f16_scale_exp(*amax) : 0;
-  Src v[8];
+  float v[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = (Src)0;
+  for (int j = 0; j < 8; ++j) v[j] = 0.f;
   if (r < R) {
     const int64_t roff = rt ? rt[r] : r * rs;
     constexpr int VW = 16 / sizeof(Src);  // elements per 16-byte load
@@ -700,17 +696,17 @@ __global__ void pack_split_kernel(const Src* __restrict__ src, const int64_t* __
       for (int j = 0; j < 8; j += VW) {
         if (sizeof(Src) == 4) {
           const float4 q = *reinterpret_cast<const float4*>(p + j);
-          v[j] = (Src)q.x; v[j + 1] = (Src)q.y; v[j + 2] = (Src)q.z; v[j + 3] = (Src)q.w;
+          v[j] = q.x; v[j + 1] = q.y; v[j + 2] = q.z; v[j + 3] = q.w;
         } else {
           const double2 q = *reinterpret_cast<const double2*>(p + j);
-          v[j] = (Src)q.x; v[j + 1] = (Src)q.y;
+          v[j] = (float)q.x; v[j + 1] = (float)q.y;
         }
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int64_t k = k0 + j;
-        if (k < K) v[j] = src[roff + (kt ? kt[k] : k * ks)];
+        if (k < K) v[j] = (float)src[roff + (kt ? kt[k] : k * ks)];
       }
     }
   }
@@ -725,7 +721,7 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
                                         int64_t rs, const int64_t* __restrict__ kt, int64_t ks, int64_t R,
                                         int64_t K, int64_t Rp, int64_t Kp, void* hi, void* lo,
                                         const unsigned* amax) {
-  __shared__ Src tile[64][65];  // [k][r]
+  __shared__ float tile[64][65];  // [k][r], converted to float on load
   __shared__ int64_t roffs[64];
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
@@ -740,7 +736,7 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
 #pragma unroll 4
     for (int kl = t >> 6; kl < 64; kl += 4) {
       const int64_t k = k0 + kl;
-      tile[kl][rl] = (roff >= 0 && k < K) ? src[roff + (kt ? kt[k] : k * ks)] : (Src)0;
+      tile[kl][rl] = (roff >= 0 && k < K) ? (float)src[roff + (kt ? kt[k] : k * ks)] : 0.f;
     }
   }
   __syncthreads();
@@ -752,7 +748,7 @@ __global__ void pack_split_tiled_kernel(const Src* __restrict__ src, const int64
   for (int h = 0; h < 2; ++h) {
     const int64_t k = k0 + kc + 8 * h;
     if (k >= Kp) break;
-    Src v[8];
+    float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = tile[kc + 8 * h + j][rl];
     store_split8<KIND>(v, hi, lo, r * Kp + k, e);

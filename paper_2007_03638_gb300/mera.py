@@ -115,7 +115,7 @@ EXPORTS = ["mera_config_default", "mera_create", "mera_destroy", "mera_num_tenso
            "mera_lbfgs_step", "mera_cg_step", "mera_gd_step", "mera_ev_sweep", "mera_solve", "mera_footprint_bytes",
            "mera_launch_count", "mera_get_stats", "mera_profile", "mera_profile_dump", "mera_dots_noalloc",
            "mera_gemm", "mera_strerror", "mera_last_error", "mera_server_create", "mera_set_device_wait",
-           "mera_set_allocator",
+           "mera_set_allocator", "mera_reset_warm_starts",
            "mera_server_submit", "mera_server_poll", "mera_server_wait", "mera_server_destroy"]
 
 _lib = None
@@ -167,6 +167,7 @@ def load(path: str = LIB_PATH):
         "mera_server_wait": (C.c_int, [C.c_void_p, C.c_double]),
         "mera_server_destroy": (C.c_int, [C.c_void_p]),
         "mera_set_device_wait": (C.c_int, [C.c_void_p, C.c_double]),
+        "mera_reset_warm_starts": (C.c_int, [C.c_void_p]),
         "mera_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
         "mera_strerror": (C.c_char_p, [C.c_int]),
         "mera_last_error": (C.c_char_p, [C.c_void_p]),
@@ -329,6 +330,10 @@ class Mera:
         self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype),
                                             _ptrs(D, keep, self.dtype) if deriv else None))
         return (e.value, G, D) if deriv else (e.value, G)
+
+    def reset_warm_starts(self):
+        """Next evaluation starts its Krylov solves afresh (mera_reset_warm_starts)."""
+        self._check(self.L.mera_reset_warm_starts(self.h))
 
     def set_device_wait(self, seconds):
         """Limit of each tensor-core pipeline wait (mera_set_device_wait)."""

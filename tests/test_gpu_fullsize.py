@@ -4,9 +4,9 @@ bench.py times), checked
 through properties that hold at any size, since the oracle cannot evaluate a
 chi = 32 network:
 
-* repeatability: two evaluations at the same point give bit-identical energy and
-  gradient (every reduction runs in a fixed order; split-K slices must not
-  race);
+* repeatability: two evaluations at the same point from the same (reset)
+  Krylov starting guesses give bit-identical energy and gradient (every
+  reduction runs in a fixed order; split-K slices must not race);
 * tangency: W^dag G = 0 for the Grassmann isometries, W^dag G skew for the
   disentanglers (Eqs. stiefel_gradient, grassmann_gradient);
 * the variational bound: the energy per spin lies above the exact ground-state
@@ -45,11 +45,16 @@ def problem(request):
 
 def test_fullsize_properties(problem):
     m, point = problem
+    m.reset_warm_starts()
     e0, G = m.energy_grad()
+    m.reset_warm_starts()
     e1, G1 = m.energy_grad()
     assert e0 == e1
     for a, b in zip(G, G1):
         assert np.array_equal(a, b)
+    # a warm-started evaluation agrees to the Krylov tolerance
+    e2, _ = m.energy_grad()
+    assert abs(e2 - e0) <= 1e-7 * max(1.0, abs(e0))
     gn = np.sqrt(sum(float(np.sum(g * g)) for g in G))
     assert np.isfinite(gn) and gn > 0
     for i, (W, g) in enumerate(zip(point, G)):
