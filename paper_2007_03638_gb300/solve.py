@@ -90,9 +90,21 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
             break
     summary = {"summary": True, "model": model, "param": par, "network": network, "z2": z2, "chi": chi,
                "n_trans": n_trans,
-               "prec": ["fp64", "3xtf32", "split_bf16"][prec], "method": ["lbfgs", "cg", "ev", "gd"][method],
+               "prec": ["fp64", "3xtf32", "split_bf16", "split_fp16"][prec],
+               "method": ["lbfgs", "cg", "ev", "gd"][method],
                "iters": rec["iter"], "energy_per_spin": rec["energy_per_spin"], "exact": ex,
                "error": rec["error"], "gnorm": rec["gnorm"], "evals": evals, "time_s": rec["time_s"]}
+    if prec != 0:
+        # the point the mixed-precision run reached, evaluated in FP64
+        final = m.get_tensors()
+        cfg64 = gm.default_config(d_b, chi, 0 if network == "mps" else n_trans, prec=0, lbfgs_m=lbfgs_m,
+                                  krylov_dim=krylov_dim, network=net, z2=int(z2))
+        m64 = gm.Mera(cfg64, h3)
+        m64.set_tensors(final)
+        e64, g64 = m64.energy_grad()
+        summary["energy_per_spin_fp64"] = e64 / spins
+        summary["gnorm_fp64"] = float(np.sqrt(sum(float(np.vdot(g, g).real) for g in g64)))
+        m64.close()
     out(json.dumps(summary))
     m.close()
     return summary
@@ -105,7 +117,7 @@ def main():
     ap.add_argument("--delta", type=float, default=1.0, help="XXZ anisotropy")
     ap.add_argument("--chi", type=int, default=4)
     ap.add_argument("--n-trans", type=int, default=2)
-    ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16")
+    ap.add_argument("--prec", type=int, default=0, help="0 FP64, 1 3xTF32, 2 split-BF16, 3 scaled split-FP16")
     ap.add_argument("--method", default="lbfgs", choices=["lbfgs", "cg", "ev", "gd"])
     ap.add_argument("--network", default="binary", choices=["binary", "ternary", "mps"])
     ap.add_argument("--z2", action="store_true",
