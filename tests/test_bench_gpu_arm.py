@@ -99,6 +99,9 @@ def fake_device(monkeypatch):
     monkeypatch.setattr(torch, "empty", lambda *a, device=None, **k: empty(*a, **k))
     monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
     monkeypatch.setattr(gm, "Mera", _Mera)
+    # the oracle comparison evaluates on the GPU: a stand-in here
+    monkeypatch.setattr(bench, "accuracy_probe", lambda gm_, prec, seed=0: {
+        "energy_abs_error": 1e-7, "energy_rel_error": 1e-7, "deriv_rel_error_max": 1e-5})
     # the serving stream needs the native server: its summary is a stand-in here
     monkeypatch.setattr(bench, "serve_measure", lambda n, chis, maxiter, workers, prec, seed: {
         "metric": "serve solves/s", "value": 1.0, "unit": "solves/s", "p50_latency_s": 0.5, "p99_latency_s": 0.9,
@@ -110,7 +113,8 @@ CONTRACT = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step
             "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks")
 
 
-@pytest.mark.parametrize("workload", ["ising_chi4_L2_fp64", "ising_chi12_L3_bf16", "ternary_ising_chi8_L2_fp64_z2",
+@pytest.mark.parametrize("workload", ["ising_chi4_L2_fp64", "ising_chi12_L3_bf16", "ising_chi12_L3_fp16",
+                                      "ternary_ising_chi8_L2_fp64_z2",
                                       "mps_xxz_D32_fp64", "ising_hz_chi8_L3_c128_fp64",
                                       "ising_chi16_L3_3xtf32_z2"])
 def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
@@ -147,3 +151,4 @@ def test_gpu_arm_line(fake_device, monkeypatch, capsys, workload):
     assert line["memory"]["device_bytes"] == 3 * 2**30 and line["memory"]["footprint_bytes"] > 0
     for k in ("value", "p50_latency_s", "p99_latency_s", "sequential", "same_results_alone_and_mixed", "deviation"):
         assert k in line["serve"], k
+    assert ("accuracy_vs_oracle" in line) == (bench.WORKLOADS[workload][4] != 0)
