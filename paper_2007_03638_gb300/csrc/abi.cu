@@ -544,7 +544,7 @@ int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const 
     const int64_t Mp = mera::tc::round_up(std::max<int64_t>(M, 1), 128), Np = mera::tc::round_up(std::max<int64_t>(N, 1), 128);
     mera::DevBuf ah(elem * Mp * Kp), al(elem * Mp * Kp), bh(elem * Np * Kp), bl(elem * Np * Kp), err(sizeof(int));
     const size_t skb = mera::tc::splitk_bytes(M, N, Kp, kind);
-    mera::DevBuf part(skb), amax(2 * sizeof(unsigned));
+    mera::DevBuf part(skb), amax(2 * sizeof(unsigned)), ctr(sizeof(unsigned long long));
     unsigned* am = amax.as<unsigned>();
     MERA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     mera::tc::pack_split(A, true, nullptr, K, nullptr, 1, M, K, Mp, Kp, kind, ah.p, al.p, false, s, am);
@@ -560,6 +560,7 @@ int mera_gemm(int prec, int64_t M, int64_t N, int64_t K, const double* A, const 
     ep.cns = 1;
     ep.rows = N == 1;
     ep.err = err.as<int>();
+    ep.work_ctr = ctr.as<unsigned long long>();
     mera::tc::gemm_packed(kind, M, N, Kp, ah.p, al.p, Mp, bh.p, bl.p, Np, ep, s, part.as<float>(), skb);
     int e = 0;
     MERA_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));

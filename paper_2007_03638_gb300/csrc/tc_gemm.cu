@@ -94,6 +94,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// mbar_wait that also gives up (false) as soon as *abort is set
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                                   const int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  const uint32_t every = limit_ns < 100000ull ? 0u : 255u;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (*(volatile const int*)abort) return false;
+    if ((it & every) == 0 && gtimer() - t0 > limit_ns) return false;
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
@@ -150,10 +166,14 @@ __host__ __device__ constexpr uint32_t idesc() {
 }
 
 constexpr int NACC = 4;  // tensor-memory accumulator buffers (4 x 128 columns)
+constexpr int IRING = 8; // work items published ahead by the producer
 
 struct Smem {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
+  uint64_t item_full[IRING];   // the producer published item[i]
+  uint64_t item_empty[IRING];  // the MMA issuer and every epilogue warp have read it
+  int64_t item[IRING];         // work item index, -1 = no more work
   uint64_t acc_full[NACC];
   uint64_t acc_empty[NACC];
   uint64_t drain;  // MMA completion after an abort
@@ -161,9 +181,14 @@ struct Smem {
   int abort;
 };
 
-// Persistent kernel, one CTA per SM walking output tiles with a static
-// stride; every CTA loads its own operand tiles (CTAs working at the same
-// time on neighbouring tiles share the long operand through L2).  Warp
+// Persistent kernel, one CTA per SM.  Work items (member, K slice, output
+// tile) are handed out in order by a device counter (ep.work_ctr; without
+// one, CTA c takes items c, c + grid, ...): CTAs that read the same operand
+// tiles get consecutive items and start them together, so the tiles they
+// share are still in L2 when the last of them reads them, however unevenly
+// the CTAs progressed on earlier items.  Every CTA loads its own operand tiles.  The producer
+// warp takes the items and passes their indices to the MMA issuer and the
+// epilogue warps through a small ring in shared memory.  Warp
 // roles (320 threads): warp 0 TMA producer, warp 1 MMA issuer, warps 2..9 fold and store (warp w reads TMEM lanes
 // 32*(w%4)..+31 = its rows, columns 64*((w-2)/4)..+63 of the accumulator).
 // The shared-memory ring, the tensor-memory accumulator ring and their
@@ -231,6 +256,10 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       mbar_init(&S->acc_full[b], 1);
       mbar_init(&S->acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
     }
+    for (int i = 0; i < IRING; ++i) {
+      mbar_init(&S->item_full[i], 1);
+      mbar_init(&S->item_empty[i], 1 + EPI_WARPS);
+    }
     mbar_init(&S->drain, 1);
     S->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -250,9 +279,23 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
     if (lane == 0) {
       for (const CUtensorMap* mp : {&a_hi, &a_lo, &b_hi, &b_lo})
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(mp)) : "memory");
-      int64_t kbg = 0;
+      int64_t kbg = 0, nit = 0;
       bool stop = false;
-      for (int64_t t = cid; t < ntiles && !stop; t += ncl) {
+      int64_t t = ep.work_ctr ? (int64_t)atomicAdd(ep.work_ctr, 1ull) : cid;
+      for (;;) {
+        // publish item t (or the end of the work) to the MMA issuer and the epilogue
+        const int sl = (int)(nit % IRING);
+        if (nit >= IRING &&
+            !mbar_wait_or_abort(&S->item_empty[sl], (uint32_t)((nit / IRING) - 1) & 1, ep.wait_ns, &S->abort)) {
+          atomicExch(&S->abort, 1);
+          break;
+        }
+        S->item[sl] = t < ntiles ? t : -1;
+        mbar_arrive(&S->item_full[sl]);
+        ++nit;
+        if (t >= ntiles) break;
+        // the next item, taken now so that the counter's latency hides behind this item's loads
+        const int64_t tn = ep.work_ctr ? (int64_t)atomicAdd(ep.work_ctr, 1ull) : t + ncl;
         int64_t m0l, n0l;
         tile_of(t % nt1, m0l, n0l);
         const int64_t mb = t / per_member;  // member
@@ -276,14 +319,25 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           tma_load_2d(&b_lo, &S->full[s], st + 2 * A_BYTES + B_BYTES, kx, n0);
           issued_loads = kbg + 1;
         }
+        if (stop) break;
+        t = tn;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t ID = idesc<KIND, BN>();
-      int64_t kbg = 0, gg = 0;
+      int64_t kbg = 0, gg = 0, nit = 0;
       bool stop = false;
-      for (int64_t t = cid; t < ntiles && !stop; t += ncl) {
+      while (!stop) {
+        const int sl = (int)(nit % IRING);
+        if (!mbar_wait_or_abort(&S->item_full[sl], (uint32_t)(nit / IRING) & 1, ep.wait_ns, &S->abort)) {
+          atomicExch(&S->abort, 1);
+          break;
+        }
+        const int64_t t = *(volatile int64_t*)&S->item[sl];
+        mbar_arrive(&S->item_empty[sl]);
+        ++nit;
+        if (t < 0) break;
         int klo, khi;
         krange(t, klo, khi);
         for (int kb = klo; kb < khi; ++kb, ++kbg) {
@@ -348,7 +402,18 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
       if (lane == 0 && m) atomicMax(ep.member_cmax[mb], m);
       smax = 0.f;
     };
-    for (int64_t t = cid; t < ntiles && ok; t += ncl) {
+    int64_t nit = 0;
+    while (ok) {
+      const int sl = (int)(nit % IRING);
+      if (!mbar_wait_or_abort(&S->item_full[sl], (uint32_t)(nit / IRING) & 1, ep.wait_ns, &S->abort)) {
+        ok = false;
+        break;
+      }
+      const int64_t t = *(volatile int64_t*)&S->item[sl];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S->item_empty[sl]);
+      ++nit;
+      if (t < 0) break;
       const int64_t mb = t / per_member;
       if (mb != cur) {
         flush_max(cur);
@@ -769,6 +834,7 @@ __global__ void amax_kernel(const Src* __restrict__ src, const int64_t* __restri
   const int64_t F = rows_fast ? R : K, S = rows_fast ? K : R;
   for (int64_t j = blockIdx.y; j < S; j += gridDim.y) {
     const int64_t so = rows_fast ? (kt ? kt[j] : j * ks) : (rt ? rt[j] : j * rs);
+#pragma unroll 4
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F; i += (int64_t)gridDim.x * blockDim.x) {
       const int64_t fo = rows_fast ? (rt ? rt[i] : i * rs) : (kt ? kt[i] : i * ks);
       const unsigned b = __float_as_uint(fabsf((float)src[so + fo]));
@@ -969,14 +1035,23 @@ void pack_split(const void* src, bool src_f64, const int64_t* rt, int64_t rs, co
 }
 
 namespace {
+// which products take their work items from the device counter (compile-time
+// tuning): 2 every product, 1 split-K products only, 0 none.  Measured at
+// chi = 32: the counter lifts the split-K Gram products from 198 to 243
+// TFLOP/s and slows the short-K products with many tiles by 7%, so 1.
+#ifndef MERA_TC_COUNTER
+#define MERA_TC_COUNTER 1
+#endif
 #ifndef MERA_TC_SPLITK_MAX
-#define MERA_TC_SPLITK_MAX 32
+#define MERA_TC_SPLITK_MAX 64
 #endif
 constexpr int SPLITK_MAX = MERA_TC_SPLITK_MAX;
 // Number of K slices for an M x N x Kp product.  Only products whose output
 // tiles cover less than half of the GPU split; each slice keeps >= 16 K
-// blocks.  Among the admissible counts the one whose work items fill the
-// SMs' last wave best is taken (the smallest of equally good ones).
+// blocks.  Long K is cut into slices of about 128 K blocks (at most
+// SPLITK_MAX), so that the CTAs sharing an operand tile (consecutive items)
+// stay close in time; from there, the count whose work items fill the SMs'
+// last wave best is taken (the smallest of equally good ones).
 int choose_split(int64_t M, int64_t N, int64_t Kp, int kind) {
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + 127) / 128);
   const int64_t kblocks = Kp / (KB_BYTES / (kind == KIND_TF32 ? 4 : 2));
@@ -985,9 +1060,10 @@ int choose_split(int64_t M, int64_t N, int64_t Kp, int kind) {
   const int64_t lo = (nsm + tiles - 1) / tiles;  // at least one wave
   const int64_t hi = std::min<int64_t>((int64_t)SPLITK_MAX, kblocks / 16);
   if (hi <= 1) return 1;
-  int64_t best = std::min(lo, hi);
+  const int64_t from = std::min(std::max(lo, kblocks / 128), hi);
+  int64_t best = from;
   double best_eff = 0.0;
-  for (int64_t sp = std::min(lo, hi); sp <= hi; ++sp) {
+  for (int64_t sp = from; sp <= hi; ++sp) {
     const int64_t items = tiles * sp, waves = (items + nsm - 1) / nsm;
     const double eff = (double)items / (double)(waves * nsm);
     if (eff > best_eff + 1e-9) {
@@ -1085,6 +1161,8 @@ int gemm_packed(int kind, int64_t M, int64_t N, int64_t Kp, const void* a_hi, co
   const CUtensorMap ah = make_map(a_hi, nb * Mp, Kp, kind, BM), al = make_map(a_lo, nb * Mp, Kp, kind, BM);
   const CUtensorMap bh = make_map(b_hi, nb * Np, Kp, kind, bn), bl = make_map(b_lo, nb * Np, Kp, kind, bn);
   const int64_t items = nb * mt * nt * run.ksplit;
+  if (MERA_TC_COUNTER == 0 || (MERA_TC_COUNTER == 1 && run.ksplit == 1)) run.work_ctr = nullptr;
+  if (run.work_ctr) MERA_CUDA(cudaMemsetAsync(run.work_ctr, 0, sizeof(unsigned long long), s));
   if (kind == KIND_TF32)
     launch<KIND_TF32, 128>(ah, al, bh, bl, run, items, s);
   else if (kind == KIND_BF16)

@@ -59,6 +59,10 @@ struct TcEpilogue {
   // the float bits; split-K: by the reduction kernel)
   unsigned* c_amax = nullptr;
   uint64_t wait_ns = 1000000000ull;  // limit of each pipeline wait (default 1 s)
+  // 8 bytes of device memory (zeroed by gemm_packed before the launch) from
+  // which the CTAs take their work items in order; null: CTA c takes items
+  // c, c + grid, ...  The items' arithmetic is the same either way.
+  unsigned long long* work_ctr = nullptr;
   // split K (set by gemm_packed): ksplit slices of kbs K blocks, slice s
   // writing a plain row-major partial at C + s * split_stride
   int ksplit = 1, kbs = 0;

@@ -195,6 +195,26 @@ HostPlan host_plan(const TDesc& A, const TDesc& B, const TDesc& C, int q) {
     }
   for (int l : A.legs)
     if (C.find(l) < 0 && B.find(l) < 0) throw Error(MERA_ERR_ARG, "make_plan: dangling leg in A");
+  // where is each operand's stride-1 leg?
+  auto fast_leg = [](const TDesc& t) {
+    int best = -1;
+    for (size_t j = 0; j < t.legs.size(); ++j)
+      if (t.ext[j] > 1 && (best < 0 || t.stride[j] < t.stride[best])) best = (int)j;
+    return best < 0 ? -1 : t.legs[best];
+  };
+  const int fa = fast_leg(A), fb = fast_leg(B);
+  {
+    // K is summed, so its enumeration order is free (both operands' tables
+    // follow it): the larger operand whose stride-1 leg is summed gets that
+    // leg innermost, so that its packing reads consecutive k along memory
+    const bool fa_k = std::find(K.begin(), K.end(), fa) != K.end();
+    const bool fb_k = std::find(K.begin(), K.end(), fb) != K.end();
+    const int pick = fa_k && fb_k ? (A.size() >= B.size() ? fa : fb) : fa_k ? fa : fb_k ? fb : -1;
+    if (pick >= 0) {
+      K.erase(std::find(K.begin(), K.end(), pick));
+      K.push_back(pick);
+    }
+  }
   HostPlan h;
   auto grp = [&](const TDesc& t, const std::vector<int>& legs) {
     return q < 0 ? dense_group(t, legs) : sector_group(t, legs, q);
@@ -212,14 +232,7 @@ HostPlan host_plan(const TDesc& A, const TDesc& B, const TDesc& C, int q) {
   h.K = h.ak.count;
   if (q >= 0 && h.M > 0 && h.N > 0 && h.K == 0)
     throw Error(MERA_ERR_UNSUPPORTED, "make_plan: a charge sector with outputs but no summed index");
-  // orientation hints for operand packing: where is each operand's stride-1 leg?
-  auto fast_leg = [](const TDesc& t) {
-    int best = -1;
-    for (size_t j = 0; j < t.legs.size(); ++j)
-      if (t.ext[j] > 1 && (best < 0 || t.stride[j] < t.stride[best])) best = (int)j;
-    return best < 0 ? -1 : t.legs[best];
-  };
-  const int fa = fast_leg(A), fb = fast_leg(B);
+  // orientation hints for operand packing
   h.a_rfast = std::find(M.begin(), M.end(), fa) != M.end();
   h.b_rfast = std::find(N.begin(), N.end(), fb) != N.end();
   set_hints(h, offsets_of(h.cm), offsets_of(h.cn));
@@ -546,6 +559,7 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   char* w = static_cast<char*>(ex.ws);
   unsigned* amax_a = reinterpret_cast<unsigned*>(w);  // maxima of the operands (FP16 planes)
   unsigned* amax_b = amax_a + 1;
+  // byte 128: the product's work-item counter
   size_t o = 1024;
   void* ah = w + o; o = align(o + elem * Mp * Kp);
   void* al = w + o; o = align(o + elem * Mp * Kp);
@@ -615,6 +629,7 @@ void contract(const GettCall& g0, const Exec& ex, cudaStream_t s, const Keep* ke
   ep.vec = g.c_vec;
   ep.err = ex.err;
   ep.wait_ns = ex.wait_ns;
+  ep.work_ctr = reinterpret_cast<unsigned long long*>(w + 128);
   if (kind == tc::KIND_F16) {
     ep.a_amax = known_a ? known_a : amax_a;
     ep.b_amax = known_b ? known_b : amax_b;
@@ -658,7 +673,7 @@ void contract_batch(const GettCall* gs, int nb, const Exec& ex, cudaStream_t s) 
   if (tc_workspace_bytes(h, ex.prec, nb) > ex.ws_bytes) throw Error(MERA_ERR_ARG, "contract_batch: workspace too small");
   auto align = [](size_t o) { return (o + 1023) & ~size_t(1023); };
   char* w = static_cast<char*>(ex.ws);
-  unsigned* amax = reinterpret_cast<unsigned*>(w);  // member b: words 2b (A), 2b + 1 (B)
+  unsigned* amax = reinterpret_cast<unsigned*>(w);  // member b: words 2b (A), 2b + 1 (B); byte 128: work counter
   size_t o = 1024;
   char* ah = w + o; o = align(o + elem * nb * Mp * Kp);
   char* al = w + o; o = align(o + elem * nb * Mp * Kp);
@@ -702,6 +717,7 @@ void contract_batch(const GettCall* gs, int nb, const Exec& ex, cudaStream_t s) 
   ep.vec = h.c_vec;
   ep.err = ex.err;
   ep.wait_ns = ex.wait_ns;
+  ep.work_ctr = reinterpret_cast<unsigned long long*>(w + 128);
   const int64_t pair = pr ? pr->begin(h.M, h.N, h.K, s) : -1;
   const int path = tc::gemm_packed(kind, h.M, h.N, Kp, ah, al, Mp, bh, bl, Np, ep, s, part, part_bytes);
   if (pr) {

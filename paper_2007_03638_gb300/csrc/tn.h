@@ -64,7 +64,8 @@ std::vector<int64_t> sector_offsets(const TDesc& t, const std::vector<int>& legs
 
 // The index bookkeeping of one contraction on the host, before upload.
 // Groups: M = legs of C from A, N = legs of C from B (in C's order), K = legs
-// shared by A and B (in B's order).  A group is addressed by a table of
+// shared by A and B (in B's order, except that the stride-1 leg of the larger
+// operand that sums its stride-1 leg moves innermost).  A group is addressed by a table of
 // offsets, or (affine) by index * stride.  q < 0: the dense contraction
 // (affine groups detected); q = 0 or 1: the Z2 charge sector q, in which every
 // group keeps its tuples of charge q (always tables).  For Z2-symmetric A and
