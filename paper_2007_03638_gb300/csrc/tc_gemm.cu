@@ -36,8 +36,19 @@ namespace mera {
 namespace tc {
 namespace {
 
+// compile-time tuning: bytes of K per pipeline stage row (128: 128-byte
+// swizzle, 64 KB stages; 64: 64-byte swizzle, 32 KB stages), the stage
+// count, and the 128-byte K blocks per folded accumulator group.  Measured
+// at chi = 32: six 32 KB stages run the large products 20% and the split-K
+// Gram products 50% slower than three 64 KB stages, so 128.
+#ifndef MERA_TC_KB_BYTES
+#define MERA_TC_KB_BYTES 128
+#endif
+#ifndef MERA_TC_STAGES
+#define MERA_TC_STAGES (MERA_TC_KB_BYTES == 64 ? 6 : 3)
+#endif
 #ifndef MERA_TC_PROMOTE_TF32
-#define MERA_TC_PROMOTE_TF32 1   // K blocks per folded accumulator group (compile-time tuning)
+#define MERA_TC_PROMOTE_TF32 1
 #endif
 #ifndef MERA_TC_PROMOTE_BF16
 #define MERA_TC_PROMOTE_BF16 2
@@ -45,13 +56,11 @@ namespace {
 #ifndef MERA_TC_PROMOTE_F16
 #define MERA_TC_PROMOTE_F16 2
 #endif
-#ifndef MERA_TC_STAGES
-#define MERA_TC_STAGES 3
-#endif
 
 constexpr int BM = 128;
 constexpr int STAGES = MERA_TC_STAGES;
-constexpr int KB_BYTES = 128;               // K block = one 128-byte swizzle row
+constexpr int KB_BYTES = MERA_TC_KB_BYTES;  // K block = one swizzle row of every operand tile row
+static_assert(KB_BYTES == 64 || KB_BYTES == 128, "K block of 64 or 128 bytes");
 // limit of the waits that drain this CTA's own copies and MMAs after an
 // abort (they complete in microseconds; the limit only bounds a broken case)
 constexpr uint64_t DRAIN_NS = 1000000000ull;
@@ -118,15 +127,15 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* ba
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major tile with 128-byte swizzle, rows
-// of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major tile with KB_BYTES-byte swizzle,
+// rows of KB_BYTES bytes, 8-row groups 8 * KB_BYTES bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address
   d |= (uint64_t)(16 >> 4) << 16;                   // leading byte offset (unused with swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)((8 * KB_BYTES) >> 4) << 32;       // stride byte offset: 8 rows
   d |= (uint64_t)1 << 46;                           // descriptor version
-  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  d |= (uint64_t)(KB_BYTES == 128 ? 2 : 4) << 61;   // 128- or 64-byte swizzle
   return d;
 }
 
@@ -215,10 +224,12 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
   constexpr int KSTEPS = KB_BYTES / KSTEP_BYTES;
   constexpr uint32_t TMEM_COLS = NACC * BN;
   // K blocks accumulated in one tensor-memory buffer before it is folded:
-  // one for TF32 (the truncation error then stays near FP32 level), two for
-  // BF16 (its split error, ~1e-5, dominates the truncation of 128 products)
+  // 128 bytes of K for TF32 (the truncation error then stays near FP32
+  // level), 256 for BF16 (its split error, ~1e-5, dominates the truncation
+  // of 128 products) and FP16 (measured)
   constexpr int PROMOTE =
-      KIND == KIND_TF32 ? MERA_TC_PROMOTE_TF32 : (KIND == KIND_BF16 ? MERA_TC_PROMOTE_BF16 : MERA_TC_PROMOTE_F16);
+      (KIND == KIND_TF32 ? MERA_TC_PROMOTE_TF32 : (KIND == KIND_BF16 ? MERA_TC_PROMOTE_BF16 : MERA_TC_PROMOTE_F16)) *
+      (128 / KB_BYTES);
   constexpr int HC = BN / 2;               // columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -364,9 +375,9 @@ __global__ __launch_bounds__(NTHREADS, 1) void tc_gemm_kernel(const __grid_const
           for (int k = 0; k < KSTEPS; ++k) {
             const uint32_t off = k * KSTEP_BYTES;
             // small products first, the dominant one last
-            mma<KIND>(dt, sdesc_sw128(alo + off), sdesc_sw128(bhi + off), ID, (first && k == 0) ? 0u : 1u);
-            mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(blo + off), ID, 1u);
-            mma<KIND>(dt, sdesc_sw128(ahi + off), sdesc_sw128(bhi + off), ID, 1u);
+            mma<KIND>(dt, sdesc_sw(alo + off), sdesc_sw(bhi + off), ID, (first && k == 0) ? 0u : 1u);
+            mma<KIND>(dt, sdesc_sw(ahi + off), sdesc_sw(blo + off), ID, 1u);
+            mma<KIND>(dt, sdesc_sw(ahi + off), sdesc_sw(bhi + off), ID, 1u);
           }
           mma_commit(&S->empty[s]);
           if (last) {
@@ -924,7 +935,8 @@ CUtensorMap make_map(const void* ptr, int64_t rows, int64_t kp, int kind, int bo
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   CUresult r = g_encode(&m, dt, 2,
                         const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        KB_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(MERA_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return m;
@@ -974,7 +986,8 @@ void launch(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
 }  // namespace
 
 int64_t padded_k(int64_t K, int kind) {
-  const int64_t kb = KB_BYTES / (kind == KIND_TF32 ? 4 : 2);
+  // whole K blocks, and a multiple of 32 elements (the packing's unit)
+  const int64_t kb = std::max(KB_BYTES / (kind == KIND_TF32 ? 4 : 2), 32);
   return (K + kb - 1) / kb * kb;
 }
 
@@ -1048,13 +1061,14 @@ namespace {
 constexpr int SPLITK_MAX = MERA_TC_SPLITK_MAX;
 // Number of K slices for an M x N x Kp product.  Only products whose output
 // tiles cover less than half of the GPU split; each slice keeps >= 16 K
-// blocks.  Long K is cut into slices of about 128 K blocks (at most
+// blocks of 128 bytes.  Long K is cut into slices of about 128 (at most
 // SPLITK_MAX), so that the CTAs sharing an operand tile (consecutive items)
 // stay close in time; from there, the count whose work items fill the SMs'
 // last wave best is taken (the smallest of equally good ones).
 int choose_split(int64_t M, int64_t N, int64_t Kp, int kind) {
   const int64_t tiles = ((M + BM - 1) / BM) * ((N + 127) / 128);
-  const int64_t kblocks = Kp / (KB_BYTES / (kind == KIND_TF32 ? 4 : 2));
+  // counted in 128-byte K blocks whatever the pipeline's K block
+  const int64_t kblocks = Kp * (kind == KIND_TF32 ? 4 : 2) / 128;
   const int64_t nsm = 152;
   if (tiles * 2 > nsm || kblocks < 32) return 1;
   const int64_t lo = (nsm + tiles - 1) / tiles;  // at least one wave
