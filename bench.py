@@ -57,6 +57,7 @@ WORKLOADS = {
     "ising_chi12_L3_fp16": ("ising", 4, 12, 3, 3, {}),
     # the same with environment recomputation (one set of intermediates for all layers)
     "xxz_chi32_L3_bf16_recompute": ("xxz", 4, 32, 3, 2, {"lbfgs_m": 16, "krylov_dim": 4, "recompute_env": 1}),
+    "xxz_chi32_L3_fp16_recompute": ("xxz", 4, 32, 3, 3, {"lbfgs_m": 16, "krylov_dim": 4, "recompute_env": 1}),
     # extra config fields: network 1 = ternary, 2 = uniform MPS (chi = bond
     # dimension D); z2 = 1: Z2 charge sectors; dtype 1 = complex128
     "ternary_ising_chi8_L2_fp64": ("ising", 2, 8, 2, 0, {"network": 1}),
@@ -80,6 +81,7 @@ DEFAULT_WORKLOAD = "xxz_chi32_L3_fp16"
 # to express the reference arm's bounded sample in gradient evaluations.
 FLOPS_PER_GRAD = {
     "xxz_chi32_L3_bf16": 4.1e15, "xxz_chi32_L3_3xtf32": 4.1e15, "xxz_chi32_L3_bf16_recompute": 4.1e15,
+    "xxz_chi32_L3_fp16_recompute": 4.42e15,
     "xxz_chi32_L3_fp16": 4.42e15,
     "xxz_chi24_L3_3xtf32": 4.7e14, "xxz_chi24_L3_bf16": 4.7e14, "xxz_chi24_L3_fp16": 4.7e14,
     "xxz_chi16_L3_3xtf32": 1.45e13, "xxz_chi16_L3_bf16": 1.2e13, "xxz_chi16_L3_fp16": 1.2e13,
