@@ -174,6 +174,8 @@ std::string config_range_error(const mera_config& cfg);
 void bind_leaves(Layer& ly, int side, const double* op, const double* u, const double* w);
 // floor of the Krylov solves' relative residual in a precision mode
 double krylov_floor(int prec);
+// whether a GMRES cycle's residual estimate may end a solve (mixed modes)
+bool trust_estimate(int prec);
 // per-tensor density matrices of the preconditioner at the last evaluation
 void compute_rho_v(Ctx& c, Eval& E, const double* W, cudaStream_t s);
 

@@ -305,10 +305,15 @@ void gmres_group(Grp& g, std::vector<GmresMember>& st, Op op) {
             q.gv[j + 1] = -q.sn[j] * q.gv[j];
             q.gv[j] = q.cs[j] * q.gv[j];
             ++q.j;
-            if (std::fabs(q.gv[j + 1]) <= 0.5 * q.tol * q.bnorm || hn == 0.0 || q.apps >= q.maxit || q.j == m)
+            const bool est_ok = std::fabs(q.gv[j + 1]) <= 0.5 * q.tol * q.bnorm;
+            if (est_ok || hn == 0.0 || q.apps >= q.maxit || q.j == m) {
               finish_cycle(q, c, g.s);
-            else
+              // the mixed modes end on the estimate (trust_estimate); the
+              // group's device flag is checked when the solve returns
+              if (est_ok && trust_estimate(c.cfg.prec)) q.state = GmresMember::DONE;
+            } else {
               q.state = GmresMember::APPLY;
+            }
             return;
           }
           default:
