@@ -248,7 +248,20 @@ def _ptr(a, dtype=None):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
-def _ptrs(arrs, keep, dtype=np.float64):
+def _numel(a):
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _ptrs(arrs, keep, dtype=np.float64, sizes=None):
+    """ctypes array of the arrays' data pointers.  With ``sizes`` (elements
+    per array) the list must hold exactly that many arrays of those sizes:
+    the library reads and writes that many elements behind each pointer."""
+    if sizes is not None:
+        if len(arrs) != len(sizes):
+            raise ValueError(f"expected {len(sizes)} tensors, got {len(arrs)}")
+        for i, (a, n) in enumerate(zip(arrs, sizes)):
+            if _numel(a) != n:
+                raise ValueError(f"tensor {i} has {_numel(a)} elements, expected {n}")
     out = (C.c_void_p * len(arrs))()
     for i, a in enumerate(arrs):
         if isinstance(a, np.ndarray) and (a.dtype != dtype or not a.flags.c_contiguous):
@@ -266,6 +279,9 @@ class Mera:
         self.cfg = cfg
         self.dtype = np.dtype(np.complex128 if cfg.dtype == MERA_C128 else np.float64)
         h = np.ascontiguousarray(h3, dtype=self.dtype) if isinstance(h3, np.ndarray) else h3
+        n_op = int(cfg.d_b) ** (6 if cfg.network == MERA_BINARY else 4)  # three- or two-site term
+        if _numel(h) != n_op:
+            raise ValueError(f"the Hamiltonian term has {_numel(h)} elements, expected {n_op}")
         handle = C.c_void_p()
         if stream is None:
             try:
@@ -284,6 +300,7 @@ class Mera:
             r, c = C.c_int64(), C.c_int64()
             self.L.mera_tensor_shape(self.h, i, C.byref(r), C.byref(c))
             self.shapes.append((r.value, c.value))
+        self.sizes = [r * c for r, c in self.shapes]
 
     def _check(self, rc):
         if rc != 0:
@@ -310,7 +327,7 @@ class Mera:
     # ---- C ABI mirrors ------------------------------------------------------
     def set_tensors(self, tensors):
         keep = []
-        self._check(self.L.mera_set_tensors(self.h, _ptrs(tensors, keep, self.dtype)))
+        self._check(self.L.mera_set_tensors(self.h, _ptrs(tensors, keep, self.dtype, self.sizes)))
 
     def init_random(self, seed):
         """Seeded sign-fixed QR-of-Gaussian point (see mera_init_random in mera.h)."""
@@ -319,7 +336,7 @@ class Mera:
     def get_tensors(self, device=False):
         out = self._alloc(device)
         keep = []
-        self._check(self.L.mera_get_tensors(self.h, _ptrs(out, keep, self.dtype)))
+        self._check(self.L.mera_get_tensors(self.h, _ptrs(out, keep, self.dtype, self.sizes)))
         return out
 
     def energy_grad(self, device=False, deriv=False):
@@ -327,8 +344,8 @@ class Mera:
         G = self._alloc(device)
         keep = []
         D = self._alloc(device) if deriv else None
-        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype),
-                                            _ptrs(D, keep, self.dtype) if deriv else None))
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype, self.sizes),
+                                            _ptrs(D, keep, self.dtype, self.sizes) if deriv else None))
         return (e.value, G, D) if deriv else (e.value, G)
 
     def reset_warm_starts(self):
@@ -343,7 +360,7 @@ class Mera:
         """Energy, with the gradient written into the given arrays (host or device)."""
         e = C.c_double()
         keep = []
-        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype), None))
+        self._check(self.L.mera_energy_grad(self.h, C.byref(e), _ptrs(G, keep, self.dtype, self.sizes), None))
         return e.value
 
     def energy(self):
@@ -361,35 +378,35 @@ class Mera:
     def project(self, D, device=False):
         G = self._alloc(device)
         keep = []
-        self._check(self.L.mera_project(self.h, _ptrs(D, keep, self.dtype), _ptrs(G, keep, self.dtype)))
+        self._check(self.L.mera_project(self.h, _ptrs(D, keep, self.dtype, self.sizes), _ptrs(G, keep, self.dtype, self.sizes)))
         return G
 
     def inner(self, X, Y):
         out = C.c_double()
         keep = []
-        self._check(self.L.mera_inner(self.h, _ptrs(X, keep, self.dtype), _ptrs(Y, keep, self.dtype),
+        self._check(self.L.mera_inner(self.h, _ptrs(X, keep, self.dtype, self.sizes), _ptrs(Y, keep, self.dtype, self.sizes),
                                       C.byref(out)))
         return out.value
 
     def transport(self, X, alpha, Y):
         keep = []
         Yc = [np.array(y, dtype=self.dtype, copy=True) if isinstance(y, np.ndarray) else y.clone() for y in Y]
-        self._check(self.L.mera_transport(self.h, _ptrs(X, keep, self.dtype), float(alpha),
-                                          _ptrs(Yc, keep, self.dtype)))
+        self._check(self.L.mera_transport(self.h, _ptrs(X, keep, self.dtype, self.sizes), float(alpha),
+                                          _ptrs(Yc, keep, self.dtype, self.sizes)))
         return Yc
 
     def retract(self, X, alpha, want_xprime=False):
         keep = []
         Xp = self._alloc(False) if want_xprime else None
-        self._check(self.L.mera_retract(self.h, _ptrs(X, keep, self.dtype), float(alpha),
-                                        _ptrs(Xp, keep, self.dtype) if want_xprime else None))
+        self._check(self.L.mera_retract(self.h, _ptrs(X, keep, self.dtype, self.sizes), float(alpha),
+                                        _ptrs(Xp, keep, self.dtype, self.sizes) if want_xprime else None))
         return Xp
 
     def precondition(self, X):
         keep = []
         out = self._alloc(False)
-        self._check(self.L.mera_precondition(self.h, _ptrs(X, keep, self.dtype),
-                                             _ptrs(out, keep, self.dtype)))
+        self._check(self.L.mera_precondition(self.h, _ptrs(X, keep, self.dtype, self.sizes),
+                                             _ptrs(out, keep, self.dtype, self.sizes)))
         return out
 
     def lbfgs_step(self):

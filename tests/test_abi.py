@@ -187,3 +187,27 @@ def test_dots_noalloc_wrapper_checks_sizes(lib):
         gm.dots_noalloc(np.zeros(24), np.zeros(7), 3, 8, 8, np.zeros(3))
     with pytest.raises(TypeError):
         gm.dots_noalloc(np.zeros(24, dtype=np.complex128), y, 3, 8, 8, np.zeros(3))
+
+
+def test_binding_checks_tensor_counts_and_sizes(lib):
+    """Per-tensor lists must hold one array per tensor with the tensor's
+    element count, and the Hamiltonian term its operator's: the library reads
+    and writes that many elements behind every pointer, so the binding refuses
+    anything else before a call."""
+    import numpy as np
+    import pytest
+
+    from paper_2007_03638_gb300 import mera as gm
+    sizes = [256, 64]
+    keep = []
+    assert len(gm._ptrs([np.zeros((16, 16)), np.zeros((16, 4))], keep, np.float64, sizes)) == 2
+    with pytest.raises(ValueError):
+        gm._ptrs([np.zeros((16, 16))], keep, np.float64, sizes)  # one tensor short
+    with pytest.raises(ValueError):
+        gm._ptrs([np.zeros((16, 16)), np.zeros((16, 3))], keep, np.float64, sizes)  # a short tensor
+    with pytest.raises(ValueError):  # a real view of complex data has twice the elements
+        gm._ptrs([np.zeros((16, 32)), np.zeros((16, 8))], keep, np.complex128, sizes)
+    with pytest.raises(ValueError):  # binary network: a three-site term, 4^3 x 4^3 at d_b = 4
+        gm.Mera(gm.default_config(4, 8, 3), np.zeros((16, 16)))
+    with pytest.raises(ValueError):  # ternary network: a two-site term, 2^2 x 2^2 at d = 2
+        gm.Mera(gm.default_config(2, 8, 2, network=gm.MERA_TERNARY), np.zeros((8, 8)))
