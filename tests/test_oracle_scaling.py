@@ -1,13 +1,18 @@
-"""Physics pin of the scale-invariant layer (App. B).
+"""Physics pin of the scale-invariant layer (App. B), binary and ternary.
 
-The fixture (written by tests/golden/make_ising_chi4_optimized.py, which runs
-the oracle only) is a Z2-symmetric binary MERA of the critical Ising chain,
-chi = 4, two transition layers, optimised by the oracle's preconditioned
-L-BFGS.  At a good optimum the ascending superoperator of the scale-invariant
-layer has eigenvalues lambda = +-2^(-Delta), with Delta the scaling dimensions
-of the Ising conformal field theory: 0 for the identity (exactly, by
+The binary fixture (written by tests/golden/make_ising_chi4_optimized.py,
+which runs the oracle only) is a Z2-symmetric binary MERA of the critical
+Ising chain, chi = 4, two transition layers, optimised by the oracle's
+preconditioned L-BFGS; the ternary fixture
+(tests/golden/make_ternary_ising_chi4_optimized.py, oracle only) the same for
+the ternary network, chi = 4, one transition layer.  At a good optimum the
+ascending superoperator of the scale-invariant layer has eigenvalues
+lambda = +-2^(-Delta) (binary) or +-3^(-Delta) (ternary), with Delta the
+scaling dimensions of the Ising conformal field theory: 0 for the identity (exactly, by
 unitality), 1/8 for the spin field sigma, 1 for the energy density epsilon,
-1 + 1/8 twice for the first descendants of sigma.  The textbook values are
+1 + 1/8 twice for the first descendants of sigma, 2 four times (the stress
+tensor's two components and the first descendants of epsilon; checked on the
+ternary network, whose chi = 4 optimum resolves them).  The textbook values are
 fixed by the theory, not by the oracle, and the parity of each eigenoperator
 is fixed too: sigma and its descendants are odd under the global spin flip,
 epsilon is even.  A transposed leg, a wrong site in the ascending map, a
@@ -23,11 +28,14 @@ import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import mera as om
+from oracle import ternary as ot
 from paper_2007_03638_gb300 import inputs as inp
 
-FIXTURE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ising_chi4_L2_z2_lbfgs.npz")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+FIXTURE = os.path.join(GOLDEN, "ising_chi4_L2_z2_lbfgs.npz")
+TERNARY_FIXTURE = os.path.join(GOLDEN, "ternary_ising_chi4_L1_z2_lbfgs.npz")
 
-# The chi = 4 optimum reproduces the dimensions to a few 1e-4; the tolerances
+# The binary chi = 4 optimum reproduces the dimensions to a few 1e-4; the tolerances
 # leave an order of magnitude of room and still separate every field of the
 # theory (the nearest wrong candidates are 0.125 apart).
 DSIGMA_TOL = 3e-3
@@ -103,3 +111,57 @@ def test_scaling_dimensions_of_the_scale_invariant_layer(optimised):
         assert odd_share[k] > 1 - 1e-10
     # nothing else between the identity and Delta = 1.125 + the tolerance
     assert delta[5] > 1.125 + DDESC_TOL
+
+
+# ---- ternary network -------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def optimised_ternary():
+    if not os.path.exists(TERNARY_FIXTURE):
+        pytest.skip("fixture missing: run tests/golden/make_ternary_ising_chi4_optimized.py")
+    z = np.load(TERNARY_FIXTURE)
+    return [z[f"arr_{i}"] for i in range(4)], float(z["energy_per_spin"])
+
+
+def test_ternary_fixture_is_a_symmetric_isometric_point(optimised_ternary):
+    tensors, e = optimised_ternary
+    for i, t in enumerate(tensors):
+        assert np.allclose(t.T @ t, np.eye(t.shape[1]), atol=1e-12)
+        if i % 2 == 0:
+            c = int(round(np.sqrt(t.shape[0])))
+            rows = cols = inp.fused_parities(c, c)
+        else:
+            c = int(round(t.shape[0] ** (1 / 3)))
+            rows, cols = inp.fused_parities(c, c, c), inp.z2_parities(t.shape[1])
+        assert np.max(np.abs(t[rows[:, None] != cols[None, :]])) < 1e-12
+    us, ws = tensors[0::2], tensors[1::2]
+    assert abs(ot.energy(inp.ising_bond(1.0), us, ws) - e) < 1e-10
+    assert inp.EXACT_ISING_CRITICAL < e < inp.EXACT_ISING_CRITICAL + 1e-4
+
+
+def test_ternary_scaling_dimensions(optimised_ternary):
+    tensors, _ = optimised_ternary
+    u, w = tensors[2], tensors[3]
+    c = w.shape[1]
+    n = c ** 4
+
+    def mv(v):
+        return ot.ascend(v.reshape(c * c, c * c), u, w).ravel()
+
+    op = spla.LinearOperator((n, n), matvec=mv, dtype=np.float64)
+    vals, vecs = spla.eigs(op, k=10, which="LM", tol=1e-12)
+    order = np.argsort(-np.abs(vals))
+    vals, vecs = vals[order], vecs[:, order]
+    assert np.max(np.abs(vals.imag)) < 1e-10
+    delta = -np.log(np.abs(vals.real)) / np.log(3.0)
+    p2 = inp.fused_parities(c, c)
+    odd = (p2[:, None] != p2[None, :]).ravel()
+    odd_share = np.array([np.linalg.norm(v[odd]) / np.linalg.norm(v) for v in vecs.T])
+
+    assert abs(vals[0].real - 1.0) < 1e-12 and odd_share[0] < 1e-10        # identity
+    assert abs(delta[1] - 0.125) < 5e-3 and odd_share[1] > 1 - 1e-10         # sigma
+    assert abs(delta[2] - 1.0) < 5e-3 and odd_share[2] < 1e-10               # epsilon
+    for k in (3, 4):                                                         # d sigma, dbar sigma
+        assert abs(delta[k] - 1.125) < 1.5e-2 and odd_share[k] > 1 - 1e-10, delta
+    for k in (5, 6, 7, 8):                                                   # T, Tbar, d eps, dbar eps
+        assert abs(delta[k] - 2.0) < 5e-2 and odd_share[k] < 1e-10, delta
