@@ -3,6 +3,7 @@
     python -m paper_2007_03638_gb300.solve --model ising --chi 4 --n-trans 2 --iters 300
     python -m paper_2007_03638_gb300.solve --model xxz --delta 1 --chi 8 --prec 1 --method cg
     python -m paper_2007_03638_gb300.solve --network ternary --z2 --chi 8 --n-trans 2 --method ev
+    python -m paper_2007_03638_gb300.solve --network ternary --z2 --chi 4 --n-trans 1 --start fig2
     python -m paper_2007_03638_gb300.solve --network mps --model ising --field 1.5 --chi 16
 
 Each iteration prints one JSON record: energy per spin, its distance to the
@@ -34,13 +35,26 @@ def exact_energy(model, par):
     return None
 
 
-def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
+def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0, start="random"):
     """(h, d_b, tensors, spins per bottom site) of a run: the binary network on
     blocked sites (two spins, three-site term), the ternary one and the uniform
     MPS (bond dimension chi, n_trans unused) on spins (two-site term); z2:
     Z2-symmetric starting point (binary: blocked pairs in the parity-ordered
     basis), and run() sets the library's Z2 mode, which contracts by charge
-    sector."""
+    sector.  start: "random" (seeded random isometries and disentanglers) or
+    "fig2" (the start of the paper's Fig. 2: the same random isometries with
+    identity disentanglers; MERA networks only)."""
+    if start not in ("random", "fig2"):
+        raise ValueError(f"unknown start {start!r}")
+    if start == "fig2" and network == "mps":
+        raise ValueError("the Fig. 2 start sets disentanglers, which the MPS has none of")
+    h, d_b, tensors, spins = _problem(model, par, chi, n_trans, network, z2, seed)
+    if start == "fig2":
+        tensors = [np.eye(t.shape[0], dtype=t.dtype) if i % 2 == 0 else t for i, t in enumerate(tensors)]
+    return h, d_b, tensors, spins
+
+
+def _problem(model, par, chi, n_trans, network, z2, seed):
     bond = inp.ising_bond(par) if model == "ising" else inp.xxz_bond(par)
     if network == "mps":
         if z2:
@@ -60,11 +74,12 @@ def problem(model, par, chi, n_trans, network="binary", z2=False, seed=0):
 
 
 def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, gtol=1e-6, seed=0,
-        lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None, network="binary", z2=False):
+        lbfgs_m=8, krylov_dim=20, out=print, ev_gamma=None, network="binary", z2=False, start="random"):
     """method: 0 L-BFGS, 1 CG, 2 Evenbly-Vidal sweeps (one record per sweep;
     ev_gamma = the Hamiltonian shift, default the largest eigenvalue of the
-    Hamiltonian term plus 0.5), 3 gradient descent.  network: "binary", "ternary" or "mps"."""
-    h3, d_b, tensors, spins = problem(model, par, chi, n_trans, network, z2, seed)
+    Hamiltonian term plus 0.5), 3 gradient descent.  network: "binary", "ternary" or "mps".
+    start: as in problem()."""
+    h3, d_b, tensors, spins = problem(model, par, chi, n_trans, network, z2, seed, start)
     net = {"binary": gm.MERA_BINARY, "ternary": gm.MERA_TERNARY, "mps": gm.MERA_MPS}[network]
     cfg = gm.default_config(d_b, chi, 0 if network == "mps" else n_trans, prec=prec, lbfgs_m=lbfgs_m,
                             krylov_dim=krylov_dim, network=net, z2=int(z2))
@@ -89,7 +104,7 @@ def run(model="ising", par=1.0, chi=4, n_trans=2, prec=0, method=0, iters=300, g
         if info["gnorm"] < gtol:
             break
     summary = {"summary": True, "model": model, "param": par, "network": network, "z2": z2, "chi": chi,
-               "n_trans": n_trans,
+               "n_trans": n_trans, "start": start,
                "prec": ["fp64", "3xtf32", "split_bf16", "split_fp16"][prec],
                "method": ["lbfgs", "cg", "ev", "gd"][method],
                "iters": rec["iter"], "energy_per_spin": rec["energy_per_spin"], "exact": ex,
@@ -124,6 +139,8 @@ def main():
                     help="Z2-symmetric problem (ternary, or binary up to chi = 16): contractions by charge sector")
     ap.add_argument("--ev-gamma", type=float, default=None,
                     help="Evenbly-Vidal Hamiltonian shift (default: largest eigenvalue of the 3-site term + 0.5)")
+    ap.add_argument("--start", default="random", choices=["random", "fig2"],
+                    help="starting point: seeded random tensors, or the paper's Fig. 2 start (identity disentanglers)")
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--gtol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
@@ -133,7 +150,7 @@ def main():
     par = a.field if a.model == "ising" else a.delta
     method = {"lbfgs": 0, "cg": 1, "ev": 2, "gd": 3}[a.method]
     run(a.model, par, a.chi, a.n_trans, a.prec, method, a.iters, a.gtol, a.seed, a.m, a.krylov_dim,
-        ev_gamma=a.ev_gamma, network=a.network, z2=a.z2)
+        ev_gamma=a.ev_gamma, network=a.network, z2=a.z2, start=a.start)
 
 
 if __name__ == "__main__":

@@ -41,3 +41,21 @@ def test_mps_problem():
     assert np.abs(A.T @ A - np.eye(12)).max() < 1e-13
     with pytest.raises(ValueError):
         solve.problem("ising", 1.0, 8, 0, network="mps", z2=True)
+
+
+@pytest.mark.parametrize("network,z2", [("binary", False), ("binary", True), ("ternary", True)])
+def test_figure_2_start_has_identity_disentanglers(network, z2):
+    """--start fig2: the random start's isometries, identity disentanglers."""
+    _, _, rand, _ = solve.problem("ising", 1.0, 8, 2 if network == "ternary" else 3, network=network, z2=z2)
+    _, _, fig2, _ = solve.problem("ising", 1.0, 8, 2 if network == "ternary" else 3, network=network, z2=z2,
+                                  start="fig2")
+    assert len(fig2) == len(rand)
+    for i, (a, b) in enumerate(zip(fig2, rand)):
+        if i % 2 == 0:
+            assert a.shape == b.shape and np.array_equal(a, np.eye(a.shape[0]))
+        else:
+            assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        solve.problem("ising", 1.0, 8, 0, network="mps", start="fig2")
+    with pytest.raises(ValueError):
+        solve.problem("ising", 1.0, 8, 3, start="zeros")
