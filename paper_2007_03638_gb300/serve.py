@@ -21,6 +21,40 @@ from . import inputs as inp
 from . import mera as gm
 
 
+def request_sizes(cfg):
+    """Elements of the Hamiltonian term and of each tensor that
+    mera_server_submit copies for this config: the level dimensions
+    chi_{l+1} = min(chi, chi_l^2) (binary) or min(chi, chi_l^3) (ternary) from
+    chi_0 = d_b, the scale-invariant layer keeping the last one."""
+    tern = cfg.network == gm.MERA_TERNARY
+    n_op = int(cfg.d_b) ** (2 if tern else 3)
+    dims = [int(cfg.d_b)]
+    for _ in range(int(cfg.n_trans)):
+        dims.append(min(int(cfg.chi), dims[-1] ** (3 if tern else 2)))
+    sizes = []
+    for l in range(int(cfg.n_trans) + 1):
+        cf = dims[l]
+        cc = dims[l + 1] if l < cfg.n_trans else dims[l]
+        sizes += [cf ** 4, (cf ** 3 if tern else cf ** 2) * cc]
+    return n_op * n_op, sizes
+
+
+def check_request(cfg, h3, tensors):
+    """Refuses a request whose arrays are shorter or longer than what the
+    library copies from them (it reads that many elements behind each
+    pointer).  MPS requests are left to the library, which refuses them."""
+    if cfg.network == gm.MERA_MPS:
+        return
+    n_h, sizes = request_sizes(cfg)
+    if int(np.size(h3)) != n_h:
+        raise ValueError(f"the Hamiltonian term has {np.size(h3)} elements, expected {n_h}")
+    if len(tensors) != len(sizes):
+        raise ValueError(f"expected {len(sizes)} tensors, got {len(tensors)}")
+    for i, (t, n) in enumerate(zip(tensors, sizes)):
+        if gm._numel(t) != n:
+            raise ValueError(f"tensor {i} has {gm._numel(t)} elements, expected {n}")
+
+
 class Server:
     def __init__(self, budget_bytes: int, workers: int = 4):
         self.L = gm.load()
@@ -35,6 +69,7 @@ class Server:
         rid = C.c_int64()
         dt = np.complex128 if cfg.dtype == gm.MERA_C128 else np.float64
         h3 = np.ascontiguousarray(h3, dtype=dt)
+        check_request(cfg, h3, tensors)
         rc = self.L.mera_server_submit(self.h, C.byref(cfg), C.c_void_p(h3.ctypes.data),
                                        gm._ptrs(tensors, keep, dt), int(method), float(gtol), int(maxiter),
                                        C.byref(rid))
