@@ -217,11 +217,20 @@ def dots_noalloc(X, y, k, n, ldx, out, stream=0):
 
 
 def gemm(prec, A, B, out, stream=0):
-    """out = A B (device float64 row-major tensors) in the arithmetic of ``prec``."""
+    """out = A B (device float64 row-major tensors) in the arithmetic of ``prec``.
+    A is M x K and B K x N; out holds M N elements (ValueError otherwise: the
+    library reads and writes exactly those extents)."""
     L = load()
+    if len(A.shape) != 2 or len(B.shape) != 2:
+        raise ValueError("gemm: A and B must be matrices")
     M, K = A.shape
+    if B.shape[0] != K:
+        raise ValueError(f"gemm: B has {B.shape[0]} rows, A has {K} columns")
     N = B.shape[1]
-    rc = L.mera_gemm(int(prec), M, N, K, C_void(A), C_void(B), C_void(out), C.c_void_p(stream))
+    if _numel(out) != M * N:
+        raise ValueError(f"gemm: out holds {_numel(out)} elements, the product has {M * N}")
+    rc = L.mera_gemm(int(prec), M, N, K, C.c_void_p(_ptr(A, np.float64)), C.c_void_p(_ptr(B, np.float64)),
+                     C.c_void_p(_ptr(out, np.float64)), C.c_void_p(stream))
     if rc != 0:
         raise MeraError(rc, L.mera_strerror(rc).decode())
     return out

@@ -211,3 +211,20 @@ def test_binding_checks_tensor_counts_and_sizes(lib):
         gm.Mera(gm.default_config(4, 8, 3), np.zeros((16, 16)))
     with pytest.raises(ValueError):  # ternary network: a two-site term, 2^2 x 2^2 at d = 2
         gm.Mera(gm.default_config(2, 8, 2, network=gm.MERA_TERNARY), np.zeros((8, 8)))
+
+
+def test_gemm_wrapper_checks_shapes(lib):
+    """mera_gemm reads M K and K N elements and writes M N: the binding
+    refuses mismatched extents and non-double arrays before the call."""
+    import numpy as np
+    import pytest
+
+    from paper_2007_03638_gb300 import mera as gm
+    with pytest.raises(ValueError):
+        gm.gemm(1, np.zeros((4, 3)), np.zeros((2, 5)), np.zeros((4, 5)))   # inner extents differ
+    with pytest.raises(ValueError):
+        gm.gemm(1, np.zeros((4, 3)), np.zeros((3, 5)), np.zeros((4, 4)))   # out too small
+    with pytest.raises(ValueError):
+        gm.gemm(1, np.zeros(12), np.zeros((3, 5)), np.zeros((4, 5)))       # A not a matrix
+    with pytest.raises(TypeError):
+        gm.gemm(1, np.zeros((4, 3), dtype=np.complex128), np.zeros((3, 5)), np.zeros((4, 5)))
