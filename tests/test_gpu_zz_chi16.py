@@ -63,9 +63,10 @@ def test_fp64_chi16_matches_the_oracle(gm, reference):
     ref, point = reference
     e, D = _evaluate(gm, ref, point, 0)
     assert abs(e - ref["energy"]) <= 1e-12 * max(1.0, abs(ref["energy"])), (e, ref["energy"])
-    assert max(_sample_errors(ref, D)) < 1e-12
-    for t, d in zip(ref["tensors"], D):
-        assert abs(np.linalg.norm(d) - t["fro"]) < 1e-12 * t["fro"]
+    errs = _sample_errors(ref, D)
+    assert max(errs) < 1e-12, errs
+    for i, (t, d) in enumerate(zip(ref["tensors"], D)):
+        assert abs(np.linalg.norm(d) - t["fro"]) < 1e-12 * t["fro"], (i, np.linalg.norm(d), t["fro"])
 
 
 @pytest.mark.parametrize("prec", [1, 3])
@@ -73,4 +74,5 @@ def test_mixed_chi16_matches_the_oracle(gm, reference, prec):
     ref, point = reference
     e, D = _evaluate(gm, ref, point, prec)
     assert abs(e - ref["energy"]) / max(1.0, abs(ref["energy"])) < 2e-6, (e, ref["energy"])
-    assert max(_sample_errors(ref, D)) < 1e-4
+    errs = _sample_errors(ref, D)
+    assert max(errs) < 1e-4, errs
